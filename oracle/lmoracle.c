@@ -1,0 +1,713 @@
+/*
+ * FP64 CPU oracle for listmode SPDHG (LM-SPDHG) with a TOF Joseph projector.
+ *
+ * TEST INFRASTRUCTURE.  This file is the slow, plain reference that the CUDA
+ * library is checked against.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library.
+ *
+ * Everything is computed in double precision, single threaded, in the order
+ * the paper states it:
+ *   - Eq. (1)      primal objective  sum_i (Px+s)_i - d_i log (Px+s)_i + beta R(Kx)
+ *   - Eq. (proxD)  prox of the Poisson conjugate, with d_i replaced by the
+ *                  event count mu_e (appendix: rescaled operator, d^LM = 1)
+ *   - Eq. (yinit)  optimal dual initialisation y = 1 - d/(Px+s)
+ *   - Eq. (lmop)   listmode operator (P^LM x)_e = (Px)_{i_e}
+ *   - Alg. 2       LM-SPDHG loop; Alg. 1 (SPDHG on a sinogram) for the
+ *                  equivalence check of the appendix
+ *   - Eq. (lm_stepsizes) step sizes S_k, T_k; S_{n+1}, T_{n+1} of Sec. 1
+ *   - Sec. "Numerical experiments": TV prior ||Kx||_{2,1}, prox of R^*
+ *
+ * The projector: the paper cites Joseph (1982) and a Gaussian TOF kernel but
+ * prints no formula.  The reading implemented here:
+ *   endpoints a = xtal[det1], b = xtal[det2] (float32 table values);
+ *   principal axis k = argmax_j |fl32(b_j - a_j)| (ties -> lowest j);
+ *   for every voxel plane i along k: lambda = (o_k + i h_k - a_k)/(b_k - a_k),
+ *   p = a + lambda (b - a); bilinear interpolation over the two other axes
+ *   with neighbours outside the grid contributing 0; sample weight
+ *   step = h_k |b - a| / |b_k - a_k|;
+ *   TOF position t = (lambda - 1/2)|b - a| (from the LOR centre toward det2),
+ *   bin centre c_m = m * bin; bin-integrated Gaussian
+ *   w_m(t) = 1/2 [erf((t - c_m + bin/2)/(sqrt2 sigma)) - erf((t - c_m - bin/2)/(sqrt2 sigma))],
+ *   kept iff |t - c_m| <= n_sigma * sigma.
+ *   J_e(x) = sum_i step * w_m(t_i) * interp(x, p_i); (P^LM x)_e = corr_e J_e(x).
+ *   The detectors lie outside the image, so the infinite line and the
+ *   detector-to-detector segment cross the same voxels.
+ *
+ * parity pinned: adjoint, TOF sum, closed-form chords, brute force on tiny
+ * grids, prox fixed points, TV adjoint and norm, LM == sinogram SPDHG (see the
+ * CPU tests).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t n_rings, n_xtal;
+    const float* xtal; /* [n_rings*n_xtal][3] */
+} or_scanner;
+
+typedef struct {
+    int32_t n[3];
+    float h[3];
+    float origin[3];
+} or_grid;
+
+typedef struct {
+    float sigma, bin, n_sigma;
+    int32_t n_bins; /* odd; 0 = non-TOF */
+} or_tof;
+
+/* kernel mode of one projection */
+enum { OR_NONTOF = 0, OR_TOFBIN = 1, OR_TOFSUM = 2 };
+
+typedef void (*or_visit)(void* ctx, int64_t j, double w);
+
+static double tof_bin_weight(double tau, const or_tof* tof)
+{
+    double sig = (double)tof->sigma, D = (double)tof->bin;
+    if (fabs(tau) > (double)tof->n_sigma * sig) return 0.0;
+    double s = sqrt(2.0) * sig;
+    return 0.5 * (erf((tau + 0.5 * D) / s) - erf((tau - 0.5 * D) / s));
+}
+
+/* Visit every (voxel, weight) pair of the Joseph projection of one LOR. */
+static void or_lor_visit(const or_scanner* sc, const or_grid* g, const or_tof* tof, int32_t d1,
+                         int32_t d2, int32_t m, int mode, or_visit f, void* ctx)
+{
+    double a[3], b[3], d[3], o[3], h[3];
+    float df[3];
+    int j;
+    for (j = 0; j < 3; ++j) {
+        a[j] = (double)sc->xtal[3 * (int64_t)d1 + j];
+        b[j] = (double)sc->xtal[3 * (int64_t)d2 + j];
+        d[j] = b[j] - a[j]; /* exact: difference of two float32 values */
+        df[j] = (float)d[j];
+        o[j] = (double)g->origin[j];
+        h[j] = (double)g->h[j];
+    }
+    int k = 0;
+    if (fabsf(df[1]) > fabsf(df[k])) k = 1;
+    if (fabsf(df[2]) > fabsf(df[k])) k = 2;
+    if (d[k] == 0.0) return;
+    int s1 = (k + 1) % 3, s2 = (k + 2) % 3;
+    double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double step = h[k] * L / fabs(d[k]);
+    for (int i = 0; i < g->n[k]; ++i) {
+        double qk = o[k] + i * h[k];
+        double lam = (qk - a[k]) / d[k];
+        double p[3];
+        for (j = 0; j < 3; ++j) p[j] = a[j] + lam * d[j];
+        double t = (lam - 0.5) * L;
+        double wt = 1.0;
+        if (mode == OR_TOFBIN) {
+            wt = tof_bin_weight(t - (double)m * (double)tof->bin, tof);
+        } else if (mode == OR_TOFSUM) {
+            int M = (tof->n_bins - 1) / 2;
+            wt = 0.0;
+            for (int mm = -M; mm <= M; ++mm) wt += tof_bin_weight(t - (double)mm * (double)tof->bin, tof);
+        }
+        if (wt == 0.0) continue;
+        double u1 = (p[s1] - o[s1]) / h[s1];
+        double u2 = (p[s2] - o[s2]) / h[s2];
+        double fl1 = floor(u1), fl2 = floor(u2);
+        int64_t i1 = (int64_t)fl1, i2 = (int64_t)fl2;
+        double f1 = u1 - fl1, f2 = u2 - fl2;
+        for (int da = 0; da < 2; ++da) {
+            int64_t j1 = i1 + da;
+            if (j1 < 0 || j1 >= g->n[s1]) continue;
+            double w1 = da ? f1 : 1.0 - f1;
+            for (int db = 0; db < 2; ++db) {
+                int64_t j2 = i2 + db;
+                if (j2 < 0 || j2 >= g->n[s2]) continue;
+                double w2 = db ? f2 : 1.0 - f2;
+                int64_t idx[3];
+                idx[k] = i;
+                idx[s1] = j1;
+                idx[s2] = j2;
+                int64_t vox = (idx[2] * g->n[1] + idx[1]) * g->n[0] + idx[0];
+                f(ctx, vox, step * wt * w1 * w2);
+            }
+        }
+    }
+}
+
+typedef struct {
+    const float* xf;
+    const double* xd;
+    double acc;
+} fwd_ctx;
+
+static void fwd_visit(void* c, int64_t j, double w)
+{
+    fwd_ctx* q = (fwd_ctx*)c;
+    q->acc += w * (q->xf ? (double)q->xf[j] : q->xd[j]);
+}
+
+typedef struct {
+    double* img;
+    double v;
+} back_ctx;
+
+static void back_visit(void* c, int64_t j, double w)
+{
+    back_ctx* q = (back_ctx*)c;
+    q->img[j] += w * q->v;
+}
+
+static void ones_visit(void* c, int64_t j, double w)
+{
+    (void)j;
+    ((fwd_ctx*)c)->acc += w;
+}
+
+static int ev_mode(const or_tof* tof) { return tof->n_bins > 0 ? OR_TOFBIN : OR_NONTOF; }
+
+/* (P^LM x)_e = corr_e J_e(x) for float32 x (Eq. lmop). corr may be NULL (=1). */
+void or_fwd(const or_scanner* sc, const or_grid* g, const or_tof* tof, const int32_t* det1,
+            const int32_t* det2, const int16_t* tbin, const float* corr, int64_t n, const float* x,
+            double* out)
+{
+    for (int64_t e = 0; e < n; ++e) {
+        fwd_ctx c = {x, NULL, 0.0};
+        or_lor_visit(sc, g, tof, det1[e], det2[e], tbin[e], ev_mode(tof), fwd_visit, &c);
+        out[e] = c.acc * (corr ? (double)corr[e] : 1.0);
+    }
+}
+
+/* img += (P^LM)^T v, i.e. img += sum_e corr_e J_e^T v_e. */
+void or_back(const or_scanner* sc, const or_grid* g, const or_tof* tof, const int32_t* det1,
+             const int32_t* det2, const int16_t* tbin, const float* corr, int64_t n,
+             const double* v, double* img)
+{
+    for (int64_t e = 0; e < n; ++e) {
+        back_ctx c = {img, v[e] * (corr ? (double)corr[e] : 1.0)};
+        or_lor_visit(sc, g, tof, det1[e], det2[e], tbin[e], ev_mode(tof), back_visit, &c);
+    }
+}
+
+/* Non-TOF projection of single LORs (used for chord pins). */
+void or_fwd_nontof(const or_scanner* sc, const or_grid* g, const int32_t* det1,
+                   const int32_t* det2, int64_t n, const double* x, double* out)
+{
+    or_tof t = {1.0f, 1.0f, 3.0f, 0};
+    for (int64_t e = 0; e < n; ++e) {
+        fwd_ctx c = {NULL, x, 0.0};
+        or_lor_visit(sc, g, &t, det1[e], det2[e], 0, OR_NONTOF, fwd_visit, &c);
+        out[e] = c.acc;
+    }
+}
+
+/* Sum over all TOF bins of one LOR, by explicit per-bin projection (TOF-sum pin). */
+double or_lor_tofsum_fwd(const or_scanner* sc, const or_grid* g, const or_tof* tof, int32_t d1,
+                         int32_t d2, const double* x)
+{
+    int M = (tof->n_bins - 1) / 2;
+    double s = 0.0;
+    for (int m = -M; m <= M; ++m) {
+        fwd_ctx c = {NULL, x, 0.0};
+        or_lor_visit(sc, g, tof, d1, d2, m, OR_TOFBIN, fwd_visit, &c);
+        s += c.acc;
+    }
+    return s;
+}
+
+/* Canonical LOR l -> (det1, det2); see the scanner description in the tests. */
+static void lor_dets(const or_scanner* sc, int64_t l, int32_t* d1, int32_t* d2)
+{
+    int64_t nr = sc->n_rings, n = sc->n_xtal;
+    int64_t rb = l % nr;
+    int64_t ra = (l / nr) % nr;
+    int64_t q = l / (nr * nr);
+    int64_t base = n * ((n - 1) / 2);
+    int64_t c1, c2;
+    if (q < base) {
+        c1 = q % n;
+        c2 = (c1 + 1 + q / n) % n;
+    } else {
+        c1 = q - base;
+        c2 = c1 + n / 2;
+    }
+    *d1 = (int32_t)(ra * n + c1);
+    *d2 = (int32_t)(rb * n + c2);
+}
+
+int64_t or_n_lor(const or_scanner* sc)
+{
+    return (int64_t)sc->n_xtal * (sc->n_xtal - 1) / 2 * sc->n_rings * sc->n_rings;
+}
+
+void or_lor_dets(const or_scanner* sc, int64_t l, int32_t* d1, int32_t* d2) { lor_dets(sc, l, d1, d2); }
+
+/* Sensitivity image P^T 1: every canonical LOR, every TOF bin (plain sum over
+ * bins), times the LOR factor (NULL = 1).  Sec. "Listmode SPDHG": "pre-compute
+ * the sensitivity image and store it". */
+void or_sens(const or_scanner* sc, const or_grid* g, const or_tof* tof, const float* lor_factor,
+             double* sens)
+{
+    int64_t nl = or_n_lor(sc);
+    int mode = tof->n_bins > 0 ? OR_TOFSUM : OR_NONTOF;
+    for (int64_t l = 0; l < nl; ++l) {
+        int32_t d1, d2;
+        lor_dets(sc, l, &d1, &d2);
+        back_ctx c = {sens, lor_factor ? (double)lor_factor[l] : 1.0};
+        or_lor_visit(sc, g, tof, d1, d2, 0, mode, back_visit, &c);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Event counts mu_e (Alg. 2 "Calculate event counts"; footnote: a data bin
+ * is the geometrical LOR together with the TOF bin).  The bin of an event is
+ * its unordered detector pair with the TOF bin signed toward the larger
+ * detector id.  Counting is over the whole list.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t lo, hi, t;
+    int64_t e;
+} ev_key;
+
+static int key_cmp(const void* A, const void* B)
+{
+    const ev_key* a = (const ev_key*)A;
+    const ev_key* b = (const ev_key*)B;
+    if (a->lo != b->lo) return a->lo < b->lo ? -1 : 1;
+    if (a->hi != b->hi) return a->hi < b->hi ? -1 : 1;
+    if (a->t != b->t) return a->t < b->t ? -1 : 1;
+    return 0;
+}
+
+void or_event_counts(const int32_t* det1, const int32_t* det2, const int16_t* tbin, int64_t n,
+                     int32_t* mu)
+{
+    ev_key* k = (ev_key*)malloc(sizeof(ev_key) * (size_t)(n > 0 ? n : 1));
+    for (int64_t e = 0; e < n; ++e) {
+        int swap = det1[e] > det2[e];
+        k[e].lo = swap ? det2[e] : det1[e];
+        k[e].hi = swap ? det1[e] : det2[e];
+        k[e].t = swap ? -(int32_t)tbin[e] : (int32_t)tbin[e];
+        k[e].e = e;
+    }
+    qsort(k, (size_t)n, sizeof(ev_key), key_cmp);
+    int64_t s = 0;
+    while (s < n) {
+        int64_t t = s + 1;
+        while (t < n && key_cmp(&k[s], &k[t]) == 0) ++t;
+        for (int64_t r = s; r < t; ++r) mu[k[r].e] = (int32_t)(t - s);
+        s = t;
+    }
+    free(k);
+}
+
+/* ------------------------------------------------------------------------
+ * TV prior (Sec. "Numerical experiments"): K = finite forward differences
+ * with unit spacing, last difference 0 (Neumann); one component per axis
+ * with more than one voxel, in axis order x, y, z.  R = mixed L2-L1 norm.
+ * ------------------------------------------------------------------------ */
+static int tv_axes(const or_grid* g, int* ax)
+{
+    int nd = 0;
+    for (int d = 0; d < 3; ++d)
+        if (g->n[d] > 1) ax[nd++] = d;
+    return nd;
+}
+
+int or_tv_ndim(const or_grid* g)
+{
+    int ax[3];
+    return tv_axes(g, ax);
+}
+
+static int64_t stride_of(const or_grid* g, int d) { return d == 0 ? 1 : d == 1 ? g->n[0] : (int64_t)g->n[0] * g->n[1]; }
+
+static int coord_of(const or_grid* g, int64_t j, int d)
+{
+    if (d == 0) return (int)(j % g->n[0]);
+    if (d == 1) return (int)((j / g->n[0]) % g->n[1]);
+    return (int)(j / ((int64_t)g->n[0] * g->n[1]));
+}
+
+/* out[c*V + j] = (Kx)_{j,c} */
+void or_tv_grad(const or_grid* g, const double* x, double* out)
+{
+    int ax[3];
+    int nd = tv_axes(g, ax);
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    for (int c = 0; c < nd; ++c) {
+        int d = ax[c];
+        int64_t st = stride_of(g, d);
+        for (int64_t j = 0; j < V; ++j)
+            out[c * V + j] = coord_of(g, j, d) < g->n[d] - 1 ? x[j + st] - x[j] : 0.0;
+    }
+}
+
+/* out = K^T q (the adjoint of or_tv_grad); -div q. */
+void or_tv_adj(const or_grid* g, const double* q, double* out)
+{
+    int ax[3];
+    int nd = tv_axes(g, ax);
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    for (int64_t j = 0; j < V; ++j) out[j] = 0.0;
+    for (int c = 0; c < nd; ++c) {
+        int d = ax[c];
+        int64_t st = stride_of(g, d);
+        for (int64_t j = 0; j < V; ++j) {
+            int cj = coord_of(g, j, d);
+            if (cj < g->n[d] - 1) out[j] -= q[c * V + j];
+            if (cj >= 1) out[j] += q[c * V + j - st];
+        }
+    }
+}
+
+/* w <- w / max(1, |w|/beta): beta * prox_{R^*}(w / beta), pointwise over
+ * the per-voxel Euclidean norm of the components.  beta = 0 gives w = 0. */
+void or_tv_prox(const or_grid* g, double* w, double beta)
+{
+    int nd = or_tv_ndim(g);
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    for (int64_t j = 0; j < V; ++j) {
+        double s = 0.0;
+        for (int c = 0; c < nd; ++c) s += w[c * V + j] * w[c * V + j];
+        double nrm = sqrt(s);
+        for (int c = 0; c < nd; ++c) {
+            if (beta <= 0.0)
+                w[c * V + j] = 0.0;
+            else
+                w[c * V + j] = w[c * V + j] / fmax(1.0, nrm / beta);
+        }
+    }
+}
+
+/* ||K|| by power iteration on K^T K from the checkerboard (-1)^(ix+iy+iz);
+ * returns sqrt of the last Rayleigh quotient <v, K^T K v>/<v, v>. */
+double or_knorm_power(const or_grid* g, int iters)
+{
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    int nd = or_tv_ndim(g);
+    double* v = (double*)malloc(sizeof(double) * V);
+    double* gr = (double*)malloc(sizeof(double) * V * (nd > 0 ? nd : 1));
+    double* u = (double*)malloc(sizeof(double) * V);
+    for (int64_t j = 0; j < V; ++j) {
+        int s = coord_of(g, j, 0) + coord_of(g, j, 1) + coord_of(g, j, 2);
+        v[j] = (s & 1) ? -1.0 : 1.0;
+    }
+    double lam = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        or_tv_grad(g, v, gr);
+        or_tv_adj(g, gr, u);
+        double vu = 0.0, vv = 0.0, uu = 0.0;
+        for (int64_t j = 0; j < V; ++j) {
+            vu += v[j] * u[j];
+            vv += v[j] * v[j];
+            uu += u[j] * u[j];
+        }
+        lam = vu / vv;
+        double nu = sqrt(uu);
+        if (nu == 0.0) break;
+        for (int64_t j = 0; j < V; ++j) v[j] = u[j] / nu;
+    }
+    free(v);
+    free(gr);
+    free(u);
+    return sqrt(lam);
+}
+
+/* ------------------------------------------------------------------------
+ * Proximal map of the Poisson conjugate D^*(.; d) with step S (Eq. proxD):
+ *   prox(a) = 1/2 (a + 1 - sqrt((a - 1)^2 + 4 S d)).
+ * In the listmode algorithm d -> 1 and S -> mu_e S_e (appendix).
+ * ------------------------------------------------------------------------ */
+double or_prox_dstar(double a, double S, double d)
+{
+    return 0.5 * (a + 1.0 - sqrt((a - 1.0) * (a - 1.0) + 4.0 * S * d));
+}
+
+/* ------------------------------------------------------------------------
+ * LM-SPDHG (Alg. 2).  State arrays are owned by the caller (numpy).
+ * Event e belongs to subset e mod n (Sec. "Listmode SPDHG": every n-th event
+ * goes to the n-th sub list).  Probabilities p_k = 1/(2n), p_{n+1} = 1/2.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const or_scanner* sc;
+    const or_grid* g;
+    const or_tof* tof;
+    const int32_t *det1, *det2;
+    const int16_t* tbin;
+    const float *corr, *contam;
+    const int32_t* mu;
+    int64_t n_ev;
+    int32_t n_subsets;
+    double beta, gamma, rho, knorm;
+} or_lm_problem;
+
+typedef struct {
+    double *x, *z, *zbar, *w, *y, *T;
+} or_lm_state;
+
+static double ev_fwd(const or_lm_problem* P, int64_t e, const double* x)
+{
+    fwd_ctx c = {NULL, x, 0.0};
+    or_lor_visit(P->sc, P->g, P->tof, P->det1[e], P->det2[e], P->tbin[e], ev_mode(P->tof), fwd_visit, &c);
+    return c.acc * (double)P->corr[e];
+}
+
+static double ev_fwd_ones(const or_lm_problem* P, int64_t e)
+{
+    fwd_ctx c = {NULL, NULL, 0.0};
+    or_lor_visit(P->sc, P->g, P->tof, P->det1[e], P->det2[e], P->tbin[e], ev_mode(P->tof), ones_visit, &c);
+    return c.acc * (double)P->corr[e];
+}
+
+static void ev_back(const or_lm_problem* P, int64_t e, double v, double* img)
+{
+    back_ctx c = {img, v * (double)P->corr[e]};
+    or_lor_visit(P->sc, P->g, P->tof, P->det1[e], P->det2[e], P->tbin[e], ev_mode(P->tof), back_visit, &c);
+}
+
+/* Initialisation, Alg. 2 steps 3-5 plus the first primal step's inputs:
+ *   y_e = 1 - mu_e / ((P^LM x0)_e + s_e)                    (Eq. yinit)
+ *   z = zbar = P^T 1 + (P^LM)^T ((y - 1)/mu) + K^T w, w = 0
+ *     (the sign reading: the first part equals P^T applied to a sinogram that
+ *      is 1 on empty bins and Eq. yinit elsewhere)
+ *   T_j = min_k T_k = (rho/gamma) min( p_k n / sens_j , p_{n+1} / ||K|| )  (Eq. lm_stepsizes)
+ */
+void or_lm_init(const or_lm_problem* P, const float* x0, const double* sens, or_lm_state* S)
+{
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    int nd = or_tv_ndim(P->g);
+    double* x0d = S->x;
+    for (int64_t j = 0; j < V; ++j) x0d[j] = (double)x0[j];
+    for (int64_t j = 0; j < V; ++j) S->z[j] = sens[j];
+    for (int64_t e = 0; e < P->n_ev; ++e) {
+        double u = ev_fwd(P, e, x0d) + (double)P->contam[e];
+        S->y[e] = 1.0 - (double)P->mu[e] / u;
+        ev_back(P, e, (S->y[e] - 1.0) / (double)P->mu[e], S->z);
+    }
+    for (int64_t j = 0; j < (int64_t)nd * V; ++j) S->w[j] = 0.0;
+    for (int64_t j = 0; j < V; ++j) S->zbar[j] = S->z[j];
+    double n = (double)P->n_subsets;
+    double p_data = 1.0 / (2.0 * n), p_prior = 0.5;
+    for (int64_t j = 0; j < V; ++j) {
+        double t_prior = P->rho * p_prior / (P->gamma * P->knorm);
+        double t_data = sens[j] > 0.0 ? P->rho * p_data / (P->gamma * sens[j] / n) : INFINITY;
+        S->T[j] = t_data < t_prior ? t_data : t_prior;
+    }
+}
+
+/* One iteration of the Alg. 2 loop with selection i (0..n-1 data subset,
+ * n = prior).  dz is caller scratch of V doubles, gw of nd*V doubles. */
+void or_lm_update(const or_lm_problem* P, or_lm_state* S, int32_t i, double* dz, double* gw)
+{
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    int nd = or_tv_ndim(P->g);
+    double n = (double)P->n_subsets;
+    /* x <- proj_{>=0}(x - T zbar) */
+    for (int64_t j = 0; j < V; ++j) {
+        double v = S->x[j] - S->T[j] * S->zbar[j];
+        S->x[j] = v > 0.0 ? v : 0.0;
+    }
+    for (int64_t j = 0; j < V; ++j) dz[j] = 0.0;
+    double p_i;
+    if (i < P->n_subsets) {
+        p_i = 1.0 / (2.0 * n);
+        for (int64_t e = i; e < P->n_ev; e += P->n_subsets) {
+            double p1 = ev_fwd_ones(P, e);
+            double Se = p1 > 0.0 ? P->gamma * P->rho / p1 : 0.0; /* S_k = gamma rho / P^LM_{N_k} 1 */
+            double a = S->y[e] + Se * (ev_fwd(P, e, S->x) + (double)P->contam[e]);
+            double mu = (double)P->mu[e];
+            double yp = or_prox_dstar(a, mu * Se, 1.0);
+            ev_back(P, e, (yp - S->y[e]) / mu, dz);
+            S->y[e] = yp;
+        }
+    } else {
+        p_i = 0.5;
+        double Sp = P->gamma * P->rho / P->knorm; /* S_{n+1} */
+        or_tv_grad(P->g, S->x, gw);
+        for (int64_t j = 0; j < (int64_t)nd * V; ++j) gw[j] = S->w[j] + Sp * gw[j];
+        or_tv_prox(P->g, gw, P->beta);                 /* gw = w^+ */
+        for (int64_t j = 0; j < (int64_t)nd * V; ++j) {
+            double t = gw[j];
+            gw[j] = t - S->w[j];                       /* w^+ - w */
+            S->w[j] = t;
+        }
+        or_tv_adj(P->g, gw, dz);                       /* dz = K^T (w^+ - w) */
+    }
+    for (int64_t j = 0; j < V; ++j) {
+        S->z[j] += dz[j];
+        S->zbar[j] = S->z[j] + dz[j] / p_i;
+    }
+}
+
+/* Objective of Eq. (1) in listmode form without the constant sum of s over
+ * all bins:  <P^T 1, x> - sum_e log((P^LM x)_e + s_e) + beta ||Kx||_{2,1}. */
+double or_lm_objective(const or_lm_problem* P, const double* x, const double* sens)
+{
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    int nd = or_tv_ndim(P->g);
+    double c = 0.0;
+    for (int64_t j = 0; j < V; ++j) c += sens[j] * x[j];
+    for (int64_t e = 0; e < P->n_ev; ++e) c -= log(ev_fwd(P, e, x) + (double)P->contam[e]);
+    if (P->beta > 0.0) {
+        double* gr = (double*)malloc(sizeof(double) * V * (nd > 0 ? nd : 1));
+        or_tv_grad(P->g, x, gr);
+        double r = 0.0;
+        for (int64_t j = 0; j < V; ++j) {
+            double s = 0.0;
+            for (int cc = 0; cc < nd; ++cc) s += gr[cc * V + j] * gr[cc * V + j];
+            r += sqrt(s);
+        }
+        free(gr);
+        c += P->beta * r;
+    }
+    return c;
+}
+
+/* ------------------------------------------------------------------------
+ * Sinogram SPDHG (Alg. 1) over every (LOR, TOF bin) of the scanner, with the
+ * memory-efficient initialisation of Sec. "Memory-efficient SPDHG": y = 1 on
+ * empty bins and Eq. (yinit) elsewhere; z = P^T y.  Bins are indexed
+ * b = l * n_bins + (m + M).  Subset of bin b: sub[b] (caller-supplied).
+ * Empty bins are processed like every other bin.  The primal step size uses
+ * P^T 1 / n as in Eq. (lm_stepsizes) so that the dual parts can be compared
+ * with the listmode algorithm update by update.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const or_scanner* sc;
+    const or_grid* g;
+    const or_tof* tof;
+    const float* lor_factor; /* [n_lor] */
+    const double* d;         /* counts [n_bins_total] */
+    const double* s;         /* contamination [n_bins_total] */
+    const int32_t* sub;      /* subset of each bin */
+    int32_t n_subsets;
+    double beta, gamma, rho, knorm;
+} or_sino_problem;
+
+static void bin_dets(const or_sino_problem* P, int64_t b, int32_t* d1, int32_t* d2, int32_t* m)
+{
+    int nb = P->tof->n_bins > 0 ? P->tof->n_bins : 1;
+    int M = (nb - 1) / 2;
+    lor_dets(P->sc, b / nb, d1, d2);
+    *m = (int32_t)(b % nb) - M;
+}
+
+static double bin_fwd(const or_sino_problem* P, int64_t b, const double* x)
+{
+    int32_t d1, d2, m;
+    bin_dets(P, b, &d1, &d2, &m);
+    int nb = P->tof->n_bins > 0 ? P->tof->n_bins : 1;
+    fwd_ctx c = {NULL, x, 0.0};
+    or_lor_visit(P->sc, P->g, P->tof, d1, d2, m, ev_mode(P->tof), x ? fwd_visit : ones_visit, &c);
+    return c.acc * (double)P->lor_factor[b / nb];
+}
+
+static void bin_back(const or_sino_problem* P, int64_t b, double v, double* img)
+{
+    int32_t d1, d2, m;
+    bin_dets(P, b, &d1, &d2, &m);
+    int nb = P->tof->n_bins > 0 ? P->tof->n_bins : 1;
+    back_ctx c = {img, v * (double)P->lor_factor[b / nb]};
+    or_lor_visit(P->sc, P->g, P->tof, d1, d2, m, ev_mode(P->tof), back_visit, &c);
+}
+
+int64_t or_sino_nbins(const or_sino_problem* P)
+{
+    int nb = P->tof->n_bins > 0 ? P->tof->n_bins : 1;
+    return or_n_lor(P->sc) * nb;
+}
+
+/* y: [n_bins_total]; x (V) initialised from x0; z, zbar, w, T as in LM. */
+void or_sino_init(const or_sino_problem* P, const float* x0, const double* sens, or_lm_state* S)
+{
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    int nd = or_tv_ndim(P->g);
+    int64_t NB = or_sino_nbins(P);
+    for (int64_t j = 0; j < V; ++j) {
+        S->x[j] = (double)x0[j];
+        S->z[j] = 0.0;
+    }
+    for (int64_t b = 0; b < NB; ++b) {
+        if (P->d[b] > 0.0)
+            S->y[b] = 1.0 - P->d[b] / (bin_fwd(P, b, S->x) + P->s[b]);
+        else
+            S->y[b] = 1.0;
+        bin_back(P, b, S->y[b], S->z); /* z = P^T y */
+    }
+    for (int64_t j = 0; j < (int64_t)nd * V; ++j) S->w[j] = 0.0;
+    for (int64_t j = 0; j < V; ++j) S->zbar[j] = S->z[j];
+    double n = (double)P->n_subsets;
+    for (int64_t j = 0; j < V; ++j) {
+        double t_prior = P->rho * 0.5 / (P->gamma * P->knorm);
+        double t_data = sens[j] > 0.0 ? P->rho * (1.0 / (2.0 * n)) / (P->gamma * sens[j] / n) : INFINITY;
+        S->T[j] = t_data < t_prior ? t_data : t_prior;
+    }
+}
+
+void or_sino_update(const or_sino_problem* P, or_lm_state* S, int32_t i, double* dz, double* gw)
+{
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    int nd = or_tv_ndim(P->g);
+    int64_t NB = or_sino_nbins(P);
+    double n = (double)P->n_subsets;
+    for (int64_t j = 0; j < V; ++j) {
+        double v = S->x[j] - S->T[j] * S->zbar[j];
+        S->x[j] = v > 0.0 ? v : 0.0;
+    }
+    for (int64_t j = 0; j < V; ++j) dz[j] = 0.0;
+    double p_i;
+    if (i < P->n_subsets) {
+        p_i = 1.0 / (2.0 * n);
+        for (int64_t b = 0; b < NB; ++b) {
+            if (P->sub[b] != i) continue;
+            double p1 = bin_fwd(P, b, NULL);
+            double Sb = p1 > 0.0 ? P->gamma * P->rho / p1 : 0.0;
+            double a = S->y[b] + Sb * (bin_fwd(P, b, S->x) + P->s[b]);
+            double yp = or_prox_dstar(a, Sb, P->d[b]);
+            bin_back(P, b, yp - S->y[b], dz);
+            S->y[b] = yp;
+        }
+    } else {
+        p_i = 0.5;
+        double Sp = P->gamma * P->rho / P->knorm;
+        or_tv_grad(P->g, S->x, gw);
+        for (int64_t j = 0; j < (int64_t)nd * V; ++j) gw[j] = S->w[j] + Sp * gw[j];
+        or_tv_prox(P->g, gw, P->beta);
+        for (int64_t j = 0; j < (int64_t)nd * V; ++j) {
+            double t = gw[j];
+            gw[j] = t - S->w[j];
+            S->w[j] = t;
+        }
+        or_tv_adj(P->g, gw, dz);
+    }
+    for (int64_t j = 0; j < V; ++j) {
+        S->z[j] += dz[j];
+        S->zbar[j] = S->z[j] + dz[j] / p_i;
+    }
+}
+
+/* Eq. (1) over all bins: sum_b (Px+s)_b - d_b log(Px+s)_b + beta ||Kx||_{2,1}. */
+double or_sino_objective(const or_sino_problem* P, const double* x)
+{
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    int nd = or_tv_ndim(P->g);
+    int64_t NB = or_sino_nbins(P);
+    double c = 0.0;
+    for (int64_t b = 0; b < NB; ++b) {
+        double u = bin_fwd(P, b, x) + P->s[b];
+        c += u;
+        if (P->d[b] > 0.0) c -= P->d[b] * log(u);
+    }
+    if (P->beta > 0.0) {
+        double* gr = (double*)malloc(sizeof(double) * V * (nd > 0 ? nd : 1));
+        or_tv_grad(P->g, x, gr);
+        double r = 0.0;
+        for (int64_t j = 0; j < V; ++j) {
+            double s = 0.0;
+            for (int cc = 0; cc < nd; ++cc) s += gr[cc * V + j] * gr[cc * V + j];
+            r += sqrt(s);
+        }
+        free(gr);
+        c += P->beta * r;
+    }
+    return c;
+}
