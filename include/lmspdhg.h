@@ -1,0 +1,284 @@
+/*
+ * lmspdhg.h - C ABI of liblmspdhg.so: listmode SPDHG (LM-SPDHG) for sparse
+ * Poisson TOF PET data on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Eq. 1 of Schramm & Holler, "Fast and memory-efficient
+ * reconstruction of sparse Poisson data in listmode with non-smooth priors
+ * with application to time-of-flight PET", arXiv 2201.05497):
+ *     argmin_{x >= 0} sum_i (Px + s)_i - d_i log (Px + s)_i + beta ||Kx||_{2,1}
+ * solved from a list of events by Alg. 2 (LM-SPDHG).  Each event is one count
+ * (d^LM_e = 1, appendix); the event count mu_e carries the multiplicity of
+ * its data bin.
+ *
+ * Conventions for every call:
+ *  - Pointers named "device" are CUDA device pointers in the caller's
+ *    context, owned by the caller (allocate them with any allocator, e.g.
+ *    PyTorch).  The library never allocates device memory; calls that need
+ *    scratch take a caller workspace whose size a *_workspace_bytes /
+ *    *_state_bytes function reports.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls are asynchronous on that stream unless documented as
+ *    synchronous (those return host scalars or report data errors found on
+ *    the device).
+ *  - Every call returns an lm status; lm_last_error() gives a message for
+ *    the calling thread's last failure.  Invalid host arguments are rejected
+ *    before any launch.  Device-side data that would index out of range
+ *    (detector ids, TOF bins) is skipped by the kernels, never dereferenced;
+ *    lm_event_setup reports it as LM_ERR_OUT_OF_RANGE.
+ *  - Images are float32, x fastest: voxel (ix, iy, iz) at (iz*ny + iy)*nx + ix.
+ *    A 2D problem is a grid with n[2] = 1 and a one-ring scanner whose
+ *    crystals lie in the plane of the voxel centres (z = origin[2]).
+ *
+ * Projector (the paper cites Joseph 1982 with a Gaussian TOF kernel and gives
+ * no formula; this is the implemented definition):
+ *   a = xtal[det1], b = xtal[det2]; principal axis k = argmax_j |b_j - a_j|
+ *   (float32 differences, ties to the lowest j); one sample per voxel plane
+ *   along k, at the line's crossing of the plane through the voxel centres;
+ *   bilinear interpolation over the two other axes (neighbours outside the
+ *   grid contribute 0); sample length h_k |b-a| / |b_k-a_k|.  TOF: t = signed
+ *   distance of the sample from the LOR centre toward det2, bin centre m*bin,
+ *   weight 1/2[erf((t-m bin+bin/2)/(sqrt2 sigma)) - erf((t-m bin-bin/2)/(sqrt2 sigma))]
+ *   for |t - m bin| <= n_sigma sigma, else 0.
+ *   (P^LM x)_e = corr_e * J_e(x)   (Eq. lmop; corr = attenuation x normalisation).
+ */
+#ifndef LMSPDHG_H
+#define LMSPDHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define LM_OK 0
+#define LM_ERR_INVALID_ARG 1  /* bad host argument (NULL, size, geometry)     */
+#define LM_ERR_OUT_OF_RANGE 2 /* detector id / TOF bin out of range, mu > 65535 */
+#define LM_ERR_DOMAIN 3       /* x0 < 0, corr <= 0, contam <= 0, ...            */
+#define LM_ERR_CUDA 4         /* a CUDA runtime call failed                     */
+#define LM_ERR_TIMEOUT 5      /* a bounded device wait gave up                  */
+#define LM_ERR_NOMEM 6        /* caller workspace / state buffer too small      */
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* lm_last_error(void);
+/* Library ABI version (major*100 + minor). */
+int lm_version(void);
+
+/* ---- descriptors ------------------------------------------------------ */
+/* Crystal centres, mm, float32 [n_rings*n_xtal][3] (device); crystal id =
+ * ring*n_xtal + transaxial index.  n_rings*n_xtal < 2^27. */
+typedef struct {
+    int32_t n_rings, n_xtal;
+    const float* xtal_xyz;
+} lm_scanner;
+
+/* Voxel grid: n = (nx, ny, nz), voxel size h (mm), centre of voxel 0 (mm).
+ * nx*ny*nz < 2^31.  2D: nz = 1. */
+typedef struct {
+    int32_t n[3];
+    float h[3];
+    float origin[3];
+} lm_grid;
+
+/* TOF kernel: Gaussian sigma (mm) integrated over bins of width bin_mm,
+ * truncated at n_sigma*sigma; n_bins odd (signed bins -(n_bins-1)/2 ..
+ * (n_bins-1)/2), n_bins <= 255; n_bins = 0 is non-TOF. */
+typedef struct {
+    float sigma_mm, bin_mm, n_sigma;
+    int32_t n_bins;
+} lm_tof;
+
+/* Listmode events, device arrays of length n: detector ids, signed TOF bin
+ * (toward det2), multiplicative correction corr_e > 0 and expected
+ * contamination s_e > 0 of the event's data bin (s^LM of Eq. lmop).
+ * corr/contam may be NULL where a call says so. */
+typedef struct {
+    const int32_t* det1;
+    const int32_t* det2;
+    const int16_t* tof;
+    const float* corr;
+    const float* contam;
+    int64_t n;
+} lm_events;
+
+/* ---- projector --------------------------------------------------------- */
+/* p_e = (P^LM x)_e = corr_e J_e(x)  (Eq. lmop).  x: device image; p: device
+ * float [ev->n].  corr NULL = 1.  ws (device, may be NULL) of at least
+ * lm_fwd_workspace_bytes() lets y-principal events read a transposed copy
+ * of x (faster gathers); results are the same either way up to rounding. */
+size_t lm_fwd_workspace_bytes(const lm_grid* grid);
+int lm_fwd(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const float* x,
+           const lm_events* ev, float* p, void* ws, size_t ws_bytes, void* stream);
+
+/* img += (P^LM)^T v = sum_e corr_e J_e^T v_e (adjoint of lm_fwd).  v: device
+ * float [ev->n]; img: device image (accumulated into).  deterministic = 0:
+ * float atomics (order of additions varies between runs); deterministic = 1:
+ * every contribution is rounded to a 64-bit fixed-point grid whose step is
+ * set from max|corr_e v_e| (at most 2^-62 of the largest possible voxel
+ * sum), summed exactly with integer atomics and converted once, so the
+ * result is bit-identical across runs and launch shapes.  ws: device
+ * workspace of lm_back_workspace_bytes(grid, deterministic) bytes. */
+size_t lm_back_workspace_bytes(const lm_grid* grid, int deterministic);
+int lm_back(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev,
+            const float* v, float* img, int deterministic, void* ws, size_t ws_bytes, void* stream);
+
+/* Sensitivity image sens = P^T 1 (Sec. "Listmode SPDHG": pre-computed once and
+ * stored), i.e. the back-projection of ones over every canonical LOR and
+ * every TOF bin, times lor_factor[l] (device float [lm_n_lor], NULL = 1).
+ * The per-sample sum of the truncated bin weights over the bins is
+ * evaluated in closed form (the bin integrals telescope).  Canonical LOR
+ * order: transaxial pairs q in [0, n_xtal(n_xtal-1)/2): with
+ * B = n_xtal*floor((n_xtal-1)/2), q < B -> c1 = q mod n_xtal,
+ * c2 = (c1 + 1 + q div n_xtal) mod n_xtal; q >= B (even n_xtal) -> c1 = q-B,
+ * c2 = c1 + n_xtal/2.  LOR l = (q*n_rings + r1)*n_rings + r2,
+ * det1 = r1*n_xtal + c1, det2 = r2*n_xtal + c2.  sens is overwritten.
+ * ws (device, may be NULL) of lm_sens_workspace_bytes() bytes speeds up
+ * y-principal LORs. */
+int64_t lm_n_lor(const lm_scanner* sc);
+size_t lm_sens_workspace_bytes(const lm_grid* grid);
+int lm_sens(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const float* lor_factor,
+            float* sens, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- TV prior (Sec. "Numerical experiments": R(Kx) = ||Kx||_{2,1}) ------- */
+/* K: unit-spacing forward differences with a Neumann boundary (last
+ * difference 0), one component per axis with n_d > 1, in axis order;
+ * components stored one after another ([ndim][V]).  lm_tv_ndim gives ndim. */
+int lm_tv_ndim(const lm_grid* grid);
+int lm_tv_grad(const lm_grid* grid, const float* x, float* g, void* stream);
+/* d = div g = -K^T g. */
+int lm_tv_div(const lm_grid* grid, const float* g, float* d, void* stream);
+/* w <- beta prox_{R^*}(w / beta) = w / max(1, |w|/beta), per voxel over the
+ * components (in place); beta = 0 sets w = 0. */
+int lm_tv_prox(const lm_grid* grid, float* w, float beta, void* stream);
+/* ||K|| by FP64 power iteration on K^T K from the checkerboard
+ * (-1)^(ix+iy+iz), `iters` iterations; *out_host = sqrt of the last Rayleigh
+ * quotient (never above ||K||).  Synchronous.  ws: device workspace of
+ * lm_knorm_workspace_bytes() bytes. */
+size_t lm_knorm_workspace_bytes(const lm_grid* grid);
+int lm_knorm_fp64(const lm_grid* grid, int32_t iters, void* ws, size_t ws_bytes, double* out_host,
+                  void* stream);
+
+/* ---- event set-up (Alg. 2 steps 2 and 6) -------------------------------- */
+/* Validates the events (0 <= det < n_det, det1 != det2, |tof| <= (n_bins-1)/2,
+ * corr > 0, contam > 0), counts mu_e = number of events of the whole list in
+ * the event's data bin (its unordered detector pair and TOF bin; footnote of
+ * Sec. "Listmode SPDHG"), and writes the events in subset-contiguous order:
+ * event e goes to subset e mod n_subsets, at rank e div n_subsets inside it
+ * (Sec. "Listmode SPDHG": every n-th event to the n-th sub list).  Outputs
+ * are device arrays of length ev->n: *_out (permuted fields) and mu_out
+ * (uint16).  sub_off_host (host int64[n_subsets+1]) receives the subset
+ * offsets.  Synchronous.  Returns LM_ERR_OUT_OF_RANGE / LM_ERR_DOMAIN on
+ * invalid events (outputs undefined), LM_ERR_OUT_OF_RANGE if some mu > 65535.
+ * ws: device workspace of lm_setup_workspace_bytes(n) bytes. */
+size_t lm_setup_workspace_bytes(int64_t n_events);
+int lm_event_setup(const lm_scanner* sc, const lm_tof* tof, const lm_events* ev, int32_t n_subsets,
+                   int32_t* det1_out, int32_t* det2_out, int16_t* tof_out, float* corr_out,
+                   float* contam_out, uint16_t* mu_out, int64_t* sub_off_host, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/* ---- LM-SPDHG state (Alg. 2) --------------------------------------------- */
+typedef struct lm_state_s lm_state;
+
+typedef struct {
+    float beta;           /* prior weight, >= 0                                   */
+    float gamma;          /* step-size ratio; <= 0: 3 / max(x0) (paper's choice)  */
+    float rho;            /* 0 < rho < 1 (paper: 0.999)                           */
+    double knorm;         /* ||K||; <= 0: FP64 power iteration (knorm_iters)      */
+    int32_t knorm_iters;  /* iterations when knorm <= 0 (0: 1000)                 */
+    int32_t n_subsets;    /* n >= 1                                               */
+    int32_t deterministic;/* 1: fixed-point back-projection (bit-reproducible)    */
+    int32_t kahan;        /* 1: compensated float32 accumulation of z             */
+} lm_params;
+
+/* Device bytes the state needs (images, duals, per-event y and scratch). */
+size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets,
+                           int32_t deterministic);
+
+/* Initialise Alg. 2 (steps 3-6) on events already in subset-contiguous
+ * order (from lm_event_setup; the arrays are referenced, not copied, and
+ * must outlive the state):
+ *   y_e = 1 - mu_e / ((P^LM x0)_e + s_e)                      (Eq. yinit)
+ *   z = zbar = P^T 1 + (P^LM)^T((y - 1)/mu) + K^T w, w = 0
+ *     (= P^T applied to the sinogram that is 1 on empty bins and Eq. yinit
+ *      elsewhere; the printed minus sign of step 5 is read as this plus)
+ *   T = min_k T_k with T_k = gamma^-1 rho p_k / (P^T 1 / n) for data subsets
+ *   and T_{n+1} = gamma^-1 p_{n+1} rho / ||K||;  S_e = gamma rho / (P^LM 1)_e
+ *   (Eq. lm_stepsizes), S_{n+1} = gamma rho / ||K||; p_k = 1/(2n), p_{n+1} = 1/2.
+ * sens: device P^T 1 (lm_sens), referenced.  x0: device image >= 0 (copied).
+ * sub_off_host: host int64[n+1].  state_buf: device buffer of
+ * lmspdhg_state_bytes() bytes owned by the caller.  Synchronous (reads
+ * max(x0), min(x0) and, if asked for, ||K||).  *out receives a host handle;
+ * free it with lmspdhg_destroy. */
+int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof,
+                   const lm_events* ev_perm, const uint16_t* mu, const int64_t* sub_off_host,
+                   const float* sens, const float* x0, const lm_params* params, void* state_buf,
+                   size_t state_bytes, void* stream);
+
+/* Run `count` updates of the Alg. 2 loop (x <- proj(x - T zbar); selected
+ * update; z <- z + dz; zbar <- z + dz/p_i).  seq_host: host uint16[count],
+ * value i < n selects data subset i, value n selects the prior.  Any count. */
+int lmspdhg_updates(lm_state* st, const uint16_t* seq_host, int32_t count, void* stream);
+
+/* One epoch = 2n updates, replayed from a CUDA graph captured on first use
+ * (the selection is read on the device, so one graph serves every sequence).
+ * seq_host: host uint16[2n]. */
+int lmspdhg_epoch(lm_state* st, const uint16_t* seq_host, void* stream);
+
+/* Copies (device to device) the x used by the most recent update (x0 before
+ * any update), the dual list y (subset-contiguous order), z (with its
+ * compensation added) and w ([ndim][V]). */
+int lmspdhg_get_x(lm_state* st, float* x_out, void* stream);
+int lmspdhg_get_y(lm_state* st, float* y_out, void* stream);
+int lmspdhg_get_z(lm_state* st, float* z_out, void* stream);
+int lmspdhg_get_w(lm_state* st, float* w_out, void* stream);
+
+/* Objective of Eq. (1) in listmode form at the x of lmspdhg_get_x, without
+ * the constant sum of s over all bins:
+ *   <P^T 1, x> - sum_e log((P^LM x)_e + s_e) + beta ||Kx||_{2,1},
+ * projections in float32, logs and sums in FP64 (fixed reduction order).
+ * Synchronous. */
+int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream);
+
+/* Number of updates run so far and the state's parameters (gamma, knorm
+ * as resolved at create). */
+int lmspdhg_info(lm_state* st, int64_t* n_updates, double* gamma, double* knorm);
+
+/* Re-initialise the state (Alg. 2 steps 3-5 as in lmspdhg_create) for the
+ * current contents of the referenced event arrays and a new x0, keeping the
+ * buffers and the captured epoch graph: the events may have been overwritten
+ * with another frame of the same size and subset split.  Synchronous. */
+int lmspdhg_reinit(lm_state* st, const float* x0, void* stream);
+
+/* Runs `count` (1..2n) updates like lmspdhg_updates, recording CUDA events on
+ * `stream` around every kernel; ms4/n4 (host, 4 entries) receive the summed
+ * milliseconds and launch counts of: [0] data-update event kernels, [1] prior
+ * dual-step kernels, [2] image passes after data updates, [3] image passes
+ * after prior updates.  Synchronous. */
+int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, double* ms4, int64_t* n4,
+                    void* stream);
+
+int lmspdhg_destroy(lm_state* st);
+
+/* ---- measurement utilities (no counterpart in the paper) ---------------- */
+/* Kernels launched by this library in this process so far (a replayed
+ * epoch graph counts each of its kernel nodes). */
+int64_t lm_kernel_launches(void);
+
+/* Exact traversal counts of an event list: samples with a non-zero TOF
+ * weight and an in-grid neighbour, and in-grid neighbour touches (each touch
+ * is one 4-byte image read in a forward projection and one 4-byte atomic add
+ * in a back-projection).  ws: device, >= 16 bytes.  Synchronous. */
+int lm_traversal_stats(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev,
+                       void* ws, size_t ws_bytes, int64_t* n_samples, int64_t* n_touches, void* stream);
+
+/* L2 throughput probe on the caller's device buffer (use one that fits in
+ * L2): mode 0 coalesced 16-byte reads, 1 coalesced float atomic adds, 2
+ * random 4-byte reads, 3 random float atomic adds; *gbs_out = payload GB/s
+ * over `iters` passes.  The buffer is overwritten.  Synchronous. */
+int lm_probe_l2(void* buf, size_t bytes, int32_t mode, int32_t iters, double* gbs_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMSPDHG_H */

@@ -105,6 +105,11 @@ def lib():
             L.or_lm_update.argtypes = [P(LmProblem), P(LmState), C.c_int32, P(C.c_double), P(C.c_double)]
             L.or_lm_objective.argtypes = [P(LmProblem), P(C.c_double), P(C.c_double)]
             L.or_lm_objective.restype = C.c_double
+            L.or_tof_edge_distance.argtypes = [P(Scanner), P(Grid), P(Tof), P(C.c_int32), P(C.c_int32),
+                                               P(C.c_int16), C.c_int64, P(C.c_double)]
+            L.or_fwd_position_sensitivity.argtypes = [P(Scanner), P(Grid), P(Tof), P(C.c_int32), P(C.c_int32),
+                                                      P(C.c_int16), P(C.c_float), C.c_int64, P(C.c_float),
+                                                      P(C.c_double)]
             L.or_sino_nbins.argtypes = [P(SinoProblem)]
             L.or_sino_nbins.restype = C.c_int64
             L.or_sino_init.argtypes = [P(SinoProblem), P(C.c_float), P(C.c_double), P(LmState)]
@@ -175,6 +180,26 @@ def fwd(geo: Geometry, ev: EventArrays, x: np.ndarray, use_corr: bool = True) ->
     lib().or_fwd(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _p(ev.det1, C.c_int32),
                  _p(ev.det2, C.c_int32), _p(ev.tof, C.c_int16),
                  _p(ev.corr, C.c_float) if use_corr else None, ev.n, _p(x, C.c_float), _p(out, C.c_double))
+    return out
+
+
+def tof_edge_distance(geo: Geometry, ev: EventArrays) -> np.ndarray:
+    """Per event, distance (mm) of its nearest in-grid sample from the TOF
+    truncation edge (inf for non-TOF or empty events)."""
+    out = np.zeros(ev.n, dtype=np.float64)
+    lib().or_tof_edge_distance(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _p(ev.det1, C.c_int32),
+                               _p(ev.det2, C.c_int32), _p(ev.tof, C.c_int16), ev.n, _p(out, C.c_double))
+    return out
+
+
+def fwd_position_sensitivity(geo: Geometry, ev: EventArrays, x: np.ndarray) -> np.ndarray:
+    """Per event, |d (P^LM x)_e / d(sample position)| summed over samples, in
+    image units per voxel of shift (see lmoracle.c)."""
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    out = np.zeros(ev.n, dtype=np.float64)
+    lib().or_fwd_position_sensitivity(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _p(ev.det1, C.c_int32),
+                                      _p(ev.det2, C.c_int32), _p(ev.tof, C.c_int16), _p(ev.corr, C.c_float), ev.n,
+                                      _p(x, C.c_float), _p(out, C.c_double))
     return out
 
 

@@ -711,3 +711,102 @@ double or_sino_objective(const or_sino_problem* P, const double* x)
     }
     return c;
 }
+
+/* Distance (mm) from the TOF truncation edge of the event's sample nearest
+ * to it: min over planes of | |t_i - c_m| - n_sigma sigma |, over samples
+ * with at least one in-grid neighbour.  Events where it is tiny are
+ * "boundary-ambiguous": float32 and FP64 may decide the cut differently. */
+void or_tof_edge_distance(const or_scanner* sc, const or_grid* g, const or_tof* tof, const int32_t* det1,
+                          const int32_t* det2, const int16_t* tbin, int64_t n, double* out)
+{
+    for (int64_t e = 0; e < n; ++e) {
+        double a[3], b[3], d[3], o[3], h[3];
+        float df[3];
+        for (int j = 0; j < 3; ++j) {
+            a[j] = (double)sc->xtal[3 * (int64_t)det1[e] + j];
+            b[j] = (double)sc->xtal[3 * (int64_t)det2[e] + j];
+            d[j] = b[j] - a[j];
+            df[j] = (float)d[j];
+            o[j] = (double)g->origin[j];
+            h[j] = (double)g->h[j];
+        }
+        int k = 0;
+        if (fabsf(df[1]) > fabsf(df[k])) k = 1;
+        if (fabsf(df[2]) > fabsf(df[k])) k = 2;
+        double best = INFINITY;
+        if (d[k] != 0.0 && tof->n_bins > 0) {
+            int s1 = (k + 1) % 3, s2 = (k + 2) % 3;
+            double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double W = (double)tof->n_sigma * (double)tof->sigma;
+            for (int i = 0; i < g->n[k]; ++i) {
+                double lam = (o[k] + i * h[k] - a[k]) / d[k];
+                double u1 = (a[s1] + lam * d[s1] - o[s1]) / h[s1];
+                double u2 = (a[s2] + lam * d[s2] - o[s2]) / h[s2];
+                if (u1 <= -1.0 || u1 >= g->n[s1] || u2 <= -1.0 || u2 >= g->n[s2]) continue;
+                double tau = (lam - 0.5) * L - (double)tbin[e] * (double)tof->bin;
+                double dist = fabs(fabs(tau) - W);
+                if (dist < best) best = dist;
+            }
+        }
+        out[e] = best;
+    }
+}
+
+/* Sensitivity of (P^LM x)_e to a shift of the sample positions: per event
+ * corr_e * sum over samples of step * w_tof * (|d interp/d u1| + |d interp/d u2|),
+ * u in voxel units.  Times the float32 resolution of a voxel coordinate it
+ * bounds the projection error that comes from representing positions in
+ * float32 (used to state the per-event tolerance of the float32 projector). */
+void or_fwd_position_sensitivity(const or_scanner* sc, const or_grid* g, const or_tof* tof,
+                                 const int32_t* det1, const int32_t* det2, const int16_t* tbin,
+                                 const float* corr, int64_t n, const float* x, double* out)
+{
+    for (int64_t e = 0; e < n; ++e) {
+        double a[3], b[3], d[3], o[3], h[3];
+        float df[3];
+        for (int j = 0; j < 3; ++j) {
+            a[j] = (double)sc->xtal[3 * (int64_t)det1[e] + j];
+            b[j] = (double)sc->xtal[3 * (int64_t)det2[e] + j];
+            d[j] = b[j] - a[j];
+            df[j] = (float)d[j];
+            o[j] = (double)g->origin[j];
+            h[j] = (double)g->h[j];
+        }
+        int k = 0;
+        if (fabsf(df[1]) > fabsf(df[k])) k = 1;
+        if (fabsf(df[2]) > fabsf(df[k])) k = 2;
+        double acc = 0.0;
+        if (d[k] != 0.0) {
+            int s1 = (k + 1) % 3, s2 = (k + 2) % 3;
+            double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double step = h[k] * L / fabs(d[k]);
+            for (int i = 0; i < g->n[k]; ++i) {
+                double lam = (o[k] + i * h[k] - a[k]) / d[k];
+                double wt = 1.0;
+                if (tof->n_bins > 0) wt = tof_bin_weight((lam - 0.5) * L - (double)tbin[e] * (double)tof->bin, tof);
+                if (wt == 0.0) continue;
+                double u1 = (a[s1] + lam * d[s1] - o[s1]) / h[s1];
+                double u2 = (a[s2] + lam * d[s2] - o[s2]) / h[s2];
+                double fl1 = floor(u1), fl2 = floor(u2);
+                int64_t i1 = (int64_t)fl1, i2 = (int64_t)fl2;
+                double f1 = u1 - fl1, f2 = u2 - fl2;
+                double v[2][2];
+                for (int da = 0; da < 2; ++da)
+                    for (int db = 0; db < 2; ++db) {
+                        int64_t j1 = i1 + da, j2 = i2 + db;
+                        v[da][db] = 0.0;
+                        if (j1 < 0 || j1 >= g->n[s1] || j2 < 0 || j2 >= g->n[s2]) continue;
+                        int64_t idx[3];
+                        idx[k] = i;
+                        idx[s1] = j1;
+                        idx[s2] = j2;
+                        v[da][db] = (double)x[(idx[2] * g->n[1] + idx[1]) * g->n[0] + idx[0]];
+                    }
+                double g1 = (1.0 - f2) * (v[1][0] - v[0][0]) + f2 * (v[1][1] - v[0][1]);
+                double g2 = (1.0 - f1) * (v[0][1] - v[0][0]) + f1 * (v[1][1] - v[1][0]);
+                acc += step * wt * (fabs(g1) + (g->n[s2] > 1 ? fabs(g2) : 0.0));
+            }
+        }
+        out[e] = acc * (corr ? (double)corr[e] : 1.0);
+    }
+}

@@ -1,0 +1,803 @@
+// Image-space kernels of LM-SPDHG (Alg. 2): the per-update image pass that
+// merges the back-projected dual change into z (compensated float32
+// summation), forms zbar = z + dz/p_i and applies the next primal step
+// x <- proj_{>=0}(x - T zbar) (Alg. 2 line 8 of the following update); the
+// TV operator K (forward differences, Neumann boundary), its adjoint and the
+// prox of R^* (Sec. "Numerical experiments"); the FP64 power iteration for
+// ||K||; the step sizes T (Eq. lm_stepsizes) and FP64 reductions of the
+// objective (Eq. 1).
+//
+// Image passes work on 32 x 32 (x, y) tiles of one z slice so that the
+// y-fastest copies are read and written through shared memory with
+// coalesced accesses in both layouts.
+#include <cmath>
+#include <cstring>
+
+#include "lm_internal.h"
+
+using namespace lmk;
+
+namespace {
+
+constexpr int TD = 32;  // tile edge
+constexpr int TR = 8;   // thread rows per tile (block 32 x 8)
+
+struct TileIdx {
+    int x0, y0, z;
+};
+
+__device__ __forceinline__ TileIdx tile_of(int64_t t, int nx, int ny)
+{
+    const int tx = (nx + TD - 1) / TD, ty = (ny + TD - 1) / TD;
+    TileIdx r;
+    r.x0 = (int)(t % tx) * TD;
+    r.y0 = (int)((t / tx) % ty) * TD;
+    r.z = (int)(t / ((int64_t)tx * ty));
+    return r;
+}
+
+__device__ __forceinline__ int64_t n_tiles(int nx, int ny, int nz)
+{
+    return (int64_t)((nx + TD - 1) / TD) * ((ny + TD - 1) / TD) * nz;
+}
+
+__global__ void __launch_bounds__(256) transpose_to_yf_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                                              int nx, int ny, int nz)
+{
+    __shared__ float sm[TD][TD + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int64_t t = blockIdx.x; t < n_tiles(nx, ny, nz); t += gridDim.x) {
+        const TileIdx T = tile_of(t, nx, ny);
+        for (int r = ty; r < TD; r += TR) {
+            const int xx = T.x0 + tx, yy = T.y0 + r;
+            if (xx < nx && yy < ny) sm[r][tx] = src[((int64_t)T.z * ny + yy) * nx + xx];
+        }
+        __syncthreads();
+        for (int r = ty; r < TD; r += TR) {
+            const int xx = T.x0 + r, yy = T.y0 + tx;
+            if (xx < nx && yy < ny) dst[((int64_t)T.z * nx + xx) * ny + yy] = sm[tx][r];
+        }
+        __syncthreads();
+    }
+}
+
+// img += transpose(yf); yf <- 0
+__global__ void __launch_bounds__(256) add_yf_kernel(float* __restrict__ img, float* __restrict__ yf, int nx, int ny,
+                                                     int nz)
+{
+    __shared__ float sm[TD][TD + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int64_t t = blockIdx.x; t < n_tiles(nx, ny, nz); t += gridDim.x) {
+        const TileIdx T = tile_of(t, nx, ny);
+        for (int r = ty; r < TD; r += TR) {
+            const int xx = T.x0 + r, yy = T.y0 + tx;
+            if (xx < nx && yy < ny) {
+                const int64_t k = ((int64_t)T.z * nx + xx) * ny + yy;
+                sm[r][tx] = yf[k];
+                yf[k] = 0.0f;
+            }
+        }
+        __syncthreads();
+        for (int r = ty; r < TD; r += TR) {
+            const int xx = T.x0 + tx, yy = T.y0 + r;
+            if (xx < nx && yy < ny) img[((int64_t)T.z * ny + yy) * nx + xx] += sm[tx][r];
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ double fx_step(const unsigned* maxbits, long long count, float stepmax)
+{
+    const float vmax = __uint_as_float(*maxbits);
+    return ldexp(1.0, -fx_exponent(vmax, count, stepmax));
+}
+
+// img += (a_std + transpose(a_yf)) * 2^-E; accumulators <- 0
+__global__ void __launch_bounds__(256) fold_fixed_kernel(float* __restrict__ img, unsigned long long* __restrict__ a_std,
+                                                         unsigned long long* __restrict__ a_yf, const unsigned* maxbits,
+                                                         long long count, float stepmax, int nx, int ny, int nz)
+{
+    __shared__ long long sm[TD][TD + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const double step = fx_step(maxbits, count, stepmax);
+    for (int64_t t = blockIdx.x; t < n_tiles(nx, ny, nz); t += gridDim.x) {
+        const TileIdx T = tile_of(t, nx, ny);
+        if (a_yf) {
+            for (int r = ty; r < TD; r += TR) {
+                const int xx = T.x0 + r, yy = T.y0 + tx;
+                if (xx < nx && yy < ny) {
+                    const int64_t k = ((int64_t)T.z * nx + xx) * ny + yy;
+                    sm[r][tx] = (long long)a_yf[k];
+                    a_yf[k] = 0ULL;
+                }
+            }
+        }
+        __syncthreads();
+        for (int r = ty; r < TD; r += TR) {
+            const int xx = T.x0 + tx, yy = T.y0 + r;
+            if (xx < nx && yy < ny) {
+                const int64_t j = ((int64_t)T.z * ny + yy) * nx + xx;
+                long long s = (long long)a_std[j];
+                a_std[j] = 0ULL;
+                if (a_yf) s += sm[tx][r];
+                img[j] += (float)((double)s * step);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Sum a + b with its exact rounding error (TwoSum, Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// dz_j = (K^T (w+ - w))_j, components in axis order for axes with n > 1
+__device__ __forceinline__ float prior_dz(const lmh::ImgArgs& A, const float* wc, const float* wn, int xx, int yy,
+                                          int zz, int64_t j)
+{
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const int64_t V = A.V;
+    float dz = 0.0f;
+    int c = 0;
+    if (nx > 1) {
+        const int64_t o = (int64_t)c * V;
+        if (xx < nx - 1) dz -= wn[o + j] - wc[o + j];
+        if (xx >= 1) dz += wn[o + j - 1] - wc[o + j - 1];
+        ++c;
+    }
+    if (ny > 1) {
+        const int64_t o = (int64_t)c * V;
+        if (yy < ny - 1) dz -= wn[o + j] - wc[o + j];
+        if (yy >= 1) dz += wn[o + j - nx] - wc[o + j - nx];
+        ++c;
+    }
+    if (nz > 1) {
+        const int64_t o = (int64_t)c * V;
+        const int64_t sz = (int64_t)nx * ny;
+        if (zz < nz - 1) dz -= wn[o + j] - wc[o + j];
+        if (zz >= 1) dz += wn[o + j - sz] - wc[o + j - sz];
+    }
+    return dz;
+}
+
+__global__ void __launch_bounds__(256) image_pass_kernel(const lmh::ImgArgs A)
+{
+    __shared__ float smf[TD][TD + 1];
+    __shared__ long long smi[TD][TD + 1];
+    __shared__ float smx[TD][TD + 1];
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    bool data = A.mode == lmh::IP_INIT, prior = false;
+    long long count = 0;
+    float inv_p = 1.0f;
+    int slot = 1;  // max-bits slot of the fixed-point scale used by this update
+    if (A.mode == lmh::IP_UPDATE) {
+        const int sel = A.seq[A.u];
+        prior = sel >= A.n_subsets;
+        data = !prior;
+        if (data) count = (long long)(A.sub_off[sel + 1] - A.sub_off[sel]);
+        inv_p = prior ? A.inv_p_prior : A.inv_p_data;
+        slot = (A.slot0 + A.u) & 1;
+        // clear the slot the next update will use
+        if (blockIdx.x == 0 && tx == 0 && ty == 0 && A.maxbits_reset) A.maxbits_reset[(A.slot0 + A.u + 1) & 1] = 0u;
+    } else {
+        count = (long long)A.sub_off[A.n_subsets];
+        if (blockIdx.x == 0 && tx == 0 && ty == 0 && A.maxbits_reset) A.maxbits_reset[0] = 0u;
+    }
+    double fx = 0.0;
+    if (data && A.det) fx = fx_step(A.maxbits + slot, count, A.stepmax);
+    const float* wc = nullptr;
+    const float* wn = nullptr;
+    if (prior) {
+        const int wp = A.wpar[A.u];
+        wc = A.w_cur[wp];
+        wn = A.w_nxt[wp];
+    }
+    const bool have_yf = ny > 1;
+    for (int64_t t = blockIdx.x; t < n_tiles(nx, ny, nz); t += gridDim.x) {
+        const TileIdx T = tile_of(t, nx, ny);
+        if (data && have_yf) {
+            for (int r = ty; r < TD; r += TR) {
+                const int xx = T.x0 + r, yy = T.y0 + tx;
+                if (xx < nx && yy < ny) {
+                    const int64_t k = ((int64_t)T.z * nx + xx) * ny + yy;
+                    if (A.det) {
+                        smi[r][tx] = (long long)A.acci_yf[k];
+                        A.acci_yf[k] = 0ULL;
+                    } else {
+                        smf[r][tx] = A.acc_yf[k];
+                        A.acc_yf[k] = 0.0f;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int r = ty; r < TD; r += TR) {
+            const int xx = T.x0 + tx, yy = T.y0 + r;
+            if (xx < nx && yy < ny) {
+                const int64_t j = ((int64_t)T.z * ny + yy) * nx + xx;
+                float dz;
+                if (data) {
+                    if (A.det) {
+                        long long s = (long long)A.acci_std[j];
+                        A.acci_std[j] = 0ULL;
+                        if (have_yf) s += smi[tx][r];
+                        dz = (float)((double)s * fx);
+                    } else {
+                        dz = A.acc_std[j];
+                        A.acc_std[j] = 0.0f;
+                        if (have_yf) dz += smf[tx][r];
+                    }
+                } else {
+                    dz = prior_dz(A, wc, wn, xx, yy, T.z, j);
+                }
+                float zh, zl = 0.0f, xn;
+                if (A.mode == lmh::IP_INIT) {
+                    // z = P^T 1 + (P^LM)^T((y-1)/mu); zbar = z; first primal step from x0
+                    float e = 0.0f;
+                    two_sum(A.sens[j], dz, zh, e);
+                    zl = A.kahan ? e : 0.0f;
+                    const float x0 = A.x_cur[j];
+                    A.x_keep[j] = x0;
+                    xn = fmaxf(0.0f, x0 - A.T[j] * (zh + zl));
+                } else {
+                    const float z0 = A.z[j];
+                    if (A.kahan) {
+                        float e;
+                        two_sum(z0, dz, zh, e);
+                        zl = A.zc[j] + e;
+                    } else {
+                        zh = z0 + dz;
+                    }
+                    const float zbar = fmaf(dz, inv_p, zh + zl);  // z + dz/p_i
+                    xn = fmaxf(0.0f, A.x_cur[j] - A.T[j] * zbar);
+                }
+                A.z[j] = zh;
+                if (A.kahan) A.zc[j] = zl;
+                A.x_nxt_std[j] = xn;
+                smx[r][tx] = xn;
+            }
+        }
+        __syncthreads();
+        if (have_yf) {
+            for (int r = ty; r < TD; r += TR) {
+                const int xx = T.x0 + r, yy = T.y0 + tx;
+                if (xx < nx && yy < ny) A.x_nxt_yf[((int64_t)T.z * nx + xx) * ny + yy] = smx[tx][r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int tile_grid(const lm_grid* g, int per_sm = 8)
+{
+    const int64_t nt = (int64_t)((g->n[0] + TD - 1) / TD) * ((g->n[1] + TD - 1) / TD) * g->n[2];
+    return (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)lmh::num_sms() * per_sm));
+}
+
+__global__ void wpar_kernel(const uint16_t* seq, int count, int n_subsets, int* wpar, int* wbase)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int p = *wbase;
+        wpar[0] = p;
+        for (int u = 0; u < count; ++u) {
+            if (seq[u] >= n_subsets) p ^= 1;
+            wpar[u + 1] = p;
+        }
+        *wbase = p;
+    }
+}
+
+__global__ void step_T_kernel(const float* __restrict__ sens, float* __restrict__ T, int64_t V, float t_prior,
+                              float c_data)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const float s = sens[j];
+        const float t_data = s > 0.0f ? c_data / s : INFINITY;
+        T[j] = fminf(t_data, t_prior);
+    }
+}
+
+constexpr int RB = 1024;  // blocks of the fixed-shape reductions
+
+// partial min / max (fixed grid of RB blocks; deterministic)
+__global__ void __launch_bounds__(256) minmax_partial(const float* __restrict__ x, int64_t n, float* part)
+{
+    __shared__ float smn[256], smx[256];
+    float mn = INFINITY, mx = -INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)RB * 256) {
+        const float v = x[i];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+    }
+    smn[threadIdx.x] = mn;
+    smx[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            smn[threadIdx.x] = fminf(smn[threadIdx.x], smn[threadIdx.x + s]);
+            smx[threadIdx.x] = fmaxf(smx[threadIdx.x], smx[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = smn[0];
+        part[RB + blockIdx.x] = smx[0];
+    }
+}
+
+__global__ void __launch_bounds__(256) minmax_final(float* part)
+{
+    __shared__ float smn[256], smx[256];
+    float mn = INFINITY, mx = -INFINITY;
+    for (int i = threadIdx.x; i < RB; i += 256) {
+        mn = fminf(mn, part[i]);
+        mx = fmaxf(mx, part[RB + i]);
+    }
+    smn[threadIdx.x] = mn;
+    smx[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            smn[threadIdx.x] = fminf(smn[threadIdx.x], smn[threadIdx.x + s]);
+            smx[threadIdx.x] = fmaxf(smx[threadIdx.x], smx[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * RB] = smn[0];
+        part[2 * RB + 1] = smx[0];
+    }
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sm)
+{
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sm[0];
+    __syncthreads();
+    return r;
+}
+
+// objective parts over voxels: <sens, x> and ||Kx||_{2,1} (FP64)
+__global__ void __launch_bounds__(256) obj_img_partial(const float* __restrict__ sens, const float* __restrict__ x,
+                                                       int nx, int ny, int nz, double* part)
+{
+    __shared__ double sm[256];
+    const int64_t V = (int64_t)nx * ny * nz;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x; j < V; j += (int64_t)RB * 256) {
+        const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / ((int64_t)nx * ny));
+        const double xj = (double)x[j];
+        s1 += (double)sens[j] * xj;
+        double g2 = 0.0, g;
+        if (nx > 1 && ix < nx - 1) { g = (double)x[j + 1] - xj; g2 += g * g; }
+        if (ny > 1 && iy < ny - 1) { g = (double)x[j + nx] - xj; g2 += g * g; }
+        if (nz > 1 && iz < nz - 1) { g = (double)x[j + (int64_t)nx * ny] - xj; g2 += g * g; }
+        s2 += sqrt(g2);
+    }
+    s1 = block_sum_d(s1, sm);
+    s2 = block_sum_d(s2, sm);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s1;
+        part[RB + blockIdx.x] = s2;
+    }
+}
+
+// sum_e log(p_e + s_e) (FP64)
+__global__ void __launch_bounds__(256) obj_ev_partial(const float* __restrict__ p, const float* __restrict__ s,
+                                                      int64_t n, double* part)
+{
+    __shared__ double sm[256];
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)RB * 256)
+        acc += log((double)p[e] + (double)s[e]);
+    acc = block_sum_d(acc, sm);
+    if (threadIdx.x == 0) part[2 * RB + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) obj_final(double* part)
+{
+    __shared__ double sm[256];
+    for (int q = 0; q < 3; ++q) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < RB; i += 256) acc += part[q * RB + i];
+        acc = block_sum_d(acc, sm);
+        if (threadIdx.x == 0) part[3 * RB + q] = acc;
+    }
+}
+
+// ---- TV operators (standalone calls) ----
+__global__ void tv_grad_kernel(const float* __restrict__ x, float* __restrict__ g, int nx, int ny, int nz)
+{
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / ((int64_t)nx * ny));
+        const float xj = x[j];
+        int c = 0;
+        if (nx > 1) g[(c++) * V + j] = ix < nx - 1 ? x[j + 1] - xj : 0.0f;
+        if (ny > 1) g[(c++) * V + j] = iy < ny - 1 ? x[j + nx] - xj : 0.0f;
+        if (nz > 1) g[(c++) * V + j] = iz < nz - 1 ? x[j + (int64_t)nx * ny] - xj : 0.0f;
+    }
+}
+
+// d = div g = -K^T g
+__global__ void tv_div_kernel(const float* __restrict__ g, float* __restrict__ d, int nx, int ny, int nz)
+{
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / ((int64_t)nx * ny));
+        float s = 0.0f;
+        int c = 0;
+        if (nx > 1) {
+            const float* q = g + (int64_t)(c++) * V;
+            if (ix < nx - 1) s += q[j];
+            if (ix >= 1) s -= q[j - 1];
+        }
+        if (ny > 1) {
+            const float* q = g + (int64_t)(c++) * V;
+            if (iy < ny - 1) s += q[j];
+            if (iy >= 1) s -= q[j - nx];
+        }
+        if (nz > 1) {
+            const float* q = g + (int64_t)(c++) * V;
+            if (iz < nz - 1) s += q[j];
+            if (iz >= 1) s -= q[j - (int64_t)nx * ny];
+        }
+        d[j] = s;
+    }
+}
+
+__global__ void tv_prox_kernel(float* __restrict__ w, int64_t V, int ndim, float beta)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        float s2 = 0.0f;
+        for (int c = 0; c < ndim; ++c) s2 = fmaf(w[c * V + j], w[c * V + j], s2);
+        const float nrm = sqrtf(s2);
+        if (beta > 0.0f) {
+            const float den = fmaxf(1.0f, nrm / beta);
+            for (int c = 0; c < ndim; ++c) w[c * V + j] = w[c * V + j] / den;
+        } else {
+            for (int c = 0; c < ndim; ++c) w[c * V + j] = 0.0f;
+        }
+    }
+}
+
+// ---- ||K|| power iteration (FP64) ----
+__global__ void kn_init(double* v, int nx, int ny, int nz)
+{
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(j % nx) + (int)((j / nx) % ny) + (int)(j / ((int64_t)nx * ny));
+        v[j] = (s & 1) ? -1.0 : 1.0;
+    }
+}
+
+// u = K^T K (c v), c = scal[0]; partial sums of (cv).u, (cv).(cv), u.u
+__global__ void __launch_bounds__(256) kn_apply(const double* __restrict__ v, double* __restrict__ u,
+                                                const double* __restrict__ scal, int nx, int ny, int nz, double* part)
+{
+    __shared__ double sm[256];
+    const int64_t V = (int64_t)nx * ny * nz;
+    const double c = scal[0];
+    const int64_t sz = (int64_t)nx * ny;
+    double a = 0.0, b = 0.0, q = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x; j < V; j += (int64_t)RB * 256) {
+        const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / sz);
+        const double vj = c * v[j];
+        double r = 0.0;
+        if (nx > 1) {
+            if (ix >= 1) r += vj - c * v[j - 1];
+            if (ix < nx - 1) r -= c * v[j + 1] - vj;
+        }
+        if (ny > 1) {
+            if (iy >= 1) r += vj - c * v[j - nx];
+            if (iy < ny - 1) r -= c * v[j + nx] - vj;
+        }
+        if (nz > 1) {
+            if (iz >= 1) r += vj - c * v[j - sz];
+            if (iz < nz - 1) r -= c * v[j + sz] - vj;
+        }
+        u[j] = r;
+        a += vj * r;
+        b += vj * vj;
+        q += r * r;
+    }
+    a = block_sum_d(a, sm);
+    b = block_sum_d(b, sm);
+    q = block_sum_d(q, sm);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = a;
+        part[RB + blockIdx.x] = b;
+        part[2 * RB + blockIdx.x] = q;
+    }
+}
+
+// scal[0] = 1/||u||, scal[1] = lambda = (v.u)/(v.v)
+__global__ void __launch_bounds__(256) kn_final(const double* part, double* scal)
+{
+    __shared__ double sm[256];
+    double r[3];
+    for (int q = 0; q < 3; ++q) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < RB; i += 256) acc += part[q * RB + i];
+        r[q] = block_sum_d(acc, sm);
+    }
+    if (threadIdx.x == 0) {
+        scal[1] = r[1] > 0.0 ? r[0] / r[1] : 0.0;
+        scal[0] = r[2] > 0.0 ? 1.0 / sqrt(r[2]) : 0.0;
+    }
+}
+
+__global__ void zadd_kernel(const float* z, const float* zc, float* out, int64_t V)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = zc ? z[j] + zc[j] : z[j];
+}
+
+// ---- L2 throughput probes (measurement utility) ----
+__device__ __forceinline__ unsigned hash32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void __launch_bounds__(256) probe_kernel(float* buf, size_t n, int mode, int iters, float* sink)
+{
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    float acc = 0.0f;
+    const size_t mask = n - 1;  // n is a power of two
+    for (int it = 0; it < iters; ++it) {
+        if (mode == 0) {
+            const float4* b4 = reinterpret_cast<const float4*>(buf);
+            for (size_t i = tid; i < n / 4; i += nth) {
+                const float4 v = __ldcg(b4 + i);
+                acc += v.x + v.y + v.z + v.w;
+            }
+        } else if (mode == 1) {
+            for (size_t i = tid; i < n; i += nth) atomicAdd(buf + i, 1.0f);
+        } else if (mode == 2) {
+            for (size_t i = tid; i < n; i += nth) acc += __ldcg(buf + (hash32((unsigned)(i + it * 7919u)) & mask));
+        } else {
+            for (size_t i = tid; i < n; i += nth) atomicAdd(buf + (hash32((unsigned)(i + it * 7919u)) & mask), 1.0f);
+        }
+    }
+    if (acc == 12345.678f) *sink = acc;
+}
+
+int flat_grid(int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)lmh::num_sms() * 16));
+}
+
+}  // namespace
+
+namespace lmh {
+
+void launch_transpose_to_yf(const lm_grid* g, const float* src, float* dst, cudaStream_t st)
+{
+    transpose_to_yf_kernel<<<tile_grid(g), dim3(TD, TR), 0, st>>>(src, dst, g->n[0], g->n[1], g->n[2]);
+    count_launch();
+}
+
+void launch_add_yf_to_std(const lm_grid* g, float* img, float* yf_acc, cudaStream_t st)
+{
+    add_yf_kernel<<<tile_grid(g), dim3(TD, TR), 0, st>>>(img, yf_acc, g->n[0], g->n[1], g->n[2]);
+    count_launch();
+}
+
+void launch_fold_fixed(const lm_grid* g, float* img, unsigned long long* a_std, unsigned long long* a_yf,
+                       const unsigned* maxbits, long long count, float stepmax, cudaStream_t st)
+{
+    fold_fixed_kernel<<<tile_grid(g), dim3(TD, TR), 0, st>>>(img, a_std, a_yf, maxbits, count, stepmax, g->n[0],
+                                                             g->n[1], g->n[2]);
+    count_launch();
+}
+
+void launch_image_pass(const ImgArgs& a, cudaStream_t st)
+{
+    lm_grid g;
+    std::memset(&g, 0, sizeof(g));
+    for (int d = 0; d < 3; ++d) g.n[d] = a.n[d];
+    image_pass_kernel<<<tile_grid(&g), dim3(TD, TR), 0, st>>>(a);
+    count_launch();
+}
+
+void launch_wpar(const uint16_t* seq, int count, int n_subsets, int* wpar, int* wbase, cudaStream_t st)
+{
+    wpar_kernel<<<1, 32, 0, st>>>(seq, count, n_subsets, wpar, wbase);
+    count_launch();
+}
+
+void launch_step_T(const lm_grid* g, const float* sens, float* T, float rho, float gamma, double knorm, int n_subsets,
+                   cudaStream_t st)
+{
+    // T_k = gamma^-1 rho p_k / (P^T 1 / n) with p_k = 1/(2n): rho / (2 gamma sens)
+    // T_{n+1} = gamma^-1 p_{n+1} rho / ||K|| with p_{n+1} = 1/2
+    const double p_data = 1.0 / (2.0 * n_subsets), p_prior = 0.5;
+    const float c_data = (float)((double)rho * p_data * n_subsets / (double)gamma);
+    const float t_prior = (float)((double)rho * p_prior / ((double)gamma * knorm));
+    const int64_t V = nvox(g);
+    step_T_kernel<<<flat_grid(V), 256, 0, st>>>(sens, T, V, t_prior, c_data);
+    count_launch();
+}
+
+int reduce_minmax(const float* x, int64_t n, float* dev_scratch, float* mn, float* mx, cudaStream_t st)
+{
+    minmax_partial<<<RB, 256, 0, st>>>(x, n, dev_scratch);
+    minmax_final<<<1, 256, 0, st>>>(dev_scratch);
+    count_launch(2);
+    float h[2];
+    LM_CUDA(cudaMemcpyAsync(h, dev_scratch + 2 * RB, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaStreamSynchronize(st));
+    *mn = h[0];
+    *mx = h[1];
+    return LM_OK;
+}
+
+size_t objective_scratch_bytes() { return align_up((3 * RB + 4) * sizeof(double)); }
+
+int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* p, const float* contam,
+                    int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st)
+{
+    obj_img_partial<<<RB, 256, 0, st>>>(sens, x, g->n[0], g->n[1], g->n[2], scratch);
+    obj_ev_partial<<<RB, 256, 0, st>>>(p, contam, n_ev, scratch);
+    obj_final<<<1, 256, 0, st>>>(scratch);
+    count_launch(3);
+    LM_CUDA(cudaGetLastError());
+    double h[3];
+    LM_CUDA(cudaMemcpyAsync(h, scratch + 3 * RB, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaStreamSynchronize(st));
+    out3[0] = h[0];
+    out3[1] = h[1];
+    out3[2] = h[2];
+    (void)beta;
+    return LM_OK;
+}
+
+void launch_zadd(const lm_grid* g, const float* z, const float* zc, float* out, cudaStream_t st)
+{
+    const int64_t V = nvox(g);
+    zadd_kernel<<<flat_grid(V), 256, 0, st>>>(z, zc, out, V);
+    count_launch();
+}
+
+}  // namespace lmh
+
+using namespace lmh;
+
+extern "C" {
+
+int lm_tv_ndim(const lm_grid* grid)
+{
+    if (check_grid(grid)) return -1;
+    return tv_ndim(grid);
+}
+
+int lm_tv_grad(const lm_grid* grid, const float* x, float* g, void* stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(x && g, LM_ERR_INVALID_ARG, "x or g is NULL");
+    const int64_t V = nvox(grid);
+    tv_grad_kernel<<<flat_grid(V), 256, 0, S(stream)>>>(x, g, grid->n[0], grid->n[1], grid->n[2]);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_tv_div(const lm_grid* grid, const float* g, float* d, void* stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(g && d, LM_ERR_INVALID_ARG, "g or d is NULL");
+    const int64_t V = nvox(grid);
+    tv_div_kernel<<<flat_grid(V), 256, 0, S(stream)>>>(g, d, grid->n[0], grid->n[1], grid->n[2]);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_tv_prox(const lm_grid* grid, float* w, float beta, void* stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(w != nullptr, LM_ERR_INVALID_ARG, "w is NULL");
+    LM_CHECK(beta >= 0.0f && std::isfinite(beta), LM_ERR_INVALID_ARG, "beta must be >= 0");
+    const int64_t V = nvox(grid);
+    tv_prox_kernel<<<flat_grid(V), 256, 0, S(stream)>>>(w, V, tv_ndim(grid), beta);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_probe_l2(void* buf, size_t bytes, int32_t mode, int32_t iters, double* gbs_out, void* stream)
+{
+    clear_error();
+    LM_CHECK(buf && gbs_out && bytes >= 4096 && mode >= 0 && mode <= 3 && iters >= 1, LM_ERR_INVALID_ARG,
+             "bad probe arguments");
+    size_t n = 1024;
+    while (n * 2 * 4 <= bytes) n *= 2;  // power-of-two float count
+    cudaStream_t st = S(stream);
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, probe_kernel, 256, 0);
+    const int grid = std::max(1, bps) * num_sms();
+    float* f = (float*)buf;
+    LM_CUDA(cudaMemsetAsync(buf, 0, n * 4, st));
+    probe_kernel<<<grid, 256, 0, st>>>(f, n, mode, 1, f);  // warm L2
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0));
+    LM_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    probe_kernel<<<grid, 256, 0, st>>>(f, n, mode, iters, f);
+    cudaEventRecord(e1, st);
+    count_launch(2);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "probe failed: %s", cudaGetErrorString(ce));
+    *gbs_out = (double)n * 4.0 * iters / (ms * 1e-3) / 1e9;
+    return LM_OK;
+}
+
+size_t lm_knorm_workspace_bytes(const lm_grid* grid)
+{
+    if (check_grid(grid)) return 0;
+    const size_t V = (size_t)nvox(grid);
+    return 2 * align_up(V * 8) + align_up((3 * RB + 8) * 8);
+}
+
+int lm_knorm_fp64(const lm_grid* grid, int32_t iters, void* ws, size_t ws_bytes, double* out_host, void* stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(out_host != nullptr, LM_ERR_INVALID_ARG, "out_host is NULL");
+    LM_CHECK(iters >= 1, LM_ERR_INVALID_ARG, "iters must be >= 1");
+    const size_t need = lm_knorm_workspace_bytes(grid);
+    LM_CHECK(ws != nullptr && ws_bytes >= need, LM_ERR_NOMEM, "knorm needs %zu workspace bytes", need);
+    cudaStream_t st = S(stream);
+    const size_t V = (size_t)nvox(grid);
+    char* w = (char*)ws;
+    double* buf[2] = {(double*)w, (double*)(w + align_up(V * 8))};
+    double* part = (double*)(w + 2 * align_up(V * 8));
+    double* scal = part + 3 * RB;
+    if (tv_ndim(grid) == 0) {
+        *out_host = 0.0;
+        return LM_OK;
+    }
+    kn_init<<<flat_grid((int64_t)V), 256, 0, st>>>(buf[0], grid->n[0], grid->n[1], grid->n[2]);
+    const double one = 1.0;
+    LM_CUDA(cudaMemcpyAsync(scal, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < iters; ++k) {
+        kn_apply<<<RB, 256, 0, st>>>(buf[k & 1], buf[(k + 1) & 1], scal, grid->n[0], grid->n[1], grid->n[2], part);
+        kn_final<<<1, 256, 0, st>>>(part, scal);
+    }
+    count_launch(1 + 2 * (int64_t)iters);
+    LM_CUDA(cudaGetLastError());
+    double lam = 0.0;
+    LM_CUDA(cudaMemcpyAsync(&lam, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaStreamSynchronize(st));
+    *out_host = std::sqrt(lam);
+    return LM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lmspdhg.h"
+#include "lm_device.cuh"
+
+namespace lmh {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define LM_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            ::lmh::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return LM_ERR_CUDA;                                                                \
+        }                                                                                      \
+    } while (0)
+
+#define LM_CHECK(cond, code, ...)             \
+    do {                                      \
+        if (!(cond)) {                        \
+            ::lmh::set_error(__VA_ARGS__);    \
+            return (code);                    \
+        }                                     \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Validates the descriptors and fills the device geometry.
+int make_geo(const lm_scanner* sc, const lm_grid* g, const lm_tof* tof, lmk::Geo& G, bool need_scanner);
+int check_grid(const lm_grid* g);
+int tv_ndim(const lm_grid* g);
+inline int64_t nvox(const lm_grid* g) { return (int64_t)g->n[0] * g->n[1] * g->n[2]; }
+inline size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
+
+int num_sms();
+
+// Kernel launches issued by the library (graph replays count their nodes).
+void count_launch(int64_t n = 1);
+int64_t launch_total();
+
+// ---- event kernels (lm_project.cu) ----
+enum EvMode {
+    EV_FWD = 0,        // out[e] = corr*J(x)
+    EV_BACK = 1,       // acc += corr*v[e]*J^T          (float atomics)
+    EV_BACK_FX = 2,    // acci += round(vin[e]*J^T*2^E) (vin already includes corr)
+    EV_DATA = 3,       // fused data update (float atomics)
+    EV_DATA_FX1 = 4,   // data update forward part: y <- y+, out[e] = corr*v, max|.|
+    EV_YINIT = 5,      // y = 1 - mu/(corr*J(x)+s); acc += corr*(y-1)/mu*J^T
+    EV_YINIT_FX1 = 6,  // y init, out[e] = corr*(y-1)/mu, max|.|
+    EV_ABSMAX = 7,     // max |corr*v[e]|
+    EV_COUNT = 8       // traversal statistics: samples and neighbour touches
+};
+
+struct EvArgs {
+    lmk::Geo G;
+    const float* x_std;
+    const float* x_yf;
+    float* acc_std;
+    float* acc_yf;
+    unsigned long long* acci_std;
+    unsigned long long* acci_yf;
+    const int32_t* det1;
+    const int32_t* det2;
+    const int16_t* tof;
+    const float* corr;
+    const float* contam;
+    const uint16_t* mu;
+    float* y;
+    const float* vin;
+    float* out;
+    int64_t e_begin, e_end;
+    // selection read on the device (epoch graphs): if seq != nullptr the
+    // range is subset seq[u] and a prior selection (seq[u] == n_subsets)
+    // runs the prior's dual step instead.
+    const uint16_t* seq;
+    int u;
+    const int64_t* sub_off;
+    int n_subsets;
+    float gamma_rho;
+    unsigned* maxbits;          // float bits of max |value| (non-negative floats order as uints)
+    float stepmax;
+    unsigned long long* queue;  // dynamic chunk counter (self-resetting)
+    unsigned* done;
+    int chunk;                  // events per warp grab (1..32)
+    // prior dual step (selection == n_subsets)
+    const float* px;            // x (std)
+    const float* w_cur[2];      // indexed by wpar[u]
+    float* w_nxt[2];
+    const int* wpar;
+    float s_prior;              // S_{n+1} = gamma rho / ||K||
+    float beta;
+    int ndim;
+};
+
+int launch_events(int mode, bool two_d, const EvArgs& a, int grid, cudaStream_t st);
+int ev_grid(int mode, bool two_d);
+
+// ---- image kernels (lm_image.cu) ----
+void launch_transpose_to_yf(const lm_grid* g, const float* src, float* dst, cudaStream_t st);
+void launch_add_yf_to_std(const lm_grid* g, float* img, float* yf_acc, cudaStream_t st);
+void launch_fold_fixed(const lm_grid* g, float* img, unsigned long long* a_std, unsigned long long* a_yf,
+                       const unsigned* maxbits, long long count, float stepmax, cudaStream_t st);
+
+struct ImgArgs {
+    int n[3];
+    int ndim;
+    int V;
+    const uint16_t* seq;   // selection (device); nullptr: mode fixed by `mode`
+    int u;
+    int n_subsets;
+    int mode;              // IP_INIT / IP_UPDATE
+    // x
+    const float* x_cur;    // std
+    float* x_nxt_std;
+    float* x_nxt_yf;
+    float* x_keep;         // IP_INIT: copy of x0 (x "used by the last update")
+    // z
+    float* z;
+    float* zc;
+    int kahan;
+    const float* T;
+    const float* sens;     // IP_INIT
+    // data accumulators
+    float* acc_std;
+    float* acc_yf;
+    unsigned long long* acci_std;
+    unsigned long long* acci_yf;
+    int det;
+    const unsigned* maxbits;
+    const int64_t* sub_off;
+    float stepmax;
+    unsigned* maxbits_reset;  // cleared for the next update
+    int slot0;                // update u uses scale slot (slot0 + u) & 1
+    // prior
+    const float* w_cur[2];
+    const float* w_nxt[2];
+    const int* wpar;
+    float inv_p_data;      // 1/p_k = 2n
+    float inv_p_prior;     // 1/p_{n+1} = 2
+};
+enum { IP_INIT = 0, IP_UPDATE = 1 };
+void launch_image_pass(const ImgArgs& a, cudaStream_t st);
+void launch_wpar(const uint16_t* seq, int count, int n_subsets, int* wpar, int* wbase, cudaStream_t st);
+void launch_step_T(const lm_grid* g, const float* sens, float* T, float rho, float gamma, double knorm, int n_subsets,
+                   cudaStream_t st);
+int reduce_minmax(const float* x, int64_t n, float* dev_scratch, float* mn, float* mx, cudaStream_t st);
+void launch_zadd(const lm_grid* g, const float* z, const float* zc, float* out, cudaStream_t st);
+int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* p, const float* contam,
+                    int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st);
+size_t objective_scratch_bytes();
+
+}  // namespace lmh

@@ -1,0 +1,613 @@
+// LM-SPDHG state and iteration (Alg. 2).
+//
+// Device memory is one caller-owned buffer, carved here.  Per update u the
+// library launches two kernels (three in deterministic mode):
+//   1. the event kernel: if the selection is a data subset, the fused
+//      forward projection / dual step / back-projection of its events into
+//      the dz accumulators; if it is the prior, the dual step of w;
+//   2. the image pass: dz (accumulators, or K^T(w+ - w) for the prior) into
+//      z with compensated summation, zbar = z + dz/p_i and the next primal
+//      step x <- proj_{>=0}(x - T zbar), written in both image layouts.
+// The selection is read on the device, so a whole epoch (2n updates) is one
+// captured CUDA graph that serves every selection sequence.  x, w and the
+// fixed-point scale slots alternate between two buffers; the w parity of
+// each update is a prefix count of prior selections computed on the device.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lm_internal.h"
+
+using namespace lmh;
+
+struct lm_state_s {
+    lm_scanner sc;
+    lm_grid g;
+    lm_tof tof;
+    lmk::Geo G;
+    lm_params P;
+    int64_t N;
+    int n;
+    int ndim;
+    int64_t V;
+    bool two_d, det, kahan;
+    double gamma, knorm;
+    // caller arrays
+    const int32_t *det1, *det2;
+    const int16_t* tofb;
+    const float *corr, *contam;
+    const uint16_t* mu;
+    const float* sens;
+    std::vector<int64_t> sub_off_h;
+    // carved device memory
+    float *x[2], *xyf[2], *z, *zc, *T, *acc_std, *acc_yf, *w[2], *y, *scr;
+    unsigned long long *acci_std, *acci_yf, *queue;
+    int64_t* sub_off;
+    uint16_t* seq;
+    int* wpar;
+    int* wbase;
+    unsigned* maxbits;
+    unsigned* done;
+    float* redf;
+    double* redd;
+    size_t scr_bytes;
+    int grid_ev, grid_fx, chunk;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t exec;
+    bool have_graph;
+    int64_t graph_nodes;
+    int xpar;           // buffer holding the x the next update starts from
+    int64_t n_updates;
+};
+
+namespace {
+
+struct Carve {
+    size_t off = 0;
+    char* base = nullptr;
+    template <class T>
+    T* take(size_t bytes)
+    {
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += align_up(bytes);
+        return p;
+    }
+};
+
+void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
+{
+    const size_t V = (size_t)nvox(g);
+    const int nd = std::max(1, tv_ndim(g));
+    const bool yf = g->n[1] > 1;
+    float* dummy = nullptr;
+    (void)dummy;
+    auto F = [&](size_t cnt) { return c.take<float>(cnt * 4); };
+    float* x0 = F(V);
+    float* x1 = F(V);
+    float* y0 = yf ? F(V) : nullptr;
+    float* y1 = yf ? F(V) : nullptr;
+    float* z = F(V);
+    float* zc = F(V);
+    float* T = F(V);
+    float* w0 = F(nd * V);
+    float* w1 = F(nd * V);
+    float* acc_std = det ? nullptr : F(V);
+    float* acc_yf = (!det && yf) ? F(V) : nullptr;
+    unsigned long long* ai_std = det ? c.take<unsigned long long>(V * 8) : nullptr;
+    unsigned long long* ai_yf = (det && yf) ? c.take<unsigned long long>(V * 8) : nullptr;
+    float* y = F((size_t)std::max<int64_t>(N, 1));
+    const size_t scr_bytes = std::max<size_t>((size_t)std::max<int64_t>(N, 1) * 4,
+                                              std::max(lm_knorm_workspace_bytes(g), objective_scratch_bytes()));
+    float* scr = c.take<float>(scr_bytes);
+    int64_t* sub_off = c.take<int64_t>((size_t)(n + 1) * 8);
+    uint16_t* seq = c.take<uint16_t>((size_t)2 * n * 2 + 64);
+    int* wpar = c.take<int>((size_t)(2 * n + 2) * 4);
+    int* wbase = c.take<int>(16);
+    unsigned* maxbits = c.take<unsigned>(16);
+    unsigned long long* queue = c.take<unsigned long long>(16);
+    unsigned* done = c.take<unsigned>(16);
+    float* redf = c.take<float>((2 * 1024 + 16) * 4);
+    double* redd = c.take<double>(objective_scratch_bytes());
+    if (st) {
+        st->x[0] = x0; st->x[1] = x1; st->xyf[0] = y0; st->xyf[1] = y1;
+        st->z = z; st->zc = zc; st->T = T; st->w[0] = w0; st->w[1] = w1;
+        st->acc_std = acc_std; st->acc_yf = acc_yf; st->acci_std = ai_std; st->acci_yf = ai_yf;
+        st->y = y; st->scr = scr; st->scr_bytes = scr_bytes; st->sub_off = sub_off; st->seq = seq;
+        st->wpar = wpar; st->wbase = wbase; st->maxbits = maxbits; st->queue = queue; st->done = done;
+        st->redf = redf; st->redd = redd;
+    }
+}
+
+EvArgs base_ev_args(const lm_state* st)
+{
+    EvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.G = st->G;
+    a.det1 = st->det1;
+    a.det2 = st->det2;
+    a.tof = st->tofb;
+    a.corr = st->corr;
+    a.contam = st->contam;
+    a.mu = st->mu;
+    a.y = st->y;
+    a.sub_off = st->sub_off;
+    a.n_subsets = st->n;
+    a.gamma_rho = (float)(st->gamma * (double)st->P.rho);
+    a.stepmax = 2.0f * std::fmax(st->g.h[0], std::fmax(st->g.h[1], st->g.h[2]));
+    a.queue = st->queue;
+    a.done = st->done;
+    a.chunk = st->chunk;
+    a.w_cur[0] = st->w[0];
+    a.w_cur[1] = st->w[1];
+    a.w_nxt[0] = st->w[1];
+    a.w_nxt[1] = st->w[0];
+    a.wpar = st->wpar;
+    a.s_prior = (float)(st->gamma * (double)st->P.rho / st->knorm);
+    a.beta = st->P.beta;
+    a.ndim = st->ndim;
+    return a;
+}
+
+ImgArgs base_img_args(const lm_state* st)
+{
+    ImgArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int d = 0; d < 3; ++d) a.n[d] = st->g.n[d];
+    a.ndim = st->ndim;
+    a.V = (int)st->V;
+    a.n_subsets = st->n;
+    a.z = st->z;
+    a.zc = st->zc;
+    a.kahan = st->kahan ? 1 : 0;
+    a.T = st->T;
+    a.sens = st->sens;
+    a.acc_std = st->acc_std;
+    a.acc_yf = st->acc_yf;
+    a.acci_std = st->acci_std;
+    a.acci_yf = st->acci_yf;
+    a.det = st->det ? 1 : 0;
+    a.maxbits = st->maxbits;
+    a.maxbits_reset = st->maxbits;
+    a.sub_off = st->sub_off;
+    a.stepmax = 2.0f * std::fmax(st->g.h[0], std::fmax(st->g.h[1], st->g.h[2]));
+    a.w_cur[0] = st->w[0];
+    a.w_cur[1] = st->w[1];
+    a.w_nxt[0] = st->w[1];
+    a.w_nxt[1] = st->w[0];
+    a.wpar = st->wpar;
+    a.inv_p_data = (float)(2 * st->n);
+    a.inv_p_prior = 2.0f;
+    return a;
+}
+
+// Launches updates 0..count-1 of the selection already in st->seq; x starts
+// in buffer xpar0; the fixed-point scale slot of update u is (slot0 + u) & 1.
+// If `ev` is given (profiling), events ev[3u], ev[3u+1], ev[3u+2] are
+// recorded before the event kernel, before the image pass and after it.
+int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s, cudaEvent_t* ev = nullptr)
+{
+    launch_wpar(st->seq, count, st->n, st->wpar, st->wbase, s);
+    for (int u = 0; u < count; ++u) {
+        const int cur = (xpar0 + u) & 1, nxt = cur ^ 1;
+        const int slot = (slot0 + u) & 1;
+        if (ev) LM_CUDA(cudaEventRecord(ev[3 * u], s));
+        EvArgs a = base_ev_args(st);
+        a.seq = st->seq;
+        a.u = u;
+        a.x_std = st->x[cur];
+        a.x_yf = st->xyf[cur];
+        a.px = st->x[cur];
+        a.maxbits = st->maxbits + slot;
+        if (!st->det) {
+            a.acc_std = st->acc_std;
+            a.acc_yf = st->acc_yf;
+            int rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
+            LM_CHECK(rc == LM_OK, rc, "data update launch failed");
+        } else {
+            a.out = st->scr;
+            int rc = launch_events(EV_DATA_FX1, st->two_d, a, st->grid_ev, s);
+            LM_CHECK(rc == LM_OK, rc, "data update launch failed");
+            EvArgs b = base_ev_args(st);
+            b.seq = st->seq;
+            b.u = u;
+            b.vin = st->scr;
+            b.acci_std = st->acci_std;
+            b.acci_yf = st->acci_yf;
+            b.maxbits = st->maxbits + slot;
+            rc = launch_events(EV_BACK_FX, st->two_d, b, st->grid_fx, s);
+            LM_CHECK(rc == LM_OK, rc, "fixed-point back-projection launch failed");
+        }
+        if (ev) LM_CUDA(cudaEventRecord(ev[3 * u + 1], s));
+        ImgArgs im = base_img_args(st);
+        im.mode = IP_UPDATE;
+        im.seq = st->seq;
+        im.u = u;
+        im.x_cur = st->x[cur];
+        im.x_nxt_std = st->x[nxt];
+        im.x_nxt_yf = st->xyf[nxt];
+        // scale slots: update u reads slot (slot0 + u) & 1, its pass clears the other one
+        im.slot0 = slot0;
+        launch_image_pass(im, s);
+        if (ev) LM_CUDA(cudaEventRecord(ev[3 * u + 2], s));
+    }
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+// Alg. 2 steps 3-5 and the first primal step for the state's current events:
+// gamma, T, y = Eq. (yinit), z = P^T 1 + (P^LM)^T((y-1)/mu), w = 0, x from x0.
+int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
+{
+    const size_t V = (size_t)st->V;
+    const bool yf = st->g.n[1] > 1;
+    LM_CUDA(cudaMemsetAsync(st->zc, 0, V * 4, s));
+    LM_CUDA(cudaMemsetAsync(st->w[0], 0, (size_t)std::max(1, st->ndim) * V * 4, s));
+    LM_CUDA(cudaMemsetAsync(st->w[1], 0, (size_t)std::max(1, st->ndim) * V * 4, s));
+    if (st->acc_std) LM_CUDA(cudaMemsetAsync(st->acc_std, 0, V * 4, s));
+    if (st->acc_yf) LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, V * 4, s));
+    if (st->acci_std) LM_CUDA(cudaMemsetAsync(st->acci_std, 0, V * 8, s));
+    if (st->acci_yf) LM_CUDA(cudaMemsetAsync(st->acci_yf, 0, V * 8, s));
+    LM_CUDA(cudaMemsetAsync(st->wbase, 0, 16, s));
+    LM_CUDA(cudaMemsetAsync(st->maxbits, 0, 16, s));
+    LM_CUDA(cudaMemsetAsync(st->queue, 0, 16, s));
+    LM_CUDA(cudaMemsetAsync(st->done, 0, 16, s));
+    // x0 >= 0 and gamma = 3 / ||x0||_inf (Sec. "Numerical experiments")
+    float mn = 0.0f, mx = 0.0f;
+    int rc = reduce_minmax(x0, st->V, st->redf, &mn, &mx, s);
+    if (rc) return rc;
+    LM_CHECK(mn >= 0.0f, LM_ERR_DOMAIN, "x0 must be >= 0 (min %g)", (double)mn);
+    if (st->P.gamma > 0.0f) {
+        st->gamma = st->P.gamma;
+    } else {
+        LM_CHECK(mx > 0.0f, LM_ERR_DOMAIN, "gamma = 3/max(x0) needs max(x0) > 0");
+        st->gamma = 3.0 / (double)mx;
+    }
+    launch_step_T(&st->g, st->sens, st->T, st->P.rho, (float)st->gamma, st->knorm, st->n, s);
+    EvArgs a = base_ev_args(st);
+    a.x_std = x0;
+    if (yf) {
+        launch_transpose_to_yf(&st->g, x0, st->xyf[1], s);
+        a.x_yf = st->xyf[1];
+    }
+    a.e_begin = 0;
+    a.e_end = st->N;
+    if (st->N > 0) {
+        if (!st->det) {
+            a.acc_std = st->acc_std;
+            a.acc_yf = st->acc_yf;
+            rc = launch_events(EV_YINIT, st->two_d, a, st->grid_ev, s);
+        } else {
+            a.out = st->scr;
+            a.maxbits = st->maxbits + 1;
+            rc = launch_events(EV_YINIT_FX1, st->two_d, a, st->grid_ev, s);
+            if (!rc) {
+                EvArgs b = base_ev_args(st);
+                b.e_begin = 0;
+                b.e_end = st->N;
+                b.vin = st->scr;
+                b.acci_std = st->acci_std;
+                b.acci_yf = st->acci_yf;
+                b.maxbits = st->maxbits + 1;
+                rc = launch_events(EV_BACK_FX, st->two_d, b, st->grid_fx, s);
+            }
+        }
+        LM_CHECK(rc == LM_OK, rc, "initialisation launch failed");
+    }
+    ImgArgs im = base_img_args(st);
+    im.mode = IP_INIT;
+    im.x_cur = x0;
+    im.x_keep = st->x[1];
+    im.x_nxt_std = st->x[0];
+    im.x_nxt_yf = st->xyf[0];
+    launch_image_pass(im, s);
+    LM_CUDA(cudaGetLastError());
+    st->xpar = 0;
+    st->n_updates = 0;
+    return LM_OK;
+}
+
+int choose_chunk(const lm_state* st)
+{
+    int64_t maxsub = 0;
+    for (int k = 0; k < st->n; ++k) maxsub = std::max<int64_t>(maxsub, st->sub_off_h[k + 1] - st->sub_off_h[k]);
+    const int64_t warps = (int64_t)st->grid_ev * 8;
+    int64_t ch = maxsub / std::max<int64_t>(1, warps * 4);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(32, ch));
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets, int32_t deterministic)
+{
+    if (check_grid(grid) || n_events < 0 || n_subsets < 1) return 0;
+    Carve c;
+    carve(nullptr, c, grid, n_events, n_subsets, deterministic != 0);
+    return c.off + 256;
+}
+
+int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof,
+                   const lm_events* ev, const uint16_t* mu, const int64_t* sub_off_host, const float* sens,
+                   const float* x0, const lm_params* params, void* state_buf, size_t state_bytes, void* stream)
+{
+    clear_error();
+    LM_CHECK(out != nullptr && params != nullptr && ev != nullptr, LM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    lmk::Geo G;
+    int rc = make_geo(sc, grid, tof, G, true);
+    if (rc) return rc;
+    const lm_params& P = *params;
+    LM_CHECK(P.n_subsets >= 1 && P.n_subsets < 65535, LM_ERR_INVALID_ARG, "n_subsets out of range");
+    LM_CHECK(P.beta >= 0.0f && std::isfinite(P.beta), LM_ERR_INVALID_ARG, "beta must be >= 0");
+    LM_CHECK(P.rho > 0.0f && std::isfinite(P.rho), LM_ERR_INVALID_ARG, "rho must be > 0");
+    LM_CHECK(ev->n >= 0 && (ev->n == 0 || (ev->det1 && ev->det2 && ev->contam && mu)), LM_ERR_INVALID_ARG,
+             "events need det1, det2, contam and mu");
+    LM_CHECK(tof->n_bins == 0 || ev->n == 0 || ev->tof != nullptr, LM_ERR_INVALID_ARG, "TOF bins NULL");
+    LM_CHECK(sens && x0 && sub_off_host && state_buf, LM_ERR_INVALID_ARG, "NULL sens, x0, sub_off or state buffer");
+    LM_CHECK(sub_off_host[0] == 0 && sub_off_host[P.n_subsets] == ev->n, LM_ERR_INVALID_ARG,
+             "subset offsets must span [0, n)");
+    for (int k = 0; k < P.n_subsets; ++k)
+        LM_CHECK(sub_off_host[k + 1] >= sub_off_host[k], LM_ERR_INVALID_ARG, "subset offsets must not decrease");
+    const size_t need = lmspdhg_state_bytes(grid, ev->n, P.n_subsets, P.deterministic);
+    LM_CHECK(state_bytes >= need, LM_ERR_NOMEM, "state buffer needs %zu bytes", need);
+
+    lm_state* st = new lm_state();
+    st->sc = *sc;
+    st->g = *grid;
+    st->tof = *tof;
+    st->G = G;
+    st->P = P;
+    st->N = ev->n;
+    st->n = P.n_subsets;
+    st->ndim = tv_ndim(grid);
+    st->V = nvox(grid);
+    st->two_d = grid->n[2] == 1 && sc->n_rings == 1;
+    st->det = P.deterministic != 0;
+    st->kahan = P.kahan != 0;
+    st->det1 = ev->det1;
+    st->det2 = ev->det2;
+    st->tofb = ev->tof;
+    st->corr = ev->corr;
+    st->contam = ev->contam;
+    st->mu = mu;
+    st->sens = sens;
+    st->sub_off_h.assign(sub_off_host, sub_off_host + P.n_subsets + 1);
+    Carve c;
+    c.base = (char*)(((uintptr_t)state_buf + 255) / 256 * 256);
+    carve(st, c, grid, ev->n, st->n, st->det);
+    st->exec = nullptr;
+    st->have_graph = false;
+    st->xpar = 0;
+    st->n_updates = 0;
+    if (cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete st;
+        set_error("cudaStreamCreate failed");
+        return LM_ERR_CUDA;
+    }
+    auto fail = [&](int code) {
+        cudaStreamDestroy(st->cap_stream);
+        delete st;
+        return code;
+    };
+    cudaStream_t s = S(stream);
+#define LM_TRY(call)                                                                    \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));                         \
+            return fail(LM_ERR_CUDA);                                                   \
+        }                                                                               \
+    } while (0)
+    LM_TRY(cudaMemcpyAsync(st->sub_off, sub_off_host, (size_t)(st->n + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (P.knorm > 0.0) {
+        st->knorm = P.knorm;
+    } else if (st->ndim == 0) {
+        st->knorm = 1.0;
+    } else {
+        double kn = 0.0;
+        rc = lm_knorm_fp64(grid, P.knorm_iters > 0 ? P.knorm_iters : 1000, st->scr, st->scr_bytes, &kn, stream);
+        if (rc) return fail(rc);
+        st->knorm = kn;
+    }
+    st->grid_ev = ev_grid(st->det ? EV_DATA_FX1 : EV_DATA, st->two_d);
+    st->grid_fx = ev_grid(EV_BACK_FX, st->two_d);
+    st->chunk = choose_chunk(st);
+    rc = init_iteration(st, x0, s);
+    if (rc) return fail(rc);
+    LM_TRY(cudaStreamSynchronize(s));
+#undef LM_TRY
+    *out = st;
+    return LM_OK;
+}
+
+int lmspdhg_updates(lm_state* st, const uint16_t* seq_host, int32_t count, void* stream)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    LM_CHECK(count >= 0, LM_ERR_INVALID_ARG, "count < 0");
+    if (count == 0) return LM_OK;
+    LM_CHECK(seq_host != nullptr, LM_ERR_INVALID_ARG, "seq is NULL");
+    for (int i = 0; i < count; ++i)
+        LM_CHECK(seq_host[i] <= st->n, LM_ERR_INVALID_ARG, "selection %d out of range", (int)seq_host[i]);
+    cudaStream_t s = S(stream);
+    const int chunk = 2 * st->n;
+    for (int b = 0; b < count; b += chunk) {
+        const int m = std::min(chunk, count - b);
+        LM_CUDA(cudaMemcpyAsync(st->seq, seq_host + b, (size_t)m * 2, cudaMemcpyHostToDevice, s));
+        int rc = launch_updates(st, m, st->xpar, (int)(st->n_updates & 1), s);
+        if (rc) return rc;
+        st->xpar ^= (m & 1);
+        st->n_updates += m;
+    }
+    return LM_OK;
+}
+
+int lmspdhg_epoch(lm_state* st, const uint16_t* seq_host, void* stream)
+{
+    clear_error();
+    LM_CHECK(st != nullptr && seq_host != nullptr, LM_ERR_INVALID_ARG, "NULL argument");
+    const int count = 2 * st->n;
+    for (int i = 0; i < count; ++i)
+        LM_CHECK(seq_host[i] <= st->n, LM_ERR_INVALID_ARG, "selection %d out of range", (int)seq_host[i]);
+    if (st->xpar != 0 || (st->n_updates & 1)) return lmspdhg_updates(st, seq_host, count, stream);
+    cudaStream_t s = S(stream);
+    if (!st->have_graph) {
+        cudaGraph_t graph = nullptr;
+        LM_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t before = launch_total();
+        int rc = launch_updates(st, count, 0, 0, st->cap_stream);
+        st->graph_nodes = launch_total() - before;
+        count_launch(-st->graph_nodes);  // captured, not run
+        cudaError_t ce = cudaStreamEndCapture(st->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&st->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+        st->have_graph = true;
+    }
+    LM_CUDA(cudaMemcpyAsync(st->seq, seq_host, (size_t)count * 2, cudaMemcpyHostToDevice, s));
+    LM_CUDA(cudaGraphLaunch(st->exec, s));
+    count_launch(st->graph_nodes);
+    st->n_updates += count;
+    return LM_OK;
+}
+
+int lmspdhg_reinit(lm_state* st, const float* x0, void* stream)
+{
+    clear_error();
+    LM_CHECK(st != nullptr && x0 != nullptr, LM_ERR_INVALID_ARG, "NULL argument");
+    return init_iteration(st, x0, S(stream));
+}
+
+int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, double* ms4, int64_t* n4,
+                    void* stream)
+{
+    clear_error();
+    LM_CHECK(st && seq_host && ms4 && n4, LM_ERR_INVALID_ARG, "NULL argument");
+    LM_CHECK(count >= 1 && count <= 2 * st->n, LM_ERR_INVALID_ARG, "count must be in [1, 2n]");
+    for (int i = 0; i < count; ++i)
+        LM_CHECK(seq_host[i] <= st->n, LM_ERR_INVALID_ARG, "selection %d out of range", (int)seq_host[i]);
+    cudaStream_t s = S(stream);
+    std::vector<cudaEvent_t> ev((size_t)3 * count);
+    for (auto& e : ev) LM_CUDA(cudaEventCreate(&e));
+    LM_CUDA(cudaMemcpyAsync(st->seq, seq_host, (size_t)count * 2, cudaMemcpyHostToDevice, s));
+    int rc = launch_updates(st, count, st->xpar, (int)(st->n_updates & 1), s, ev.data());
+    if (rc == LM_OK) {
+        st->xpar ^= (count & 1);
+        st->n_updates += count;
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = LM_ERR_CUDA;
+    }
+    for (int k = 0; k < 4; ++k) {
+        ms4[k] = 0.0;
+        n4[k] = 0;
+    }
+    if (rc == LM_OK) {
+        for (int u = 0; u < count; ++u) {
+            const int prior = seq_host[u] >= st->n;
+            float t1 = 0.0f, t2 = 0.0f;
+            cudaEventElapsedTime(&t1, ev[3 * u], ev[3 * u + 1]);
+            cudaEventElapsedTime(&t2, ev[3 * u + 1], ev[3 * u + 2]);
+            ms4[prior] += t1;
+            n4[prior] += 1;
+            ms4[2 + prior] += t2;
+            n4[2 + prior] += 1;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc == LM_ERR_CUDA) set_error("profiling run failed");
+    return rc;
+}
+
+int lmspdhg_get_x(lm_state* st, float* x_out, void* stream)
+{
+    clear_error();
+    LM_CHECK(st && x_out, LM_ERR_INVALID_ARG, "NULL argument");
+    LM_CUDA(cudaMemcpyAsync(x_out, st->x[st->xpar ^ 1], (size_t)st->V * 4, cudaMemcpyDeviceToDevice, S(stream)));
+    return LM_OK;
+}
+
+int lmspdhg_get_y(lm_state* st, float* y_out, void* stream)
+{
+    clear_error();
+    LM_CHECK(st && y_out, LM_ERR_INVALID_ARG, "NULL argument");
+    if (st->N == 0) return LM_OK;
+    LM_CUDA(cudaMemcpyAsync(y_out, st->y, (size_t)st->N * 4, cudaMemcpyDeviceToDevice, S(stream)));
+    return LM_OK;
+}
+
+int lmspdhg_get_z(lm_state* st, float* z_out, void* stream)
+{
+    clear_error();
+    LM_CHECK(st && z_out, LM_ERR_INVALID_ARG, "NULL argument");
+    launch_zadd(&st->g, st->z, st->kahan ? st->zc : nullptr, z_out, S(stream));
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int lmspdhg_get_w(lm_state* st, float* w_out, void* stream)
+{
+    clear_error();
+    LM_CHECK(st && w_out, LM_ERR_INVALID_ARG, "NULL argument");
+    if (st->ndim == 0) return LM_OK;
+    // the current w buffer is given by the device-side parity base
+    int wb = 0;
+    LM_CUDA(cudaMemcpyAsync(&wb, st->wbase, 4, cudaMemcpyDeviceToHost, S(stream)));
+    LM_CUDA(cudaStreamSynchronize(S(stream)));
+    LM_CUDA(cudaMemcpyAsync(w_out, st->w[wb & 1], (size_t)st->ndim * st->V * 4, cudaMemcpyDeviceToDevice,
+                            S(stream)));
+    return LM_OK;
+}
+
+int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
+{
+    clear_error();
+    LM_CHECK(st && out_host, LM_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    const int xb = st->xpar ^ 1;
+    float* p = st->scr;
+    if (st->N > 0) {
+        EvArgs a = base_ev_args(st);
+        a.x_std = st->x[xb];
+        a.x_yf = st->xyf[xb];
+        a.out = p;
+        a.e_begin = 0;
+        a.e_end = st->N;
+        a.queue = nullptr;
+        a.done = nullptr;
+        a.chunk = 32;
+        int rc = launch_events(EV_FWD, st->two_d, a, ev_grid(EV_FWD, st->two_d), s);
+        LM_CHECK(rc == LM_OK, rc, "objective projection failed");
+    }
+    double parts[3];
+    int rc = objective_parts(&st->g, st->sens, st->x[xb], p, st->contam, st->N, st->P.beta, st->redd, parts, s);
+    if (rc) return rc;
+    *out_host = parts[0] - parts[2] + (double)st->P.beta * parts[1];
+    return LM_OK;
+}
+
+int lmspdhg_info(lm_state* st, int64_t* n_updates, double* gamma, double* knorm)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    if (n_updates) *n_updates = st->n_updates;
+    if (gamma) *gamma = st->gamma;
+    if (knorm) *knorm = st->knorm;
+    return LM_OK;
+}
+
+int lmspdhg_destroy(lm_state* st)
+{
+    clear_error();
+    if (!st) return LM_OK;
+    if (st->exec) cudaGraphExecDestroy(st->exec);
+    cudaStreamDestroy(st->cap_stream);
+    delete st;
+    return LM_OK;
+}
+
+}  // extern "C"

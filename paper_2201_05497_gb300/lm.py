@@ -1,0 +1,414 @@
+"""Python binding of liblmspdhg.so (the C ABI in include/lmspdhg.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (used for memory and streams);
+calls run on torch's current CUDA stream unless a stream is given.  There is
+no CPU fallback: importing this module without the built library, or calling
+it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblmspdhg.so")
+
+LM_OK = 0
+ERRORS = {1: "LM_ERR_INVALID_ARG", 2: "LM_ERR_OUT_OF_RANGE", 3: "LM_ERR_DOMAIN", 4: "LM_ERR_CUDA",
+          5: "LM_ERR_TIMEOUT", 6: "LM_ERR_NOMEM"}
+
+
+class LMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lm_scanner(C.Structure):
+    _fields_ = [("n_rings", C.c_int32), ("n_xtal", C.c_int32), ("xtal_xyz", C.c_void_p)]
+
+
+class lm_grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("h", C.c_float * 3), ("origin", C.c_float * 3)]
+
+
+class lm_tof(C.Structure):
+    _fields_ = [("sigma_mm", C.c_float), ("bin_mm", C.c_float), ("n_sigma", C.c_float), ("n_bins", C.c_int32)]
+
+
+class lm_events(C.Structure):
+    _fields_ = [("det1", C.c_void_p), ("det2", C.c_void_p), ("tof", C.c_void_p), ("corr", C.c_void_p),
+                ("contam", C.c_void_p), ("n", C.c_int64)]
+
+
+class lm_params(C.Structure):
+    _fields_ = [("beta", C.c_float), ("gamma", C.c_float), ("rho", C.c_float), ("knorm", C.c_double),
+                ("knorm_iters", C.c_int32), ("n_subsets", C.c_int32), ("deterministic", C.c_int32),
+                ("kahan", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load liblmspdhg.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with `python -m paper_2201_05497_gb300.build`")
+    L = C.CDLL(path)
+    P, V, I32, I64, F, D, SZ = C.POINTER, C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_size_t
+    sig = {
+        "lm_last_error": ([], C.c_char_p),
+        "lm_version": ([], C.c_int),
+        "lm_fwd_workspace_bytes": ([P(lm_grid)], SZ),
+        "lm_fwd": ([P(lm_scanner), P(lm_grid), P(lm_tof), V, P(lm_events), V, V, SZ, V], C.c_int),
+        "lm_back_workspace_bytes": ([P(lm_grid), C.c_int], SZ),
+        "lm_back": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, V, C.c_int, V, SZ, V], C.c_int),
+        "lm_n_lor": ([P(lm_scanner)], I64),
+        "lm_sens_workspace_bytes": ([P(lm_grid)], SZ),
+        "lm_sens": ([P(lm_scanner), P(lm_grid), P(lm_tof), V, V, V, SZ, V], C.c_int),
+        "lm_tv_ndim": ([P(lm_grid)], C.c_int),
+        "lm_tv_grad": ([P(lm_grid), V, V, V], C.c_int),
+        "lm_tv_div": ([P(lm_grid), V, V, V], C.c_int),
+        "lm_tv_prox": ([P(lm_grid), V, F, V], C.c_int),
+        "lm_knorm_workspace_bytes": ([P(lm_grid)], SZ),
+        "lm_knorm_fp64": ([P(lm_grid), I32, V, SZ, P(D), V], C.c_int),
+        "lm_setup_workspace_bytes": ([I64], SZ),
+        "lm_event_setup": ([P(lm_scanner), P(lm_tof), P(lm_events), I32, V, V, V, V, V, V, P(I64), V, SZ, V],
+                           C.c_int),
+        "lmspdhg_state_bytes": ([P(lm_grid), I64, I32, I32], SZ),
+        "lmspdhg_create": ([P(V), P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, P(I64), V, V,
+                            P(lm_params), V, SZ, V], C.c_int),
+        "lmspdhg_updates": ([V, P(C.c_uint16), I32, V], C.c_int),
+        "lmspdhg_epoch": ([V, P(C.c_uint16), V], C.c_int),
+        "lmspdhg_get_x": ([V, V, V], C.c_int),
+        "lmspdhg_get_y": ([V, V, V], C.c_int),
+        "lmspdhg_get_z": ([V, V, V], C.c_int),
+        "lmspdhg_get_w": ([V, V, V], C.c_int),
+        "lmspdhg_objective_fp64": ([V, P(D), V], C.c_int),
+        "lmspdhg_info": ([V, P(I64), P(D), P(D)], C.c_int),
+        "lmspdhg_destroy": ([V], C.c_int),
+        "lmspdhg_reinit": ([V, V, V], C.c_int),
+        "lmspdhg_profile": ([V, P(C.c_uint16), I32, P(D), P(I64), V], C.c_int),
+        "lm_kernel_launches": ([], I64),
+        "lm_traversal_stats": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, SZ, P(I64), P(I64), V],
+                               C.c_int),
+        "lm_probe_l2": ([V, SZ, I32, I32, P(D), V], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != LM_OK:
+        raise LMError(rc, load_library().lm_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# descriptors
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Geometry:
+    """Scanner (crystal table on the device), image grid and TOF kernel."""
+    xtal: torch.Tensor          # float32 [n_det, 3] on the device
+    n_rings: int
+    n_xtal: int
+    n: Sequence[int]
+    h: Sequence[float]
+    origin: Sequence[float]
+    tof_sigma: float = 1.0
+    tof_bin: float = 1.0
+    tof_nsigma: float = 3.0
+    tof_nbins: int = 0
+
+    def __post_init__(self):
+        self.sc = lm_scanner(self.n_rings, self.n_xtal, C.c_void_p(self.xtal.data_ptr()))
+        self.g = lm_grid((C.c_int32 * 3)(*[int(v) for v in self.n]), (C.c_float * 3)(*self.h),
+                         (C.c_float * 3)(*self.origin))
+        self.tof = lm_tof(self.tof_sigma, self.tof_bin, self.tof_nsigma, self.tof_nbins)
+
+    @classmethod
+    def from_workload(cls, wl, device="cuda"):
+        sc, g, t = wl.scanner, wl.grid, wl.tof
+        xtal = torch.from_numpy(sc.crystal_table()).to(device)
+        return cls(xtal, sc.n_rings, sc.n_xtal, g.n, g.h, g.origin, t.sigma, t.bin, t.n_sigma, t.n_bins)
+
+    @property
+    def V(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+    @property
+    def ndim(self) -> int:
+        return int(load_library().lm_tv_ndim(C.byref(self.g)))
+
+    @property
+    def n_lor(self) -> int:
+        return int(load_library().lm_n_lor(C.byref(self.sc)))
+
+
+@dataclasses.dataclass
+class DeviceEvents:
+    det1: torch.Tensor
+    det2: torch.Tensor
+    tof: Optional[torch.Tensor]
+    corr: Optional[torch.Tensor]
+    contam: Optional[torch.Tensor]
+
+    @property
+    def n(self) -> int:
+        return int(self.det1.shape[0])
+
+    def desc(self) -> lm_events:
+        return lm_events(_ptr(self.det1), _ptr(self.det2), _ptr(self.tof), _ptr(self.corr), _ptr(self.contam),
+                         self.n)
+
+    @classmethod
+    def from_numpy(cls, ev, device="cuda"):
+        t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return cls(t(ev.det1), t(ev.det2), t(ev.tof), t(ev.corr), t(ev.contam))
+
+
+def _ws(nbytes: int, device) -> Optional[torch.Tensor]:
+    if nbytes <= 0:
+        return None
+    return torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+
+
+# --------------------------------------------------------------------------
+# operators
+# --------------------------------------------------------------------------
+def fwd(geo: Geometry, x: torch.Tensor, ev: DeviceEvents, out: Optional[torch.Tensor] = None,
+        use_workspace: bool = True, stream=None) -> torch.Tensor:
+    """(P^LM x)_e (Eq. lmop)."""
+    L = load_library()
+    if out is None:
+        out = torch.empty(ev.n, dtype=torch.float32, device=x.device)
+    ws = _ws(L.lm_fwd_workspace_bytes(C.byref(geo.g)), x.device) if use_workspace else None
+    d = ev.desc()
+    _check(L.lm_fwd(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _ptr(x), C.byref(d), _ptr(out),
+                    _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream)))
+    return out
+
+
+def back(geo: Geometry, v: torch.Tensor, ev: DeviceEvents, img: Optional[torch.Tensor] = None,
+         deterministic: bool = False, use_workspace: bool = True, stream=None) -> torch.Tensor:
+    """img += (P^LM)^T v."""
+    L = load_library()
+    if img is None:
+        img = torch.zeros(geo.V, dtype=torch.float32, device=v.device)
+    nb = L.lm_back_workspace_bytes(C.byref(geo.g), int(deterministic))
+    ws = _ws(nb, v.device) if (use_workspace or deterministic) else None
+    d = ev.desc()
+    _check(L.lm_back(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d), _ptr(v), _ptr(img),
+                     int(deterministic), _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream)))
+    return img
+
+
+def sens(geo: Geometry, lor_factor: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+         use_workspace: bool = True, stream=None) -> torch.Tensor:
+    """P^T 1 over every canonical LOR and TOF bin."""
+    L = load_library()
+    dev = geo.xtal.device
+    if out is None:
+        out = torch.empty(geo.V, dtype=torch.float32, device=dev)
+    ws = _ws(L.lm_sens_workspace_bytes(C.byref(geo.g)), dev) if use_workspace else None
+    _check(L.lm_sens(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _ptr(lor_factor), _ptr(out), _ptr(ws),
+                     0 if ws is None else ws.numel(), _stream(stream)))
+    return out
+
+
+def tv_grad(geo: Geometry, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    L = load_library()
+    if out is None:
+        out = torch.empty(geo.ndim * geo.V, dtype=torch.float32, device=x.device)
+    _check(L.lm_tv_grad(C.byref(geo.g), _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def tv_div(geo: Geometry, g: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    L = load_library()
+    if out is None:
+        out = torch.empty(geo.V, dtype=torch.float32, device=g.device)
+    _check(L.lm_tv_div(C.byref(geo.g), _ptr(g), _ptr(out), _stream(stream)))
+    return out
+
+
+def tv_prox(geo: Geometry, w: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
+    L = load_library()
+    _check(L.lm_tv_prox(C.byref(geo.g), _ptr(w), float(beta), _stream(stream)))
+    return w
+
+
+def knorm_fp64(geo: Geometry, iters: int, stream=None) -> float:
+    L = load_library()
+    ws = _ws(L.lm_knorm_workspace_bytes(C.byref(geo.g)), geo.xtal.device)
+    out = C.c_double()
+    _check(L.lm_knorm_fp64(C.byref(geo.g), int(iters), _ptr(ws), ws.numel(), C.byref(out), _stream(stream)))
+    return float(out.value)
+
+
+def kernel_launches() -> int:
+    return int(load_library().lm_kernel_launches())
+
+
+def traversal_stats(geo: Geometry, ev: DeviceEvents, stream=None):
+    """(samples, neighbour touches) of the events' traversals."""
+    L = load_library()
+    ws = torch.empty(16, dtype=torch.uint8, device=ev.det1.device)
+    ns, nt = C.c_int64(), C.c_int64()
+    d = ev.desc()
+    _check(L.lm_traversal_stats(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d), _ptr(ws), 16,
+                                C.byref(ns), C.byref(nt), _stream(stream)))
+    return ns.value, nt.value
+
+
+def probe_l2(nbytes: int, mode: int, iters: int = 20, device="cuda", stream=None) -> float:
+    """L2 throughput (GB/s) of the library's probe kernel on a buffer of nbytes."""
+    buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+    out = C.c_double()
+    _check(load_library().lm_probe_l2(_ptr(buf), buf.numel(), int(mode), int(iters), C.byref(out), _stream(stream)))
+    return float(out.value)
+
+
+@dataclasses.dataclass
+class PermutedEvents:
+    events: DeviceEvents        # subset-contiguous order
+    mu: torch.Tensor            # uint16 event counts (same order)
+    sub_off: np.ndarray         # int64 [n_subsets + 1]
+
+
+def event_setup(geo: Geometry, ev: DeviceEvents, n_subsets: int, stream=None) -> PermutedEvents:
+    """Validation, event counts mu and the subset-contiguous split."""
+    L = load_library()
+    dev = ev.det1.device
+    n = ev.n
+    out = DeviceEvents(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+                       torch.empty(n, dtype=torch.int16, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
+                       torch.empty(n, dtype=torch.float32, device=dev))
+    mu = torch.empty(n, dtype=torch.uint16, device=dev)
+    off = np.zeros(n_subsets + 1, dtype=np.int64)
+    ws = _ws(L.lm_setup_workspace_bytes(n), dev)
+    d = ev.desc()
+    _check(L.lm_event_setup(C.byref(geo.sc), C.byref(geo.tof), C.byref(d), int(n_subsets), _ptr(out.det1),
+                            _ptr(out.det2), _ptr(out.tof), _ptr(out.corr), _ptr(out.contam), _ptr(mu),
+                            off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(ws), ws.numel(), _stream(stream)))
+    return PermutedEvents(out, mu, off)
+
+
+class LMSPDHG:
+    """Alg. 2 on the device.  Holds the state buffer and the library handle."""
+
+    def __init__(self, geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x0: torch.Tensor, *,
+                 beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
+                 knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, stream=None):
+        L = load_library()
+        self.geo, self.pe, self.sens = geo, pe, sens_img
+        self.n_subsets = n_subsets
+        nbytes = L.lmspdhg_state_bytes(C.byref(geo.g), pe.events.n, int(n_subsets), int(deterministic))
+        if nbytes == 0:
+            raise LMError(1, "invalid state size")
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=x0.device)
+        self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan))
+        self._ev = pe.events.desc()
+        self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
+        h = C.c_void_p()
+        _check(L.lmspdhg_create(C.byref(h), C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(self._ev),
+                                _ptr(pe.mu), self._off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(sens_img),
+                                _ptr(x0), C.byref(self.params), _ptr(self.buf), self.buf.numel(), _stream(stream)))
+        self.h = h
+
+    def _seq(self, seq):
+        a = np.ascontiguousarray(np.asarray(seq, dtype=np.uint16))
+        return a, a.ctypes.data_as(C.POINTER(C.c_uint16))
+
+    def updates(self, seq, stream=None):
+        a, p = self._seq(seq)
+        _check(load_library().lmspdhg_updates(self.h, p, int(a.shape[0]), _stream(stream)))
+
+    def epoch(self, seq, stream=None):
+        a, p = self._seq(seq)
+        if a.shape[0] != 2 * self.n_subsets:
+            raise ValueError("an epoch is 2n updates")
+        _check(load_library().lmspdhg_epoch(self.h, p, _stream(stream)))
+
+    def x(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.geo.V, dtype=torch.float32, device=self.buf.device)
+        _check(load_library().lmspdhg_get_x(self.h, _ptr(out), _stream(stream)))
+        return out
+
+    def y(self, stream=None) -> torch.Tensor:
+        out = torch.empty(max(1, self.pe.events.n), dtype=torch.float32, device=self.buf.device)
+        _check(load_library().lmspdhg_get_y(self.h, _ptr(out), _stream(stream)))
+        return out[:self.pe.events.n]
+
+    def z(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.geo.V, dtype=torch.float32, device=self.buf.device)
+        _check(load_library().lmspdhg_get_z(self.h, _ptr(out), _stream(stream)))
+        return out
+
+    def w(self, stream=None) -> torch.Tensor:
+        out = torch.empty(max(1, self.geo.ndim) * self.geo.V, dtype=torch.float32, device=self.buf.device)
+        _check(load_library().lmspdhg_get_w(self.h, _ptr(out), _stream(stream)))
+        return out
+
+    def reinit(self, x0: torch.Tensor, stream=None):
+        _check(load_library().lmspdhg_reinit(self.h, _ptr(x0), _stream(stream)))
+
+    def profile(self, seq, stream=None):
+        """Per-kernel timing of `seq` (direct launches with CUDA events)."""
+        a, p = self._seq(seq)
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        _check(load_library().lmspdhg_profile(self.h, p, int(a.shape[0]), ms, n, _stream(stream)))
+        keys = ["data_events", "prior_dual", "image_after_data", "image_after_prior"]
+        return {k: (ms[i], n[i]) for i, k in enumerate(keys)}
+
+    def objective(self, stream=None) -> float:
+        v = C.c_double()
+        _check(load_library().lmspdhg_objective_fp64(self.h, C.byref(v), _stream(stream)))
+        return float(v.value)
+
+    def info(self):
+        n = C.c_int64()
+        g = C.c_double()
+        k = C.c_double()
+        _check(load_library().lmspdhg_info(self.h, C.byref(n), C.byref(g), C.byref(k)))
+        return dict(n_updates=n.value, gamma=g.value, knorm=k.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().lmspdhg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -451,6 +451,190 @@ def monte_carlo_events(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, seed: 
                   np.full(n_events, s_flat, dtype=np.float32))
 
 
+def monte_carlo_events_torch(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, seed: int,
+                             contamination: float = 0.2, lor_att=None, device="cuda", batch: int = 1 << 24):
+    """The Monte Carlo of `monte_carlo_events`, run with torch on `device`
+    (for the large workloads: the 3D rejection rate is ~98%, which makes
+    the numpy version slow).  Same physics and conventions; a different
+    random stream, so the lists differ from the numpy version's.  Returns
+    an Events of torch tensors on `device`.  lor_att: torch float32 [n_lor]
+    on `device` or None."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = torch.float64
+    is2d = sc.n_rings == 1
+    tab = torch.from_numpy(sc.crystal_table().astype(np.float64)).to(device)
+    zr = sc.ring_z()
+    zlo = float(zr[0] - 0.5 * sc.ring_pitch)
+    zhi = float(zr[-1] + 0.5 * sc.ring_pitch)
+    n_true = int(round((1.0 - contamination) * n_events))
+    n_rand = n_events - n_true
+    M = tof.half if tof.n_bins > 0 else 0
+    bx, by, bz = ph.body_axes
+    amax = max([1.0] + [a for (_, _, a) in ph.inner])
+    A, B = ph.att_axes
+
+    def U(m, lo=0.0, hi=1.0):
+        return torch.rand(m, generator=g, device=device, dtype=f64) * (hi - lo) + lo
+
+    def activity(p):
+        r = (p[:, 0] / bx) ** 2 + (p[:, 1] / by) ** 2
+        if not is2d:
+            r = r + (p[:, 2] / bz) ** 2
+        act = torch.where(r <= 1.0, 1.0, 0.0).to(f64)
+        for (c, ax, a) in ph.inner:
+            ri = ((p[:, 0] - c[0]) / ax[0]) ** 2 + ((p[:, 1] - c[1]) / ax[1]) ** 2
+            if not is2d:
+                ri = ri + ((p[:, 2] - c[2]) / ax[2]) ** 2
+            act = torch.where((ri <= 1.0) & (r <= 1.0), torch.full_like(act, a), act)
+        return act
+
+    def chord_param(a, d):
+        al = (d[:, 0] / A) ** 2 + (d[:, 1] / B) ** 2
+        be = 2.0 * (a[:, 0] * d[:, 0] / A ** 2 + a[:, 1] * d[:, 1] / B ** 2)
+        ga = (a[:, 0] / A) ** 2 + (a[:, 1] / B) ** 2 - 1.0
+        disc = be * be - 4.0 * al * ga
+        ok = (disc > 0) & (al > 0)
+        return torch.where(ok, torch.sqrt(torch.clamp(disc, min=0.0)) / torch.where(al > 0, al, torch.ones_like(al)),
+                           torch.zeros_like(al))
+
+    def det_of(hp):
+        ang = torch.remainder(torch.atan2(hp[:, 1], hp[:, 0]), 2.0 * np.pi)
+        c = torch.remainder(torch.round(ang * sc.n_xtal / (2.0 * np.pi)).long(), sc.n_xtal)
+        if is2d:
+            r = torch.zeros_like(c)
+        else:
+            r = torch.clamp(torch.floor((hp[:, 2] - zlo) / sc.ring_pitch).long(), 0, sc.n_rings - 1)
+        return r * sc.n_xtal + c
+
+    d1s, d2s, tbs = [], [], []
+    got = 0
+    while got < n_true:
+        m = batch
+        p = torch.stack([U(m, -bx, bx), U(m, -by, by), torch.zeros(m, device=device, dtype=f64) if is2d
+                         else U(m, -bz, bz)], dim=1)
+        keep = U(m, 0.0, amax) < activity(p)
+        if is2d:
+            phi = U(m, 0.0, np.pi)
+            u = torch.stack([torch.cos(phi), torch.sin(phi), torch.zeros_like(phi)], dim=1)
+        else:
+            cz = U(m, -1.0, 1.0)
+            phi = U(m, 0.0, 2.0 * np.pi)
+            st = torch.sqrt(1.0 - cz * cz)
+            u = torch.stack([st * torch.cos(phi), st * torch.sin(phi), cz], dim=1)
+        uu = u[:, 0] ** 2 + u[:, 1] ** 2
+        pu = p[:, 0] * u[:, 0] + p[:, 1] * u[:, 1]
+        pp = p[:, 0] ** 2 + p[:, 1] ** 2
+        disc = pu * pu - uu * (pp - sc.radius ** 2)
+        keep &= (uu > 1e-12) & (disc > 0)
+        sq = torch.sqrt(torch.clamp(disc, min=0.0))
+        den = torch.where(uu > 0, uu, torch.ones_like(uu))
+        h_lo = p + ((-pu - sq) / den)[:, None] * u
+        h_hi = p + ((-pu + sq) / den)[:, None] * u
+        if not is2d:
+            keep &= (h_lo[:, 2] >= zlo) & (h_lo[:, 2] < zhi) & (h_hi[:, 2] >= zlo) & (h_hi[:, 2] < zhi)
+        keep &= U(m) < torch.exp(-ph.mu_att * chord_param(p, u) * torch.sqrt((u * u).sum(1)))
+        p, h_lo, h_hi = p[keep], h_lo[keep], h_hi[keep]
+        da, db = det_of(h_lo), det_of(h_hi)
+        ok = torch.remainder(da, sc.n_xtal) != torch.remainder(db, sc.n_xtal)
+        da, db, p = da[ok], db[ok], p[ok]
+        Aa, Bb = tab[da], tab[db]
+        dd = Bb - Aa
+        Ld = torch.sqrt((dd * dd).sum(1))
+        t_true = ((p - 0.5 * (Aa + Bb)) * dd).sum(1) / Ld
+        if tof.n_bins > 0:
+            noise = torch.randn(t_true.shape[0], generator=g, device=device, dtype=f64) * tof.sigma
+            tb = torch.clamp(torch.round((t_true + noise) / tof.bin), -M, M).long()
+        else:
+            tb = torch.zeros_like(da)
+        d1s.append(da)
+        d2s.append(db)
+        tbs.append(tb)
+        got += int(da.shape[0])
+    det1 = torch.cat(d1s)[:n_true]
+    det2 = torch.cat(d2s)[:n_true]
+    tb = torch.cat(tbs)[:n_true]
+    q = torch.randint(0, sc.n_pairs, (n_rand,), generator=g, device=device)
+    base = sc.n_xtal * ((sc.n_xtal - 1) // 2)
+    c1 = torch.where(q < base, torch.remainder(q, sc.n_xtal), q - base)
+    off = torch.where(q < base, 1 + torch.div(q, sc.n_xtal, rounding_mode="floor"),
+                      torch.full_like(q, sc.n_xtal // 2))
+    c2 = torch.remainder(c1 + off, sc.n_xtal)
+    r1 = torch.randint(0, sc.n_rings, (n_rand,), generator=g, device=device)
+    r2 = torch.randint(0, sc.n_rings, (n_rand,), generator=g, device=device)
+    rtb = (torch.randint(-M, M + 1, (n_rand,), generator=g, device=device) if tof.n_bins > 0
+           else torch.zeros(n_rand, dtype=torch.long, device=device))
+    det1 = torch.cat([det1, r1 * sc.n_xtal + c1])
+    det2 = torch.cat([det2, r2 * sc.n_xtal + c2])
+    tb = torch.cat([tb, rtb])
+    sw = U(n_events) < 0.5
+    det1, det2 = torch.where(sw, det2, det1), torch.where(sw, det1, det2)
+    tb = torch.where(sw, -tb, tb)
+    perm = torch.randperm(n_events, generator=g, device=device)
+    det1, det2, tb = det1[perm], det2[perm], tb[perm]
+    n_bins_eff = max(tof.n_bins, 1)
+    s_flat = float(np.float32(n_rand / (sc.n_lor * n_bins_eff))) if n_rand > 0 else 1e-3
+    if lor_att is None:
+        corr = torch.ones(n_events, dtype=torch.float32, device=device)
+    else:
+        corr = lor_att[lor_of_events_torch(sc, det1, det2)].to(torch.float32)
+    return Events(det1.to(torch.int32), det2.to(torch.int32), tb.to(torch.int16), corr,
+                  torch.full((n_events,), s_flat, dtype=torch.float32, device=device))
+
+
+def lor_of_events_torch(sc: Scanner, det1, det2):
+    """Canonical LOR index of events (torch tensors), as lor_of_events."""
+    import torch
+    n = sc.n_xtal
+    d1 = det1.long()
+    d2 = det2.long()
+    r1, c1 = torch.div(d1, n, rounding_mode="floor"), torch.remainder(d1, n)
+    r2, c2 = torch.div(d2, n, rounding_mode="floor"), torch.remainder(d2, n)
+    off = torch.remainder(c2 - c1, n)
+    half = (n - 1) // 2
+    base = n * half
+    direct = (off >= 1) & (off <= half)
+    even_mid = (off == n // 2) & (n % 2 == 0)
+    q = torch.where(direct, (off - 1) * n + c1, (n - off - 1) * n + c2)
+    q = torch.where(even_mid, base + torch.minimum(c1, c2), q)
+    sw = torch.where(even_mid, c1 > c2, ~direct)
+    ra = torch.where(sw, r2, r1)
+    rb = torch.where(sw, r1, r2)
+    return (q * sc.n_rings + ra) * sc.n_rings + rb
+
+
+def lor_attenuation_torch(sc: Scanner, ph: Phantom, device="cuda"):
+    """lor_attenuation computed with torch on `device` (float32 [n_lor])."""
+    import torch
+    tab = torch.from_numpy(sc.crystal_table().astype(np.float64)).to(device)
+    n = sc.n_xtal
+    q = torch.arange(sc.n_pairs, device=device)
+    base = n * ((n - 1) // 2)
+    c1 = torch.where(q < base, torch.remainder(q, n), q - base)
+    off = torch.where(q < base, 1 + torch.div(q, n, rounding_mode="floor"), torch.full_like(q, n // 2))
+    c2 = torch.remainder(c1 + off, n)
+    a, b = tab[c1], tab[c2]
+    d = b - a
+    A, B = ph.att_axes
+    al = (d[:, 0] / A) ** 2 + (d[:, 1] / B) ** 2
+    be = 2.0 * (a[:, 0] * d[:, 0] / A ** 2 + a[:, 1] * d[:, 1] / B ** 2)
+    ga = (a[:, 0] / A) ** 2 + (a[:, 1] / B) ** 2 - 1.0
+    disc = be * be - 4.0 * al * ga
+    dt = torch.where((disc > 0) & (al > 0), torch.sqrt(torch.clamp(disc, min=0.0)) / al, torch.zeros_like(al))
+    lxy = torch.sqrt(d[:, 0] ** 2 + d[:, 1] ** 2)
+    z = torch.from_numpy(sc.ring_z()).to(device)
+    dz = (z[None, :] - z[:, None]).reshape(-1)
+    out = torch.empty(sc.n_lor, dtype=torch.float32, device=device)
+    nr2 = sc.n_rings * sc.n_rings
+    step = max(1, (1 << 24) // nr2)
+    for s in range(0, sc.n_pairs, step):
+        e = min(sc.n_pairs, s + step)
+        L3 = torch.sqrt(lxy[s:e, None] ** 2 + dz[None, :] ** 2)
+        out[s * nr2:e * nr2] = torch.exp(-ph.mu_att * dt[s:e, None] * L3).reshape(-1).to(torch.float32)
+    return out
+
+
 def uniform_events(sc: Scanner, tof: Tof, n_events: int, seed: int) -> Events:
     """Events uniform over (LOR, TOF bin), for operator tests."""
     rng = np.random.default_rng(seed)
