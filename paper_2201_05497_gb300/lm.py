@@ -304,17 +304,28 @@ class PermutedEvents:
     sub_off: np.ndarray         # int64 [n_subsets + 1]
 
 
-def event_setup(geo: Geometry, ev: DeviceEvents, n_subsets: int, stream=None) -> PermutedEvents:
-    """Validation, event counts mu and the subset-contiguous split."""
+def event_setup(geo: Geometry, ev: DeviceEvents, n_subsets: int, stream=None, into: "PermutedEvents" = None,
+                ws: Optional[torch.Tensor] = None) -> PermutedEvents:
+    """Validation, event counts mu and the subset-contiguous split.  `into`
+    reuses the buffers of an earlier result (same size); `ws` a workspace of
+    at least lm_setup_workspace_bytes(n) bytes."""
     L = load_library()
     dev = ev.det1.device
     n = ev.n
-    out = DeviceEvents(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
-                       torch.empty(n, dtype=torch.int16, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
-                       torch.empty(n, dtype=torch.float32, device=dev))
-    mu = torch.empty(n, dtype=torch.uint16, device=dev)
-    off = np.zeros(n_subsets + 1, dtype=np.int64)
-    ws = _ws(L.lm_setup_workspace_bytes(n), dev)
+    if into is not None:
+        if into.events.n != n or into.sub_off.shape[0] != n_subsets + 1:
+            raise ValueError("buffers of a different size")
+        out, mu, off = into.events, into.mu, into.sub_off
+    else:
+        out = DeviceEvents(torch.empty(n, dtype=torch.int32, device=dev),
+                           torch.empty(n, dtype=torch.int32, device=dev),
+                           torch.empty(n, dtype=torch.int16, device=dev),
+                           torch.empty(n, dtype=torch.float32, device=dev),
+                           torch.empty(n, dtype=torch.float32, device=dev))
+        mu = torch.empty(n, dtype=torch.uint16, device=dev)
+        off = np.zeros(n_subsets + 1, dtype=np.int64)
+    if ws is None:
+        ws = _ws(L.lm_setup_workspace_bytes(n), dev)
     d = ev.desc()
     _check(L.lm_event_setup(C.byref(geo.sc), C.byref(geo.tof), C.byref(d), int(n_subsets), _ptr(out.det1),
                             _ptr(out.det2), _ptr(out.tof), _ptr(out.corr), _ptr(out.contam), _ptr(mu),
