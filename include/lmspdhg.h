@@ -123,6 +123,22 @@ size_t lm_back_workspace_bytes(const lm_grid* grid, int deterministic);
 int lm_back(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev,
             const float* v, float* img, int deterministic, void* ws, size_t ws_bytes, void* stream);
 
+/* The deterministic back-projection of lm_back(..., deterministic = 1, ...)
+ * for callers that cannot allocate device memory or pass a workspace (a
+ * plug-in whose host application owns all device memory, a real-time path
+ * that must not allocate after start-up).  It allocates nothing: its scratch
+ * is one fixed array inside the library, 2^22 voxels (64-bit sums) plus a
+ * few words, 32 MiB + 256 B, held on every GPU that loads the library until
+ * the process exits.  Grids above 2^22 voxels are rejected with
+ * LM_ERR_NOMEM.  The result equals lm_back's deterministic result.  The first
+ * call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Every call
+ * clears and reuses the same array, so calls that overlap on the GPU (other
+ * streams, other threads, concurrent graph replays) race and must be
+ * serialised by the caller.  The paper has no counterpart to this call. */
+int lm_back_deterministic_noalloc(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof,
+                                  const lm_events* ev, const float* v, float* img, void* stream);
+
 /* Sensitivity image sens = P^T 1 (Sec. "Listmode SPDHG": pre-computed once and
  * stored), i.e. the back-projection of ones over every canonical LOR and
  * every TOF bin, times lor_factor[l] (device float [lm_n_lor], NULL = 1).
