@@ -452,7 +452,7 @@ def run_gpu(args):
             "frames_per_s": world * args.steps / t_max,
             "sens_ms": sens_ms, "knorm_ms": knorm_ms, "generate_s": gen_s, "wall_s": wall,
             "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(launches), "clocks": clocks,
+            "gpu_launches": int(launches), "clocks": clocks, "tuning": st.tuning(),
             "objective_last": f_last,
         }
         print(json.dumps(out))

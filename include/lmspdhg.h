@@ -205,6 +205,9 @@ typedef struct {
     int32_t n_subsets;    /* n >= 1                                               */
     int32_t deterministic;/* 1: fixed-point back-projection (bit-reproducible)    */
     int32_t kahan;        /* 1: compensated float32 accumulation of z             */
+    int32_t group;        /* lanes per event in the event kernels: 8, 16 or 32;  */
+                          /* 0: chosen at create by timing the forward projection */
+                          /* of subset 0 with each width (autotuner)             */
 } lm_params;
 
 /* Device bytes the state needs (images, duals, per-event y and scratch). */
@@ -260,6 +263,10 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream);
  * as resolved at create). */
 int lmspdhg_info(lm_state* st, int64_t* n_updates, double* gamma, double* knorm);
 
+/* The event-kernel width in use and, if it was autotuned, the measured
+ * forward-projection times of subset 0 (ms) for widths 8, 16, 32 (else 0). */
+int lmspdhg_tuning(lm_state* st, int32_t* group, double* ms3);
+
 /* Re-initialise the state (Alg. 2 steps 3-5 as in lmspdhg_create) for the
  * current contents of the referenced event arrays and a new x0, keeping the
  * buffers and the captured epoch graph: the events may have been overwritten
@@ -275,6 +282,95 @@ int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, doubl
                     void* stream);
 
 int lmspdhg_destroy(lm_state* st);
+
+/* ---- batched epochs of several frames ----------------------------------- */
+/* A batch advances every occupied slot (an lm_state) by one epoch of Alg. 2
+ * in one captured CUDA graph: each update is one event kernel whose work
+ * items span the events of every frame's selected subset (or the voxels of
+ * its prior step) and one image pass over all frames' tiles, so small
+ * frames share the GPU instead of each leaving most of it idle.  The states
+ * of a batch must share the grid, TOF kernel, subset count, crystal count
+ * and mode (deterministic / compensated); each keeps its own events, duals,
+ * images and selection sequence.  Results equal lmspdhg_epoch on each state
+ * alone (bit for bit in deterministic mode; within float32 rounding of the
+ * atomic back-projection otherwise).  Slots are filled or emptied between
+ * epochs (continuous batching); the graph does not change.
+ * buf: device workspace of lmspdhg_batch_bytes(capacity, n_subsets) bytes;
+ * capacity <= 64. */
+typedef struct lm_batch_s lm_batch;
+size_t lmspdhg_batch_bytes(int32_t capacity, int32_t n_subsets);
+int lmspdhg_batch_create(lm_batch** out, int32_t capacity, int32_t n_subsets, void* buf, size_t bytes,
+                         void* stream);
+/* Puts `st` into `slot` (NULL empties it).  A state joins after an even
+ * number of updates (e.g. after create/reinit or whole epochs) and may not
+ * occupy two slots.  Synchronous. */
+int lmspdhg_batch_set(lm_batch* b, int32_t slot, lm_state* st, void* stream);
+/* One epoch for every occupied slot; seqs_host: host uint16[capacity][2n]
+ * (rows of empty slots are ignored). */
+int lmspdhg_batch_epoch(lm_batch* b, const uint16_t* seqs_host, void* stream);
+int lmspdhg_batch_destroy(lm_batch* b);
+
+/* ---- reconstruction server: continuous batching of frames ---------------- */
+/* The paper reconstructs one frame at a time; a server of many short frames
+ * (dynamic or gated studies, Sec. "Discussion") has no counterpart there.
+ * A server owns one lm_batch and a worker thread.  Frames are queued by
+ * lm_server_submit (host arrays, copied) and admitted in arrival order when
+ * a slot is free and the caller's device pool has room for the frame
+ * (lm_server_frame_bytes; first-fit with coalescing); admission uploads the
+ * events, runs lm_event_setup and lmspdhg_create from the uniform image
+ * x0_value.  Every loop of the worker advances all admitted frames by one
+ * epoch of their own selection sequence in one batched launch, then retires
+ * the frames that finished (x and the FP64 objective copied to the host,
+ * pool memory released), so frames join and leave between epochs while the
+ * others keep running.  A frame's result equals a lone lmspdhg run of it
+ * (bit for bit in deterministic mode).  */
+typedef struct lm_server_s lm_server;
+
+typedef struct {
+    float beta;             /* TV weight                                        */
+    float rho;              /* step-size safety factor (paper: 0.999)           */
+    double knorm;           /* ||K|| (> 0; from lm_knorm_fp64)                  */
+    int32_t n_subsets;      /* data subsets n                                   */
+    int32_t epochs;         /* epochs per frame (>= 1)                          */
+    int32_t max_slots;      /* frames on the GPU at once (1..64)                */
+    int32_t deterministic;  /* fixed-point back-projection                      */
+    int32_t kahan;          /* compensated z                                    */
+    int32_t group;          /* lanes per event (8, 16, 32; 0: 32)               */
+    int64_t max_events;     /* largest frame accepted                           */
+} lm_server_config;
+
+/* Pool bytes one admitted frame of n_events holds. */
+size_t lm_server_frame_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets, int32_t deterministic);
+
+/* sens: device P^T 1, referenced.  pool: device memory owned by the caller
+ * (must outlive the server); it must hold the event set-up workspace of
+ * max_events, the batch workspace and one frame of max_events, else
+ * LM_ERR_NOMEM.  The server runs on the calling thread's current device. */
+int lm_server_create(lm_server** out, const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof,
+                     const float* sens, const lm_server_config* cfg, void* pool, size_t pool_bytes);
+
+/* Queues one frame.  Host arrays of n events (tof may be NULL for non-TOF,
+ * corr NULL for all ones); x0_value > 0; seqs_host: host
+ * uint16[epochs][2 n_subsets], the frame's selection sequence (values <=
+ * n_subsets).  n > max_events gives LM_ERR_NOMEM.  Returns at once; invalid
+ * events are reported by lm_server_wait. */
+int lm_server_submit(lm_server* s, const int32_t* det1, const int32_t* det2, const int16_t* tof,
+                     const float* corr, const float* contam, int64_t n, float x0_value,
+                     const uint16_t* seqs_host, int64_t* ticket);
+
+/* Waits at most timeout_ms for a ticket: LM_ERR_TIMEOUT if unfinished (the
+ * ticket stays valid), else the frame's status; on LM_OK fills x_host
+ * (float[V], may be NULL), *objective and *latency_ms (submit to retire) and
+ * the ticket is released. */
+int lm_server_wait(lm_server* s, int64_t ticket, float* x_host, double* objective, double* latency_ms,
+                   int32_t timeout_ms);
+
+/* Frames finished, on the GPU, queued; pool bytes in use. */
+int lm_server_stats(lm_server* s, int64_t* completed, int64_t* in_flight, int64_t* queued, size_t* pool_used);
+
+/* Stops the worker after its current epoch and frees everything; queued and
+ * unfinished frames are dropped. */
+int lm_server_destroy(lm_server* s);
 
 /* ---- measurement utilities (no counterpart in the paper) ---------------- */
 /* Kernels launched by this library in this process so far (a replayed

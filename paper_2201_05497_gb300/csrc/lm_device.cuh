@@ -41,6 +41,7 @@ struct Lor {
     int sk, sA, sB;       // voxel strides of the plane index and the secondary axes
     int nA, nB;
     int yf;               // 1: use the y-fastest image (principal axis y)
+    int k;                // principal axis
 };
 
 __device__ __forceinline__ float sel3(int k, float a, float b, float c) { return k == 0 ? a : (k == 1 ? b : c); }
@@ -62,6 +63,7 @@ __device__ __forceinline__ bool lor_setup(const Geo& G, int d1, int d2, int m, i
     if (adk == 0.0f) return false;
     const int ka = (k == 0) ? 1 : 0;
     const int kb = (k == 2) ? 1 : 2;
+    L.k = k;
     const float dk = sel3(k, d0, dd1, dd2);
     const float da = sel3(ka, d0, dd1, dd2), db = sel3(kb, d0, dd1, dd2);
     // line centre c = a + d/2; plane i: mu_i = (o_k + i h_k - c_k)/d_k, point c + mu_i d

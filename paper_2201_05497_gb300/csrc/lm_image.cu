@@ -164,113 +164,229 @@ __device__ __forceinline__ float prior_dz(const lmh::ImgArgs& A, const float* wc
     return dz;
 }
 
-__global__ void __launch_bounds__(256) image_pass_kernel(const lmh::ImgArgs A)
+// What an image pass does at update u: merge the data accumulators (data
+// update, or the initialisation) or form K^T(w+ - w) (prior update).
+struct PassMode {
+    bool data, prior, init;
+    float inv_p;
+    double fx;  // fixed-point step of the data accumulators (deterministic mode)
+    const float* wc;
+    const float* wn;
+};
+
+__device__ __forceinline__ PassMode pass_mode(const lmh::ImgArgs& A, int u)
 {
-    __shared__ float smf[TD][TD + 1];
-    __shared__ long long smi[TD][TD + 1];
-    __shared__ float smx[TD][TD + 1];
-    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    bool data = A.mode == lmh::IP_INIT, prior = false;
+    PassMode m;
+    m.init = A.mode == lmh::IP_INIT;
+    m.data = m.init;
+    m.prior = false;
+    m.inv_p = 1.0f;
+    m.fx = 0.0;
+    m.wc = m.wn = nullptr;
     long long count = 0;
-    float inv_p = 1.0f;
     int slot = 1;  // max-bits slot of the fixed-point scale used by this update
     if (A.mode == lmh::IP_UPDATE) {
-        const int sel = A.seq[A.u];
-        prior = sel >= A.n_subsets;
-        data = !prior;
-        if (data) count = (long long)(A.sub_off[sel + 1] - A.sub_off[sel]);
-        inv_p = prior ? A.inv_p_prior : A.inv_p_data;
-        slot = (A.slot0 + A.u) & 1;
-        // clear the slot the next update will use
-        if (blockIdx.x == 0 && tx == 0 && ty == 0 && A.maxbits_reset) A.maxbits_reset[(A.slot0 + A.u + 1) & 1] = 0u;
+        const int sel = A.seq[u];
+        m.prior = sel >= A.n_subsets;
+        m.data = !m.prior;
+        if (m.data) count = (long long)(A.sub_off[sel + 1] - A.sub_off[sel]);
+        m.inv_p = m.prior ? A.inv_p_prior : A.inv_p_data;
+        slot = (A.slot0 + u) & 1;
     } else {
         count = (long long)A.sub_off[A.n_subsets];
-        if (blockIdx.x == 0 && tx == 0 && ty == 0 && A.maxbits_reset) A.maxbits_reset[0] = 0u;
     }
-    double fx = 0.0;
-    if (data && A.det) fx = fx_step(A.maxbits + slot, count, A.stepmax);
-    const float* wc = nullptr;
-    const float* wn = nullptr;
-    if (prior) {
-        const int wp = A.wpar[A.u];
-        wc = A.w_cur[wp];
-        wn = A.w_nxt[wp];
+    if (m.data && A.det) m.fx = fx_step(A.maxbits + slot, count, A.stepmax);
+    if (m.prior) {
+        const int wp = A.wpar[u];
+        m.wc = A.w_cur[wp];
+        m.wn = A.w_nxt[wp];
     }
+    return m;
+}
+
+// Clears the fixed-point scale slot the next update will use (one thread).
+__device__ __forceinline__ void reset_next_slot(const lmh::ImgArgs& A, int u)
+{
+    if (!A.maxbits_reset) return;
+    if (A.mode == lmh::IP_UPDATE) A.maxbits_reset[(A.slot0 + u + 1) & 1] = 0u;
+    else A.maxbits_reset[0] = 0u;
+}
+
+struct TileSmem {
+    float f[TD][TD + 1];
+    long long i[TD][TD + 1];
+    float x[TD][TD + 1];
+};
+
+// One 32 x 32 tile of one z slice: all loads of the thread's rows first
+// (memory-level parallelism), then compute and store; the y-fastest arrays
+// go through shared memory so both layouts are accessed coalesced.
+__device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode& m, int u, const TileIdx& Tl,
+                                           const float* __restrict__ xcur, float* __restrict__ x_nxt_std,
+                                           float* __restrict__ x_nxt_yf, TileSmem& sm)
+{
+    constexpr int RPT = TD / TR;  // rows per thread in a tile
+    const int nx = A.n[0], ny = A.n[1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const bool have_yf = ny > 1;
-    for (int64_t t = blockIdx.x; t < n_tiles(nx, ny, nz); t += gridDim.x) {
-        const TileIdx T = tile_of(t, nx, ny);
-        if (data && have_yf) {
-            for (int r = ty; r < TD; r += TR) {
-                const int xx = T.x0 + r, yy = T.y0 + tx;
-                if (xx < nx && yy < ny) {
-                    const int64_t k = ((int64_t)T.z * nx + xx) * ny + yy;
-                    if (A.det) {
-                        smi[r][tx] = (long long)A.acci_yf[k];
-                        A.acci_yf[k] = 0ULL;
-                    } else {
-                        smf[r][tx] = A.acc_yf[k];
-                        A.acc_yf[k] = 0.0f;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        for (int r = ty; r < TD; r += TR) {
-            const int xx = T.x0 + tx, yy = T.y0 + r;
+    const bool kahan = A.kahan != 0;
+    const bool det = A.det != 0;
+    const float* __restrict__ Tm = A.T;
+    float* __restrict__ zz = A.z;
+    float* __restrict__ zc = A.zc;
+    float* __restrict__ acc_std = A.acc_std;
+    float* __restrict__ acc_yf = A.acc_yf;
+    unsigned long long* __restrict__ acci_std = A.acci_std;
+    unsigned long long* __restrict__ acci_yf = A.acci_yf;
+    if (m.data && have_yf) {
+        float vf[RPT];
+        long long vi[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int r = ty + q * TR;
+            const int xx = Tl.x0 + r, yy = Tl.y0 + tx;
+            vf[q] = 0.0f;
+            vi[q] = 0;
             if (xx < nx && yy < ny) {
-                const int64_t j = ((int64_t)T.z * ny + yy) * nx + xx;
-                float dz;
-                if (data) {
-                    if (A.det) {
-                        long long s = (long long)A.acci_std[j];
-                        A.acci_std[j] = 0ULL;
-                        if (have_yf) s += smi[tx][r];
-                        dz = (float)((double)s * fx);
-                    } else {
-                        dz = A.acc_std[j];
-                        A.acc_std[j] = 0.0f;
-                        if (have_yf) dz += smf[tx][r];
-                    }
-                } else {
-                    dz = prior_dz(A, wc, wn, xx, yy, T.z, j);
-                }
-                float zh, zl = 0.0f, xn;
-                if (A.mode == lmh::IP_INIT) {
-                    // z = P^T 1 + (P^LM)^T((y-1)/mu); zbar = z; first primal step from x0
-                    float e = 0.0f;
-                    two_sum(A.sens[j], dz, zh, e);
-                    zl = A.kahan ? e : 0.0f;
-                    const float x0 = A.x_cur[j];
-                    A.x_keep[j] = x0;
-                    xn = fmaxf(0.0f, x0 - A.T[j] * (zh + zl));
-                } else {
-                    const float z0 = A.z[j];
-                    if (A.kahan) {
-                        float e;
-                        two_sum(z0, dz, zh, e);
-                        zl = A.zc[j] + e;
-                    } else {
-                        zh = z0 + dz;
-                    }
-                    const float zbar = fmaf(dz, inv_p, zh + zl);  // z + dz/p_i
-                    xn = fmaxf(0.0f, A.x_cur[j] - A.T[j] * zbar);
-                }
-                A.z[j] = zh;
-                if (A.kahan) A.zc[j] = zl;
-                A.x_nxt_std[j] = xn;
-                smx[r][tx] = xn;
+                const int64_t k = ((int64_t)Tl.z * nx + xx) * ny + yy;
+                if (det) vi[q] = (long long)acci_yf[k];
+                else vf[q] = acc_yf[k];
             }
         }
-        __syncthreads();
-        if (have_yf) {
-            for (int r = ty; r < TD; r += TR) {
-                const int xx = T.x0 + r, yy = T.y0 + tx;
-                if (xx < nx && yy < ny) A.x_nxt_yf[((int64_t)T.z * nx + xx) * ny + yy] = smx[tx][r];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int r = ty + q * TR;
+            const int xx = Tl.x0 + r, yy = Tl.y0 + tx;
+            if (xx < nx && yy < ny) {
+                const int64_t k = ((int64_t)Tl.z * nx + xx) * ny + yy;
+                if (det) {
+                    sm.i[r][tx] = vi[q];
+                    acci_yf[k] = 0ULL;
+                } else {
+                    sm.f[r][tx] = vf[q];
+                    acc_yf[k] = 0.0f;
+                }
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
+    float dz[RPT], x0[RPT], tm[RPT], z0[RPT], zl0[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int xx = Tl.x0 + tx, yy = Tl.y0 + ty + q * TR;
+        dz[q] = x0[q] = tm[q] = z0[q] = zl0[q] = 0.0f;
+        if (xx < nx && yy < ny) {
+            const int64_t j = ((int64_t)Tl.z * ny + yy) * nx + xx;
+            x0[q] = xcur[j];
+            tm[q] = Tm[j];
+            if (m.init) {
+                z0[q] = A.sens[j];
+            } else {
+                z0[q] = zz[j];
+                if (kahan) zl0[q] = zc[j];
+            }
+            if (m.data) {
+                if (det) {
+                    long long s = (long long)acci_std[j];
+                    if (have_yf) s += sm.i[tx][ty + q * TR];
+                    dz[q] = (float)((double)s * m.fx);
+                } else {
+                    dz[q] = acc_std[j];
+                    if (have_yf) dz[q] += sm.f[tx][ty + q * TR];
+                }
+            } else {
+                dz[q] = prior_dz(A, m.wc, m.wn, xx, yy, Tl.z, j);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int r = ty + q * TR;
+        const int xx = Tl.x0 + tx, yy = Tl.y0 + r;
+        if (xx < nx && yy < ny) {
+            const int64_t j = ((int64_t)Tl.z * ny + yy) * nx + xx;
+            if (m.data) {
+                if (det) acci_std[j] = 0ULL;
+                else acc_std[j] = 0.0f;
+            }
+            float zh, zl = 0.0f, xn;
+            if (m.init) {
+                // z = P^T 1 + (P^LM)^T((y-1)/mu); zbar = z; first primal step from x0
+                float e = 0.0f;
+                two_sum(z0[q], dz[q], zh, e);
+                zl = kahan ? e : 0.0f;
+                A.x_keep[j] = x0[q];
+                xn = fmaxf(0.0f, x0[q] - tm[q] * (zh + zl));
+            } else {
+                if (kahan) {
+                    float e;
+                    two_sum(z0[q], dz[q], zh, e);
+                    zl = zl0[q] + e;
+                } else {
+                    zh = z0[q] + dz[q];
+                }
+                const float zbar = fmaf(dz[q], m.inv_p, zh + zl);  // z + dz/p_i
+                xn = fmaxf(0.0f, x0[q] - tm[q] * zbar);
+            }
+            zz[j] = zh;
+            if (kahan) zc[j] = zl;
+            x_nxt_std[j] = xn;
+            sm.x[r][tx] = xn;
+        }
+    }
+    __syncthreads();
+    if (have_yf) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int r = ty + q * TR;
+            const int xx = Tl.x0 + r, yy = Tl.y0 + tx;
+            if (xx < nx && yy < ny) x_nxt_yf[((int64_t)Tl.z * nx + xx) * ny + yy] = sm.x[tx][r];
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) image_pass_kernel(const lmh::ImgArgs A)
+{
+    __shared__ TileSmem sm;
+    const int u = A.u;
+    const PassMode m = pass_mode(A, u);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) reset_next_slot(A, u);
+    for (int64_t t = blockIdx.x; t < n_tiles(A.n[0], A.n[1], A.n[2]); t += gridDim.x)
+        image_tile(A, m, u, tile_of(t, A.n[0], A.n[1]), A.x_cur, A.x_nxt_std, A.x_nxt_yf, sm);
+}
+
+// Image passes of every active frame of a batch at update u: work items are
+// (frame, tile) pairs; x alternates between the frame's two buffers.
+__global__ void __launch_bounds__(256) image_batch_kernel(const lmh::BatchImgArgs B)
+{
+    __shared__ TileSmem sm;
+    const int par = B.u & 1;
+    for (int64_t t = blockIdx.x; t < (int64_t)B.cap * B.tiles_per_slot; t += gridDim.x) {
+        const int s = (int)(t / B.tiles_per_slot);
+        if (!B.active[s]) continue;
+        const lmh::ImgArgs& A = B.slots[s];
+        const int64_t lt = t - (int64_t)s * B.tiles_per_slot;
+        const PassMode m = pass_mode(A, B.u);
+        if (lt == 0 && threadIdx.x == 0 && threadIdx.y == 0) reset_next_slot(A, B.u);
+        image_tile(A, m, B.u, tile_of(lt, A.n[0], A.n[1]), A.xbuf[par], A.xbuf[par ^ 1], A.xbuf_yf[par ^ 1], sm);
+    }
+}
+
+// Prefix parity of the w buffers for every active frame of a batch.
+__global__ void wpar_batch_kernel(const lmh::BatchImgArgs B, int count)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.cap || !B.active[s]) return;
+    const lmh::ImgArgs& A = B.slots[s];
+    int p = *A.wbase;
+    int* wpar = A.wpar_w;
+    wpar[0] = p;
+    for (int u = 0; u < count; ++u) {
+        if (A.seq[u] >= A.n_subsets) p ^= 1;
+        wpar[u + 1] = p;
+    }
+    *A.wbase = p;
 }
 
 int tile_grid(const lm_grid* g, int per_sm = 8)
@@ -614,6 +730,29 @@ void launch_image_pass(const ImgArgs& a, cudaStream_t st)
     for (int d = 0; d < 3; ++d) g.n[d] = a.n[d];
     image_pass_kernel<<<tile_grid(&g), dim3(TD, TR), 0, st>>>(a);
     count_launch();
+}
+
+void launch_image_batch(const BatchImgArgs& b, int grid, cudaStream_t st)
+{
+    image_batch_kernel<<<grid, dim3(TD, TR), 0, st>>>(b);
+    count_launch();
+}
+
+void launch_wpar_batch(const BatchImgArgs& b, int count, cudaStream_t st)
+{
+    wpar_batch_kernel<<<(b.cap + 63) / 64, 64, 0, st>>>(b, count);
+    count_launch();
+}
+
+int image_batch_grid(const lm_grid* g, int cap)
+{
+    const int64_t nt = (int64_t)((g->n[0] + TD - 1) / TD) * ((g->n[1] + TD - 1) / TD) * g->n[2] * cap;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)num_sms() * 8));
+}
+
+int64_t image_tiles(const lm_grid* g)
+{
+    return (int64_t)((g->n[0] + TD - 1) / TD) * ((g->n[1] + TD - 1) / TD) * g->n[2];
 }
 
 void launch_wpar(const uint16_t* seq, int count, int n_subsets, int* wpar, int* wbase, cudaStream_t st)

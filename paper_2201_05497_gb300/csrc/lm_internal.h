@@ -43,6 +43,11 @@ inline size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
 int num_sms();
 
+// Intervals of the tabulated TOF kernel (bin-integrated Gaussian on [-W, W]).
+constexpr int TOF_TAB_N = 4096;
+// Fills tab[0..TOF_TAB_N] (host) with w(tau) at tau = -W + k 2W/TOF_TAB_N.
+void tof_table(const lm_tof* tof, float* tab);
+
 // Kernel launches issued by the library (graph replays count their nodes).
 void count_launch(int64_t n = 1);
 int64_t launch_total();
@@ -99,10 +104,37 @@ struct EvArgs {
     float s_prior;              // S_{n+1} = gamma rho / ||K||
     float beta;
     int ndim;
+    const float* tof_tab;       // device table (TOF_TAB_N + 1 floats) or nullptr (erf per sample)
+    int group;                  // lanes per event: 8, 16 or 32 (0 = 16)
+    // batched epochs: both x buffers (index = update parity) and the scale slots
+    const float* xb[2];
+    const float* xbyf[2];
+    unsigned* maxbits_base;
 };
 
+// Batched multi-frame epochs: per-frame argument tables in device memory.
+constexpr int BATCH_MAX = 64;
+
+struct BatchEvArgs {
+    const EvArgs* slots;        // [cap]
+    const int* active;          // [cap]
+    const uint16_t* seqs;       // [cap][seq_stride]
+    int seq_stride;
+    int cap;
+    int u;
+    int slot0;                  // scale slot of update u: (slot0 + u) & 1
+    unsigned long long* queue;  // self-resetting work counter
+    unsigned* done;
+    const float* tof_tab;       // shared TOF table (all frames have the same TOF kernel) or nullptr
+    float tof_W;
+    int vitem;                  // voxels per prior work item
+};
+int launch_events_batch(int mode, bool two_d, int group, const BatchEvArgs& b, int grid, cudaStream_t st);
+int ev_batch_grid(int mode, bool two_d, int group);  // group 0: smallest over 8/16/32
+
 int launch_events(int mode, bool two_d, const EvArgs& a, int grid, cudaStream_t st);
-int ev_grid(int mode, bool two_d);
+int ev_grid(int mode, bool two_d);  // smallest over the group widths
+int ev_grid_g(int mode, bool two_d, int group);
 
 // ---- image kernels (lm_image.cu) ----
 void launch_transpose_to_yf(const lm_grid* g, const float* src, float* dst, cudaStream_t st);
@@ -146,7 +178,24 @@ struct ImgArgs {
     const int* wpar;
     float inv_p_data;      // 1/p_k = 2n
     float inv_p_prior;     // 1/p_{n+1} = 2
+    // batched epochs
+    float* xbuf[2];
+    float* xbuf_yf[2];
+    int* wpar_w;
+    int* wbase;
 };
+
+struct BatchImgArgs {
+    const ImgArgs* slots;  // [cap]
+    const int* active;     // [cap]
+    int cap;
+    int u;
+    int64_t tiles_per_slot;
+};
+void launch_image_batch(const BatchImgArgs& b, int grid, cudaStream_t st);
+void launch_wpar_batch(const BatchImgArgs& b, int count, cudaStream_t st);
+int image_batch_grid(const lm_grid* g, int cap);
+int64_t image_tiles(const lm_grid* g);
 enum { IP_INIT = 0, IP_UPDATE = 1 };
 void launch_image_pass(const ImgArgs& a, cudaStream_t st);
 void launch_wpar(const uint16_t* seq, int count, int n_subsets, int* wpar, int* wbase, cudaStream_t st);

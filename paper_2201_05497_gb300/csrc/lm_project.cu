@@ -25,6 +25,16 @@ void set_error(const char* fmt, ...)
 
 void clear_error() { g_err.clear(); }
 
+void tof_table(const lm_tof* tof, float* tab)
+{
+    const double sig = tof->sigma_mm, D = tof->bin_mm, W = (double)tof->n_sigma * sig;
+    const double s = std::sqrt(2.0) * sig;
+    for (int k = 0; k <= TOF_TAB_N; ++k) {
+        const double tau = -W + 2.0 * W * k / TOF_TAB_N;
+        tab[k] = (float)(0.5 * (std::erf((tau + 0.5 * D) / s) - std::erf((tau - 0.5 * D) / s)));
+    }
+}
+
 static std::atomic<int64_t> g_launches{0};
 void count_launch(int64_t n) { g_launches.fetch_add(n); }
 int64_t launch_total() { return g_launches.load(); }
@@ -104,35 +114,95 @@ using lmh::EvArgs;
 
 namespace {
 
-// Dual step of the prior (Alg. 2 line 15): w+ = beta prox_{R^*}((w + S Kx)/beta)
-// = v / max(1, |v|/beta) with v = w + S_{n+1} Kx, per voxel.
-__device__ void prior_dual(const EvArgs& A)
+// Dual step of the prior at voxel j (Alg. 2 line 15):
+// w+ = v / max(1, |v|/beta), v = w + S_{n+1} K x.
+__device__ __forceinline__ void prior_voxel(const EvArgs& A, const float* __restrict__ x,
+                                            const float* __restrict__ wc, float* __restrict__ wn, int j)
 {
-    const int wp = A.wpar[A.u];
-    const float* __restrict__ wc = A.w_cur[wp];
-    float* __restrict__ wn = A.w_nxt[wp];
-    const float* __restrict__ x = A.px;
     const int nx = A.G.n[0], ny = A.G.n[1], nz = A.G.n[2];
     const int V = A.G.V;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t jj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; jj < V; jj += stride) {
-        const int j = (int)jj;
-        const int ix = j % nx;
-        const int iy = (j / nx) % ny;
-        const int iz = j / (nx * ny);
-        const float x0 = x[j];
-        int c = 0;
-        float vx = 0.0f, vy = 0.0f, vz = 0.0f;
-        int cx = -1, cy = -1, cz = -1;
-        if (nx > 1) { cx = c++; vx = fmaf(A.s_prior, ix < nx - 1 ? x[j + 1] - x0 : 0.0f, wc[(int64_t)cx * V + j]); }
-        if (ny > 1) { cy = c++; vy = fmaf(A.s_prior, iy < ny - 1 ? x[j + nx] - x0 : 0.0f, wc[(int64_t)cy * V + j]); }
-        if (nz > 1) { cz = c++; vz = fmaf(A.s_prior, iz < nz - 1 ? x[j + nx * ny] - x0 : 0.0f, wc[(int64_t)cz * V + j]); }
+    const int ix = j % nx;
+    const int iy = (j / nx) % ny;
+    const int iz = j / (nx * ny);
+    const float x0 = x[j];
+    int c = 0;
+    float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+    int cx = -1, cy = -1, cz = -1;
+    if (nx > 1) { cx = c++; vx = fmaf(A.s_prior, ix < nx - 1 ? x[j + 1] - x0 : 0.0f, wc[(int64_t)cx * V + j]); }
+    if (ny > 1) { cy = c++; vy = fmaf(A.s_prior, iy < ny - 1 ? x[j + nx] - x0 : 0.0f, wc[(int64_t)cy * V + j]); }
+    if (nz > 1) { cz = c++; vz = fmaf(A.s_prior, iz < nz - 1 ? x[j + nx * ny] - x0 : 0.0f, wc[(int64_t)cz * V + j]); }
+    const float nrm = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+    const float den = A.beta > 0.0f ? fmaxf(1.0f, nrm / A.beta) : 0.0f;
+    if (cx >= 0) wn[(int64_t)cx * V + j] = den > 0.0f ? vx / den : 0.0f;
+    if (cy >= 0) wn[(int64_t)cy * V + j] = den > 0.0f ? vy / den : 0.0f;
+    if (cz >= 0) wn[(int64_t)cz * V + j] = den > 0.0f ? vz / den : 0.0f;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float f4(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
+// The prior's dual step at the four voxels j..j+3 of one image row (nx a
+// multiple of 4, so the quad never crosses a row and every 16-byte access is
+// aligned): all loads are issued before any arithmetic.  Same arithmetic per
+// voxel as prior_voxel.
+__device__ __forceinline__ void prior_quad(const EvArgs& A, const float* __restrict__ x,
+                                           const float* __restrict__ wc, float* __restrict__ wn, int64_t j)
+{
+    const int nx = A.G.n[0], ny = A.G.n[1], nz = A.G.n[2];
+    const int64_t V = A.G.V;
+    const int ix = (int)(j % nx);
+    const int64_t r = j / nx;
+    const int iy = (int)(r % ny);
+    const int iz = (int)(r / ny);
+    const bool hx = nx > 1, hy = ny > 1, hz = nz > 1;
+    const int cy = hx ? 1 : 0, cz = cy + (hy ? 1 : 0);
+    const bool iny = iy < ny - 1, inz = iz < nz - 1;
+    const float4 xc = ld4(x + j);
+    const float xr = (hx && ix + 4 < nx) ? __ldg(x + j + 4) : 0.0f;
+    const float4 xy = (hy && iny) ? ld4(x + j + nx) : xc;
+    const float4 xz = (hz && inz) ? ld4(x + j + (int64_t)nx * ny) : xc;
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4 wx = hx ? ld4(wc + j) : z4;
+    const float4 wy = hy ? ld4(wc + (int64_t)cy * V + j) : z4;
+    const float4 wz = hz ? ld4(wc + (int64_t)cz * V + j) : z4;
+    float ox[4], oy[4], oz[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float x0 = f4(xc, k);
+        const float xn = k < 3 ? f4(xc, k + 1) : xr;
+        const float vx = hx ? fmaf(A.s_prior, ix + k < nx - 1 ? xn - x0 : 0.0f, f4(wx, k)) : 0.0f;
+        const float vy = hy ? fmaf(A.s_prior, iny ? f4(xy, k) - x0 : 0.0f, f4(wy, k)) : 0.0f;
+        const float vz = hz ? fmaf(A.s_prior, inz ? f4(xz, k) - x0 : 0.0f, f4(wz, k)) : 0.0f;
         const float nrm = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
         const float den = A.beta > 0.0f ? fmaxf(1.0f, nrm / A.beta) : 0.0f;
-        if (cx >= 0) wn[(int64_t)cx * V + j] = den > 0.0f ? vx / den : 0.0f;
-        if (cy >= 0) wn[(int64_t)cy * V + j] = den > 0.0f ? vy / den : 0.0f;
-        if (cz >= 0) wn[(int64_t)cz * V + j] = den > 0.0f ? vz / den : 0.0f;
+        ox[k] = den > 0.0f ? vx / den : 0.0f;
+        oy[k] = den > 0.0f ? vy / den : 0.0f;
+        oz[k] = den > 0.0f ? vz / den : 0.0f;
     }
+    if (hx) *reinterpret_cast<float4*>(wn + j) = make_float4(ox[0], ox[1], ox[2], ox[3]);
+    if (hy) *reinterpret_cast<float4*>(wn + (int64_t)cy * V + j) = make_float4(oy[0], oy[1], oy[2], oy[3]);
+    if (hz) *reinterpret_cast<float4*>(wn + (int64_t)cz * V + j) = make_float4(oz[0], oz[1], oz[2], oz[3]);
+}
+
+// Prior dual step over voxels [j0, j1) by `nthr` threads numbered t: quads
+// when rows are a multiple of 4 long, single voxels otherwise.
+__device__ __forceinline__ void prior_range(const EvArgs& A, const float* __restrict__ x, int wp, int64_t j0,
+                                            int64_t j1, int64_t t, int64_t nthr)
+{
+    const float* wc = A.w_cur[wp];
+    float* wn = A.w_nxt[wp];
+    if ((A.G.n[0] & 3) == 0) {
+        for (int64_t j = j0 + 4 * t; j < j1; j += 4 * nthr) prior_quad(A, x, wc, wn, j);
+    } else {
+        for (int64_t j = j0 + t; j < j1; j += nthr) prior_voxel(A, x, wc, wn, (int)j);
+    }
+}
+
+// The prior's dual step over the whole image, grid-stride.
+__device__ __noinline__ void prior_dual(const EvArgs& A)
+{
+    prior_range(A, A.px, A.wpar[A.u], 0, A.G.V, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
 }
 
 template <int MODE>
@@ -151,12 +221,294 @@ struct ModeTraits {
     static constexpr bool prior_branch = MODE == lmh::EV_DATA || MODE == lmh::EV_DATA_FX1;
 };
 
-constexpr int PCACHE = 3;  // cached passes of 32 samples (96 samples) per lane
+// Cached sample capacity per lane (3D: the 3-sigma window spans at most ~62
+// planes of 2.5 mm; 2D: ~80 planes of 2 mm); larger traversals recompute.
+template <bool TWO_D, int G>
+struct Cache {
+    static constexpr int passes = ((TWO_D ? 80 : 64) + G - 1) / G;
+};
 
-template <int MODE, bool TWO_D>
-__global__ void __launch_bounds__(256) ev_kernel(const EvArgs A)
+// TOF weight of the event's bin from the shared-memory table of the
+// bin-integrated Gaussian w(tau), tau in [-W, W] on TOF_TAB_N intervals,
+// linear interpolation; the 3-sigma cut is the same test as tof_weight's.
+__device__ __forceinline__ float tof_weight_tab(const Geo& G, const float* tab, float inv_dt, float tau)
+{
+    if (fabsf(tau) > G.W) return 0.0f;
+    const float u = fminf(fmaxf((tau + G.W) * inv_dt, 0.0f), (float)lmh::TOF_TAB_N);
+    const int k = min((int)u, lmh::TOF_TAB_N - 1);
+    const float f = u - (float)k;
+    const float a = tab[k];
+    return fmaf(f, tab[k + 1] - a, a);
+}
+
+template <bool TWO_D>
+__device__ __forceinline__ bool sample_tab(const Geo& G, const Lor& L, const float* tab, float inv_dt, int i, Smp& s)
+{
+    const float fi = (float)i;
+    const float tau = fmaf(fi, L.dtau, L.tau0);
+    const float wt = L.step * tof_weight_tab(G, tab, inv_dt, tau);
+    if (wt == 0.0f) return false;
+    const float ua = fmaf(fi, L.sa, L.ua0);
+    const float fla = floorf(ua);
+    const int ia = (int)fla;
+    const float fa = ua - fla;
+    const float wa0 = (ia >= 0 && ia < L.nA) ? (1.0f - fa) : 0.0f;
+    const float wa1 = (ia + 1 >= 0 && ia + 1 < L.nA) ? fa : 0.0f;
+    if (TWO_D) {
+        s.base = i * L.sk + ia * L.sA;
+        s.w0 = wt * wa0;
+        s.w1 = wt * wa1;
+        s.w2 = 0.0f;
+        s.w3 = 0.0f;
+        return (wa0 != 0.0f) || (wa1 != 0.0f);
+    } else {
+        const float ub = fmaf(fi, L.sb, L.ub0);
+        const float flb = floorf(ub);
+        const int ib = (int)flb;
+        const float fb = ub - flb;
+        const float wb0 = (ib >= 0 && ib < L.nB) ? (1.0f - fb) : 0.0f;
+        const float wb1 = (ib + 1 >= 0 && ib + 1 < L.nB) ? fb : 0.0f;
+        s.base = i * L.sk + ia * L.sA + ib * L.sB;
+        const float wtA0 = wt * wa0, wtA1 = wt * wa1;
+        s.w0 = wtA0 * wb0;
+        s.w1 = wtA1 * wb0;
+        s.w2 = wtA0 * wb1;
+        s.w3 = wtA1 * wb1;
+        return (s.w0 != 0.0f) || (s.w1 != 0.0f) || (s.w2 != 0.0f) || (s.w3 != 0.0f);
+    }
+}
+
+// One sample, TOF weight from the table when the caller gave one.
+template <bool TWO_D>
+__device__ __forceinline__ bool sample_any(const Geo& G, const Lor& L, int tofmode, const float* tab, float inv_dt,
+                                           int i, Smp& s)
+{
+    if (tofmode == TOF_BIN && tab != nullptr) return sample_tab<TWO_D>(G, L, tab, inv_dt, i, s);
+    return sample_at<TWO_D>(G, L, tofmode, i, s);
+}
+
+// Strides and extents of the traversal for principal axis k (set-up results
+// travel between lanes as k plus the affine coefficients).
+__device__ __forceinline__ void lor_strides(const Geo& G, int k, bool has_yf, Lor& L)
+{
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    if (k == 0) {
+        L.sk = 1; L.sA = nx; L.sB = nx * ny; L.nA = ny; L.nB = nz; L.yf = 0;
+    } else if (k == 1) {
+        L.nA = nx; L.nB = nz;
+        if (has_yf) { L.sk = 1; L.sA = ny; L.sB = nx * ny; L.yf = 1; }
+        else { L.sk = nx; L.sA = 1; L.sB = nx * ny; L.yf = 0; }
+    } else {
+        L.sk = nx * ny; L.sA = 1; L.sB = nx; L.nA = nx; L.nB = ny; L.yf = 0;
+    }
+}
+
+// One chunk of events [e0, e0 + nev) processed by the calling warp (see
+// ev_kernel).  x_std_in / x_yf_in: the image being projected, both layouts.
+template <int MODE, bool TWO_D, int G>
+__device__ __forceinline__ void event_chunk(const EvArgs& A, const float* __restrict__ x_std_in,
+                                            const float* __restrict__ x_yf_in, bool has_yf, int64_t e0, int nev,
+                                            const float* tab, float inv_dt, float fx_scale, float& wmax,
+                                            unsigned long long& cnt_s, unsigned long long& cnt_t)
 {
     using T = ModeTraits<MODE>;
+    constexpr int NG = 32 / G;
+    constexpr int PC = Cache<TWO_D, G>::passes;
+    const Geo& Gm = A.G;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, sub = lane % G;
+    const int tofmode = Gm.tof_on ? TOF_BIN : TOF_NONE;
+    const int R = (nev + NG - 1) / NG;  // rounds; event (grp*R + r) is owned by lane grp*G + r
+    const int q = grp * R + sub;
+    const bool own = sub < R && q < nev;
+    // ---- per-lane load and set-up of the owned event ----
+    float mc = 1.0f, ms = 0.0f, my = 0.0f, mv = 0.0f, mmu = 1.0f;
+    Lor L;
+    int mk = 0;
+    bool mok = false;
+    if (own) {
+        const int64_t e = e0 + q;
+        const int d1 = A.det1[e], d2 = A.det2[e];
+        const int m = A.tof ? (int)A.tof[e] : 0;
+        if (A.corr) mc = A.corr[e];
+        if (T::needs_s) ms = A.contam[e];
+        if (T::needs_y) my = A.y[e];
+        if (T::needs_mu) mmu = (float)A.mu[e];
+        if (T::needs_vin) mv = A.vin[e];
+        if (T::traverse) {
+            mok = d1 >= 0 && d1 < Gm.n_det && d2 >= 0 && d2 < Gm.n_det && d1 != d2 &&
+                  (tofmode == TOF_NONE || (m >= -Gm.M && m <= Gm.M));
+            mok = mok && lor_setup(Gm, d1, d2, m, tofmode, has_yf, L);
+            if (mok) mk = L.k;
+        }
+    }
+    if (MODE == lmh::EV_ABSMAX) {
+        if (own) wmax = fmaxf(wmax, fabsf(mc * mv));
+        return;
+    }
+    if (!mok) {
+        L.i0 = 0;
+        L.cnt = 0;
+        L.ua0 = L.sa = L.ub0 = L.sb = L.tau0 = L.dtau = L.step = 0.0f;
+    }
+    float r_out = 0.0f, r_y = 0.0f;
+    for (int r = 0; r < R; ++r) {
+        const int src = grp * G + r;
+        // parameters of this group's event from its owner lane
+        Lor E;
+        E.i0 = __shfl_sync(FULL, L.i0, src);
+        E.cnt = __shfl_sync(FULL, L.cnt, src);
+        const int k = __shfl_sync(FULL, mk, src);
+        E.ua0 = __shfl_sync(FULL, L.ua0, src);
+        E.sa = __shfl_sync(FULL, L.sa, src);
+        if (!TWO_D) {
+            E.ub0 = __shfl_sync(FULL, L.ub0, src);
+            E.sb = __shfl_sync(FULL, L.sb, src);
+        } else {
+            E.ub0 = 0.0f;
+            E.sb = 0.0f;
+        }
+        E.tau0 = __shfl_sync(FULL, L.tau0, src);
+        E.dtau = __shfl_sync(FULL, L.dtau, src);
+        E.step = __shfl_sync(FULL, L.step, src);
+        const float cj = __shfl_sync(FULL, mc, src);
+        const bool valid = r < R && (grp * R + r) < nev;
+        if (!valid) E.cnt = 0;
+        lor_strides(Gm, k, has_yf, E);
+        const int npass = (E.cnt + G - 1) / G;
+        const int iend = E.i0 + E.cnt;
+        float acc = 0.0f, acc1 = 0.0f;
+        Smp cs[PC];
+        if (T::gather) {
+            const float* __restrict__ img = E.yf ? x_yf_in : x_std_in;
+#pragma unroll
+            for (int p = 0; p < PC; ++p) {
+                cs[p].base = 0;
+                cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
+                if (p < npass) {
+                    const int i = E.i0 + p * G + sub;
+                    if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, cs[p])) {
+                        acc += gather<TWO_D>(img, E, cs[p]);
+                        acc1 += wsum<TWO_D>(cs[p]);
+                    } else {
+                        cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
+                    }
+                }
+            }
+            for (int p = PC; p < npass; ++p) {
+                const int i = E.i0 + p * G + sub;
+                Smp s;
+                if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s)) {
+                    acc += gather<TWO_D>(img, E, s);
+                    acc1 += wsum<TWO_D>(s);
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                acc += __shfl_xor_sync(FULL, acc, o);
+                acc1 += __shfl_xor_sync(FULL, acc1, o);
+            }
+        }
+        float bval = 0.0f;
+        if (MODE == lmh::EV_FWD) {
+            if (lane == src) r_out = cj * acc;
+        } else if (MODE == lmh::EV_DATA || MODE == lmh::EV_DATA_FX1) {
+            const float sj = __shfl_sync(FULL, ms, src);
+            const float yj = __shfl_sync(FULL, my, src);
+            const float muj = __shfl_sync(FULL, mmu, src);
+            const float p1 = cj * acc1;                            // (P^LM 1)_e
+            const float Se = p1 > 0.0f ? A.gamma_rho / p1 : 0.0f;  // S_k = gamma rho / P^LM_{N_k} 1
+            const float a = fmaf(Se, fmaf(cj, acc, sj), yj);       // y + S (P^LM x + s)
+            const float yp = prox_dstar(a, muj * Se);
+            const float v = (yp - yj) / muj;
+            if (lane == src) {
+                r_y = yp;
+                r_out = v;
+            }
+            if (MODE == lmh::EV_DATA) bval = valid ? cj * v : 0.0f;
+            else if (valid) wmax = fmaxf(wmax, fabsf(cj * v));
+        } else if (MODE == lmh::EV_YINIT || MODE == lmh::EV_YINIT_FX1) {
+            const float sj = __shfl_sync(FULL, ms, src);
+            const float muj = __shfl_sync(FULL, mmu, src);
+            const float u = fmaf(cj, acc, sj);
+            const float yv = 1.0f - muj / u;    // Eq. (yinit) with d -> mu
+            const float v = (yv - 1.0f) / muj;  // = -1/u
+            if (lane == src) {
+                r_y = yv;
+                r_out = v;
+            }
+            if (MODE == lmh::EV_YINIT) bval = valid ? cj * v : 0.0f;
+            else if (valid) wmax = fmaxf(wmax, fabsf(cj * v));
+        } else if (MODE == lmh::EV_BACK || MODE == lmh::EV_BACK_FX) {
+            // every lane takes part in the shuffle; groups without an event discard the value
+            const float vj = __shfl_sync(FULL, mv, src);
+            bval = valid ? cj * vj : 0.0f;
+        }
+        if (T::back_float && bval != 0.0f) {
+            float* acc_img = E.yf ? A.acc_yf : A.acc_std;
+            if (T::gather) {
+#pragma unroll
+                for (int p = 0; p < PC; ++p)
+                    if (p < npass) scatter<TWO_D>(acc_img, E, cs[p], bval);
+                for (int p = PC; p < npass; ++p) {
+                    const int i = E.i0 + p * G + sub;
+                    Smp s;
+                    if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s))
+                        scatter<TWO_D>(acc_img, E, s, bval);
+                }
+            } else {
+                for (int p = 0; p < npass; ++p) {
+                    const int i = E.i0 + p * G + sub;
+                    Smp s;
+                    if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s))
+                        scatter<TWO_D>(acc_img, E, s, bval);
+                }
+            }
+        }
+        if (T::count) {
+            for (int p = 0; p < npass; ++p) {
+                const int i = E.i0 + p * G + sub;
+                Smp s;
+                if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s)) {
+                    cnt_s += 1;
+                    cnt_t += (s.w0 != 0.0f) + (s.w1 != 0.0f) + (s.w2 != 0.0f) + (s.w3 != 0.0f);
+                }
+            }
+        }
+        if (T::back_fx && bval != 0.0f) {
+            unsigned long long* acc_img = E.yf ? A.acci_yf : A.acci_std;
+            const float v2 = bval * fx_scale;
+            for (int p = 0; p < npass; ++p) {
+                const int i = E.i0 + p * G + sub;
+                Smp s;
+                if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s))
+                    scatter_fx<TWO_D>(acc_img, E, s, v2);
+            }
+        }
+    }
+    if (own) {
+        const int64_t e = e0 + q;
+        if (MODE == lmh::EV_FWD) A.out[e] = r_out;
+        if (MODE == lmh::EV_DATA || MODE == lmh::EV_YINIT) A.y[e] = r_y;
+        if (MODE == lmh::EV_DATA_FX1 || MODE == lmh::EV_YINIT_FX1) {
+            A.y[e] = r_y;
+            A.out[e] = r_out;
+        }
+    }
+}
+
+// Event kernel.  A warp takes chunks of up to `chunk` consecutive events; the
+// lanes load them coalesced and each lane sets up the traversal of its own
+// event.  Groups of G lanes then process one event each (32/G events in
+// flight per warp): lane s of a group takes planes i0 + s, i0 + s + G, ...,
+// fetching the event's parameters from the owning lane by shuffles.
+template <int MODE, bool TWO_D, int G>
+__global__ void __launch_bounds__(256, G == 8 ? 2 : 3) ev_kernel(const EvArgs A)
+{
+    using T = ModeTraits<MODE>;
+    constexpr int NG = 32 / G;
+    constexpr int PC = Cache<TWO_D, G>::passes;
+    extern __shared__ float s_tab[];
     int64_t eb = A.e_begin, ee = A.e_end;
     if (A.seq != nullptr) {
         const int sel = A.seq[A.u];
@@ -167,23 +519,31 @@ __global__ void __launch_bounds__(256) ev_kernel(const EvArgs A)
         eb = A.sub_off[sel];
         ee = A.sub_off[sel + 1];
     }
-    const Geo& G = A.G;
+    const Geo& Gm = A.G;
     const int lane = threadIdx.x & 31;
-    const int tofmode = G.tof_on ? TOF_BIN : TOF_NONE;
+    const int grp = lane / G, sub = lane % G;
+    const int tofmode = Gm.tof_on ? TOF_BIN : TOF_NONE;
     const bool has_yf = A.x_yf != nullptr || A.acc_yf != nullptr || A.acci_yf != nullptr;
+    const float* tab = nullptr;
+    float inv_dt = 0.0f;
+    if (T::traverse && A.tof_tab != nullptr && tofmode == TOF_BIN) {
+        for (int k = threadIdx.x; k <= lmh::TOF_TAB_N; k += blockDim.x) s_tab[k] = A.tof_tab[k];
+        __syncthreads();
+        tab = s_tab;
+        inv_dt = (float)lmh::TOF_TAB_N / (2.0f * Gm.W);
+    }
     const int CH = A.chunk;
     const int64_t count = ee - eb;
     const int64_t nchunks = count > 0 ? (count + CH - 1) / CH : 0;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t total_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int fx_E = 0;
     float fx_scale = 1.0f;
     if (T::back_fx) {
         const float vmax = __uint_as_float(*A.maxbits);
-        fx_E = fx_exponent(vmax, (long long)count, A.stepmax);
-        fx_scale = ldexpf(1.0f, fx_E);
+        fx_scale = ldexpf(1.0f, fx_exponent(vmax, (long long)count, A.stepmax));
     }
-    float wmax = 0.0f;  // per-lane max for the FX1 / ABSMAX modes
+    float wmax = 0.0f;
+    unsigned long long cnt_s = 0, cnt_t = 0;
     int64_t it = 0;
     for (;;) {
         int64_t c;
@@ -198,161 +558,17 @@ __global__ void __launch_bounds__(256) ev_kernel(const EvArgs A)
         if (c >= nchunks) break;
         const int64_t e0 = eb + c * CH;
         const int nev = (int)min((int64_t)CH, ee - e0);
-        int md1 = -1, md2 = -1, mt = 0;
-        float mc = 1.0f, ms = 0.0f, my = 0.0f, mv = 0.0f, mmu = 1.0f;
-        if (lane < nev) {
-            const int64_t e = e0 + lane;
-            md1 = A.det1[e];
-            md2 = A.det2[e];
-            if (A.tof) mt = A.tof[e];
-            if (A.corr) mc = A.corr[e];
-            if (T::needs_s) ms = A.contam[e];
-            if (T::needs_y) my = A.y[e];
-            if (T::needs_mu) mmu = (float)A.mu[e];
-            if (T::needs_vin) mv = A.vin[e];
-        }
-        if (MODE == lmh::EV_ABSMAX) {
-            if (lane < nev) wmax = fmaxf(wmax, fabsf(mc * mv));
-            continue;
-        }
-        float r_out = 0.0f, r_y = 0.0f;
-        for (int j = 0; j < nev; ++j) {
-            const int d1 = __shfl_sync(FULL, md1, j);
-            const int d2 = __shfl_sync(FULL, md2, j);
-            const int m = __shfl_sync(FULL, mt, j);
-            const float cj = __shfl_sync(FULL, mc, j);
-            Lor L;
-            bool ok = d1 >= 0 && d1 < G.n_det && d2 >= 0 && d2 < G.n_det && d1 != d2 &&
-                      (tofmode == TOF_NONE || (m >= -G.M && m <= G.M));
-            ok = ok && lor_setup(G, d1, d2, m, tofmode, has_yf, L);
-            if (!ok) {
-                L.i0 = 0;
-                L.cnt = 0;
-                L.yf = 0;
-                L.sA = L.sB = L.sk = 0;
-            }
-            const int npass = (L.cnt + 31) >> 5;
-            const int iend = L.i0 + L.cnt;
-            float acc = 0.0f, acc1 = 0.0f;
-            Smp cs[PCACHE];
-            if (T::gather) {
-                const float* __restrict__ img = L.yf ? A.x_yf : A.x_std;
+        event_chunk<MODE, TWO_D, G>(A, A.x_std, A.x_yf, has_yf, e0, nev, tab, inv_dt, fx_scale, wmax, cnt_s, cnt_t);
+    }
+    if (T::count) {
 #pragma unroll
-                for (int p = 0; p < PCACHE; ++p) {
-                    cs[p].base = 0;
-                    cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
-                    if (p < npass) {
-                        const int i = L.i0 + p * 32 + lane;
-                        if (i < iend && sample_at<TWO_D>(G, L, tofmode, i, cs[p])) {
-                            acc += gather<TWO_D>(img, L, cs[p]);
-                            acc1 += wsum<TWO_D>(cs[p]);
-                        } else {
-                            cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
-                        }
-                    }
-                }
-                for (int p = PCACHE; p < npass; ++p) {
-                    const int i = L.i0 + p * 32 + lane;
-                    Smp s;
-                    if (i < iend && sample_at<TWO_D>(G, L, tofmode, i, s)) {
-                        acc += gather<TWO_D>(img, L, s);
-                        acc1 += wsum<TWO_D>(s);
-                    }
-                }
-                acc = warp_sum(acc);
-                acc1 = warp_sum(acc1);
-            }
-            // per-event scalar step (all lanes hold the same values)
-            float bval = 0.0f;  // value to back-project (before the weights)
-            if (MODE == lmh::EV_FWD) {
-                if (lane == j) r_out = cj * acc;
-            } else if (MODE == lmh::EV_DATA || MODE == lmh::EV_DATA_FX1) {
-                const float sj = __shfl_sync(FULL, ms, j);
-                const float yj = __shfl_sync(FULL, my, j);
-                const float muj = __shfl_sync(FULL, mmu, j);
-                const float p1 = cj * acc1;                            // (P^LM 1)_e
-                const float Se = p1 > 0.0f ? A.gamma_rho / p1 : 0.0f;  // S_k = gamma rho / P^LM_{N_k} 1
-                const float a = fmaf(Se, fmaf(cj, acc, sj), yj);       // y + S (P^LM x + s)
-                const float yp = prox_dstar(a, muj * Se);
-                const float v = (yp - yj) / muj;
-                if (lane == j) {
-                    r_y = yp;
-                    r_out = v;
-                }
-                if (MODE == lmh::EV_DATA) bval = cj * v;
-                else wmax = fmaxf(wmax, fabsf(cj * v));
-            } else if (MODE == lmh::EV_YINIT || MODE == lmh::EV_YINIT_FX1) {
-                const float sj = __shfl_sync(FULL, ms, j);
-                const float muj = __shfl_sync(FULL, mmu, j);
-                const float u = fmaf(cj, acc, sj);
-                const float yv = 1.0f - muj / u;          // Eq. (yinit) with d -> mu
-                const float v = (yv - 1.0f) / muj;        // = -1/u
-                if (lane == j) {
-                    r_y = yv;
-                    r_out = v;
-                }
-                if (MODE == lmh::EV_YINIT) bval = cj * v;
-                else wmax = fmaxf(wmax, fabsf(cj * v));
-            } else if (MODE == lmh::EV_BACK || MODE == lmh::EV_BACK_FX) {
-                bval = cj * __shfl_sync(FULL, mv, j);
-            }
-            if (T::back_float && bval != 0.0f) {
-                float* acc_img = L.yf ? A.acc_yf : A.acc_std;
-                if (T::gather) {
-#pragma unroll
-                    for (int p = 0; p < PCACHE; ++p)
-                        if (p < npass) scatter<TWO_D>(acc_img, L, cs[p], bval);
-                    for (int p = PCACHE; p < npass; ++p) {
-                        const int i = L.i0 + p * 32 + lane;
-                        Smp s;
-                        if (i < iend && sample_at<TWO_D>(G, L, tofmode, i, s)) scatter<TWO_D>(acc_img, L, s, bval);
-                    }
-                } else {
-                    for (int p = 0; p < npass; ++p) {
-                        const int i = L.i0 + p * 32 + lane;
-                        Smp s;
-                        if (i < iend && sample_at<TWO_D>(G, L, tofmode, i, s)) scatter<TWO_D>(acc_img, L, s, bval);
-                    }
-                }
-            }
-            if (T::count) {
-                unsigned long long ns = 0, nt = 0;
-                for (int p = 0; p < npass; ++p) {
-                    const int i = L.i0 + p * 32 + lane;
-                    Smp s;
-                    if (i < iend && sample_at<TWO_D>(G, L, tofmode, i, s)) {
-                        ns += 1;
-                        nt += (s.w0 != 0.0f) + (s.w1 != 0.0f) + (s.w2 != 0.0f) + (s.w3 != 0.0f);
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    ns += __shfl_xor_sync(FULL, ns, o);
-                    nt += __shfl_xor_sync(FULL, nt, o);
-                }
-                if (lane == 0) {
-                    atomicAdd(A.acci_std, ns);
-                    atomicAdd(A.acci_std + 1, nt);
-                }
-            }
-            if (T::back_fx && bval != 0.0f) {
-                unsigned long long* acc_img = L.yf ? A.acci_yf : A.acci_std;
-                const float v2 = bval * fx_scale;
-                for (int p = 0; p < npass; ++p) {
-                    const int i = L.i0 + p * 32 + lane;
-                    Smp s;
-                    if (i < iend && sample_at<TWO_D>(G, L, tofmode, i, s)) scatter_fx<TWO_D>(acc_img, L, s, v2);
-                }
-            }
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt_s += __shfl_xor_sync(FULL, cnt_s, o);
+            cnt_t += __shfl_xor_sync(FULL, cnt_t, o);
         }
-        if (lane < nev) {
-            const int64_t e = e0 + lane;
-            if (MODE == lmh::EV_FWD) A.out[e] = r_out;
-            if (MODE == lmh::EV_DATA || MODE == lmh::EV_YINIT) A.y[e] = r_y;
-            if (MODE == lmh::EV_DATA_FX1 || MODE == lmh::EV_YINIT_FX1) {
-                A.y[e] = r_y;
-                A.out[e] = r_out;
-            }
+        if (lane == 0 && (cnt_s | cnt_t)) {
+            atomicAdd(A.acci_std, cnt_s);
+            atomicAdd(A.acci_std + 1, cnt_t);
         }
     }
     if (MODE == lmh::EV_DATA_FX1 || MODE == lmh::EV_YINIT_FX1 || MODE == lmh::EV_ABSMAX) {
@@ -376,21 +592,145 @@ __global__ void __launch_bounds__(256) ev_kernel(const EvArgs A)
     }
 }
 
+// Event kernels of every active frame of a batch at update u.  Work items:
+// for a frame whose selection is a data subset, chunks of its events; for a
+// prior selection, ranges of `vitem` voxels of its prior dual step.  Warps
+// take items from one self-resetting counter; a block finds an item's frame
+// in a shared prefix table.
+template <int MODE, bool TWO_D, int G>
+__global__ void __launch_bounds__(256, G == 8 ? 2 : 3) ev_batch_kernel(const lmh::BatchEvArgs B)
+{
+    using T = ModeTraits<MODE>;
+    extern __shared__ float s_tab[];
+    __shared__ long long s_pre[lmh::BATCH_MAX + 1];
+    __shared__ long long s_eb[lmh::BATCH_MAX];
+    __shared__ long long s_ee[lmh::BATCH_MAX];
+    __shared__ int s_kind[lmh::BATCH_MAX];  // 0 none, 1 data, 2 prior
+    __shared__ float s_fx[lmh::BATCH_MAX];
+    const int cap = B.cap;
+    const int par = B.u & 1;
+    const int sidx = (B.slot0 + B.u) & 1;
+    if (threadIdx.x < cap) {
+        const int s = threadIdx.x;
+        long long items = 0, eb = 0, ee = 0;
+        int kind = 0;
+        float fxs = 1.0f;
+        if (B.active[s]) {
+            const EvArgs& A = B.slots[s];
+            const int sel = B.seqs[(size_t)s * B.seq_stride + B.u];
+            if (sel >= A.n_subsets) {
+                if (T::prior_branch) {
+                    kind = 2;
+                    items = ((long long)A.G.V + B.vitem - 1) / B.vitem;
+                }
+            } else {
+                kind = 1;
+                eb = A.sub_off[sel];
+                ee = A.sub_off[sel + 1];
+                items = (ee - eb + A.chunk - 1) / A.chunk;
+                if (T::back_fx) {
+                    const float vmax = __uint_as_float(A.maxbits_base[sidx]);
+                    fxs = ldexpf(1.0f, fx_exponent(vmax, ee - eb, A.stepmax));
+                }
+            }
+        }
+        s_kind[s] = kind;
+        s_eb[s] = eb;
+        s_ee[s] = ee;
+        s_fx[s] = fxs;
+        s_pre[s + 1] = items;
+    }
+    const float* tab = nullptr;
+    float inv_dt = 0.0f;
+    if (T::traverse && B.tof_tab != nullptr) {
+        for (int k = threadIdx.x; k <= lmh::TOF_TAB_N; k += blockDim.x) s_tab[k] = B.tof_tab[k];
+        tab = s_tab;
+        inv_dt = (float)lmh::TOF_TAB_N / (2.0f * B.tof_W);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_pre[0] = 0;
+        for (int s = 0; s < cap; ++s) s_pre[s + 1] += s_pre[s];
+    }
+    __syncthreads();
+    const long long total = s_pre[cap];
+    const int lane = threadIdx.x & 31;
+    const long long total_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (;;) {
+        unsigned long long cc = 0;
+        if (lane == 0) cc = atomicAdd(B.queue, 1ULL);
+        const long long c = (long long)__shfl_sync(FULL, cc, 0);
+        if (c >= total) break;
+        int s = 0;
+        while (s_pre[s + 1] <= c) ++s;
+        const long long local = c - s_pre[s];
+        const EvArgs& A = B.slots[s];
+        if (s_kind[s] == 1) {
+            const int64_t e0 = s_eb[s] + local * A.chunk;
+            const int nev = (int)min((long long)A.chunk, s_ee[s] - e0);
+            float wmax = 0.0f;
+            unsigned long long cs = 0, ct = 0;
+            const bool has_yf = A.xbyf[par] != nullptr;
+            event_chunk<MODE, TWO_D, G>(A, A.xb[par], A.xbyf[par], has_yf, e0, nev, tab, inv_dt, s_fx[s], wmax, cs, ct);
+            if (MODE == lmh::EV_DATA_FX1) {
+                float mm = wmax;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mm = fmaxf(mm, __shfl_xor_sync(FULL, mm, o));
+                if (lane == 0 && mm > 0.0f) atomicMax(A.maxbits_base + sidx, __float_as_uint(mm));
+            }
+        } else if (T::prior_branch && s_kind[s] == 2) {
+            const long long j0 = local * B.vitem;
+            const long long j1 = min((long long)A.G.V, j0 + B.vitem);
+            prior_range(A, A.xb[par], A.wpar[B.u], j0, j1, lane, 32);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned d = atomicAdd(B.done, 1u);
+        if (d == (unsigned)total_warps - 1) {
+            *B.queue = 0ULL;
+            *B.done = 0u;
+        }
+    }
+}
+
+size_t ev_smem(const EvArgs& a) { return a.tof_tab ? (size_t)(lmh::TOF_TAB_N + 1) * sizeof(float) : 0; }
+
 template <int MODE, bool TWO_D>
 int launch_mode(const EvArgs& a, int grid, cudaStream_t st)
 {
-    ev_kernel<MODE, TWO_D><<<grid, 256, 0, st>>>(a);
+    switch (a.group) {
+        case 8:
+            ev_kernel<MODE, TWO_D, 8><<<grid, 256, ev_smem(a), st>>>(a);
+            break;
+        case 32:
+            ev_kernel<MODE, TWO_D, 32><<<grid, 256, ev_smem(a), st>>>(a);
+            break;
+        default:
+            ev_kernel<MODE, TWO_D, 16><<<grid, 256, ev_smem(a), st>>>(a);
+            break;
+    }
     lmh::count_launch();
     return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
+}
+
+template <int MODE, bool TWO_D, int G>
+int occupancy_grid_g()
+{
+    int bps = 0;
+    const size_t smem = (size_t)(lmh::TOF_TAB_N + 1) * sizeof(float);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ev_kernel<MODE, TWO_D, G>, 256, smem) != cudaSuccess ||
+        bps < 1)
+        bps = 1;
+    return bps * lmh::num_sms();
 }
 
 template <int MODE, bool TWO_D>
 int occupancy_grid()
 {
-    int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ev_kernel<MODE, TWO_D>, 256, 0) != cudaSuccess || bps < 1)
-        bps = 1;
-    return bps * lmh::num_sms();
+    // the grid is sized for the most register-hungry group width
+    return std::min(occupancy_grid_g<MODE, TWO_D, 8>(),
+                    std::min(occupancy_grid_g<MODE, TWO_D, 16>(), occupancy_grid_g<MODE, TWO_D, 32>()));
 }
 
 // Sensitivity image: every canonical LOR, TOF-summed sample weights.
@@ -452,6 +792,112 @@ int launch_events(int mode, bool two_d, const EvArgs& a, int grid, cudaStream_t 
         LM_CASE(EV_COUNT)
         default:
             return LM_ERR_INVALID_ARG;
+    }
+#undef LM_CASE
+}
+
+template <int MODE, bool TWO_D>
+int launch_batch_mode(int group, const BatchEvArgs& b, int grid, cudaStream_t st)
+{
+    const size_t smem = b.tof_tab ? (size_t)(TOF_TAB_N + 1) * sizeof(float) : 0;
+    switch (group) {
+        case 8:
+            ev_batch_kernel<MODE, TWO_D, 8><<<grid, 256, smem, st>>>(b);
+            break;
+        case 32:
+            ev_batch_kernel<MODE, TWO_D, 32><<<grid, 256, smem, st>>>(b);
+            break;
+        default:
+            ev_batch_kernel<MODE, TWO_D, 16><<<grid, 256, smem, st>>>(b);
+            break;
+    }
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
+}
+
+int launch_events_batch(int mode, bool two_d, int group, const BatchEvArgs& b, int grid, cudaStream_t st)
+{
+    switch (mode) {
+        case EV_DATA:
+            return two_d ? launch_batch_mode<EV_DATA, true>(group, b, grid, st)
+                         : launch_batch_mode<EV_DATA, false>(group, b, grid, st);
+        case EV_DATA_FX1:
+            return two_d ? launch_batch_mode<EV_DATA_FX1, true>(group, b, grid, st)
+                         : launch_batch_mode<EV_DATA_FX1, false>(group, b, grid, st);
+        case EV_BACK_FX:
+            return two_d ? launch_batch_mode<EV_BACK_FX, true>(group, b, grid, st)
+                         : launch_batch_mode<EV_BACK_FX, false>(group, b, grid, st);
+        default:
+            return LM_ERR_INVALID_ARG;
+    }
+}
+
+template <int MODE, bool TWO_D>
+int batch_occupancy(int group)
+{
+    int g = 1 << 30;
+    const size_t smem = (size_t)(TOF_TAB_N + 1) * sizeof(float);
+    int bps = 0;
+    if ((group == 8 || group == 0) &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ev_batch_kernel<MODE, TWO_D, 8>, 256, smem) == cudaSuccess)
+        g = std::min(g, std::max(1, bps));
+    if ((group == 16 || group == 0) &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ev_batch_kernel<MODE, TWO_D, 16>, 256, smem) == cudaSuccess)
+        g = std::min(g, std::max(1, bps));
+    if ((group == 32 || group == 0) &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ev_batch_kernel<MODE, TWO_D, 32>, 256, smem) == cudaSuccess)
+        g = std::min(g, std::max(1, bps));
+    if (g == (1 << 30)) g = 1;
+    return g * num_sms();
+}
+
+int ev_batch_grid(int mode, bool two_d, int group)
+{
+    switch (mode) {
+        case EV_DATA:
+            return two_d ? batch_occupancy<EV_DATA, true>(group) : batch_occupancy<EV_DATA, false>(group);
+        case EV_DATA_FX1:
+            return two_d ? batch_occupancy<EV_DATA_FX1, true>(group) : batch_occupancy<EV_DATA_FX1, false>(group);
+        case EV_BACK_FX:
+            return two_d ? batch_occupancy<EV_BACK_FX, true>(group) : batch_occupancy<EV_BACK_FX, false>(group);
+        default:
+            return num_sms();
+    }
+}
+
+template <int MODE, bool TWO_D>
+int occupancy_grid_for(int group)
+{
+    switch (group) {
+        case 8:
+            return occupancy_grid_g<MODE, TWO_D, 8>();
+        case 32:
+            return occupancy_grid_g<MODE, TWO_D, 32>();
+        case 16:
+            return occupancy_grid_g<MODE, TWO_D, 16>();
+        default:
+            return occupancy_grid<MODE, TWO_D>();
+    }
+}
+
+// Resident blocks x SMs of the event kernel with `group` lanes per event.
+int ev_grid_g(int mode, bool two_d, int group)
+{
+#define LM_CASE(M) \
+    case M:        \
+        return two_d ? occupancy_grid_for<M, true>(group) : occupancy_grid_for<M, false>(group);
+    switch (mode) {
+        LM_CASE(EV_FWD)
+        LM_CASE(EV_BACK)
+        LM_CASE(EV_BACK_FX)
+        LM_CASE(EV_DATA)
+        LM_CASE(EV_DATA_FX1)
+        LM_CASE(EV_YINIT)
+        LM_CASE(EV_YINIT_FX1)
+        LM_CASE(EV_ABSMAX)
+        LM_CASE(EV_COUNT)
+        default:
+            return num_sms();
     }
 #undef LM_CASE
 }

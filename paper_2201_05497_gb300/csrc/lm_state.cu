@@ -50,8 +50,11 @@ struct lm_state_s {
     unsigned* done;
     float* redf;
     double* redd;
+    float* tof_tab;   // tabulated TOF kernel (TOF_TAB_N + 1 floats)
     size_t scr_bytes;
     int grid_ev, grid_fx, chunk;
+    int group;          // lanes per event of the event kernels
+    double tune_ms[3];  // autotuner: forward projection of subset 0 with 8, 16, 32 lanes
     cudaStream_t cap_stream;
     cudaGraphExec_t exec;
     bool have_graph;
@@ -108,7 +111,9 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
     unsigned* done = c.take<unsigned>(16);
     float* redf = c.take<float>((2 * 1024 + 16) * 4);
     double* redd = c.take<double>(objective_scratch_bytes());
+    float* tof_tab = c.take<float>((size_t)(TOF_TAB_N + 1) * 4);
     if (st) {
+        st->tof_tab = tof_tab;
         st->x[0] = x0; st->x[1] = x1; st->xyf[0] = y0; st->xyf[1] = y1;
         st->z = z; st->zc = zc; st->T = T; st->w[0] = w0; st->w[1] = w1;
         st->acc_std = acc_std; st->acc_yf = acc_yf; st->acci_std = ai_std; st->acci_yf = ai_yf;
@@ -145,6 +150,8 @@ EvArgs base_ev_args(const lm_state* st)
     a.s_prior = (float)(st->gamma * (double)st->P.rho / st->knorm);
     a.beta = st->P.beta;
     a.ndim = st->ndim;
+    a.tof_tab = st->tof.n_bins > 0 ? st->tof_tab : nullptr;
+    a.group = st->group;
     return a;
 }
 
@@ -306,6 +313,57 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     return LM_OK;
 }
 
+// Autotuner: times the forward projection of subset 0 (x of the first
+// update, both layouts) with 8, 16 and 32 lanes per event and keeps the
+// fastest width.  Output goes to the per-event scratch; state is unchanged.
+int autotune_group(lm_state* st, cudaStream_t s)
+{
+    st->tune_ms[0] = st->tune_ms[1] = st->tune_ms[2] = 0.0;
+    const int64_t n0 = st->sub_off_h[1] - st->sub_off_h[0];
+    if (n0 <= 0) return LM_OK;
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0));
+    LM_CUDA(cudaEventCreate(&e1));
+    const int widths[3] = {8, 16, 32};
+    double best = 1e30;
+    int best_g = 16;
+    for (int w = 0; w < 3; ++w) {
+        EvArgs a = base_ev_args(st);
+        a.group = widths[w];
+        a.x_std = st->x[0];
+        a.x_yf = st->xyf[0];
+        a.out = st->scr;
+        a.e_begin = st->sub_off_h[0];
+        a.e_end = st->sub_off_h[1];
+        a.queue = nullptr;
+        a.done = nullptr;
+        float tot = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, s);
+            int rc = launch_events(EV_FWD, st->two_d, a, ev_grid_g(EV_FWD, st->two_d, widths[w]), s);
+            cudaEventRecord(e1, s);
+            if (rc) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return rc;
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;  // first run warms caches
+        }
+        st->tune_ms[w] = tot / 2.0;
+        if (st->tune_ms[w] < best) {
+            best = st->tune_ms[w];
+            best_g = widths[w];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st->group = best_g;
+    return LM_OK;
+}
+
 int choose_chunk(const lm_state* st)
 {
     int64_t maxsub = 0;
@@ -400,6 +458,12 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         }                                                                               \
     } while (0)
     LM_TRY(cudaMemcpyAsync(st->sub_off, sub_off_host, (size_t)(st->n + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (tof->n_bins > 0) {
+        std::vector<float> tab(TOF_TAB_N + 1);
+        tof_table(tof, tab.data());
+        LM_TRY(cudaMemcpyAsync(st->tof_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, s));
+        LM_TRY(cudaStreamSynchronize(s));
+    }
     if (P.knorm > 0.0) {
         st->knorm = P.knorm;
     } else if (st->ndim == 0) {
@@ -413,8 +477,17 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->grid_ev = ev_grid(st->det ? EV_DATA_FX1 : EV_DATA, st->two_d);
     st->grid_fx = ev_grid(EV_BACK_FX, st->two_d);
     st->chunk = choose_chunk(st);
+    st->group = (P.group == 8 || P.group == 16 || P.group == 32) ? P.group : 16;
     rc = init_iteration(st, x0, s);
     if (rc) return fail(rc);
+    if (P.group == 0) {
+        rc = autotune_group(st, s);
+        if (rc) return fail(rc);
+    }
+    // the event kernels run with as many resident blocks as the chosen width allows
+    st->grid_ev = ev_grid_g(st->det ? EV_DATA_FX1 : EV_DATA, st->two_d, st->group);
+    st->grid_fx = ev_grid_g(EV_BACK_FX, st->two_d, st->group);
+    st->chunk = choose_chunk(st);
     LM_TRY(cudaStreamSynchronize(s));
 #undef LM_TRY
     *out = st;
@@ -580,7 +653,7 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
         a.queue = nullptr;
         a.done = nullptr;
         a.chunk = 32;
-        int rc = launch_events(EV_FWD, st->two_d, a, ev_grid(EV_FWD, st->two_d), s);
+        int rc = launch_events(EV_FWD, st->two_d, a, ev_grid_g(EV_FWD, st->two_d, st->group), s);
         LM_CHECK(rc == LM_OK, rc, "objective projection failed");
     }
     double parts[3];
@@ -600,6 +673,16 @@ int lmspdhg_info(lm_state* st, int64_t* n_updates, double* gamma, double* knorm)
     return LM_OK;
 }
 
+int lmspdhg_tuning(lm_state* st, int32_t* group, double* ms3)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    if (group) *group = st->group;
+    if (ms3)
+        for (int k = 0; k < 3; ++k) ms3[k] = st->tune_ms[k];
+    return LM_OK;
+}
+
 int lmspdhg_destroy(lm_state* st)
 {
     clear_error();
@@ -607,6 +690,270 @@ int lmspdhg_destroy(lm_state* st)
     if (st->exec) cudaGraphExecDestroy(st->exec);
     cudaStreamDestroy(st->cap_stream);
     delete st;
+    return LM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched epochs: several frames (states of the same scanner, grid, TOF
+// kernel, subset count and mode) advance by one epoch in one captured graph
+// whose kernels spread work over all occupied slots.  The per-slot argument
+// tables live in a caller workspace; filling or emptying a slot rewrites its
+// table entry only, so the same graph serves any occupancy and frames can
+// join or leave between epochs.
+// ---------------------------------------------------------------------------
+struct lm_batch_s {
+    int cap = 0;
+    int n = 0;
+    lm_state* slot[BATCH_MAX] = {};
+    lm_state* ref = nullptr;  // a state fixing the shared configuration
+    EvArgs* d_ev = nullptr;
+    ImgArgs* d_im = nullptr;
+    int* d_active = nullptr;
+    uint16_t* d_seqs = nullptr;
+    unsigned long long* d_queue = nullptr;
+    unsigned* d_done = nullptr;
+    std::vector<EvArgs> h_ev;
+    std::vector<ImgArgs> h_im;
+    std::vector<int> h_active;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool have_graph = false;
+    int64_t graph_nodes = 0;
+};
+
+namespace {
+
+struct BatchLayout {
+    size_t ev, im, active, seqs, ctr, total;
+};
+
+BatchLayout batch_layout(int cap, int n)
+{
+    BatchLayout L;
+    size_t off = 0;
+    L.ev = off;
+    off += align_up(sizeof(EvArgs) * (size_t)cap);
+    L.im = off;
+    off += align_up(sizeof(ImgArgs) * (size_t)cap);
+    L.active = off;
+    off += align_up(sizeof(int) * (size_t)cap);
+    L.seqs = off;
+    off += align_up(sizeof(uint16_t) * (size_t)cap * 2 * n);
+    L.ctr = off;
+    off += 256;
+    L.total = off + 256;
+    return L;
+}
+
+bool same_config(const lm_state* a, const lm_state* b)
+{
+    for (int d = 0; d < 3; ++d)
+        if (a->g.n[d] != b->g.n[d]) return false;
+    return a->n == b->n && a->two_d == b->two_d && a->det == b->det && a->kahan == b->kahan &&
+           a->tof.n_bins == b->tof.n_bins && a->tof.sigma_mm == b->tof.sigma_mm && a->tof.bin_mm == b->tof.bin_mm &&
+           a->tof.n_sigma == b->tof.n_sigma && a->G.n_det == b->G.n_det && a->group == b->group;
+}
+
+void fill_slot(lm_batch* b, int s, lm_state* st)
+{
+    EvArgs a = base_ev_args(st);
+    a.queue = nullptr;
+    a.done = nullptr;
+    a.seq = b->d_seqs + (size_t)s * 2 * b->n;
+    a.xb[0] = st->x[0];
+    a.xb[1] = st->x[1];
+    a.xbyf[0] = st->xyf[0];
+    a.xbyf[1] = st->xyf[1];
+    a.maxbits_base = st->maxbits;
+    if (!st->det) {
+        a.acc_std = st->acc_std;
+        a.acc_yf = st->acc_yf;
+    } else {
+        a.acci_std = st->acci_std;
+        a.acci_yf = st->acci_yf;
+        a.out = st->scr;
+        a.vin = st->scr;
+    }
+    ImgArgs im = base_img_args(st);
+    im.mode = IP_UPDATE;
+    im.seq = b->d_seqs + (size_t)s * 2 * b->n;
+    im.slot0 = 0;
+    im.xbuf[0] = st->x[0];
+    im.xbuf[1] = st->x[1];
+    im.xbuf_yf[0] = st->xyf[0];
+    im.xbuf_yf[1] = st->xyf[1];
+    im.wpar_w = st->wpar;
+    im.wbase = st->wbase;
+    b->h_ev[s] = a;
+    b->h_im[s] = im;
+}
+
+int launch_batch_epoch(lm_batch* b, cudaStream_t s)
+{
+    const lm_state* r = b->ref;
+    const int count = 2 * b->n;
+    BatchImgArgs bi;
+    bi.slots = b->d_im;
+    bi.active = b->d_active;
+    bi.cap = b->cap;
+    bi.u = 0;
+    bi.tiles_per_slot = image_tiles(&r->g);
+    launch_wpar_batch(bi, count, s);
+    BatchEvArgs be;
+    std::memset(&be, 0, sizeof(be));
+    be.slots = b->d_ev;
+    be.active = b->d_active;
+    be.seqs = b->d_seqs;
+    be.seq_stride = count;
+    be.cap = b->cap;
+    be.slot0 = 0;
+    be.queue = b->d_queue;
+    be.done = (unsigned*)(b->d_queue + 1);
+    be.tof_tab = r->tof.n_bins > 0 ? r->tof_tab : nullptr;
+    be.tof_W = r->G.W;
+    be.vitem = 2048;
+    const int g_ev = ev_batch_grid(r->det ? EV_DATA_FX1 : EV_DATA, r->two_d, r->group);
+    const int g_fx = ev_batch_grid(EV_BACK_FX, r->two_d, r->group);
+    const int g_im = image_batch_grid(&r->g, b->cap);
+    for (int u = 0; u < count; ++u) {
+        be.u = u;
+        bi.u = u;
+        int rc;
+        if (!r->det) {
+            rc = launch_events_batch(EV_DATA, r->two_d, r->group, be, g_ev, s);
+        } else {
+            rc = launch_events_batch(EV_DATA_FX1, r->two_d, r->group, be, g_ev, s);
+            if (!rc) rc = launch_events_batch(EV_BACK_FX, r->two_d, r->group, be, g_fx, s);
+        }
+        LM_CHECK(rc == LM_OK, rc, "batched event kernel launch failed");
+        launch_image_batch(bi, g_im, s);
+    }
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lmspdhg_batch_bytes(int32_t capacity, int32_t n_subsets)
+{
+    if (capacity < 1 || capacity > BATCH_MAX || n_subsets < 1) return 0;
+    return batch_layout(capacity, n_subsets).total;
+}
+
+int lmspdhg_batch_create(lm_batch** out, int32_t capacity, int32_t n_subsets, void* buf, size_t bytes,
+                         void* stream)
+{
+    clear_error();
+    LM_CHECK(out != nullptr, LM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    LM_CHECK(capacity >= 1 && capacity <= BATCH_MAX, LM_ERR_INVALID_ARG, "capacity must be in [1, %d]", BATCH_MAX);
+    LM_CHECK(n_subsets >= 1, LM_ERR_INVALID_ARG, "n_subsets must be >= 1");
+    const BatchLayout L = batch_layout(capacity, n_subsets);
+    LM_CHECK(buf != nullptr && bytes >= L.total, LM_ERR_NOMEM, "batch buffer needs %zu bytes", L.total);
+    lm_batch* b = new lm_batch();
+    b->cap = capacity;
+    b->n = n_subsets;
+    char* base = (char*)(((uintptr_t)buf + 255) / 256 * 256);
+    b->d_ev = (EvArgs*)(base + L.ev);
+    b->d_im = (ImgArgs*)(base + L.im);
+    b->d_active = (int*)(base + L.active);
+    b->d_seqs = (uint16_t*)(base + L.seqs);
+    b->d_queue = (unsigned long long*)(base + L.ctr);
+    b->h_ev.assign(capacity, EvArgs());
+    b->h_im.assign(capacity, ImgArgs());
+    b->h_active.assign(capacity, 0);
+    cudaStream_t s = S(stream);
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMemsetAsync(base, 0, L.total - 256, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+        delete b;
+        set_error("batch initialisation failed");
+        return LM_ERR_CUDA;
+    }
+    *out = b;
+    return LM_OK;
+}
+
+int lmspdhg_batch_set(lm_batch* b, int32_t slot, lm_state* st, void* stream)
+{
+    clear_error();
+    LM_CHECK(b != nullptr && slot >= 0 && slot < b->cap, LM_ERR_INVALID_ARG, "bad batch or slot");
+    cudaStream_t s = S(stream);
+    if (st != nullptr) {
+        LM_CHECK(st->n == b->n, LM_ERR_INVALID_ARG, "state has %d subsets, batch %d", st->n, b->n);
+        LM_CHECK(b->ref == nullptr || same_config(b->ref, st), LM_ERR_INVALID_ARG,
+                 "state differs from the batch's grid, TOF kernel or mode");
+        LM_CHECK(st->xpar == 0 && (st->n_updates & 1) == 0, LM_ERR_INVALID_ARG,
+                 "a state joins a batch at an even update count");
+        for (int k = 0; k < b->cap; ++k)
+            LM_CHECK(k == slot || b->slot[k] != st, LM_ERR_INVALID_ARG, "state is already in slot %d", k);
+        if (b->ref == nullptr) b->ref = st;
+        fill_slot(b, slot, st);
+        b->slot[slot] = st;
+        b->h_active[slot] = 1;
+        LM_CUDA(cudaMemcpyAsync(b->d_ev + slot, &b->h_ev[slot], sizeof(EvArgs), cudaMemcpyHostToDevice, s));
+        LM_CUDA(cudaMemcpyAsync(b->d_im + slot, &b->h_im[slot], sizeof(ImgArgs), cudaMemcpyHostToDevice, s));
+    } else {
+        b->slot[slot] = nullptr;
+        b->h_active[slot] = 0;
+    }
+    LM_CUDA(cudaMemcpyAsync(b->d_active + slot, &b->h_active[slot], sizeof(int), cudaMemcpyHostToDevice, s));
+    LM_CUDA(cudaStreamSynchronize(s));
+    return LM_OK;
+}
+
+int lmspdhg_batch_epoch(lm_batch* b, const uint16_t* seqs_host, void* stream)
+{
+    clear_error();
+    LM_CHECK(b != nullptr && seqs_host != nullptr, LM_ERR_INVALID_ARG, "NULL argument");
+    const int count = 2 * b->n;
+    int active = 0;
+    for (int k = 0; k < b->cap; ++k) {
+        if (!b->h_active[k]) continue;
+        ++active;
+        for (int u = 0; u < count; ++u)
+            LM_CHECK(seqs_host[(size_t)k * count + u] <= b->n, LM_ERR_INVALID_ARG, "slot %d: selection out of range", k);
+    }
+    if (active == 0) return LM_OK;
+    cudaStream_t s = S(stream);
+    if (!b->have_graph) {
+        cudaGraph_t graph = nullptr;
+        LM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t before = launch_total();
+        int rc = launch_batch_epoch(b, b->cap_stream);
+        b->graph_nodes = launch_total() - before;
+        count_launch(-b->graph_nodes);
+        cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(ce));
+        b->have_graph = true;
+    }
+    LM_CUDA(cudaMemcpyAsync(b->d_seqs, seqs_host, (size_t)b->cap * count * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                            s));
+    LM_CUDA(cudaGraphLaunch(b->exec, s));
+    count_launch(b->graph_nodes);
+    for (int k = 0; k < b->cap; ++k)
+        if (b->h_active[k]) b->slot[k]->n_updates += count;
+    return LM_OK;
+}
+
+int lmspdhg_batch_destroy(lm_batch* b)
+{
+    clear_error();
+    if (!b) return LM_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
     return LM_OK;
 }
 

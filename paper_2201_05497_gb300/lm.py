@@ -50,10 +50,16 @@ class lm_events(C.Structure):
 class lm_params(C.Structure):
     _fields_ = [("beta", C.c_float), ("gamma", C.c_float), ("rho", C.c_float), ("knorm", C.c_double),
                 ("knorm_iters", C.c_int32), ("n_subsets", C.c_int32), ("deterministic", C.c_int32),
-                ("kahan", C.c_int32)]
+                ("kahan", C.c_int32), ("group", C.c_int32)]
 
 
 _lib = None
+
+
+class lm_server_config(C.Structure):
+    _fields_ = [("beta", C.c_float), ("rho", C.c_float), ("knorm", C.c_double), ("n_subsets", C.c_int32),
+                ("epochs", C.c_int32), ("max_slots", C.c_int32), ("deterministic", C.c_int32),
+                ("kahan", C.c_int32), ("group", C.c_int32), ("max_events", C.c_int64)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -97,11 +103,24 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lmspdhg_info": ([V, P(I64), P(D), P(D)], C.c_int),
         "lmspdhg_destroy": ([V], C.c_int),
         "lmspdhg_reinit": ([V, V, V], C.c_int),
+        "lmspdhg_tuning": ([V, P(I32), P(D)], C.c_int),
         "lmspdhg_profile": ([V, P(C.c_uint16), I32, P(D), P(I64), V], C.c_int),
         "lm_kernel_launches": ([], I64),
         "lm_traversal_stats": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, SZ, P(I64), P(I64), V],
                                C.c_int),
         "lm_probe_l2": ([V, SZ, I32, I32, P(D), V], C.c_int),
+        "lmspdhg_batch_bytes": ([I32, I32], SZ),
+        "lmspdhg_batch_create": ([P(V), I32, I32, V, SZ, V], C.c_int),
+        "lmspdhg_batch_set": ([V, I32, V, V], C.c_int),
+        "lmspdhg_batch_epoch": ([V, P(C.c_uint16), V], C.c_int),
+        "lmspdhg_batch_destroy": ([V], C.c_int),
+        "lm_server_frame_bytes": ([P(lm_grid), I64, I32, I32], SZ),
+        "lm_server_create": ([P(V), P(lm_scanner), P(lm_grid), P(lm_tof), V, P(lm_server_config), V, SZ],
+                             C.c_int),
+        "lm_server_submit": ([V, V, V, V, V, V, I64, F, P(C.c_uint16), P(I64)], C.c_int),
+        "lm_server_wait": ([V, I64, V, P(D), P(D), I32], C.c_int),
+        "lm_server_stats": ([V, P(I64), P(I64), P(I64), P(SZ)], C.c_int),
+        "lm_server_destroy": ([V], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -338,7 +357,8 @@ class LMSPDHG:
 
     def __init__(self, geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x0: torch.Tensor, *,
                  beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
-                 knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, stream=None):
+                 knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
+                 stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.n_subsets = n_subsets
@@ -346,7 +366,8 @@ class LMSPDHG:
         if nbytes == 0:
             raise LMError(1, "invalid state size")
         self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=x0.device)
-        self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan))
+        self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan),
+                                int(group))
         self._ev = pe.events.desc()
         self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
         h = C.c_void_p()
@@ -413,9 +434,128 @@ class LMSPDHG:
         _check(load_library().lmspdhg_info(self.h, C.byref(n), C.byref(g), C.byref(k)))
         return dict(n_updates=n.value, gamma=g.value, knorm=k.value)
 
+    def tuning(self):
+        g = C.c_int32()
+        ms = (C.c_double * 3)()
+        _check(load_library().lmspdhg_tuning(self.h, C.byref(g), ms))
+        return dict(group=g.value, ms_g8=ms[0], ms_g16=ms[1], ms_g32=ms[2])
+
     def close(self):
         if getattr(self, "h", None):
             load_library().lmspdhg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several LMSPDHG states advanced together, one graph per epoch."""
+
+    def __init__(self, capacity: int, n_subsets: int, device="cuda", stream=None):
+        L = load_library()
+        self.capacity, self.n_subsets = int(capacity), int(n_subsets)
+        nbytes = L.lmspdhg_batch_bytes(self.capacity, self.n_subsets)
+        if nbytes == 0:
+            raise LMError(1, "invalid batch size")
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        h = C.c_void_p()
+        _check(L.lmspdhg_batch_create(C.byref(h), self.capacity, self.n_subsets, _ptr(self.buf), self.buf.numel(),
+                                      _stream(stream)))
+        self.h = h
+        self.states = [None] * self.capacity
+
+    def set(self, slot: int, state: Optional["LMSPDHG"], stream=None):
+        _check(load_library().lmspdhg_batch_set(self.h, int(slot), None if state is None else state.h,
+                                                _stream(stream)))
+        self.states[slot] = state
+
+    def epoch(self, seqs, stream=None):
+        """seqs: dict slot -> sequence (2n) or an array [capacity, 2n]."""
+        a = np.zeros((self.capacity, 2 * self.n_subsets), dtype=np.uint16)
+        if isinstance(seqs, dict):
+            for k, v in seqs.items():
+                a[k] = np.asarray(v, dtype=np.uint16)
+        else:
+            a[:] = np.asarray(seqs, dtype=np.uint16)
+        a = np.ascontiguousarray(a)
+        _check(load_library().lmspdhg_batch_epoch(self.h, a.ctypes.data_as(C.POINTER(C.c_uint16)),
+                                                  _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().lmspdhg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching reconstruction server (lm_server_*): frames are
+    submitted from host arrays and reconstructed by the library's worker
+    thread, several at a time, inside a caller-owned device pool."""
+
+    def __init__(self, geo: "Geometry", sens: torch.Tensor, *, beta: float, knorm: float, n_subsets: int,
+                 epochs: int, max_slots: int, max_events: int, pool_bytes: int, rho: float = 0.999,
+                 deterministic: bool = False, kahan: bool = True, group: int = 32):
+        L = load_library()
+        self.geo = geo
+        self.sens = sens
+        self.n_subsets, self.epochs = int(n_subsets), int(epochs)
+        self.cfg = lm_server_config(float(beta), float(rho), float(knorm), self.n_subsets, self.epochs,
+                                    int(max_slots), int(deterministic), int(kahan), int(group), int(max_events))
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=sens.device)
+        h = C.c_void_p()
+        _check(L.lm_server_create(C.byref(h), C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _ptr(sens),
+                                  C.byref(self.cfg), _ptr(self.pool), self.pool.numel()))
+        self.h = h
+
+    @staticmethod
+    def frame_bytes(geo: "Geometry", n_events: int, n_subsets: int, deterministic: bool = False) -> int:
+        return int(load_library().lm_server_frame_bytes(C.byref(geo.g), int(n_events), int(n_subsets),
+                                                        int(deterministic)))
+
+    def submit(self, det1, det2, tof, corr, contam, x0_value: float, seqs) -> int:
+        """Host arrays (numpy); seqs: uint16 [epochs, 2n].  Returns a ticket."""
+        d1 = np.ascontiguousarray(det1, dtype=np.int32)
+        d2 = np.ascontiguousarray(det2, dtype=np.int32)
+        tb = None if tof is None else np.ascontiguousarray(tof, dtype=np.int16)
+        cr = None if corr is None else np.ascontiguousarray(corr, dtype=np.float32)
+        ct = np.ascontiguousarray(contam, dtype=np.float32)
+        sq = np.ascontiguousarray(seqs, dtype=np.uint16).reshape(-1)
+        if sq.size != self.epochs * 2 * self.n_subsets:
+            raise ValueError("seqs must hold epochs * 2 * n_subsets selections")
+        t = C.c_int64()
+        hp = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+        _check(load_library().lm_server_submit(self.h, hp(d1), hp(d2), hp(tb), hp(cr), hp(ct), int(d1.size),
+                                               float(x0_value), sq.ctypes.data_as(C.POINTER(C.c_uint16)),
+                                               C.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000, want_x: bool = True):
+        """Returns (x or None, objective, latency_ms); raises LMError on
+        timeout (code LM_ERR_TIMEOUT, the ticket stays valid) or failure."""
+        x = np.empty(self.geo.V, dtype=np.float32) if want_x else None
+        obj, lat = C.c_double(), C.c_double()
+        _check(load_library().lm_server_wait(self.h, int(ticket), None if x is None else x.ctypes.data_as(C.c_void_p),
+                                             C.byref(obj), C.byref(lat), int(timeout_ms)))
+        return x, obj.value, lat.value
+
+    def stats(self):
+        c, f, q, u = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
+        _check(load_library().lm_server_stats(self.h, C.byref(c), C.byref(f), C.byref(q), C.byref(u)))
+        return {"completed": c.value, "in_flight": f.value, "queued": q.value, "pool_used": u.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().lm_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -452,7 +452,7 @@ def monte_carlo_events(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, seed: 
 
 
 def monte_carlo_events_torch(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, seed: int,
-                             contamination: float = 0.2, lor_att=None, device="cuda", batch: int = 1 << 24):
+                             contamination: float = 0.2, lor_att=None, device="cuda", batch: int = 0):
     """The Monte Carlo of `monte_carlo_events`, run with torch on `device`
     (for the large workloads: the 3D rejection rate is ~98%, which makes
     the numpy version slow).  Same physics and conventions; a different
@@ -463,6 +463,9 @@ def monte_carlo_events_torch(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, 
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     f64 = torch.float64
+    if batch <= 0:
+        # candidates per pass: the 3D acceptance is ~0.2 %, so large passes keep the launch count low
+        batch = 1 << (26 if n_events >= 1_000_000 else 22)
     is2d = sc.n_rings == 1
     tab = torch.from_numpy(sc.crystal_table().astype(np.float64)).to(device)
     zr = sc.ring_z()
@@ -705,6 +708,12 @@ def workload(name: str) -> Workload:
         g = Grid((70, 66, 24), (4.0, 4.0, 4.0))
         ph = Phantom.seeded(13, (120.0, 90.0, 40.0), (120.0, 90.0), 6)
         return Workload(name, sc, g, tof_400ps(27, tof_bin), ph, 200_000, 14, 0.03, 2)
+    if name == "3d_quad":
+        # row length a multiple of 4 (the image kernels' vector path), ragged 32-tiles in x and y
+        sc = Scanner(6, 112, 160.0, 8.0)
+        g = Grid((44, 36, 10), (5.0, 5.0, 4.0))
+        ph = Phantom.seeded(14, (80.0, 60.0, 18.0), (80.0, 60.0), 4)
+        return Workload(name, sc, g, tof_400ps(17, tof_bin), ph, 40_000, 7, 0.03, 2)
     raise KeyError(name)
 
 

@@ -1,0 +1,89 @@
+"""Batched epochs: frames of different sizes advanced together in one graph
+give the same results as each frame alone (bit-identical in deterministic
+mode, within float32 rounding otherwise), including a frame that joins the
+batch while others are in flight and a frame that leaves."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2201_05497_gb300 import synth as S
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lm():
+    from paper_2201_05497_gb300 import build, lm as _lm
+    build.build()
+    _lm.load_library()
+    return _lm
+
+
+def _frames(lm, name, sizes, det):
+    wl = S.workload(name)
+    geo = lm.Geometry.from_workload(wl)
+    lf = torch.from_numpy(S.lor_attenuation(wl.scanner, wl.phantom)).cuda()
+    sens = lm.sens(geo, lf)
+    out = []
+    for k, n in enumerate(sizes):
+        ev = S.monte_carlo_events(wl.scanner, wl.phantom, wl.tof, n, seed=100 + k,
+                                  lor_att=lf.cpu().numpy())
+        dev = lm.DeviceEvents.from_numpy(ev)
+        x0 = torch.full((geo.V,), 0.8 * n / float(sens.double().sum()), device="cuda")
+        out.append((dev, x0))
+    return wl, geo, sens, out
+
+
+def _state(lm, wl, geo, sens, dev, x0, det):
+    pe = lm.event_setup(geo, dev, wl.n_subsets)
+    return lm.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=wl.n_subsets, knorm=H.knorm_closed(wl.grid.n),
+                      deterministic=det, group=16)
+
+
+@pytest.mark.parametrize("name,sizes", [("3d_small", [40000, 7000, 23000]), ("3d_quad", [30000, 9000, 15000]),
+                                        ("2d_small", [20000, 3000])])
+@pytest.mark.parametrize("det", [True, False])
+def test_batch_equals_alone(lm, name, sizes, det):
+    wl, geo, sens, frames = _frames(lm, name, sizes, det)
+    n = wl.n_subsets
+    E = 3
+    seqs = [S.selection_sequence(n, 2 * n * E, seed=3 + k) for k in range(len(frames))]
+    alone = []
+    for k, (dev, x0) in enumerate(frames):
+        st = _state(lm, wl, geo, sens, dev, x0, det)
+        for e in range(E):
+            st.epoch(seqs[k][2 * n * e:2 * n * (e + 1)])
+        alone.append((st.x().cpu().numpy(), st.y().cpu().numpy(), st.z().cpu().numpy()))
+        st.close()
+    b = lm.Batch(4, n)
+    states = [_state(lm, wl, geo, sens, dev, x0, det) for dev, x0 in frames]
+    # frame 1 joins at epoch 1 (it then runs epochs 0..E-1 of its own sequence), slot 3 stays empty
+    b.set(0, states[0])
+    b.set(2, states[2])
+    done = {0: 0, 1: 0, 2: 0}
+    for e in range(E + 1):
+        if e == 1:
+            b.set(1, states[1])
+        active = {k: states_k for k, states_k in enumerate(states)
+                  if (k != 1 or e >= 1) and done[k] < E}
+        slots = {0: 0, 1: 1, 2: 2}
+        q = {}
+        for k in active:
+            q[slots[k]] = seqs[k][2 * n * done[k]:2 * n * (done[k] + 1)]
+        b.epoch(q)
+        for k in active:
+            done[k] += 1
+            if done[k] == E:
+                b.set(slots[k], None)   # the frame leaves the batch
+    for k, st in enumerate(states):
+        x, y, z = st.x().cpu().numpy(), st.y().cpu().numpy(), st.z().cpu().numpy()
+        if det:
+            np.testing.assert_array_equal(x, alone[k][0])
+            np.testing.assert_array_equal(y, alone[k][1])
+            np.testing.assert_array_equal(z, alone[k][2])
+        else:
+            assert H.rel_l2(x, alone[k][0]) < H.REL_EVENT
+            assert H.rel_l2(z, alone[k][2]) < H.REL_EVENT
+    b.close()

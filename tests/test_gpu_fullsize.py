@@ -1,0 +1,154 @@
+"""Parity at the benchmark's full sizes, in its launch configuration: the 3D
+short frame (1e7 events, 28 subsets) and the 3D long acquisition (5e8 events
+resident, 56 subsets).  The oracle cannot run these end to end, so the
+checks are (i) bit-exact integer outputs (event counts, subset split) on the
+whole list or on samples the oracle counts by brute force, (ii) per-event
+outputs the oracle computes one by one (the initial duals y_e = 1 - mu_e /
+((P^LM x0)_e + s_e) of sampled events, produced by the fused event kernel
+that the benchmark times), and (iii) properties that hold at any size
+(x >= 0, finite objective, bit-identical repeat in deterministic mode)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2201_05497_gb300 import synth as S
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lm():
+    from paper_2201_05497_gb300 import build, lm as _lm
+    build.build()
+    _lm.load_library()
+    return _lm
+
+
+def _frame(lm, name, n_events=None, seed=2):
+    wl = S.workload(name)
+    N = wl.n_events if n_events is None else n_events
+    att = S.lor_attenuation_torch(wl.scanner, wl.phantom, device="cuda")
+    raw = S.monte_carlo_events_torch(wl.scanner, wl.phantom, wl.tof, N, seed=seed, lor_att=att, device="cuda")
+    geo = lm.Geometry.from_workload(wl)
+    return wl, att, raw, geo
+
+
+def _sampled_yinit_check(wl, geo, ev_s, g, x0_val, perm_pos, mu_or):
+    """y of sampled events (fields in ev_s, positions perm_pos in the
+    subset-contiguous list) after the initialisation against the oracle."""
+    geo_o = O.Geometry.from_workload(wl)
+    E = O.EventArrays(ev_s["det1"], ev_s["det2"], ev_s["tof"], ev_s["corr"], ev_s["contam"])
+    x0 = np.full(geo.V, np.float32(x0_val), dtype=np.float32)
+    p_or = O.fwd(geo_o, E, x0)
+    y_or = 1.0 - mu_or / (p_or + E.contam.astype(np.float64))
+    y_gpu = g.y().cpu().numpy()[perm_pos]
+    # dy = mu p dp / (p + s)^2: the per-event projection tolerance carried through Eq. (yinit)
+    u = p_or + E.contam
+    sens_pos = O.fwd_position_sensitivity(geo_o, E, x0)
+    dp = H.REL_EVENT * np.abs(p_or) + H.position_eps(max(wl.grid.n)) * sens_pos
+    tol = mu_or * dp / u ** 2 + 4 * np.finfo(np.float32).eps * np.abs(y_or)
+    edge = O.tof_edge_distance(geo_o, E) < H.EDGE_MM
+    bad = (~edge) & (np.abs(y_gpu - y_or) > tol)
+    assert not bad.any(), f"{bad.sum()} sampled events: gpu {y_gpu[bad][:4]} oracle {y_or[bad][:4]}"
+
+
+def test_3d_short_full_size(lm):
+    wl, att, raw, geo = _frame(lm, "3d_short")
+    N, n = wl.n_events, wl.n_subsets
+    raw_dev = lm.DeviceEvents(raw.det1, raw.det2, raw.tof, raw.corr, raw.contam)
+    pe = lm.event_setup(geo, raw_dev, n)
+    raw_np = {k: getattr(raw, k).cpu().numpy() for k in ("det1", "det2", "tof", "corr", "contam")}
+    # (i) subset split bit-exact on the whole list; event counts bit-exact against the oracle
+    perm = O.subset_permutation(N, n)
+    inv = np.empty(N, dtype=np.int64)
+    inv[perm] = np.arange(N)
+    np.testing.assert_array_equal(pe.sub_off, O.subset_offsets(N, n))
+    for k in ("det1", "det2", "tof", "corr", "contam"):
+        np.testing.assert_array_equal(getattr(pe.events, k).cpu().numpy(), raw_np[k][inv])
+    mu_or = O.event_counts(raw_np["det1"], raw_np["det2"], raw_np["tof"])
+    np.testing.assert_array_equal(pe.mu.cpu().numpy().astype(np.int64), mu_or[inv].astype(np.int64))
+    # (ii) initial duals of 3000 sampled events, from the fused event kernel of the benchmark
+    sens = lm.sens(geo, att)
+    del att
+    x0_val = float(np.float32(0.8 * N / float(sens.double().sum().item())))
+    x0 = torch.full((geo.V,), x0_val, dtype=torch.float32, device="cuda")
+    kn = H.knorm_closed(wl.grid.n)
+    g = lm.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=n, knorm=kn)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(N, 3000, replace=False))
+    _sampled_yinit_check(wl, geo, {f: v[idx] for f, v in raw_np.items()}, g, x0_val, perm[idx], mu_or[idx])
+    # (iii) properties after one graph-replayed epoch
+    seq = S.selection_sequence(n, 2 * n, seed=3)
+    g.epoch(seq)
+    x = g.x()
+    assert bool(torch.isfinite(x).all()) and float(x.min()) >= 0.0
+    assert np.isfinite(g.objective())
+
+
+def test_3d_short_deterministic_repeat_full_size(lm):
+    """Deterministic mode at full size: a repeated frame (event set-up,
+    initialisation, one epoch) is bit-identical."""
+    wl, att, raw, geo = _frame(lm, "3d_short", seed=5)
+    n = wl.n_subsets
+    raw_dev = lm.DeviceEvents(raw.det1, raw.det2, raw.tof, raw.corr, raw.contam)
+    sens = lm.sens(geo, att)
+    del att
+    x0 = torch.full((geo.V,), 0.8 * wl.n_events / float(sens.double().sum().item()), device="cuda")
+    seq = S.selection_sequence(n, 2 * n, seed=3)
+    out = []
+    for _ in range(2):
+        pe = lm.event_setup(geo, raw_dev, n)
+        g = lm.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=n, knorm=H.knorm_closed(wl.grid.n),
+                       deterministic=True, group=16)
+        g.epoch(seq)
+        out.append((g.x().cpu().numpy(), g.y().cpu().numpy()))
+        g.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_3d_long_full_size(lm):
+    """5e8 events resident (24 B/event in the subset-contiguous lists):
+    event counts of sampled events by brute force over the whole list,
+    subset split of sampled positions, initial duals of sampled events, one
+    epoch of 112 updates."""
+    wl, att, raw, geo = _frame(lm, "3d_long")
+    N, n = wl.n_events, wl.n_subsets
+    raw_dev = lm.DeviceEvents(raw.det1, raw.det2, raw.tof, raw.corr, raw.contam)
+    pe = lm.event_setup(geo, raw_dev, n)
+    rng = np.random.default_rng(11)
+    pos = np.sort(rng.choice(N, 2000, replace=False))
+    off = O.subset_offsets(N, n)
+    k = np.searchsorted(off, pos, side="right") - 1
+    src = (pos - off[k]) * n + k                     # event index at each sampled position
+    pos_t = torch.from_numpy(pos).cuda()
+    src_t = torch.from_numpy(src).cuda()
+    for f in ("det1", "det2", "tof", "corr", "contam"):
+        assert torch.equal(getattr(pe.events, f)[pos_t], getattr(raw, f)[src_t])
+    np.testing.assert_array_equal(pe.sub_off, off)
+    # brute-force event counts of 50 sampled events over all 5e8 (canonical keys on the host)
+    d1 = raw.det1.cpu().numpy().astype(np.int64)
+    d2 = raw.det2.cpu().numpy().astype(np.int64)
+    tb = raw.tof.cpu().numpy().astype(np.int64)
+    sw = d1 > d2
+    key = np.where(sw, d2, d1) * (1 << 36) + np.where(sw, d1, d2) * 256 + (np.where(sw, -tb, tb) + 127)
+    del d1, d2, tb, sw
+    q50 = np.arange(50)
+    mu_or = np.array([np.count_nonzero(key == key[src[q]]) for q in q50], dtype=np.float64)
+    del key
+    mu_gpu = pe.mu[pos_t[:50]].cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(mu_gpu, mu_or)
+    sens = lm.sens(geo, att)
+    del att
+    x0_val = float(np.float32(0.8 * N / float(sens.double().sum().item())))
+    x0 = torch.full((geo.V,), x0_val, dtype=torch.float32, device="cuda")
+    g = lm.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=n, knorm=H.knorm_closed(wl.grid.n))
+    ev_s = {f: getattr(raw, f)[src_t[:50]].cpu().numpy() for f in ("det1", "det2", "tof", "corr", "contam")}
+    _sampled_yinit_check(wl, geo, ev_s, g, x0_val, pos[:50], mu_or)
+    seq = S.selection_sequence(n, 2 * n, seed=3)
+    g.epoch(seq)
+    x = g.x()
+    assert bool(torch.isfinite(x).all()) and float(x.min()) >= 0.0

@@ -73,7 +73,7 @@ def test_init_matches_oracle(lm, name, det):
     assert info["n_updates"] == 0 and abs(info["gamma"] - c.gamma) < 1e-7 * c.gamma
 
 
-@pytest.mark.parametrize("name", ["2d_small", "3d_small"])
+@pytest.mark.parametrize("name", ["2d_small", "3d_small", "3d_quad"])
 @pytest.mark.parametrize("sel", ["data", "prior"])
 def test_single_update_matches_oracle(lm, name, sel):
     c = Case(lm, name)
@@ -91,7 +91,7 @@ def test_single_update_matches_oracle(lm, name, sel):
     np.testing.assert_allclose(g.y().cpu().numpy()[c.perm], o.y, rtol=1e-4, atol=1e-4 * np.abs(o.y).max())
 
 
-@pytest.mark.parametrize("name,epochs", [("2d_small", 3), ("3d_small", 2), ("3d_mid", 2)])
+@pytest.mark.parametrize("name,epochs", [("2d_small", 3), ("3d_small", 2), ("3d_mid", 2), ("3d_quad", 2)])
 def test_epochs_match_oracle(lm, name, epochs):
     """Images after N epochs within 1e-3 relative L2 of the FP64 oracle;
     epochs are replayed from the captured CUDA graph."""
