@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="events in the oracle's timed sample")
     ap.add_argument("--knorm-iters", type=int, default=1000)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving run: a stream of dynamic frames through the continuous-batching server")
+    ap.add_argument("--frames", type=int, default=64, help="frames in the serving run")
+    ap.add_argument("--max-slots", type=int, default=16, help="frames on the GPU at once in the serving run")
     return ap.parse_args()
 
 
@@ -462,6 +466,161 @@ def run_gpu(args):
     return 0
 
 
+def serving_frames(wl, n_frames, device):
+    """The serving stream: frame k has N_k ~ log-uniform[1e5, 2e7] events
+    (seeded) of a phantom with seed 100 + k inside the workload's attenuating
+    cylinder (dynamic frames of one study share the attenuation map, so one
+    P^T 1 serves all).  Events are generated on the device and returned as
+    host arrays, the form a scanner host hands to the server."""
+    import torch
+    from paper_2201_05497_gb300 import synth as S
+    rng = np.random.default_rng(7)
+    sizes = np.exp(rng.uniform(np.log(1e5), np.log(2e7), n_frames)).round().astype(np.int64)
+    lor_att = S.lor_attenuation_torch(wl.scanner, wl.phantom, device=device)
+    frames = []
+    for k, n in enumerate(sizes):
+        ph = S.Phantom.seeded(100 + k, wl.phantom.body_axes, wl.phantom.att_axes, 8, mu_att=wl.phantom.mu_att)
+        ev = S.monte_carlo_events_torch(wl.scanner, ph, wl.tof, int(n), seed=100 + k, lor_att=lor_att, device=device)
+        frames.append(tuple(t.cpu().numpy() for t in (ev.det1, ev.det2, ev.tof, ev.corr, ev.contam)))
+        del ev
+    return frames, lor_att
+
+
+def run_serve(args):
+    """Serving: every frame of the stream reconstructed (E epochs) by the
+    continuous-batching server, against plain LM-SPDHG one frame at a time.
+    Throughput with all frames queued at t=0; latency (arrival to x on the
+    host) under Poisson arrivals at 0.8 x the one-at-a-time capacity."""
+    import torch
+    from paper_2201_05497_gb300 import build, lm as L, synth as S
+    build.build()
+    L.load_library()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = S.workload(args.workload)
+    n_sub, E = wl.n_subsets, args.epochs
+    geo = L.Geometry.from_workload(wl, device=dev)
+    t0 = time.perf_counter()
+    frames, lor_att = serving_frames(wl, args.frames, dev)
+    gen_s = time.perf_counter() - t0
+    sens = L.sens(geo, lor_att)
+    del lor_att
+    kn = L.knorm_fp64(geo, args.knorm_iters)
+    ssum = float(sens.double().sum().item())
+    seqs = [np.asarray(S.selection_sequence(n_sub, 2 * n_sub * E, seed=3 + k), dtype=np.uint16).reshape(E, -1)
+            for k in range(len(frames))]
+    x0v = [np.float32(0.8 * f[0].size / ssum) for f in frames]
+    n_ev = [int(f[0].size) for f in frames]
+    det = bool(args.deterministic)
+
+    # one frame at a time: host arrays -> device, set-up, create, E epochs, objective, x -> host
+    def one(k):
+        d1, d2, tb, cr, ct = (torch.from_numpy(a).to(dev, non_blocking=False) for a in frames[k])
+        pe = L.event_setup(geo, L.DeviceEvents(d1, d2, tb, cr, ct), n_sub)
+        st = L.LMSPDHG(geo, pe, sens, torch.full((geo.V,), float(x0v[k]), device=dev), beta=wl.beta,
+                       n_subsets=n_sub, knorm=kn, deterministic=det, kahan=True, group=32)
+        for e in range(E):
+            st.epoch(seqs[k][e])
+        obj = st.objective()
+        x = st.x().cpu().numpy()
+        st.close()
+        return x, obj
+
+    one(0)  # warm-up (graph capture paths, allocator)
+    torch.cuda.synchronize()
+    service = []
+    for k in range(len(frames)):
+        a = time.perf_counter()
+        one(k)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - a)
+    seq_total = sum(service)
+    cap_one = len(frames) / seq_total
+
+    free, _ = torch.cuda.mem_get_info()
+    fb_max = L.Server.frame_bytes(geo, max(n_ev), n_sub, det)
+    pool = int(min(0.6 * free, max(4 * fb_max, 48 << 30)))
+
+    def server():
+        return L.Server(geo, sens, beta=wl.beta, knorm=kn, n_subsets=n_sub, epochs=E, max_slots=args.max_slots,
+                        max_events=max(n_ev), pool_bytes=pool, deterministic=det, kahan=True, group=32)
+
+    def drain(srv, tickets):
+        out = {}
+        max_inflight = 0
+        while len(out) < len(tickets):
+            max_inflight = max(max_inflight, srv.stats()["in_flight"])
+            for k, t in enumerate(tickets):
+                if k in out:
+                    continue
+                try:
+                    out[k] = srv.wait(t, timeout_ms=1, want_x=True)
+                except L.LMError as e:
+                    if e.code != 5:
+                        raise
+        return out, max_inflight
+
+    def submit(srv, k):
+        d1, d2, tb, cr, ct = frames[k]
+        return srv.submit(d1, d2, tb, cr, ct, x0v[k], seqs[k])
+
+    # throughput: all frames queued at t = 0
+    srv = server()
+    drain(srv, [submit(srv, 0)])  # warm-up: graph capture of the batched epoch
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    tickets = [submit(srv, k) for k in range(len(frames))]
+    res, inflight_sat = drain(srv, tickets)
+    sat_s = time.perf_counter() - a
+    srv.close()
+    cap_srv = len(frames) / sat_s
+
+    # latency: Poisson arrivals at 0.8 x the one-at-a-time capacity
+    lam = 0.8 * cap_one
+    arr = np.cumsum(np.random.default_rng(11).exponential(1.0 / lam, len(frames)))
+    srv = server()
+    drain(srv, [submit(srv, 0)])
+    torch.cuda.synchronize()
+    tickets = []
+    a = time.perf_counter()
+    for k in range(len(frames)):
+        dt = arr[k] - (time.perf_counter() - a)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(submit(srv, k))
+    res2, inflight_poi = drain(srv, tickets)
+    srv.close()
+    lat = np.array([res2[k][2] for k in range(len(frames))])
+    # plain LM-SPDHG under the same arrivals: FIFO with the measured service times
+    done, lat_one = 0.0, []
+    for k in range(len(frames)):
+        start = max(arr[k], done)
+        done = start + service[k]
+        lat_one.append(1e3 * (done - arr[k]))
+    lat_one = np.array(lat_one)
+    out = {
+        "metric": "serving frames/sec and p99 latency", "value": cap_srv, "unit": "frames/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving: {len(frames)} frames of the {args.workload} scanner and grid, "
+                               f"N log-uniform[1e5, 2e7] (total {sum(n_ev)} events), {E} epochs each, "
+                               f"{n_sub} subsets, FP32 with Kahan z, "
+                               f"{'deterministic' if det else 'atomic'} back-projection",
+                   "max_slots": args.max_slots, "pool_bytes": pool},
+        "serving": {
+            "frames_per_s": cap_srv, "frames_per_s_one_at_a_time": cap_one, "speedup": cap_srv / cap_one,
+            "events_per_s": sum(n_ev) * (1 + E) / sat_s,
+            "max_in_flight_saturated": inflight_sat, "max_in_flight_poisson": inflight_poi,
+            "lambda_per_s": lam, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_one_at_a_time": float(np.percentile(lat_one, 50)),
+            "p99_ms_one_at_a_time": float(np.percentile(lat_one, 99)),
+            "latency": "submit of the host arrays to x copied back to the host; one-at-a-time latencies "
+                       "from a FIFO of its measured per-frame service times under the same arrivals",
+        },
+        "generate_s": gen_s,
+    }
+    print(json.dumps(out))
+    return 0
+
+
 def measured_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -475,6 +634,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_gpu(args)
 
 

@@ -208,6 +208,11 @@ typedef struct {
     int32_t group;        /* lanes per event in the event kernels: 8, 16 or 32;  */
                           /* 0: chosen at create by timing the forward projection */
                           /* of subset 0 with each width (autotuner)             */
+    int32_t image_kernel; /* image passes: 0 auto (TMA-staged where the grid has */
+                          /* nx, ny multiples of 4, nx >= 40, ny >= 36, with the  */
+                          /* prior's dual step fused in; plain loads otherwise),  */
+                          /* 1 plain loads, 2 TMA-staged (LM_ERR_INVALID_ARG if  */
+                          /* the grid does not allow it).  Same results.          */
 } lm_params;
 
 /* Device bytes the state needs (images, duals, per-event y and scratch). */
@@ -280,6 +285,10 @@ int lmspdhg_reinit(lm_state* st, const float* x0, void* stream);
  * after prior updates.  Synchronous. */
 int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, double* ms4, int64_t* n4,
                     void* stream);
+
+/* Which image-pass kernel the state uses: 1 plain loads, 2 TMA-staged with
+ * the prior's dual step fused in (lm_params.image_kernel). */
+int lmspdhg_image_kernel(lm_state* st, int32_t* kind);
 
 int lmspdhg_destroy(lm_state* st);
 

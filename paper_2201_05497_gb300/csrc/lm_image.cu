@@ -10,8 +10,10 @@
 // Image passes work on 32 x 32 (x, y) tiles of one z slice so that the
 // y-fastest copies are read and written through shared memory with
 // coalesced accesses in both layouts.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "lm_internal.h"
 
@@ -316,7 +318,7 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
                 two_sum(z0[q], dz[q], zh, e);
                 zl = kahan ? e : 0.0f;
                 A.x_keep[j] = x0[q];
-                xn = fmaxf(0.0f, x0[q] - tm[q] * (zh + zl));
+                xn = fmaxf(0.0f, fmaf(-tm[q], zh + zl, x0[q]));
             } else {
                 if (kahan) {
                     float e;
@@ -326,7 +328,7 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
                     zh = z0[q] + dz[q];
                 }
                 const float zbar = fmaf(dz[q], m.inv_p, zh + zl);  // z + dz/p_i
-                xn = fmaxf(0.0f, x0[q] - tm[q] * zbar);
+                xn = fmaxf(0.0f, fmaf(-tm[q], zbar, x0[q]));
             }
             zz[j] = zh;
             if (kahan) zc[j] = zl;
@@ -370,6 +372,450 @@ __global__ void __launch_bounds__(256) image_batch_kernel(const lmh::BatchImgArg
         const PassMode m = pass_mode(A, B.u);
         if (lt == 0 && threadIdx.x == 0 && threadIdx.y == 0) reset_next_slot(A, B.u);
         image_tile(A, m, B.u, tile_of(lt, A.n[0], A.n[1]), A.xbuf[par], A.xbuf[par ^ 1], A.xbuf_yf[par ^ 1], sm);
+    }
+}
+
+// ---- TMA-staged image passes ---------------------------------------------
+// A block owns a 32 x 32 column of the x-y plane and a run of z slices and
+// marches through them.  While slice z is computed, the tensor memory
+// accelerator fetches the inputs of slice z+1 into the other half of a
+// two-stage shared-memory ring (one thread issues the copies, an mbarrier
+// counts their bytes), so each block keeps a whole slice of loads in flight
+// without holding them in registers.  Data updates merge the accumulators
+// into z; prior updates fuse the prior's dual step (Alg. 2 line 15: w+ from
+// x over the tile and a one-voxel halo), dz = K^T(w+ - w) and the primal
+// step into the same pass, and the event kernel does nothing for them.
+// Needs rows of a multiple of 4 floats (16-byte tensor strides) and
+// nx >= 40, ny >= 36 (boxes inside the tensor); other grids use
+// image_pass_kernel.  Results equal image_pass_kernel's (and the event
+// kernel's prior step) bit for bit: same operations in the same order.
+
+constexpr int XHW = 40, XHH = 34;  // x halo box: x0-4 .. x0+35, y0-1 .. y0+32
+constexpr int WBW = 36, WBH = 33;  // w box: x0-4 .. x0+31, y0-1 .. y0+31 (per component)
+constexpr int EW = 33;             // region of w+: x0-1 .. x0+31, y0-1 .. y0+31
+constexpr int EWW = EW * EW;
+constexpr int TP = 33;             // pitch of the transposed tiles
+
+struct TmaLayout {  // byte offsets into dynamic shared memory
+    static constexpr int bars = 0;
+    static constexpr int xh = 128;  // ring of 3 x-halo slices
+    static constexpr int xh_sz = 5504;
+    static constexpr int stage = xh + 3 * xh_sz;  // 2 stages
+    static constexpr int stage_sz = 32768;
+    // prior stage: w (<= 3 components), T, z, zc
+    static constexpr int p_wc = 0, p_T = 14336, p_z = p_T + 4096, p_zc = p_z + 4096;
+    // data stage: acc_std, acc_yf (u64 when deterministic), x, T, z, zc
+    static constexpr int d_as = 0, d_ay = 8192, d_x = 16384, d_T = 20480, d_z = 24576, d_zc = 28672;
+    static constexpr int dbuf = stage + 2 * stage_sz;  // w+ - w (3 x 33 x 33 floats) / transposed acc_yf
+    static constexpr int dbuf_sz = 13184;
+    static constexpr int xo = dbuf + dbuf_sz;  // transposed x tile
+    static constexpr int xo_sz = 4224;
+    static constexpr int total = xo + xo_sz;
+};
+static_assert(TmaLayout::p_zc + 4096 <= TmaLayout::stage_sz, "prior stage");
+static_assert(TmaLayout::d_zc + 4096 <= TmaLayout::stage_sz, "data stage");
+static_assert(XHW * XHH * 4 <= TmaLayout::xh_sz && 3 * EWW * 4 <= TmaLayout::dbuf_sz &&
+                  TD * TP * 8 <= TmaLayout::dbuf_sz && TD * TP * 4 <= TmaLayout::xo_sz,
+              "buffers");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Orders this thread's earlier shared-memory accesses before later
+// asynchronous-proxy (TMA) accesses of the same memory.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// The maps live in global memory and are rewritten by the host when a state
+// is created (possibly at the address of a destroyed state's maps): make the
+// tensor-map proxy read the current contents before a copy uses them.
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+
+// Two-stage ring state: stage parities and the block's abort flag.
+struct Pipe {
+    uint64_t* bar;
+    uint32_t ph;
+    int* abort;
+};
+
+// Bounded wait for stage s; a wait that gives up marks the block aborted
+// and sets *err.  Ends with a block barrier, so the result is uniform.
+__device__ __forceinline__ bool stage_wait(Pipe& p, int s, unsigned* err)
+{
+    const uint32_t par = (p.ph >> s) & 1u;
+    bool ok = false;
+    for (int i = 0; i < (1 << 22) && !ok; ++i) ok = mbar_try_wait(p.bar + s, par);
+    p.ph ^= 1u << s;
+    if (!ok) {
+        *p.abort = 1;
+        if (err) atomicOr(err, 1u);
+    }
+    __syncthreads();
+    return *p.abort == 0;
+}
+
+struct Item {
+    int x0, y0, zb, ze;
+};
+
+__device__ __forceinline__ int64_t tma_items(const lmh::ImgArgs& A)
+{
+    const int ncol = ((A.n[0] + TD - 1) / TD) * ((A.n[1] + TD - 1) / TD);
+    return (int64_t)ncol * ((A.n[2] + A.zlen - 1) / A.zlen);
+}
+
+__device__ __forceinline__ Item item_of(const lmh::ImgArgs& A, int64_t it)
+{
+    const int ncx = (A.n[0] + TD - 1) / TD, ncol = ncx * ((A.n[1] + TD - 1) / TD);
+    const int col = (int)(it % ncol), ch = (int)(it / ncol);
+    Item r;
+    r.x0 = (col % ncx) * TD;
+    r.y0 = (col / ncx) * TD;
+    r.zb = ch * A.zlen;
+    r.ze = min(A.n[2], r.zb + A.zlen);
+    return r;
+}
+
+// Copies of one slice (thread 0).  Prior: x slices z (first only) and z+1
+// with halo, w(z) with halo and, for slices the block owns, T, z, zc.
+// Data: both accumulators, x, T, z, zc of the tile.
+__device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, int xcur, int wp, uint8_t* sm, int s,
+                                            int z, int zs, const Item& I, bool first, uint64_t* bar)
+{
+    const lmh::TmaMaps* M = A.tm;
+    uint8_t* st = sm + TmaLayout::stage + s * TmaLayout::stage_sz;
+    const uint32_t tile = TD * TD * 4;
+    if (first) {
+        if (prior) {
+            tmap_acquire(&M->xh[xcur]);
+            tmap_acquire(&M->w[wp]);
+        } else {
+            tmap_acquire(&M->acc_std);
+            tmap_acquire(&M->acc_yf);
+            tmap_acquire(&M->xt[xcur]);
+        }
+        tmap_acquire(&M->T);
+        tmap_acquire(&M->z);
+        tmap_acquire(&M->zc);
+    }
+    fence_proxy_async();
+    if (prior) {
+        const bool own = z >= I.zb;
+        const uint32_t xb = XHW * XHH * 4, wb = (uint32_t)(WBW * WBH * A.ndim * 4);
+        const uint32_t bytes = xb * (first ? 2u : 1u) + wb + (own ? tile * (A.kahan ? 3u : 2u) : 0u);
+        mbar_expect_tx(bar + s, bytes);
+        const CUtensorMap* xm = &M->xh[xcur];
+        if (first) tma_load_3d(sm + TmaLayout::xh + ((z - zs) % 3) * TmaLayout::xh_sz, xm, I.x0 - 4, I.y0 - 1, z, bar + s);
+        tma_load_3d(sm + TmaLayout::xh + ((z + 1 - zs) % 3) * TmaLayout::xh_sz, xm, I.x0 - 4, I.y0 - 1, z + 1,
+                    bar + s);
+        tma_load_4d(st + TmaLayout::p_wc, &M->w[wp], I.x0 - 4, I.y0 - 1, z, 0, bar + s);
+        if (own) {
+            tma_load_3d(st + TmaLayout::p_T, &M->T, I.x0, I.y0, z, bar + s);
+            tma_load_3d(st + TmaLayout::p_z, &M->z, I.x0, I.y0, z, bar + s);
+            if (A.kahan) tma_load_3d(st + TmaLayout::p_zc, &M->zc, I.x0, I.y0, z, bar + s);
+        }
+    } else {
+        const uint32_t acc = A.det ? 2 * tile : tile;
+        mbar_expect_tx(bar + s, 2 * acc + 3 * tile + (A.kahan ? tile : 0u));
+        tma_load_3d(st + TmaLayout::d_as, &M->acc_std, I.x0, I.y0, z, bar + s);
+        tma_load_3d(st + TmaLayout::d_ay, &M->acc_yf, I.y0, I.x0, z, bar + s);
+        tma_load_3d(st + TmaLayout::d_x, &M->xt[xcur], I.x0, I.y0, z, bar + s);
+        tma_load_3d(st + TmaLayout::d_T, &M->T, I.x0, I.y0, z, bar + s);
+        tma_load_3d(st + TmaLayout::d_z, &M->z, I.x0, I.y0, z, bar + s);
+        if (A.kahan) tma_load_3d(st + TmaLayout::d_zc, &M->zc, I.x0, I.y0, z, bar + s);
+    }
+}
+
+// z update, zbar and the primal step at one voxel (same operations as
+// image_tile).
+__device__ __forceinline__ float primal_step(float x0, float tm, float z0, float zl0, float dz, float inv_p, bool kahan,
+                                             float& zh, float& zl)
+{
+    zl = 0.0f;
+    if (kahan) {
+        float e;
+        two_sum(z0, dz, zh, e);
+        zl = zl0 + e;
+    } else {
+        zh = z0 + dz;
+    }
+    const float zbar = fmaf(dz, inv_p, zh + zl);
+    return fmaxf(0.0f, fmaf(-tm, zbar, x0));
+}
+
+// Writes the transposed x tile of slice z to the y-fastest copy.
+__device__ __forceinline__ void store_x_yf(const lmh::ImgArgs& A, const float* XO, float* x_nxt_yf, const Item& I,
+                                           int z)
+{
+    const int nx = A.n[0], ny = A.n[1];
+    const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = wrow + 8 * k;  // x offset
+        const int ix = I.x0 + r, iy = I.y0 + lane;
+        if (ix < nx && iy < ny) x_nxt_yf[((int64_t)z * nx + ix) * ny + iy] = XO[lane * TP + r];
+    }
+}
+
+// Fused prior update for slice z of item I (z < I.zb: halo slice, only the
+// z component of w+ - w is kept for the next slice).
+__device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8_t* sm, int s, int z, int zs,
+                                            const Item& I, float* dprev, float* x_nxt_std, float* x_nxt_yf)
+{
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const int64_t V = A.V;
+    const bool hz = nz > 1;
+    const bool own = z >= I.zb;
+    const float* X0 = (const float*)(sm + TmaLayout::xh + ((z - zs) % 3) * TmaLayout::xh_sz);
+    const float* X1 = (const float*)(sm + TmaLayout::xh + ((z + 1 - zs) % 3) * TmaLayout::xh_sz);
+    const uint8_t* st = sm + TmaLayout::stage + s * TmaLayout::stage_sz;
+    const float* WC = (const float*)(st + TmaLayout::p_wc);
+    float* D = (float*)(sm + TmaLayout::dbuf);
+    float* XO = (float*)(sm + TmaLayout::xo);
+    float* wn = A.w_nxt[wp];
+    const float sp = A.s_prior, beta = A.beta;
+    // w+ = v / max(1, |v|/beta), v = w + S K x, over the tile and its -1 halo
+    for (int p = threadIdx.x; p < EWW; p += blockDim.x) {
+        const int ex = p % EW, ey = p / EW;
+        const int ix = I.x0 - 1 + ex, iy = I.y0 - 1 + ey;
+        float dx = 0.0f, dy = 0.0f, dzc = 0.0f;
+        if (ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
+            const int xb = ey * XHW + ex + 3;
+            const int wb = ey * WBW + ex + 3;
+            const float xc = X0[xb];
+            const float wx = WC[wb], wy = WC[WBW * WBH + wb];
+            const float vx = fmaf(sp, ix < nx - 1 ? X0[xb + 1] - xc : 0.0f, wx);
+            const float vy = fmaf(sp, iy < ny - 1 ? X0[xb + XHW] - xc : 0.0f, wy);
+            float vz = 0.0f, wz = 0.0f;
+            if (hz) {
+                wz = WC[2 * WBW * WBH + wb];
+                vz = fmaf(sp, z < nz - 1 ? X1[xb] - xc : 0.0f, wz);
+            }
+            const float nrm = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+            const float den = beta > 0.0f ? fmaxf(1.0f, nrm / beta) : 0.0f;
+            const float ox = den > 0.0f ? vx / den : 0.0f;
+            const float oy = den > 0.0f ? vy / den : 0.0f;
+            const float oz = den > 0.0f ? vz / den : 0.0f;
+            dx = ox - wx;
+            dy = oy - wy;
+            dzc = oz - wz;
+            if (own && ex >= 1 && ey >= 1) {
+                const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
+                wn[j] = ox;
+                wn[V + j] = oy;
+                if (hz) wn[2 * V + j] = oz;
+            }
+        }
+        D[p] = dx;
+        D[EWW + p] = dy;
+        D[2 * EWW + p] = dzc;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
+    const float* Tt = (const float*)(st + TmaLayout::p_T);
+    const float* Zt = (const float*)(st + TmaLayout::p_z);
+    const float* ZCt = (const float*)(st + TmaLayout::p_zc);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ty = wrow + 8 * k, tx = lane;
+        const int ix = I.x0 + tx, iy = I.y0 + ty;
+        const int e = (ty + 1) * EW + tx + 1;
+        if (own && ix < nx && iy < ny) {
+            // dz = (K^T (w+ - w))_j, component order and signs of prior_dz
+            float dz = 0.0f;
+            if (ix < nx - 1) dz -= D[e];
+            if (ix >= 1) dz += D[e - 1];
+            if (iy < ny - 1) dz -= D[EWW + e];
+            if (iy >= 1) dz += D[EWW + e - EW];
+            if (hz) {
+                if (z < nz - 1) dz -= D[2 * EWW + e];
+                if (z >= 1) dz += dprev[k];
+            }
+            const int t = ty * TD + tx;
+            float zh, zl;
+            const float xn = primal_step(X0[(ty + 1) * XHW + tx + 4], Tt[t], Zt[t], A.kahan ? ZCt[t] : 0.0f, dz,
+                                         A.inv_p_prior, A.kahan != 0, zh, zl);
+            const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
+            A.z[j] = zh;
+            if (A.kahan) A.zc[j] = zl;
+            x_nxt_std[j] = xn;
+            XO[ty * TP + tx] = xn;
+        }
+        dprev[k] = hz ? D[2 * EWW + e] : 0.0f;
+    }
+    if (own) {
+        __syncthreads();
+        store_x_yf(A, XO, x_nxt_yf, I, z);
+    }
+}
+
+// Data update merge for slice z of item I.
+__device__ __forceinline__ void data_slice(const lmh::ImgArgs& A, const PassMode& m, uint8_t* sm, int s, int z,
+                                           const Item& I, float* x_nxt_std, float* x_nxt_yf)
+{
+    const int nx = A.n[0], ny = A.n[1];
+    const bool det = A.det != 0;
+    const uint8_t* st = sm + TmaLayout::stage + s * TmaLayout::stage_sz;
+    const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
+    float* AYT = (float*)(sm + TmaLayout::dbuf);
+    long long* AYT64 = (long long*)(sm + TmaLayout::dbuf);
+    float* XO = (float*)(sm + TmaLayout::xo);
+    // acc_yf tile (rows x, columns y) -> transposed buffer [y][x]; clear it in memory
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = wrow + 8 * k, c = lane;
+        const int ix = I.x0 + r, iy = I.y0 + c;
+        if (det) AYT64[c * TP + r] = ((const long long*)(st + TmaLayout::d_ay))[r * TD + c];
+        else AYT[c * TP + r] = ((const float*)(st + TmaLayout::d_ay))[r * TD + c];
+        if (ix < nx && iy < ny) {
+            const int64_t k2 = ((int64_t)z * nx + ix) * ny + iy;
+            if (det) A.acci_yf[k2] = 0ULL;
+            else A.acc_yf[k2] = 0.0f;
+        }
+    }
+    __syncthreads();
+    const float* Xt = (const float*)(st + TmaLayout::d_x);
+    const float* Tt = (const float*)(st + TmaLayout::d_T);
+    const float* Zt = (const float*)(st + TmaLayout::d_z);
+    const float* ZCt = (const float*)(st + TmaLayout::d_zc);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ty = wrow + 8 * k, tx = lane;
+        const int ix = I.x0 + tx, iy = I.y0 + ty;
+        if (ix < nx && iy < ny) {
+            const int t = ty * TD + tx;
+            const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
+            float dz;
+            if (det) {
+                long long sacc = ((const long long*)(st + TmaLayout::d_as))[t];
+                sacc += AYT64[ty * TP + tx];
+                dz = (float)((double)sacc * m.fx);
+                A.acci_std[j] = 0ULL;
+            } else {
+                dz = ((const float*)(st + TmaLayout::d_as))[t];
+                dz += AYT[ty * TP + tx];
+                A.acc_std[j] = 0.0f;
+            }
+            float zh, zl;
+            const float xn =
+                primal_step(Xt[t], Tt[t], Zt[t], A.kahan ? ZCt[t] : 0.0f, dz, m.inv_p, A.kahan != 0, zh, zl);
+            A.z[j] = zh;
+            if (A.kahan) A.zc[j] = zl;
+            x_nxt_std[j] = xn;
+            XO[ty * TP + tx] = xn;
+        }
+    }
+    __syncthreads();
+    store_x_yf(A, XO, x_nxt_yf, I, z);
+}
+
+// One work item: its slices in order, inputs of slice z+1 in flight while
+// slice z is computed.  Returns false if a wait gave up.
+__device__ bool tma_item(const lmh::ImgArgs& A, const PassMode& m, int u, int64_t it, int xcur, float* x_nxt_std,
+                         float* x_nxt_yf, uint8_t* sm, Pipe& p)
+{
+    const Item I = item_of(A, it);
+    const bool prior = m.prior;
+    const int wp = prior ? A.wpar[u] : 0;
+    const int zs = (prior && I.zb > 0) ? I.zb - 1 : I.zb;
+    float dprev[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (threadIdx.x == 0) issue_slice(A, prior, xcur, wp, sm, 0, zs, zs, I, true, p.bar);
+    for (int z = zs, i = 0; z < I.ze; ++z, ++i) {
+        const int s = i & 1;
+        if (threadIdx.x == 0 && z + 1 < I.ze) issue_slice(A, prior, xcur, wp, sm, s ^ 1, z + 1, zs, I, false, p.bar);
+        if (!stage_wait(p, s, A.err)) return false;
+        if (prior) prior_slice(A, wp, sm, s, z, zs, I, dprev, x_nxt_std, x_nxt_yf);
+        else data_slice(A, m, sm, s, z, I, x_nxt_std, x_nxt_yf);
+        __syncthreads();
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_block_init(uint8_t* sm, int* abort_flag)
+{
+    if (threadIdx.x == 0) {
+        uint64_t* bar = (uint64_t*)(sm + TmaLayout::bars);
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256, 2) image_tma_kernel(const lmh::ImgArgs A)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ int abort_flag;
+    tma_block_init(sm, &abort_flag);
+    Pipe p{(uint64_t*)(sm + TmaLayout::bars), 0u, &abort_flag};
+    const int u = A.u;
+    const PassMode m = pass_mode(A, u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_next_slot(A, u);
+    const int64_t n = tma_items(A);
+    for (int64_t it = blockIdx.x; it < n; it += gridDim.x)
+        if (!tma_item(A, m, u, it, A.xcur, A.x_nxt_std, A.x_nxt_yf, sm, p)) break;
+}
+
+// Batched epochs: work items (frame, column, z run) over the active frames.
+__global__ void __launch_bounds__(256, 2) image_tma_batch_kernel(const lmh::BatchImgArgs B)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ int abort_flag;
+    tma_block_init(sm, &abort_flag);
+    Pipe p{(uint64_t*)(sm + TmaLayout::bars), 0u, &abort_flag};
+    const int par = B.u & 1;
+    for (int64_t t = blockIdx.x; t < (int64_t)B.cap * B.tiles_per_slot; t += gridDim.x) {
+        const int s = (int)(t / B.tiles_per_slot);
+        if (!B.active[s]) continue;
+        const lmh::ImgArgs& A = B.slots[s];
+        const int64_t lt = t - (int64_t)s * B.tiles_per_slot;
+        const PassMode m = pass_mode(A, B.u);
+        if (lt == 0 && threadIdx.x == 0) reset_next_slot(A, B.u);
+        if (!tma_item(A, m, B.u, lt, par, A.xbuf[par ^ 1], A.xbuf_yf[par ^ 1], sm, p)) break;
     }
 }
 
@@ -730,6 +1176,122 @@ void launch_image_pass(const ImgArgs& a, cudaStream_t st)
     for (int d = 0; d < 3; ++d) g.n[d] = a.n[d];
     image_pass_kernel<<<tile_grid(&g), dim3(TD, TR), 0, st>>>(a);
     count_launch();
+}
+
+bool tma_capable(const lm_grid* g)
+{
+    return g->n[0] % 4 == 0 && g->n[1] % 4 == 0 && g->n[0] >= 40 && g->n[1] >= 36;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+static void tma_attributes()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(image_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaLayout::total);
+        cudaFuncSetAttribute(image_tma_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaLayout::total);
+    });
+}
+
+// rank <= 4; dims innermost first; strides in bytes for dims 1..rank-1
+static int encode_one(CUtensorMap* m, CUtensorMapDataType t, int rank, void* base, const cuuint64_t* dims,
+               const cuuint64_t* strides, const cuuint32_t* box)
+{
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = encoder()(m, t, (cuuint32_t)rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LM_CHECK(r == CUDA_SUCCESS, LM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LM_OK;
+}
+
+int encode_tma_maps(const lm_grid* g, float* const x[2], float* const w[2], int ndim, float* T, float* z, float* zc,
+                    void* acc_std, void* acc_yf, bool det, TmaMaps* out)
+{
+    LM_CHECK(tma_capable(g), LM_ERR_INVALID_ARG, "grid not supported by the TMA-staged image pass");
+    LM_CHECK(encoder() != nullptr, LM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    tma_attributes();
+    std::memset(out, 0, sizeof(*out));
+    const cuuint64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    const cuuint64_t dims[3] = {nx, ny, nz}, strides[2] = {nx * 4, nx * ny * 4};
+    const cuuint32_t box_h[3] = {XHW, XHH, 1}, box_t[3] = {TD, TD, 1};
+    const CUtensorMapDataType F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    int rc;
+    for (int k = 0; k < 2; ++k) {
+        if ((rc = encode_one(&out->xh[k], F32, 3, x[k], dims, strides, box_h))) return rc;
+        if ((rc = encode_one(&out->xt[k], F32, 3, x[k], dims, strides, box_t))) return rc;
+        const cuuint64_t wd[4] = {nx, ny, nz, (cuuint64_t)ndim};
+        const cuuint64_t ws[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+        const cuuint32_t wb[4] = {WBW, WBH, 1, (cuuint32_t)ndim};
+        if ((rc = encode_one(&out->w[k], F32, 4, w[k], wd, ws, wb))) return rc;
+    }
+    if ((rc = encode_one(&out->T, F32, 3, T, dims, strides, box_t))) return rc;
+    if ((rc = encode_one(&out->z, F32, 3, z, dims, strides, box_t))) return rc;
+    if ((rc = encode_one(&out->zc, F32, 3, zc, dims, strides, box_t))) return rc;
+    const cuuint64_t es = det ? 8 : 4;
+    const CUtensorMapDataType at = det ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : F32;
+    const cuuint64_t s_std[2] = {nx * es, nx * ny * es};
+    if ((rc = encode_one(&out->acc_std, at, 3, acc_std, dims, s_std, box_t))) return rc;
+    const cuuint64_t d_yf[3] = {ny, nx, nz}, s_yf[2] = {ny * es, nx * ny * es};
+    if ((rc = encode_one(&out->acc_yf, at, 3, acc_yf, d_yf, s_yf, box_t))) return rc;
+    return LM_OK;
+}
+
+int tma_zlen(const lm_grid* g)
+{
+    const int ncol = ((g->n[0] + TD - 1) / TD) * ((g->n[1] + TD - 1) / TD);
+    int nch = std::max(1, 2 * num_sms() / ncol);
+    nch = std::min(nch, g->n[2]);
+    return (g->n[2] + nch - 1) / nch;
+}
+
+int64_t tma_items_host(const lm_grid* g, int zlen)
+{
+    const int ncol = ((g->n[0] + TD - 1) / TD) * ((g->n[1] + TD - 1) / TD);
+    return (int64_t)ncol * ((g->n[2] + zlen - 1) / zlen);
+}
+
+void launch_image_tma(const ImgArgs& a, cudaStream_t st)
+{
+    tma_attributes();
+    lm_grid g;
+    std::memset(&g, 0, sizeof(g));
+    for (int d = 0; d < 3; ++d) g.n[d] = a.n[d];
+    const int64_t items = tma_items_host(&g, a.zlen);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, 2 * (int64_t)num_sms()));
+    image_tma_kernel<<<grid, 256, TmaLayout::total, st>>>(a);
+    count_launch();
+}
+
+void launch_image_tma_batch(const BatchImgArgs& b, int grid, cudaStream_t st)
+{
+    tma_attributes();
+    image_tma_batch_kernel<<<grid, 256, TmaLayout::total, st>>>(b);
+    count_launch();
+}
+
+int image_tma_batch_grid(const lm_grid* g, int cap)
+{
+    const int64_t items = tma_items_host(g, tma_zlen(g)) * cap;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(items, 2 * (int64_t)num_sms()));
 }
 
 void launch_image_batch(const BatchImgArgs& b, int grid, cudaStream_t st)

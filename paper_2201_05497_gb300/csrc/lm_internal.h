@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <string>
 
+#include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include "../../include/lmspdhg.h"
@@ -110,6 +111,7 @@ struct EvArgs {
     const float* xb[2];
     const float* xbyf[2];
     unsigned* maxbits_base;
+    int prior_fused;            // 1: the prior's dual step runs inside the TMA image pass instead
 };
 
 // Batched multi-frame epochs: per-frame argument tables in device memory.
@@ -141,6 +143,20 @@ void launch_transpose_to_yf(const lm_grid* g, const float* src, float* dst, cuda
 void launch_add_yf_to_std(const lm_grid* g, float* img, float* yf_acc, cudaStream_t st);
 void launch_fold_fixed(const lm_grid* g, float* img, unsigned long long* a_std, unsigned long long* a_yf,
                        const unsigned* maxbits, long long count, float stepmax, cudaStream_t st);
+
+// Tensor maps of one state's images for the TMA-staged image passes
+// (grids with nx, ny multiples of 4, nx >= 40, ny >= 36).
+struct alignas(128) TmaMaps {
+    CUtensorMap xh[2];     // x (std), box {40, 34, 1} around a 32 x 32 tile (halo -4..+4 in x, -1..+1 in y)
+    CUtensorMap xt[2];     // x (std), box {32, 32, 1}
+    CUtensorMap w[2];      // w, (nx, ny, nz, ndim), box {36, 33, 1, ndim}
+    CUtensorMap T, z, zc;  // box {32, 32, 1}
+    CUtensorMap acc_std;   // f32 (or u64 when deterministic), box {32, 32, 1}
+    CUtensorMap acc_yf;    // y-fastest layout (ny, nx, nz), box {32, 32, 1}
+};
+bool tma_capable(const lm_grid* g);
+int encode_tma_maps(const lm_grid* g, float* const x[2], float* const w[2], int ndim, float* T, float* z, float* zc,
+                    void* acc_std, void* acc_yf, bool det, TmaMaps* out);
 
 struct ImgArgs {
     int n[3];
@@ -174,15 +190,22 @@ struct ImgArgs {
     int slot0;                // update u uses scale slot (slot0 + u) & 1
     // prior
     const float* w_cur[2];
-    const float* w_nxt[2];
+    float* w_nxt[2];
     const int* wpar;
     float inv_p_data;      // 1/p_k = 2n
     float inv_p_prior;     // 1/p_{n+1} = 2
+    float s_prior;         // S_{n+1} = gamma rho / ||K|| (fused prior step)
+    float beta;
     // batched epochs
     float* xbuf[2];
     float* xbuf_yf[2];
     int* wpar_w;
     int* wbase;
+    // TMA-staged passes
+    const TmaMaps* tm;     // device copy of the state's maps, or nullptr
+    int xcur;              // index of x_cur among the two x buffers
+    int zlen;              // z slices per work item
+    unsigned* err;         // set when a bounded wait gave up
 };
 
 struct BatchImgArgs {
@@ -198,6 +221,11 @@ int image_batch_grid(const lm_grid* g, int cap);
 int64_t image_tiles(const lm_grid* g);
 enum { IP_INIT = 0, IP_UPDATE = 1 };
 void launch_image_pass(const ImgArgs& a, cudaStream_t st);
+void launch_image_tma(const ImgArgs& a, cudaStream_t st);
+void launch_image_tma_batch(const BatchImgArgs& b, int grid, cudaStream_t st);
+int image_tma_batch_grid(const lm_grid* g, int cap);
+int tma_zlen(const lm_grid* g);                       // z slices per TMA work item
+int64_t tma_items_host(const lm_grid* g, int zlen);   // TMA work items of one image
 void launch_wpar(const uint16_t* seq, int count, int n_subsets, int* wpar, int* wbase, cudaStream_t st);
 void launch_step_T(const lm_grid* g, const float* sens, float* T, float rho, float gamma, double knorm, int n_subsets,
                    cudaStream_t st);

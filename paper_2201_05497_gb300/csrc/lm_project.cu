@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(256, G == 8 ? 2 : 3) ev_kernel(const EvArgs A)
     if (A.seq != nullptr) {
         const int sel = A.seq[A.u];
         if (sel >= A.n_subsets) {
-            if (T::prior_branch) prior_dual(A);
+            if (T::prior_branch && !A.prior_fused) prior_dual(A);
             return;
         }
         eb = A.sub_off[sel];
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(256, G == 8 ? 2 : 3) ev_batch_kernel(const lmh
             const EvArgs& A = B.slots[s];
             const int sel = B.seqs[(size_t)s * B.seq_stride + B.u];
             if (sel >= A.n_subsets) {
-                if (T::prior_branch) {
+                if (T::prior_branch && !A.prior_fused) {
                     kind = 2;
                     items = ((long long)A.G.V + B.vitem - 1) / B.vitem;
                 }

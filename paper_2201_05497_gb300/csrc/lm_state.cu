@@ -51,6 +51,10 @@ struct lm_state_s {
     float* redf;
     double* redd;
     float* tof_tab;   // tabulated TOF kernel (TOF_TAB_N + 1 floats)
+    TmaMaps* tmaps;   // device copy of the tensor maps (TMA-staged image passes)
+    unsigned* err;    // set by a bounded device wait that gave up
+    bool tma;         // image passes staged by TMA (grid permitting, unless disabled)
+    int zlen;         // z slices per TMA work item
     size_t scr_bytes;
     int grid_ev, grid_fx, chunk;
     int group;          // lanes per event of the event kernels
@@ -112,8 +116,12 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
     float* redf = c.take<float>((2 * 1024 + 16) * 4);
     double* redd = c.take<double>(objective_scratch_bytes());
     float* tof_tab = c.take<float>((size_t)(TOF_TAB_N + 1) * 4);
+    TmaMaps* tmaps = c.take<TmaMaps>(sizeof(TmaMaps));
+    unsigned* err = c.take<unsigned>(16);
     if (st) {
         st->tof_tab = tof_tab;
+        st->tmaps = tmaps;
+        st->err = err;
         st->x[0] = x0; st->x[1] = x1; st->xyf[0] = y0; st->xyf[1] = y1;
         st->z = z; st->zc = zc; st->T = T; st->w[0] = w0; st->w[1] = w1;
         st->acc_std = acc_std; st->acc_yf = acc_yf; st->acci_std = ai_std; st->acci_yf = ai_yf;
@@ -152,6 +160,7 @@ EvArgs base_ev_args(const lm_state* st)
     a.ndim = st->ndim;
     a.tof_tab = st->tof.n_bins > 0 ? st->tof_tab : nullptr;
     a.group = st->group;
+    a.prior_fused = st->tma ? 1 : 0;
     return a;
 }
 
@@ -184,6 +193,11 @@ ImgArgs base_img_args(const lm_state* st)
     a.wpar = st->wpar;
     a.inv_p_data = (float)(2 * st->n);
     a.inv_p_prior = 2.0f;
+    a.s_prior = (float)(st->gamma * (double)st->P.rho / st->knorm);
+    a.beta = st->P.beta;
+    a.tm = st->tma ? st->tmaps : nullptr;
+    a.err = st->err;
+    a.zlen = st->zlen;
     return a;
 }
 
@@ -234,7 +248,9 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         im.x_nxt_yf = st->xyf[nxt];
         // scale slots: update u reads slot (slot0 + u) & 1, its pass clears the other one
         im.slot0 = slot0;
-        launch_image_pass(im, s);
+        im.xcur = cur;
+        if (st->tma) launch_image_tma(im, s);
+        else launch_image_pass(im, s);
         if (ev) LM_CUDA(cudaEventRecord(ev[3 * u + 2], s));
     }
     LM_CUDA(cudaGetLastError());
@@ -458,6 +474,24 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         }                                                                               \
     } while (0)
     LM_TRY(cudaMemcpyAsync(st->sub_off, sub_off_host, (size_t)(st->n + 1) * 8, cudaMemcpyHostToDevice, s));
+    LM_TRY(cudaMemsetAsync(st->err, 0, 16, s));
+    st->tma = false;
+    st->zlen = 1;
+    if (P.image_kernel == 2 && !tma_capable(grid)) {
+        set_error("the TMA-staged image pass needs nx, ny multiples of 4 with nx >= 40, ny >= 36");
+        return fail(LM_ERR_INVALID_ARG);
+    }
+    if (P.image_kernel != 1 && tma_capable(grid)) {
+        TmaMaps h;
+        rc = encode_tma_maps(grid, st->x, st->w, std::max(1, st->ndim), st->T, st->z, st->zc,
+                             st->det ? (void*)st->acci_std : (void*)st->acc_std,
+                             st->det ? (void*)st->acci_yf : (void*)st->acc_yf, st->det, &h);
+        if (rc) return fail(rc);
+        LM_TRY(cudaMemcpyAsync(st->tmaps, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+        LM_TRY(cudaStreamSynchronize(s));
+        st->tma = true;
+        st->zlen = tma_zlen(grid);
+    }
     if (tof->n_bins > 0) {
         std::vector<float> tab(TOF_TAB_N + 1);
         tof_table(tof, tab.data());
@@ -659,6 +693,10 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
     double parts[3];
     int rc = objective_parts(&st->g, st->sens, st->x[xb], p, st->contam, st->N, st->P.beta, st->redd, parts, s);
     if (rc) return rc;
+    unsigned err = 0;
+    LM_CUDA(cudaMemcpyAsync(&err, st->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+    LM_CUDA(cudaStreamSynchronize(s));
+    LM_CHECK(err == 0, LM_ERR_TIMEOUT, "a bounded wait of the image pass gave up; the iterate is not valid");
     *out_host = parts[0] - parts[2] + (double)st->P.beta * parts[1];
     return LM_OK;
 }
@@ -670,6 +708,14 @@ int lmspdhg_info(lm_state* st, int64_t* n_updates, double* gamma, double* knorm)
     if (n_updates) *n_updates = st->n_updates;
     if (gamma) *gamma = st->gamma;
     if (knorm) *knorm = st->knorm;
+    return LM_OK;
+}
+
+int lmspdhg_image_kernel(lm_state* st, int32_t* kind)
+{
+    clear_error();
+    LM_CHECK(st && kind, LM_ERR_INVALID_ARG, "NULL argument");
+    *kind = st->tma ? 2 : 1;
     return LM_OK;
 }
 
@@ -753,7 +799,8 @@ bool same_config(const lm_state* a, const lm_state* b)
         if (a->g.n[d] != b->g.n[d]) return false;
     return a->n == b->n && a->two_d == b->two_d && a->det == b->det && a->kahan == b->kahan &&
            a->tof.n_bins == b->tof.n_bins && a->tof.sigma_mm == b->tof.sigma_mm && a->tof.bin_mm == b->tof.bin_mm &&
-           a->tof.n_sigma == b->tof.n_sigma && a->G.n_det == b->G.n_det && a->group == b->group;
+           a->tof.n_sigma == b->tof.n_sigma && a->G.n_det == b->G.n_det && a->group == b->group &&
+           a->tma == b->tma;
 }
 
 void fill_slot(lm_batch* b, int s, lm_state* st)
@@ -799,7 +846,7 @@ int launch_batch_epoch(lm_batch* b, cudaStream_t s)
     bi.active = b->d_active;
     bi.cap = b->cap;
     bi.u = 0;
-    bi.tiles_per_slot = image_tiles(&r->g);
+    bi.tiles_per_slot = r->tma ? tma_items_host(&r->g, r->zlen) : image_tiles(&r->g);
     launch_wpar_batch(bi, count, s);
     BatchEvArgs be;
     std::memset(&be, 0, sizeof(be));
@@ -816,7 +863,7 @@ int launch_batch_epoch(lm_batch* b, cudaStream_t s)
     be.vitem = 2048;
     const int g_ev = ev_batch_grid(r->det ? EV_DATA_FX1 : EV_DATA, r->two_d, r->group);
     const int g_fx = ev_batch_grid(EV_BACK_FX, r->two_d, r->group);
-    const int g_im = image_batch_grid(&r->g, b->cap);
+    const int g_im = r->tma ? image_tma_batch_grid(&r->g, b->cap) : image_batch_grid(&r->g, b->cap);
     for (int u = 0; u < count; ++u) {
         be.u = u;
         bi.u = u;
@@ -828,7 +875,8 @@ int launch_batch_epoch(lm_batch* b, cudaStream_t s)
             if (!rc) rc = launch_events_batch(EV_BACK_FX, r->two_d, r->group, be, g_fx, s);
         }
         LM_CHECK(rc == LM_OK, rc, "batched event kernel launch failed");
-        launch_image_batch(bi, g_im, s);
+        if (r->tma) launch_image_tma_batch(bi, g_im, s);
+        else launch_image_batch(bi, g_im, s);
     }
     LM_CUDA(cudaGetLastError());
     return LM_OK;

@@ -511,6 +511,12 @@ def monte_carlo_events_torch(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, 
             r = torch.clamp(torch.floor((hp[:, 2] - zlo) / sc.ring_pitch).long(), 0, sc.n_rings - 1)
         return r * sc.n_xtal + c
 
+    rmax = max(bx, by)
+    cz_max = 1.0
+    if not is2d and rmax < sc.radius:
+        chord_min = 2.0 * math.sqrt(sc.radius ** 2 - rmax ** 2)
+        t = (zhi - zlo) / chord_min
+        cz_max = min(1.0, 1.001 * t / math.sqrt(1.0 + t * t))
     d1s, d2s, tbs = [], [], []
     got = 0
     while got < n_true:
@@ -522,7 +528,11 @@ def monte_carlo_events_torch(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, 
             phi = U(m, 0.0, np.pi)
             u = torch.stack([torch.cos(phi), torch.sin(phi), torch.zeros_like(phi)], dim=1)
         else:
-            cz = U(m, -1.0, 1.0)
+            # Directions are isotropic; only |cos theta| <= cz_max can put both cylinder hits inside the
+            # axial extent (the in-plane chord through any emission point is at least chord_min), so
+            # drawing cos theta uniformly on [-cz_max, cz_max] leaves the accepted events' distribution
+            # unchanged and saves the candidates that would all be rejected.
+            cz = U(m, -cz_max, cz_max)
             phi = U(m, 0.0, 2.0 * np.pi)
             st = torch.sqrt(1.0 - cz * cz)
             u = torch.stack([st * torch.cos(phi), st * torch.sin(phi), cz], dim=1)

@@ -60,15 +60,16 @@ def test_batch_equals_alone(lm, name, sizes, det):
     b = lm.Batch(4, n)
     states = [_state(lm, wl, geo, sens, dev, x0, det) for dev, x0 in frames]
     # frame 1 joins at epoch 1 (it then runs epochs 0..E-1 of its own sequence), slot 3 stays empty
-    b.set(0, states[0])
-    b.set(2, states[2])
-    done = {0: 0, 1: 0, 2: 0}
+    for k in range(len(states)):
+        if k != 1:
+            b.set(k, states[k])
+    done = {k: 0 for k in range(len(states))}
     for e in range(E + 1):
         if e == 1:
             b.set(1, states[1])
         active = {k: states_k for k, states_k in enumerate(states)
                   if (k != 1 or e >= 1) and done[k] < E}
-        slots = {0: 0, 1: 1, 2: 2}
+        slots = {k: k for k in range(len(states))}
         q = {}
         for k in active:
             q[slots[k]] = seqs[k][2 * n * done[k]:2 * n * (done[k] + 1)]

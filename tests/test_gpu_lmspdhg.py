@@ -49,14 +49,14 @@ class Case:
         o.init(self.x0, self.sens_or)
         return o
 
-    def gpu(self, deterministic=False, kahan=True, sens=None):
+    def gpu(self, deterministic=False, kahan=True, sens=None, image_kernel=0, group=0):
         lm = self.lm
         pe = lm.event_setup(self.geo_g, lm.DeviceEvents.from_numpy(self.ev), self.n_sub)
         if sens is None:
             sens = torch.from_numpy(self.sens_or.astype(np.float32)).cuda()
         return lm.LMSPDHG(self.geo_g, pe, sens, torch.from_numpy(self.x0).cuda(), beta=self.beta,
                           n_subsets=self.n_sub, gamma=self.gamma, rho=0.999, knorm=self.knorm,
-                          deterministic=deterministic, kahan=kahan)
+                          deterministic=deterministic, kahan=kahan, image_kernel=image_kernel, group=group)
 
 
 @pytest.mark.parametrize("name", ["2d_small", "3d_small"])
@@ -197,3 +197,30 @@ def test_x0_negative_rejected(lm):
         lm.LMSPDHG(c.geo_g, pe, torch.from_numpy(c.sens_or.astype(np.float32)).cuda(), x0, beta=0.03,
                    n_subsets=c.n_sub)
     assert ei.value.code == 3
+
+
+@pytest.mark.parametrize("name", ["3d_quad", "2d"])
+@pytest.mark.parametrize("kahan", [True, False])
+def test_tma_and_plain_image_passes_agree(lm, name, kahan):
+    """The TMA-staged image pass (prior dual step fused in) and the
+    plain-load pass compute the same operations in the same order: in
+    deterministic mode x, z, w and y agree bit for bit after two epochs."""
+    c = Case(lm, name, n_events=30000 if name == "2d" else None)
+    seq = S.selection_sequence(c.n_sub, 4 * c.n_sub, seed=5)
+    out = {}
+    for kind in (1, 2):
+        g = c.gpu(deterministic=True, kahan=kahan, image_kernel=kind, group=16)
+        assert g.tuning()["image_kernel"] == {1: "plain", 2: "tma"}[kind]
+        g.epoch(seq[:2 * c.n_sub])
+        g.epoch(seq[2 * c.n_sub:])
+        out[kind] = [a.cpu().numpy() for a in (g.x(), g.z(), g.w(), g.y())]
+        g.close()
+    for a, b in zip(out[1], out[2]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_image_kernel_choice(lm):
+    assert Case(lm, "3d_quad").gpu().tuning()["image_kernel"] == "tma"
+    assert Case(lm, "3d_small").gpu().tuning()["image_kernel"] == "plain"
+    with pytest.raises(lm.LMError):
+        Case(lm, "3d_small").gpu(image_kernel=2)
