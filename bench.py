@@ -406,10 +406,20 @@ def run_gpu(args):
             "achieved_gbs": (b_gather + b_atomic) / t / 1e9, "peak_gbs": eff_peak,
             "frac": ((b_gather + b_atomic) / t / 1e9) / eff_peak,
             "hbm_event_stream_gbs": b_events / t / 1e9, "hbm_frac": b_events / t / 1e9 / hbm_peak}
-    for key, idx, bpv in [("prior_dual", 1, 4 + 8 * nd), ("image_pass_data", 2, 48),
-                          ("image_pass_prior", 3, 32 + 8 * nd)]:
+    fused = st.tuning()["image_kernel"] == "tma"
+    if fused:
+        # TMA-staged passes: the prior's dual step runs inside the image pass; the event
+        # kernel launched for a prior update only reads the selection and returns
+        rows = [("event_kernel_prior_update_idle", 1, 0), ("image_pass_data_tma", 2, 48),
+                ("prior_update_fused_tma", 3, 32 + 8 * nd)]
+    else:
+        rows = [("prior_dual", 1, 4 + 8 * nd), ("image_pass_data", 2, 48), ("image_pass_prior", 3, 32 + 8 * nd)]
+    for key, idx, bpv in rows:
         ms, n = prof[list(prof.keys())[idx]]
         if n:
+            if bpv == 0:
+                kern[key] = {"launches": n, "avg_us": 1e3 * ms / n, "bound": "launch"}
+                continue
             gbs = bpv * V * n / (ms / 1e3) / 1e9
             kern[key] = {"launches": n, "avg_us": 1e3 * ms / n, "bound": "hbm", "bytes_per_launch": bpv * V,
                          "achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak}
@@ -546,9 +556,7 @@ def run_serve(args):
 
     def drain(srv, tickets):
         out = {}
-        max_inflight = 0
         while len(out) < len(tickets):
-            max_inflight = max(max_inflight, srv.stats()["in_flight"])
             for k, t in enumerate(tickets):
                 if k in out:
                     continue
@@ -557,7 +565,7 @@ def run_serve(args):
                 except L.LMError as e:
                     if e.code != 5:
                         raise
-        return out, max_inflight
+        return out, srv.stats()["max_in_flight"]
 
     def submit(srv, k):
         d1, d2, tb, cr, ct = frames[k]

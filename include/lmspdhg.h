@@ -374,8 +374,10 @@ int lm_server_submit(lm_server* s, const int32_t* det1, const int32_t* det2, con
 int lm_server_wait(lm_server* s, int64_t ticket, float* x_host, double* objective, double* latency_ms,
                    int32_t timeout_ms);
 
-/* Frames finished, on the GPU, queued; pool bytes in use. */
-int lm_server_stats(lm_server* s, int64_t* completed, int64_t* in_flight, int64_t* queued, size_t* pool_used);
+/* Frames finished, on the GPU now, queued; pool bytes in use; the most
+ * frames that were on the GPU together so far.  NULL outputs are skipped. */
+int lm_server_stats(lm_server* s, int64_t* completed, int64_t* in_flight, int64_t* queued, size_t* pool_used,
+                    int64_t* max_in_flight);
 
 /* Stops the worker after its current epoch and frees everything; queued and
  * unfinished frames are dropped. */

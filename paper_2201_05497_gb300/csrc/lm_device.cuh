@@ -242,6 +242,15 @@ __device__ __forceinline__ void scatter_fx(unsigned long long* img, const Lor& L
     }
 }
 
+// Factor of the projection onto the ball of radius beta (the prox of R^*
+// for the isotropic TV, Sec. "Numerical experiments"):
+// w+ = v / max(1, |v|/beta) = v * tv_ball_scale(|v|^2, beta); beta = 0 gives
+// w+ = 0.  One reciprocal square root instead of a square root and divisions.
+__device__ __forceinline__ float tv_ball_scale(float n2, float beta)
+{
+    return n2 > beta * beta ? beta * rsqrtf(n2) : 1.0f;
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

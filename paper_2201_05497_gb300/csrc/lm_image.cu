@@ -617,9 +617,9 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
     float* XO = (float*)(sm + TmaLayout::xo);
     float* wn = A.w_nxt[wp];
     const float sp = A.s_prior, beta = A.beta;
-    // w+ = v / max(1, |v|/beta), v = w + S K x, over the tile and its -1 halo
-    for (int p = threadIdx.x; p < EWW; p += blockDim.x) {
-        const int ex = p % EW, ey = p / EW;
+    // w+ = v / max(1, |v|/beta), v = w + S K x, over the tile (4 points per
+    // thread) and its -1 halo (row y0-1 and column x0-1: 65 points)
+    auto wplus = [&](int ex, int ey, bool tile_pt) {
         const int ix = I.x0 - 1 + ex, iy = I.y0 - 1 + ey;
         float dx = 0.0f, dy = 0.0f, dzc = 0.0f;
         if (ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
@@ -634,24 +634,30 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
                 wz = WC[2 * WBW * WBH + wb];
                 vz = fmaf(sp, z < nz - 1 ? X1[xb] - xc : 0.0f, wz);
             }
-            const float nrm = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
-            const float den = beta > 0.0f ? fmaxf(1.0f, nrm / beta) : 0.0f;
-            const float ox = den > 0.0f ? vx / den : 0.0f;
-            const float oy = den > 0.0f ? vy / den : 0.0f;
-            const float oz = den > 0.0f ? vz / den : 0.0f;
+            const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), beta);
+            const float ox = vx * sc, oy = vy * sc, oz = vz * sc;
             dx = ox - wx;
             dy = oy - wy;
             dzc = oz - wz;
-            if (own && ex >= 1 && ey >= 1) {
+            if (own && tile_pt) {
                 const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
                 wn[j] = ox;
                 wn[V + j] = oy;
                 if (hz) wn[2 * V + j] = oz;
             }
         }
+        const int p = ey * EW + ex;
         D[p] = dx;
         D[EWW + p] = dy;
         D[2 * EWW + p] = dzc;
+    };
+    {
+        const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wplus(lane + 1, wrow + 8 * k + 1, true);
+        const int t = threadIdx.x;
+        if (t < EW) wplus(t, 0, false);
+        else if (t < 2 * EW - 1) wplus(0, t - EW + 1, false);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;

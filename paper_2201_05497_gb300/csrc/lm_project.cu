@@ -131,11 +131,10 @@ __device__ __forceinline__ void prior_voxel(const EvArgs& A, const float* __rest
     if (nx > 1) { cx = c++; vx = fmaf(A.s_prior, ix < nx - 1 ? x[j + 1] - x0 : 0.0f, wc[(int64_t)cx * V + j]); }
     if (ny > 1) { cy = c++; vy = fmaf(A.s_prior, iy < ny - 1 ? x[j + nx] - x0 : 0.0f, wc[(int64_t)cy * V + j]); }
     if (nz > 1) { cz = c++; vz = fmaf(A.s_prior, iz < nz - 1 ? x[j + nx * ny] - x0 : 0.0f, wc[(int64_t)cz * V + j]); }
-    const float nrm = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
-    const float den = A.beta > 0.0f ? fmaxf(1.0f, nrm / A.beta) : 0.0f;
-    if (cx >= 0) wn[(int64_t)cx * V + j] = den > 0.0f ? vx / den : 0.0f;
-    if (cy >= 0) wn[(int64_t)cy * V + j] = den > 0.0f ? vy / den : 0.0f;
-    if (cz >= 0) wn[(int64_t)cz * V + j] = den > 0.0f ? vz / den : 0.0f;
+    const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), A.beta);
+    if (cx >= 0) wn[(int64_t)cx * V + j] = vx * sc;
+    if (cy >= 0) wn[(int64_t)cy * V + j] = vy * sc;
+    if (cz >= 0) wn[(int64_t)cz * V + j] = vz * sc;
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
@@ -173,11 +172,10 @@ __device__ __forceinline__ void prior_quad(const EvArgs& A, const float* __restr
         const float vx = hx ? fmaf(A.s_prior, ix + k < nx - 1 ? xn - x0 : 0.0f, f4(wx, k)) : 0.0f;
         const float vy = hy ? fmaf(A.s_prior, iny ? f4(xy, k) - x0 : 0.0f, f4(wy, k)) : 0.0f;
         const float vz = hz ? fmaf(A.s_prior, inz ? f4(xz, k) - x0 : 0.0f, f4(wz, k)) : 0.0f;
-        const float nrm = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
-        const float den = A.beta > 0.0f ? fmaxf(1.0f, nrm / A.beta) : 0.0f;
-        ox[k] = den > 0.0f ? vx / den : 0.0f;
-        oy[k] = den > 0.0f ? vy / den : 0.0f;
-        oz[k] = den > 0.0f ? vz / den : 0.0f;
+        const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), A.beta);
+        ox[k] = vx * sc;
+        oy[k] = vy * sc;
+        oz[k] = vz * sc;
     }
     if (hx) *reinterpret_cast<float4*>(wn + j) = make_float4(ox[0], ox[1], ox[2], ox[3]);
     if (hy) *reinterpret_cast<float4*>(wn + (int64_t)cy * V + j) = make_float4(oy[0], oy[1], oy[2], oy[3]);

@@ -113,7 +113,8 @@ struct lm_server_s {
     size_t setup_ws_bytes = 0;
     lm_batch* batch = nullptr;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // batched epochs and retirement
+    cudaStream_t astream = nullptr;  // admission (uploads, event set-up, create), overlapping the epochs
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Frame*> queue;
@@ -121,6 +122,7 @@ struct lm_server_s {
     std::map<int64_t, Frame*> frames;
     int64_t next_ticket = 1;
     int64_t completed = 0;
+    int64_t max_in_flight = 0;
     bool stop = false;
     std::thread worker;
 };
@@ -147,10 +149,13 @@ void fail_frame(lm_server_s* s, Frame* f, int code, const char* msg)
     s->completed++;
 }
 
-// Admission of one frame into `slot`; called by the worker without the lock.
-int admit(lm_server_s* s, Frame* f, int slot)
+// Admission of one frame: events uploaded into its pool range, set up, and
+// its state created (on the admission stream, while the batch runs the
+// current epoch on the other); joining the batch happens after the epoch.
+// Called by the worker without the lock.
+int prepare(lm_server_s* s, Frame* f)
 {
-    cudaStream_t st = s->stream;
+    cudaStream_t st = s->astream;
     const int64_t n = f->n;
     char* base = s->pool + f->off;
     size_t o = 0;
@@ -200,13 +205,7 @@ int admit(lm_server_s* s, Frame* f, int slot)
     rc0 = lmspdhg_create(&state, &s->sc, &s->g, &s->tof, &perm, mu, off.data(), s->sens, x0, &P, stbuf, stbytes,
                          st);
     if (rc0) return rc0;
-    rc0 = lmspdhg_batch_set(s->batch, slot, state, st);
-    if (rc0) {
-        lmspdhg_destroy(state);
-        return rc0;
-    }
     f->st = state;
-    f->slot = slot;
     f->scratch = x0;
     // the host copies are no longer needed
     std::vector<int32_t>().swap(f->det1);
@@ -235,6 +234,23 @@ int retire(lm_server_s* s, Frame* f)
     return rc;
 }
 
+void finish_frame(lm_server_s* s, Frame* f, int rc, const char* what)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->alloc->release(f->off, f->bytes);
+    if (rc) {
+        fail_frame(s, f, rc, what);
+    } else {
+        f->done = true;
+        f->t_done = Clock::now();
+        s->completed++;
+    }
+}
+
+// Worker loop: plan admissions; launch one batched epoch of the frames on
+// the GPU; prepare the admitted frames meanwhile; wait for the epoch, retire
+// the frames that are done and let the prepared ones join for the next
+// epoch.
 void worker_main(lm_server_s* s)
 {
     cudaSetDevice(s->device);
@@ -242,71 +258,78 @@ void worker_main(lm_server_s* s)
     const int count = 2 * s->cfg.n_subsets;
     std::vector<uint16_t> seqs((size_t)cap * count);
     for (;;) {
-        std::vector<std::pair<Frame*, int>> to_admit;
+        std::vector<Frame*> to_admit;
+        std::vector<Frame*> act;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait_for(lk, std::chrono::milliseconds(50),
                                 [&] { return s->stop || !s->queue.empty() || !s->active.empty(); });
             if (s->stop) break;
             // admission: FIFO, while a slot is free and the pool has room
-            std::vector<int> free_slots;
             std::vector<bool> used(cap, false);
             for (Frame* f : s->active) used[f->slot] = true;
-            for (int k = 0; k < cap; ++k)
-                if (!used[k]) free_slots.push_back(k);
-            size_t fi = 0;
-            while (!s->queue.empty() && fi < free_slots.size()) {
+            int k = 0;
+            while (!s->queue.empty()) {
+                while (k < cap && used[k]) ++k;
+                if (k == cap) break;
                 Frame* f = s->queue.front();
                 size_t off = 0;
                 if (!s->alloc->alloc(f->bytes, &off)) break;  // wait for memory
                 f->off = off;
-                f->slot = free_slots[fi++];
+                f->slot = k;
+                used[k] = true;
                 s->queue.pop_front();
-                to_admit.push_back({f, f->slot});
+                to_admit.push_back(f);
             }
-        }
-        for (auto& fa : to_admit) {
-            Frame* f = fa.first;
-            const int rc = admit(s, f, fa.second);
-            std::lock_guard<std::mutex> lk(s->mu);
-            if (rc) {
-                s->alloc->release(f->off, f->bytes);
-                fail_frame(s, f, rc, lm_last_error());
-                s->cv_done.notify_all();
-            } else {
-                s->active.push_back(f);
-            }
-        }
-        std::vector<Frame*> act;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
             act = s->active;
         }
-        if (act.empty()) continue;
-        std::fill(seqs.begin(), seqs.end(), (uint16_t)0);
-        for (Frame* f : act)
-            std::memcpy(&seqs[(size_t)f->slot * count], &f->seqs[(size_t)f->epochs_done * count], count * 2);
-        int rc = lmspdhg_batch_epoch(s->batch, seqs.data(), s->stream);
-        if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LM_ERR_CUDA;
-        std::vector<Frame*> finished;
-        for (Frame* f : act) {
-            f->epochs_done++;
-            if (rc || f->epochs_done >= s->cfg.epochs) finished.push_back(f);
+        int rc = LM_OK;
+        if (!act.empty()) {
+            std::fill(seqs.begin(), seqs.end(), (uint16_t)0);
+            for (Frame* f : act)
+                std::memcpy(&seqs[(size_t)f->slot * count], &f->seqs[(size_t)f->epochs_done * count], count * 2);
+            rc = lmspdhg_batch_epoch(s->batch, seqs.data(), s->stream);
         }
-        for (Frame* f : finished) {
-            const int r2 = rc ? rc : retire(s, f);
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->alloc->release(f->off, f->bytes);
-            s->active.erase(std::find(s->active.begin(), s->active.end(), f));
-            if (r2) {
-                fail_frame(s, f, r2, "epoch or retirement failed");
+        std::vector<Frame*> ready;
+        for (Frame* f : to_admit) {
+            const int r = prepare(s, f);
+            if (r) {
+                finish_frame(s, f, r, lm_last_error());
+                s->cv_done.notify_all();
             } else {
-                f->done = true;
-                f->t_done = Clock::now();
-                s->completed++;
+                ready.push_back(f);
             }
         }
-        if (!finished.empty()) s->cv_done.notify_all();
+        if (!act.empty()) {
+            if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LM_ERR_CUDA;
+            std::vector<Frame*> finished;
+            for (Frame* f : act) {
+                f->epochs_done++;
+                if (rc || f->epochs_done >= s->cfg.epochs) finished.push_back(f);
+            }
+            for (Frame* f : finished) {
+                const int r2 = rc ? rc : retire(s, f);
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    s->active.erase(std::find(s->active.begin(), s->active.end(), f));
+                }
+                finish_frame(s, f, r2, "epoch or retirement failed");
+            }
+            if (!finished.empty()) s->cv_done.notify_all();
+        }
+        for (Frame* f : ready) {
+            const int r = lmspdhg_batch_set(s->batch, f->slot, f->st, s->stream);
+            if (r) {
+                lmspdhg_destroy(f->st);
+                f->st = nullptr;
+                finish_frame(s, f, r, "joining the batch failed");
+                s->cv_done.notify_all();
+                continue;
+            }
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->active.push_back(f);
+            s->max_in_flight = std::max<int64_t>(s->max_in_flight, (int64_t)s->active.size());
+        }
     }
 }
 
@@ -360,7 +383,9 @@ int lm_server_create(lm_server** out, const lm_scanner* sc, const lm_grid* grid,
     void* bbuf = base + align_up(s->setup_ws_bytes);
     s->pool = base + head;
     s->alloc = new PoolAllocator(usable - head);
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->astream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (s->stream) cudaStreamDestroy(s->stream);
         delete s->alloc;
         delete s;
         set_error("stream creation failed");
@@ -369,6 +394,7 @@ int lm_server_create(lm_server** out, const lm_scanner* sc, const lm_grid* grid,
     rc = lmspdhg_batch_create(&s->batch, cfg->max_slots, cfg->n_subsets, bbuf, bb, s->stream);
     if (rc) {
         cudaStreamDestroy(s->stream);
+        cudaStreamDestroy(s->astream);
         delete s->alloc;
         delete s;
         return rc;
@@ -441,7 +467,8 @@ int lm_server_wait(lm_server* s, int64_t ticket, float* x_host, double* objectiv
     return status;
 }
 
-int lm_server_stats(lm_server* s, int64_t* completed, int64_t* in_flight, int64_t* queued, size_t* pool_used)
+int lm_server_stats(lm_server* s, int64_t* completed, int64_t* in_flight, int64_t* queued, size_t* pool_used,
+                    int64_t* max_in_flight)
 {
     clear_error();
     LM_CHECK(s != nullptr, LM_ERR_INVALID_ARG, "server is NULL");
@@ -450,6 +477,7 @@ int lm_server_stats(lm_server* s, int64_t* completed, int64_t* in_flight, int64_
     if (in_flight) *in_flight = (int64_t)s->active.size();
     if (queued) *queued = (int64_t)s->queue.size();
     if (pool_used) *pool_used = s->alloc->used();
+    if (max_in_flight) *max_in_flight = s->max_in_flight;
     return LM_OK;
 }
 
@@ -473,6 +501,7 @@ int lm_server_destroy(lm_server* s)
     for (auto& kv : s->frames) delete kv.second;
     lmspdhg_batch_destroy(s->batch);
     cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->astream);
     delete s->alloc;
     delete s;
     return LM_OK;

@@ -749,11 +749,23 @@ int lmspdhg_destroy(lm_state* st)
 // table entry only, so the same graph serves any occupancy and frames can
 // join or leave between epochs.
 // ---------------------------------------------------------------------------
+// The configuration every state of a batch shares (copied from the first
+// state set, which may be destroyed while the batch lives on).
+struct BatchCfg {
+    lm_grid g;
+    lm_tof tof;
+    float W;
+    int n, n_det, group, zlen;
+    bool two_d, det, kahan, tma;
+};
+
 struct lm_batch_s {
     int cap = 0;
     int n = 0;
     lm_state* slot[BATCH_MAX] = {};
-    lm_state* ref = nullptr;  // a state fixing the shared configuration
+    bool have_cfg = false;
+    BatchCfg cfg;
+    float* d_tof = nullptr;   // the batch's own copy of the TOF table
     EvArgs* d_ev = nullptr;
     ImgArgs* d_im = nullptr;
     int* d_active = nullptr;
@@ -772,7 +784,7 @@ struct lm_batch_s {
 namespace {
 
 struct BatchLayout {
-    size_t ev, im, active, seqs, ctr, total;
+    size_t ev, im, active, seqs, ctr, tof, total;
 };
 
 BatchLayout batch_layout(int cap, int n)
@@ -789,18 +801,37 @@ BatchLayout batch_layout(int cap, int n)
     off += align_up(sizeof(uint16_t) * (size_t)cap * 2 * n);
     L.ctr = off;
     off += 256;
+    L.tof = off;
+    off += align_up((size_t)(TOF_TAB_N + 1) * 4);
     L.total = off + 256;
     return L;
 }
 
-bool same_config(const lm_state* a, const lm_state* b)
+BatchCfg cfg_of(const lm_state* st)
 {
+    BatchCfg c;
+    c.g = st->g;
+    c.tof = st->tof;
+    c.W = st->G.W;
+    c.n = st->n;
+    c.n_det = st->G.n_det;
+    c.group = st->group;
+    c.zlen = st->zlen;
+    c.two_d = st->two_d;
+    c.det = st->det;
+    c.kahan = st->kahan;
+    c.tma = st->tma;
+    return c;
+}
+
+bool same_config(const BatchCfg& a, const lm_state* st)
+{
+    const BatchCfg b = cfg_of(st);
     for (int d = 0; d < 3; ++d)
-        if (a->g.n[d] != b->g.n[d]) return false;
-    return a->n == b->n && a->two_d == b->two_d && a->det == b->det && a->kahan == b->kahan &&
-           a->tof.n_bins == b->tof.n_bins && a->tof.sigma_mm == b->tof.sigma_mm && a->tof.bin_mm == b->tof.bin_mm &&
-           a->tof.n_sigma == b->tof.n_sigma && a->G.n_det == b->G.n_det && a->group == b->group &&
-           a->tma == b->tma;
+        if (a.g.n[d] != b.g.n[d]) return false;
+    return a.n == b.n && a.two_d == b.two_d && a.det == b.det && a.kahan == b.kahan && a.tof.n_bins == b.tof.n_bins &&
+           a.tof.sigma_mm == b.tof.sigma_mm && a.tof.bin_mm == b.tof.bin_mm && a.tof.n_sigma == b.tof.n_sigma &&
+           a.n_det == b.n_det && a.group == b.group && a.tma == b.tma && a.zlen == b.zlen;
 }
 
 void fill_slot(lm_batch* b, int s, lm_state* st)
@@ -839,14 +870,14 @@ void fill_slot(lm_batch* b, int s, lm_state* st)
 
 int launch_batch_epoch(lm_batch* b, cudaStream_t s)
 {
-    const lm_state* r = b->ref;
+    const BatchCfg& r = b->cfg;
     const int count = 2 * b->n;
     BatchImgArgs bi;
     bi.slots = b->d_im;
     bi.active = b->d_active;
     bi.cap = b->cap;
     bi.u = 0;
-    bi.tiles_per_slot = r->tma ? tma_items_host(&r->g, r->zlen) : image_tiles(&r->g);
+    bi.tiles_per_slot = r.tma ? tma_items_host(&r.g, r.zlen) : image_tiles(&r.g);
     launch_wpar_batch(bi, count, s);
     BatchEvArgs be;
     std::memset(&be, 0, sizeof(be));
@@ -858,24 +889,24 @@ int launch_batch_epoch(lm_batch* b, cudaStream_t s)
     be.slot0 = 0;
     be.queue = b->d_queue;
     be.done = (unsigned*)(b->d_queue + 1);
-    be.tof_tab = r->tof.n_bins > 0 ? r->tof_tab : nullptr;
-    be.tof_W = r->G.W;
+    be.tof_tab = r.tof.n_bins > 0 ? b->d_tof : nullptr;
+    be.tof_W = r.W;
     be.vitem = 2048;
-    const int g_ev = ev_batch_grid(r->det ? EV_DATA_FX1 : EV_DATA, r->two_d, r->group);
-    const int g_fx = ev_batch_grid(EV_BACK_FX, r->two_d, r->group);
-    const int g_im = r->tma ? image_tma_batch_grid(&r->g, b->cap) : image_batch_grid(&r->g, b->cap);
+    const int g_ev = ev_batch_grid(r.det ? EV_DATA_FX1 : EV_DATA, r.two_d, r.group);
+    const int g_fx = ev_batch_grid(EV_BACK_FX, r.two_d, r.group);
+    const int g_im = r.tma ? image_tma_batch_grid(&r.g, b->cap) : image_batch_grid(&r.g, b->cap);
     for (int u = 0; u < count; ++u) {
         be.u = u;
         bi.u = u;
         int rc;
-        if (!r->det) {
-            rc = launch_events_batch(EV_DATA, r->two_d, r->group, be, g_ev, s);
+        if (!r.det) {
+            rc = launch_events_batch(EV_DATA, r.two_d, r.group, be, g_ev, s);
         } else {
-            rc = launch_events_batch(EV_DATA_FX1, r->two_d, r->group, be, g_ev, s);
-            if (!rc) rc = launch_events_batch(EV_BACK_FX, r->two_d, r->group, be, g_fx, s);
+            rc = launch_events_batch(EV_DATA_FX1, r.two_d, r.group, be, g_ev, s);
+            if (!rc) rc = launch_events_batch(EV_BACK_FX, r.two_d, r.group, be, g_fx, s);
         }
         LM_CHECK(rc == LM_OK, rc, "batched event kernel launch failed");
-        if (r->tma) launch_image_tma_batch(bi, g_im, s);
+        if (r.tma) launch_image_tma_batch(bi, g_im, s);
         else launch_image_batch(bi, g_im, s);
     }
     LM_CUDA(cudaGetLastError());
@@ -911,6 +942,7 @@ int lmspdhg_batch_create(lm_batch** out, int32_t capacity, int32_t n_subsets, vo
     b->d_active = (int*)(base + L.active);
     b->d_seqs = (uint16_t*)(base + L.seqs);
     b->d_queue = (unsigned long long*)(base + L.ctr);
+    b->d_tof = (float*)(base + L.tof);
     b->h_ev.assign(capacity, EvArgs());
     b->h_im.assign(capacity, ImgArgs());
     b->h_active.assign(capacity, 0);
@@ -933,13 +965,19 @@ int lmspdhg_batch_set(lm_batch* b, int32_t slot, lm_state* st, void* stream)
     cudaStream_t s = S(stream);
     if (st != nullptr) {
         LM_CHECK(st->n == b->n, LM_ERR_INVALID_ARG, "state has %d subsets, batch %d", st->n, b->n);
-        LM_CHECK(b->ref == nullptr || same_config(b->ref, st), LM_ERR_INVALID_ARG,
+        LM_CHECK(!b->have_cfg || same_config(b->cfg, st), LM_ERR_INVALID_ARG,
                  "state differs from the batch's grid, TOF kernel or mode");
         LM_CHECK(st->xpar == 0 && (st->n_updates & 1) == 0, LM_ERR_INVALID_ARG,
                  "a state joins a batch at an even update count");
         for (int k = 0; k < b->cap; ++k)
             LM_CHECK(k == slot || b->slot[k] != st, LM_ERR_INVALID_ARG, "state is already in slot %d", k);
-        if (b->ref == nullptr) b->ref = st;
+        if (!b->have_cfg) {
+            b->cfg = cfg_of(st);
+            b->have_cfg = true;
+            if (st->tof.n_bins > 0)
+                LM_CUDA(cudaMemcpyAsync(b->d_tof, st->tof_tab, (size_t)(TOF_TAB_N + 1) * 4, cudaMemcpyDeviceToDevice,
+                                        s));
+        }
         fill_slot(b, slot, st);
         b->slot[slot] = st;
         b->h_active[slot] = 1;

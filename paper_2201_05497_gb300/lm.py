@@ -120,7 +120,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                              C.c_int),
         "lm_server_submit": ([V, V, V, V, V, V, I64, F, P(C.c_uint16), P(I64)], C.c_int),
         "lm_server_wait": ([V, I64, V, P(D), P(D), I32], C.c_int),
-        "lm_server_stats": ([V, P(I64), P(I64), P(I64), P(SZ)], C.c_int),
+        "lm_server_stats": ([V, P(I64), P(I64), P(I64), P(SZ), P(I64)], C.c_int),
         "lm_server_destroy": ([V], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -553,9 +553,10 @@ class Server:
         return x, obj.value, lat.value
 
     def stats(self):
-        c, f, q, u = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
-        _check(load_library().lm_server_stats(self.h, C.byref(c), C.byref(f), C.byref(q), C.byref(u)))
-        return {"completed": c.value, "in_flight": f.value, "queued": q.value, "pool_used": u.value}
+        c, f, q, u, m = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t(), C.c_int64()
+        _check(load_library().lm_server_stats(self.h, C.byref(c), C.byref(f), C.byref(q), C.byref(u), C.byref(m)))
+        return {"completed": c.value, "in_flight": f.value, "queued": q.value, "pool_used": u.value,
+                "max_in_flight": m.value}
 
     def close(self):
         if getattr(self, "h", None):

@@ -88,3 +88,35 @@ def test_batch_equals_alone(lm, name, sizes, det):
             assert H.rel_l2(x, alone[k][0]) < H.REL_EVENT
             assert H.rel_l2(z, alone[k][2]) < H.REL_EVENT
     b.close()
+
+
+def test_batch_outlives_its_first_state(lm):
+    """The first state set into a batch leaves, is destroyed and its memory
+    overwritten; the batch keeps running the other frames unchanged (it owns
+    its configuration and TOF table)."""
+    wl, geo, sens, frames = _frames(lm, "3d_quad", [20000, 8000, 12000], True)
+    n = wl.n_subsets
+    E = 3
+    seqs = [S.selection_sequence(n, 2 * n * E, seed=7 + k) for k in range(3)]
+    alone = []
+    for k in (1, 2):
+        dev, x0 = frames[k]
+        st = _state(lm, wl, geo, sens, dev, x0, True)
+        for e in range(E):
+            st.epoch(seqs[k][2 * n * e:2 * n * (e + 1)])
+        alone.append(st.x().cpu().numpy())
+        st.close()
+    b = lm.Batch(3, n)
+    states = [_state(lm, wl, geo, sens, dev, x0, True) for dev, x0 in frames]
+    for k in range(3):
+        b.set(k, states[k])
+    b.epoch({k: seqs[k][:2 * n] for k in range(3)})
+    b.set(0, None)
+    states[0].close()
+    states[0].buf.fill_(255)
+    torch.cuda.synchronize()
+    for e in range(1, E):
+        b.epoch({k: seqs[k][2 * n * e:2 * n * (e + 1)] for k in (1, 2)})
+    for i, k in enumerate((1, 2)):
+        np.testing.assert_array_equal(states[k].x().cpu().numpy(), alone[i])
+    b.close()

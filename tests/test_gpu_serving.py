@@ -95,6 +95,7 @@ def test_server_mix_equals_alone(lm, problem, det):
                 results[k] = srv.wait(t, timeout_ms=1)
             except lm.LMError as e:
                 assert e.code == 5, e  # LM_ERR_TIMEOUT: not finished yet
+    max_inflight = srv.stats()["max_in_flight"]
     srv.close()
     assert len(results) == len(frames)
     assert max_inflight >= 2, "frames never overlapped on the GPU"
@@ -124,6 +125,7 @@ def test_server_admits_by_memory(lm, problem):
         done = st["completed"]
         time.sleep(0.0005)
     outs = [srv.wait(t, timeout_ms=60000) for t in tickets]
+    seen = max(seen, srv.stats()["max_in_flight"])
     srv.close()
     assert seen == 1
     ev, x0v, seqs = big[0]
@@ -133,7 +135,7 @@ def test_server_admits_by_memory(lm, problem):
 
 def test_server_errors_are_per_frame(lm, problem):
     wl, geo, sens, frames = problem
-    srv = _server(lm, wl, geo, sens, True, max_slots=2)
+    srv = _server(lm, wl, geo, sens, True, max_slots=1)
     ev, x0v, seqs = frames[1]
     # oversize frame: refused at submit
     with pytest.raises(lm.LMError) as ei:
@@ -144,23 +146,27 @@ def test_server_errors_are_per_frame(lm, problem):
     with pytest.raises(lm.LMError) as ei:
         _submit(srv, (ev, np.float32(0.0), seqs))
     assert ei.value.code == 3
-    # a frame with a detector index out of range fails on its own ...
+    # one slot: the largest frame occupies it for two epochs; the others queue behind it
+    t_big = _submit(srv, frames[2])
     bad_det = ev.det1.copy()
     bad_det[17] = wl.scanner.n_det + 5
     t_bad = srv.submit(bad_det, ev.det2, ev.tof, ev.corr, ev.contam, x0v, seqs)
     t_good = _submit(srv, frames[1])
-    # ... a wait that runs out reports LM_ERR_TIMEOUT and leaves the ticket valid
-    try:
+    # a wait that runs out reports LM_ERR_TIMEOUT and leaves the ticket valid
+    with pytest.raises(lm.LMError) as ei:
         srv.wait(t_good, timeout_ms=0)
-    except lm.LMError as e:
-        assert e.code == 5
+    assert ei.value.code == 5
+    # the frame with a detector index out of range fails on its own
     with pytest.raises(lm.LMError) as ei:
         srv.wait(t_bad, timeout_ms=60000)
     assert ei.value.code == 2
     x, obj, lat = srv.wait(t_good, timeout_ms=60000)
+    xb, objb, latb = srv.wait(t_big, timeout_ms=60000)
     srv.close()
-    x_alone, obj_alone = _alone(lm, wl, geo, sens, ev, x0v, seqs, True)
-    np.testing.assert_array_equal(x, x_alone)
+    assert latb < lat
+    np.testing.assert_array_equal(x, _alone(lm, wl, geo, sens, ev, x0v, seqs, True)[0])
+    e2, x02, s2 = frames[2]
+    np.testing.assert_array_equal(xb, _alone(lm, wl, geo, sens, e2, x02, s2, True)[0])
 
 
 def test_server_pool_too_small(lm, problem):
