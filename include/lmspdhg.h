@@ -213,7 +213,21 @@ typedef struct {
                           /* prior's dual step fused in; plain loads otherwise),  */
                           /* 1 plain loads, 2 TMA-staged (LM_ERR_INVALID_ARG if  */
                           /* the grid does not allow it).  Same results.          */
+    void* tile_buf;       /* device buffer of lmspdhg_tile_bytes() bytes for the  */
+    size_t tile_bytes;    /* tile-binned projector of the data updates, or NULL:  */
+                          /* used for TOF data in float-atomic mode (the batch    */
+                          /* and the deterministic mode use the direct kernel).   */
+                          /* The events' traversals are cut into segments per     */
+                          /* 32x32x8 image tile at create/reinit; each data update*/
+                          /* then projects tile by tile in shared memory.  Same   */
+                          /* per-sample arithmetic, sums in another order.  If the*/
+                          /* events need more segments than the buffer holds     */
+                          /* (6 per event), the direct kernel is used.            */
 } lm_params;
+
+/* Bytes of the optional tile-binned projector buffer (lm_params.tile_buf):
+ * about 136 per event plus per-tile tables. */
+size_t lmspdhg_tile_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets);
 
 /* Device bytes the state needs (images, duals, per-event y and scratch). */
 size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets,
@@ -289,6 +303,11 @@ int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, doubl
 /* Which image-pass kernel the state uses: 1 plain loads, 2 TMA-staged with
  * the prior's dual step fused in (lm_params.image_kernel). */
 int lmspdhg_image_kernel(lm_state* st, int32_t* kind);
+
+/* Which projector the data updates use: 1 direct event kernel, 2 tile-binned
+ * (lm_params.tile_buf); *n_segments receives the number of tile segments of
+ * the current events (0 for the direct kernel). */
+int lmspdhg_projector(lm_state* st, int32_t* kind, int64_t* n_segments);
 
 int lmspdhg_destroy(lm_state* st);
 

@@ -635,7 +635,8 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
                 vz = fmaf(sp, z < nz - 1 ? X1[xb] - xc : 0.0f, wz);
             }
             const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), beta);
-            const float ox = vx * sc, oy = vy * sc, oz = vz * sc;
+            // rounded products (never fused into the differences below), as stored by the plain path
+            const float ox = __fmul_rn(vx, sc), oy = __fmul_rn(vy, sc), oz = __fmul_rn(vz, sc);
             dx = ox - wx;
             dy = oy - wy;
             dzc = oz - wz;

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime's driver entry point)
 #include <cuda_runtime.h>
@@ -48,6 +49,20 @@ int num_sms();
 constexpr int TOF_TAB_N = 4096;
 // Fills tab[0..TOF_TAB_N] (host) with w(tau) at tau = -W + k 2W/TOF_TAB_N.
 void tof_table(const lm_tof* tof, float* tab);
+
+// TOF weight of the event's bin from the (shared-memory) table of the
+// bin-integrated Gaussian w(tau), tau in [-W, W] on TOF_TAB_N intervals,
+// linear interpolation; the 3-sigma cut is the same test as tof_weight's.
+// inv_dt = TOF_TAB_N / (2W).
+__device__ __forceinline__ float tof_weight_tab(const lmk::Geo& G, const float* tab, float inv_dt, float tau)
+{
+    if (fabsf(tau) > G.W) return 0.0f;
+    const float u = fminf(fmaxf((tau + G.W) * inv_dt, 0.0f), (float)TOF_TAB_N);
+    const int k = min((int)u, TOF_TAB_N - 1);
+    const float f = u - (float)k;
+    const float a = tab[k];
+    return fmaf(f, tab[k + 1] - a, a);
+}
 
 // Kernel launches issued by the library (graph replays count their nodes).
 void count_launch(int64_t n = 1);
@@ -137,6 +152,65 @@ int ev_batch_grid(int mode, bool two_d, int group);  // group 0: smallest over 8
 int launch_events(int mode, bool two_d, const EvArgs& a, int grid, cudaStream_t st);
 int ev_grid(int mode, bool two_d);  // smallest over the group widths
 int ev_grid_g(int mode, bool two_d, int group);
+
+// ---- tile-binned projector (lm_tile.cu) ----
+constexpr int TL_TX = 32, TL_TY = 32, TL_TZ = 8;  // image tile (2D grids: TL_TZ -> 1)
+constexpr int TL_CH = 512;                        // segments per work item
+constexpr int TL_SEGCAP = 6;                      // segment capacity per event
+
+struct TileItem {
+    int tile;
+    unsigned start;
+    int count;
+    int pad;
+};
+
+struct TileArgs {
+    lmk::Geo G;
+    int ntile[3];
+    int tz;
+    int64_t n_tiles;
+    int n_subsets;
+    const float* tof_tab;
+    // events (subset-contiguous)
+    const int32_t* det1;
+    const int32_t* det2;
+    const int16_t* tofb;
+    const float* corr;
+    const float* contam;
+    const uint16_t* mu;
+    float* y;
+    const int64_t* sub_off;
+    // per-frame binning
+    float4* evp;         // 2 per event: (ua0, sa, ub0, sb), (tau0, dtau, step, k | 4 if valid)
+    float* p1;           // (P^LM 1)_e
+    unsigned* seg_off;   // [N+1] first segment of each event (event order)
+    uint2* seg;          // tile-sorted segments: (event, first plane | planes << 16)
+    unsigned* seg_pos;   // [segments] tile-sorted position of the event's s-th segment
+    float* part;         // forward partial sum of each tile-sorted segment
+    TileItem* items;     // work items, subset by subset
+    int* item_off;       // [n+1]
+    int max_items;       // most items of one subset
+    // one update
+    const uint16_t* seq;
+    int u;
+    const float* x;      // std layout
+    float* acc;          // std-layout accumulator
+    float* v;            // c_e (y+ - y)/mu per event
+    float gamma_rho;
+};
+
+struct TileLayout {
+    size_t evp, p1, seg_off, nseg, seg, seg_pos, part, tiles, items, item_off, bsums, total;
+    int64_t cap, max_items;
+};
+void tile_geometry(const lm_grid* g, int ntile[3], int* tz, int64_t* n_tiles);
+TileLayout tile_layout(const lm_grid* g, int64_t N, int n_subsets);
+// Bins the events (synchronous); LM_ERR_NOMEM if they need more segments than the layout holds.
+int tile_build(TileArgs& A, const TileLayout& L, char* base, int64_t N, const std::vector<int64_t>& sub_off_h,
+               bool two_d, cudaStream_t st, int64_t* n_segments);
+void tile_attributes();
+int launch_tile_update(const TileArgs& A, bool two_d, cudaStream_t st);
 
 // ---- image kernels (lm_image.cu) ----
 void launch_transpose_to_yf(const lm_grid* g, const float* src, float* dst, cudaStream_t st);

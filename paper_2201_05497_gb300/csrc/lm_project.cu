@@ -132,9 +132,9 @@ __device__ __forceinline__ void prior_voxel(const EvArgs& A, const float* __rest
     if (ny > 1) { cy = c++; vy = fmaf(A.s_prior, iy < ny - 1 ? x[j + nx] - x0 : 0.0f, wc[(int64_t)cy * V + j]); }
     if (nz > 1) { cz = c++; vz = fmaf(A.s_prior, iz < nz - 1 ? x[j + nx * ny] - x0 : 0.0f, wc[(int64_t)cz * V + j]); }
     const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), A.beta);
-    if (cx >= 0) wn[(int64_t)cx * V + j] = vx * sc;
-    if (cy >= 0) wn[(int64_t)cy * V + j] = vy * sc;
-    if (cz >= 0) wn[(int64_t)cz * V + j] = vz * sc;
+    if (cx >= 0) wn[(int64_t)cx * V + j] = __fmul_rn(vx, sc);
+    if (cy >= 0) wn[(int64_t)cy * V + j] = __fmul_rn(vy, sc);
+    if (cz >= 0) wn[(int64_t)cz * V + j] = __fmul_rn(vz, sc);
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
@@ -173,9 +173,9 @@ __device__ __forceinline__ void prior_quad(const EvArgs& A, const float* __restr
         const float vy = hy ? fmaf(A.s_prior, iny ? f4(xy, k) - x0 : 0.0f, f4(wy, k)) : 0.0f;
         const float vz = hz ? fmaf(A.s_prior, inz ? f4(xz, k) - x0 : 0.0f, f4(wz, k)) : 0.0f;
         const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), A.beta);
-        ox[k] = vx * sc;
-        oy[k] = vy * sc;
-        oz[k] = vz * sc;
+        ox[k] = __fmul_rn(vx, sc);
+        oy[k] = __fmul_rn(vy, sc);
+        oz[k] = __fmul_rn(vz, sc);
     }
     if (hx) *reinterpret_cast<float4*>(wn + j) = make_float4(ox[0], ox[1], ox[2], ox[3]);
     if (hy) *reinterpret_cast<float4*>(wn + (int64_t)cy * V + j) = make_float4(oy[0], oy[1], oy[2], oy[3]);
@@ -226,18 +226,7 @@ struct Cache {
     static constexpr int passes = ((TWO_D ? 80 : 64) + G - 1) / G;
 };
 
-// TOF weight of the event's bin from the shared-memory table of the
-// bin-integrated Gaussian w(tau), tau in [-W, W] on TOF_TAB_N intervals,
-// linear interpolation; the 3-sigma cut is the same test as tof_weight's.
-__device__ __forceinline__ float tof_weight_tab(const Geo& G, const float* tab, float inv_dt, float tau)
-{
-    if (fabsf(tau) > G.W) return 0.0f;
-    const float u = fminf(fmaxf((tau + G.W) * inv_dt, 0.0f), (float)lmh::TOF_TAB_N);
-    const int k = min((int)u, lmh::TOF_TAB_N - 1);
-    const float f = u - (float)k;
-    const float a = tab[k];
-    return fmaf(f, tab[k + 1] - a, a);
-}
+using lmh::tof_weight_tab;
 
 template <bool TWO_D>
 __device__ __forceinline__ bool sample_tab(const Geo& G, const Lor& L, const float* tab, float inv_dt, int i, Smp& s)

@@ -55,6 +55,11 @@ struct lm_state_s {
     unsigned* err;    // set by a bounded device wait that gave up
     bool tma;         // image passes staged by TMA (grid permitting, unless disabled)
     int zlen;         // z slices per TMA work item
+    bool tiled;       // data updates by the tile-binned projector
+    TileArgs ta;      // its per-frame tables (pointers into the caller's tile buffer)
+    TileLayout tl;
+    char* tile_base;
+    int64_t n_segments;
     size_t scr_bytes;
     int grid_ev, grid_fx, chunk;
     int group;          // lanes per event of the event kernels
@@ -219,7 +224,17 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         a.x_yf = st->xyf[cur];
         a.px = st->x[cur];
         a.maxbits = st->maxbits + slot;
-        if (!st->det) {
+        if (st->tiled) {
+            TileArgs t = st->ta;
+            t.seq = st->seq;
+            t.u = u;
+            t.x = st->x[cur];
+            t.acc = st->acc_std;
+            t.v = st->scr;
+            t.gamma_rho = (float)(st->gamma * (double)st->P.rho);
+            int rc = launch_tile_update(t, st->two_d, s);
+            LM_CHECK(rc == LM_OK, rc, "tile data update launch failed");
+        } else if (!st->det) {
             a.acc_std = st->acc_std;
             a.acc_yf = st->acc_yf;
             int rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
@@ -393,6 +408,12 @@ int choose_chunk(const lm_state* st)
 
 extern "C" {
 
+size_t lmspdhg_tile_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets)
+{
+    if (check_grid(grid) || n_events < 0 || n_subsets < 1) return 0;
+    return tile_layout(grid, n_events, n_subsets).total;
+}
+
 size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets, int32_t deterministic)
 {
     if (check_grid(grid) || n_events < 0 || n_subsets < 1) return 0;
@@ -498,6 +519,55 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         LM_TRY(cudaMemcpyAsync(st->tof_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, s));
         LM_TRY(cudaStreamSynchronize(s));
     }
+    st->tiled = false;
+    st->n_segments = 0;
+    st->tile_base = nullptr;
+    if (P.tile_buf != nullptr && tof->n_bins > 0 && !st->det && grid->n[0] < 16384 && grid->n[1] < 16384 &&
+        grid->n[2] < 16384) {
+        st->tl = tile_layout(grid, ev->n, st->n);
+        if (P.tile_bytes < st->tl.total) {
+            set_error("tile buffer of %zu bytes, %zu needed", P.tile_bytes, st->tl.total);
+            return fail(LM_ERR_NOMEM);
+        }
+        char* tb = (char*)(((uintptr_t)P.tile_buf + 255) / 256 * 256);
+        if (P.tile_bytes - (size_t)(tb - (char*)P.tile_buf) < st->tl.total - 256) {
+            set_error("tile buffer too small after alignment");
+            return fail(LM_ERR_NOMEM);
+        }
+        st->tile_base = tb;
+        TileArgs& t = st->ta;
+        std::memset(&t, 0, sizeof(t));
+        t.G = st->G;
+        tile_geometry(grid, t.ntile, &t.tz, &t.n_tiles);
+        t.n_subsets = st->n;
+        t.tof_tab = st->tof_tab;
+        t.det1 = st->det1;
+        t.det2 = st->det2;
+        t.tofb = st->tofb;
+        t.corr = st->corr;
+        t.contam = st->contam;
+        t.mu = st->mu;
+        t.y = st->y;
+        t.sub_off = st->sub_off;
+        t.evp = (float4*)(tb + st->tl.evp);
+        t.p1 = (float*)(tb + st->tl.p1);
+        t.seg_off = (unsigned*)(tb + st->tl.seg_off);
+        t.seg = (uint2*)(tb + st->tl.seg);
+        t.seg_pos = (unsigned*)(tb + st->tl.seg_pos);
+        t.part = (float*)(tb + st->tl.part);
+        t.items = (TileItem*)(tb + st->tl.items);
+        t.item_off = (int*)(tb + st->tl.item_off);
+        tile_attributes();
+        rc = tile_build(t, st->tl, tb, ev->n, st->sub_off_h, st->two_d, s, &st->n_segments);
+        if (rc == LM_ERR_NOMEM) {
+            clear_error();  // more segments than the buffer holds: the direct kernel serves this frame
+            st->n_segments = 0;
+        } else if (rc) {
+            return fail(rc);
+        } else {
+            st->tiled = true;
+        }
+    }
     if (P.knorm > 0.0) {
         st->knorm = P.knorm;
     } else if (st->ndim == 0) {
@@ -588,7 +658,28 @@ int lmspdhg_reinit(lm_state* st, const float* x0, void* stream)
 {
     clear_error();
     LM_CHECK(st != nullptr && x0 != nullptr, LM_ERR_INVALID_ARG, "NULL argument");
+    if (st->tiled) {
+        // the events may be another frame's: bin them again
+        int rc = tile_build(st->ta, st->tl, st->tile_base, st->N, st->sub_off_h, st->two_d, S(stream),
+                            &st->n_segments);
+        if (rc == LM_ERR_NOMEM) {
+            clear_error();  // this frame needs more segments than the buffer holds: direct kernel
+            st->tiled = false;
+            st->n_segments = 0;
+        } else if (rc) {
+            return rc;
+        }
+    }
     return init_iteration(st, x0, S(stream));
+}
+
+int lmspdhg_projector(lm_state* st, int32_t* kind, int64_t* n_segments)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    if (kind) *kind = st->tiled ? 2 : 1;
+    if (n_segments) *n_segments = st->tiled ? st->n_segments : 0;
+    return LM_OK;
 }
 
 int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, double* ms4, int64_t* n4,

@@ -50,7 +50,8 @@ class lm_events(C.Structure):
 class lm_params(C.Structure):
     _fields_ = [("beta", C.c_float), ("gamma", C.c_float), ("rho", C.c_float), ("knorm", C.c_double),
                 ("knorm_iters", C.c_int32), ("n_subsets", C.c_int32), ("deterministic", C.c_int32),
-                ("kahan", C.c_int32), ("group", C.c_int32), ("image_kernel", C.c_int32)]
+                ("kahan", C.c_int32), ("group", C.c_int32), ("image_kernel", C.c_int32),
+                ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t)]
 
 
 _lib = None
@@ -105,6 +106,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lmspdhg_reinit": ([V, V, V], C.c_int),
         "lmspdhg_tuning": ([V, P(I32), P(D)], C.c_int),
         "lmspdhg_image_kernel": ([V, P(I32)], C.c_int),
+        "lmspdhg_projector": ([V, P(I32), P(I64)], C.c_int),
+        "lmspdhg_tile_bytes": ([P(lm_grid), I64, I32], SZ),
         "lmspdhg_profile": ([V, P(C.c_uint16), I32, P(D), P(I64), V], C.c_int),
         "lm_kernel_launches": ([], I64),
         "lm_traversal_stats": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, SZ, P(I64), P(I64), V],
@@ -359,7 +362,7 @@ class LMSPDHG:
     def __init__(self, geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x0: torch.Tensor, *,
                  beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
-                 image_kernel: int = 0, stream=None):
+                 image_kernel: int = 0, projector: str = "auto", stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.n_subsets = n_subsets
@@ -367,8 +370,18 @@ class LMSPDHG:
         if nbytes == 0:
             raise LMError(1, "invalid state size")
         self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=x0.device)
+        # tile-binned projector: TOF data in float-atomic mode; "auto" when its
+        # buffer takes at most a quarter of the free device memory
+        self.tile = None
+        if projector not in ("auto", "direct", "tiled"):
+            raise ValueError("projector must be 'auto', 'direct' or 'tiled'")
+        if projector != "direct" and geo.tof_nbins > 0 and not deterministic:
+            tb = int(L.lmspdhg_tile_bytes(C.byref(geo.g), pe.events.n, int(n_subsets)))
+            if projector == "tiled" or tb <= torch.cuda.mem_get_info(x0.device)[0] // 4:
+                self.tile = torch.empty(tb, dtype=torch.uint8, device=x0.device)
         self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan),
-                                int(group), int(image_kernel))
+                                int(group), int(image_kernel), None if self.tile is None else self.tile.data_ptr(),
+                                0 if self.tile is None else self.tile.numel())
         self._ev = pe.events.desc()
         self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
         h = C.c_void_p()
@@ -441,8 +454,11 @@ class LMSPDHG:
         _check(load_library().lmspdhg_tuning(self.h, C.byref(g), ms))
         kind = C.c_int32()
         _check(load_library().lmspdhg_image_kernel(self.h, C.byref(kind)))
+        pk, nseg = C.c_int32(), C.c_int64()
+        _check(load_library().lmspdhg_projector(self.h, C.byref(pk), C.byref(nseg)))
         return dict(group=g.value, ms_g8=ms[0], ms_g16=ms[1], ms_g32=ms[2],
-                    image_kernel={1: "plain", 2: "tma"}[kind.value])
+                    image_kernel={1: "plain", 2: "tma"}[kind.value],
+                    projector={1: "direct", 2: "tiled"}[pk.value], tile_segments=nseg.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -38,8 +38,9 @@ def _frames(lm, name, sizes, det):
 
 def _state(lm, wl, geo, sens, dev, x0, det):
     pe = lm.event_setup(geo, dev, wl.n_subsets)
+    # batched epochs run the direct event kernel: compare with the same projector alone
     return lm.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=wl.n_subsets, knorm=H.knorm_closed(wl.grid.n),
-                      deterministic=det, group=16)
+                      deterministic=det, group=16, projector="direct")
 
 
 @pytest.mark.parametrize("name,sizes", [("3d_small", [40000, 7000, 23000]), ("3d_quad", [30000, 9000, 15000]),
