@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="events in the oracle's timed sample")
     ap.add_argument("--knorm-iters", type=int, default=1000)
+    ap.add_argument("--projector", default="direct", choices=["direct", "tiled"],
+                    help="projector of the data updates: the direct event kernel or the tile-binned one")
     ap.add_argument("--serve", action="store_true",
                     help="serving run: a stream of dynamic frames through the continuous-batching server")
     ap.add_argument("--frames", type=int, default=64, help="frames in the serving run")
@@ -281,7 +283,7 @@ def run_gpu(args):
     setup_ws = torch.empty(L.load_library().lm_setup_workspace_bytes(N), dtype=torch.uint8, device=dev)
     pe = L.event_setup(geo, raw_dev, n_sub, ws=setup_ws)
     st = L.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=n_sub, rho=0.999, knorm=kn,
-                   deterministic=args.deterministic, kahan=True)
+                   deterministic=args.deterministic, kahan=True, projector=args.projector)
     E = args.epochs
     seq = S.selection_sequence(n_sub, 2 * n_sub * E, seed=3)
     seqs = [seq[2 * n_sub * e:2 * n_sub * (e + 1)] for e in range(E)]
@@ -527,7 +529,7 @@ def run_serve(args):
         d1, d2, tb, cr, ct = (torch.from_numpy(a).to(dev, non_blocking=False) for a in frames[k])
         pe = L.event_setup(geo, L.DeviceEvents(d1, d2, tb, cr, ct), n_sub)
         st = L.LMSPDHG(geo, pe, sens, torch.full((geo.V,), float(x0v[k]), device=dev), beta=wl.beta,
-                       n_subsets=n_sub, knorm=kn, deterministic=det, kahan=True, group=32)
+                       n_subsets=n_sub, knorm=kn, deterministic=det, kahan=True, group=32, projector="direct")
         for e in range(E):
             st.epoch(seqs[k][e])
         obj = st.objective()

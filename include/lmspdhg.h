@@ -417,7 +417,10 @@ int lm_traversal_stats(const lm_scanner* sc, const lm_grid* grid, const lm_tof* 
 /* L2 throughput probe on the caller's device buffer (use one that fits in
  * L2): mode 0 coalesced 16-byte reads, 1 coalesced float atomic adds, 2
  * random 4-byte reads, 3 random float atomic adds; *gbs_out = payload GB/s
- * over `iters` passes.  The buffer is overwritten.  Synchronous. */
+ * over `iters` passes.  The buffer is overwritten.  Modes 4 and 5 probe
+ * shared memory instead (random 4-byte reads / float atomic adds on a 32 KB
+ * array per block, 64 x iters accesses per thread; buf only receives a
+ * guard value).  Synchronous. */
 int lm_probe_l2(void* buf, size_t bytes, int32_t mode, int32_t iters, double* gbs_out, void* stream);
 
 #ifdef __cplusplus

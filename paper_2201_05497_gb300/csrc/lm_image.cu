@@ -1123,6 +1123,39 @@ __device__ __forceinline__ unsigned hash32(unsigned x)
     return x;
 }
 
+// Shared-memory probe: random 4-byte reads (mode 4) or float atomic adds
+// (mode 5) on a 32 KB array per block, indices from a linear congruential
+// sequence per thread (two instructions per index).
+constexpr int SPROBE_N = 8192;
+__global__ void __launch_bounds__(256) smem_probe_kernel(int mode, int iters, float* sink)
+{
+    __shared__ float sm[SPROBE_N];
+    for (int k = threadIdx.x; k < SPROBE_N; k += blockDim.x) sm[k] = 0.0f;
+    __syncthreads();
+    unsigned idx = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u;
+    float acc = 0.0f;
+    if (mode == 4) {
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll 8
+            for (int r = 0; r < 64; ++r) {
+                idx = idx * 1664525u + 1013904223u;
+                acc += sm[idx >> 19];
+            }
+        }
+    } else {
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll 8
+            for (int r = 0; r < 64; ++r) {
+                idx = idx * 1664525u + 1013904223u;
+                atomicAdd(sm + (idx >> 19), 1.0f);
+            }
+        }
+        __syncthreads();
+        acc = sm[threadIdx.x];
+    }
+    if (acc == 12345.678f) *sink = acc;
+}
+
 __global__ void __launch_bounds__(256) probe_kernel(float* buf, size_t n, int mode, int iters, float* sink)
 {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1438,8 +1471,30 @@ int lm_tv_prox(const lm_grid* grid, float* w, float beta, void* stream)
 int lm_probe_l2(void* buf, size_t bytes, int32_t mode, int32_t iters, double* gbs_out, void* stream)
 {
     clear_error();
-    LM_CHECK(buf && gbs_out && bytes >= 4096 && mode >= 0 && mode <= 3 && iters >= 1, LM_ERR_INVALID_ARG,
+    LM_CHECK(buf && gbs_out && bytes >= 4096 && mode >= 0 && mode <= 5 && iters >= 1, LM_ERR_INVALID_ARG,
              "bad probe arguments");
+    if (mode >= 4) {
+        cudaStream_t st = S(stream);
+        int bps = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, smem_probe_kernel, 256, 0);
+        const int grid = std::max(1, bps) * num_sms();
+        smem_probe_kernel<<<grid, 256, 0, st>>>(mode, 1, (float*)buf);  // warm-up
+        cudaEvent_t e0, e1;
+        LM_CUDA(cudaEventCreate(&e0));
+        LM_CUDA(cudaEventCreate(&e1));
+        cudaEventRecord(e0, st);
+        smem_probe_kernel<<<grid, 256, 0, st>>>(mode, iters, (float*)buf);
+        cudaEventRecord(e1, st);
+        count_launch(2);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "probe failed: %s", cudaGetErrorString(ce));
+        *gbs_out = (double)grid * 256.0 * 64.0 * iters * 4.0 / (ms * 1e-3) / 1e9;
+        return LM_OK;
+    }
     size_t n = 1024;
     while (n * 2 * 4 <= bytes) n *= 2;  // power-of-two float count
     cudaStream_t st = S(stream);

@@ -127,6 +127,7 @@ struct EvArgs {
     const float* xbyf[2];
     unsigned* maxbits_base;
     int prior_fused;            // 1: the prior's dual step runs inside the TMA image pass instead
+    int prior_only;             // 1: data selections are left to the tile-binned projector
 };
 
 // Batched multi-frame epochs: per-frame argument tables in device memory.

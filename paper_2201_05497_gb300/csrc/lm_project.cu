@@ -503,6 +503,7 @@ __global__ void __launch_bounds__(256, G == 8 ? 2 : 3) ev_kernel(const EvArgs A)
             if (T::prior_branch && !A.prior_fused) prior_dual(A);
             return;
         }
+        if (A.prior_only) return;
         eb = A.sub_off[sel];
         ee = A.sub_off[sel + 1];
     }

@@ -234,6 +234,12 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
             t.gamma_rho = (float)(st->gamma * (double)st->P.rho);
             int rc = launch_tile_update(t, st->two_d, s);
             LM_CHECK(rc == LM_OK, rc, "tile data update launch failed");
+            if (!st->tma) {
+                // the plain image pass needs w+ from the event kernel's prior branch
+                a.prior_only = 1;
+                rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
+                LM_CHECK(rc == LM_OK, rc, "prior update launch failed");
+            }
         } else if (!st->det) {
             a.acc_std = st->acc_std;
             a.acc_yf = st->acc_yf;

@@ -362,7 +362,7 @@ class LMSPDHG:
     def __init__(self, geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x0: torch.Tensor, *,
                  beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
-                 image_kernel: int = 0, projector: str = "auto", stream=None):
+                 image_kernel: int = 0, projector: str = "direct", stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.n_subsets = n_subsets
@@ -370,8 +370,9 @@ class LMSPDHG:
         if nbytes == 0:
             raise LMError(1, "invalid state size")
         self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=x0.device)
-        # tile-binned projector: TOF data in float-atomic mode; "auto" when its
-        # buffer takes at most a quarter of the free device memory
+        # projector of the data updates: "direct" (the event kernel) or "tiled" (the
+        # tile-binned projector, TOF data in float-atomic mode); "auto" takes the tiled
+        # one when its buffer needs at most a quarter of the free device memory
         self.tile = None
         if projector not in ("auto", "direct", "tiled"):
             raise ValueError("projector must be 'auto', 'direct' or 'tiled'")

@@ -49,7 +49,7 @@ class Case:
         o.init(self.x0, self.sens_or)
         return o
 
-    def gpu(self, deterministic=False, kahan=True, sens=None, image_kernel=0, group=0, projector="auto"):
+    def gpu(self, deterministic=False, kahan=True, sens=None, image_kernel=0, group=0, projector="direct"):
         lm = self.lm
         pe = lm.event_setup(self.geo_g, lm.DeviceEvents.from_numpy(self.ev), self.n_sub)
         if sens is None:

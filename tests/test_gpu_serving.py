@@ -154,17 +154,20 @@ def test_server_errors_are_per_frame(lm, problem):
     t_bad = srv.submit(bad_det, ev.det2, ev.tof, ev.corr, ev.contam, x0v, seqs)
     t_good = _submit(srv, frames[1])
     # a wait that runs out reports LM_ERR_TIMEOUT and leaves the ticket valid
-    with pytest.raises(lm.LMError) as ei:
-        srv.wait(t_good, timeout_ms=0)
-    assert ei.value.code == 5
+    # (unless the frame already finished, which a zero timeout cannot exclude)
+    try:
+        got = srv.wait(t_good, timeout_ms=0)
+    except lm.LMError as e:
+        assert e.code == 5
+        got = None
     # the frame with a detector index out of range fails on its own
     with pytest.raises(lm.LMError) as ei:
         srv.wait(t_bad, timeout_ms=60000)
     assert ei.value.code == 2
-    x, obj, lat = srv.wait(t_good, timeout_ms=60000)
+    x, obj, lat = got if got is not None else srv.wait(t_good, timeout_ms=60000)
     xb, objb, latb = srv.wait(t_big, timeout_ms=60000)
     srv.close()
-    assert latb < lat
+    assert latb < lat, (latb, lat)
     np.testing.assert_array_equal(x, _alone(lm, wl, geo, sens, ev, x0v, seqs, True)[0])
     e2, x02, s2 = frames[2]
     np.testing.assert_array_equal(xb, _alone(lm, wl, geo, sens, e2, x02, s2, True)[0])
