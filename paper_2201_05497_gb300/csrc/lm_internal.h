@@ -202,9 +202,11 @@ struct TileArgs {
 };
 
 struct TileLayout {
-    size_t evp, p1, seg_off, nseg, seg, seg_pos, part, tiles, items, item_off, bsums, total;
-    int64_t cap, max_items;
+    size_t evp, p1, seg_off, nseg, seg, seg_pos, part, tiles, items, item_off, bsums, bblocks, bhist, total;
+    int64_t cap, max_items, max_bblocks;
 };
+constexpr int TL_EPB = 4096;        // events per binning block
+constexpr int TL_MAX_TILES = 16384; // larger tile grids use the direct kernel
 void tile_geometry(const lm_grid* g, int ntile[3], int* tz, int64_t* n_tiles);
 TileLayout tile_layout(const lm_grid* g, int64_t N, int n_subsets);
 // Bins the events (synchronous); LM_ERR_NOMEM if they need more segments than the layout holds.

@@ -3,10 +3,10 @@
 // The direct event kernel gathers and scatters each event's samples straight
 // from/to L2; its atomics land on scattered sectors (a 32-lane request covers
 // ~15 sectors), which bounds it by L2 atomic throughput.  Here the traversal
-// of every event (its TOF window, Sec. "Listmode SPDHG"'s Joseph projector)
-// is cut once per frame into segments: maximal runs of consecutive planes
-// whose base voxel lies in one 32 x 32 x 8 image tile.  Segments are sorted
-// by tile (and by subset), so a data update becomes
+// of every event (its TOF window, the Joseph projector of Sec. "Listmode
+// SPDHG") is cut once per frame into segments: maximal runs of consecutive
+// planes whose base voxel lies in one 32 x 32 x 8 image tile.  Segments are
+// sorted by (subset, tile), so a data update becomes
 //   1. tl_fwd:  per work item (<= TL_CH segments of one tile) the tile of x
 //               plus a one-voxel halo is loaded into shared memory and each
 //               segment's partial forward projection is written to its slot;
@@ -18,6 +18,10 @@
 // Per sample the arithmetic is the direct kernel's (same positions, TOF
 // table, bilinear weights, skip of zero weights); only the order of the sums
 // differs.  (P^LM 1)_e, which S_e needs, is also computed once per frame.
+//
+// Latency: a warp loads the records of 32 segments (or the set-up of 32
+// events) at once, one per lane, and hands them to its two 16-lane halves by
+// shuffles, so one round trip to L2 serves 32 segments.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -33,41 +37,35 @@ namespace {
 constexpr int TX = lmh::TL_TX, TY = lmh::TL_TY;
 constexpr int BXW = 36;  // shared tile row pitch (33 used: tile + halo)
 constexpr int BYH = 33;
+constexpr int GL = 16;   // lanes per segment
+
+struct BinBlock {
+    long long e0, e1;
+    int sub, pad;
+};
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Stored traversal of one event: (ua0, sa, ub0, sb), (tau0, dtau, step, info)
-// with info = k | 4 (valid) | i0 << 3 | cnt << 17.  Every later pass works
-// from these stored values, so all of them cut and sample the traversal
-// identically.
+// with info = k | 4 (valid) | i0 << 3 | cnt << 17.  Every pass works from
+// these stored values, so all of them cut and sample a traversal identically.
 __device__ __forceinline__ int info_k(int info) { return info & 3; }
 __device__ __forceinline__ int info_i0(int info) { return (info >> 3) & 0x3FFF; }
 __device__ __forceinline__ int info_cnt(int info) { return (info >> 17) & 0x3FFF; }
 
 // Tile of the (clamped) base voxel of plane i.
-__device__ __forceinline__ int tile_of_plane(const TileArgs& A, const float4& e0, int k, bool two_d, int i)
+__device__ __forceinline__ int tile_of_plane(const TileArgs& A, float ua0, float sa, float ub0, float sb, int k,
+                                             bool two_d, int i)
 {
     const float fi = (float)i;
     const int nA = k == 0 ? A.G.n[1] : A.G.n[0];
     const int nB = k == 2 ? A.G.n[1] : A.G.n[2];
-    const int ia = clampi((int)floorf(fmaf(fi, e0.y, e0.x)), 0, nA - 1);
-    const int ib = two_d ? 0 : clampi((int)floorf(fmaf(fi, e0.w, e0.z)), 0, nB - 1);
+    const int ia = clampi((int)floorf(fmaf(fi, sa, ua0)), 0, nA - 1);
+    const int ib = two_d ? 0 : clampi((int)floorf(fmaf(fi, sb, ub0)), 0, nB - 1);
     const int c0 = k == 0 ? i : ia;
     const int c1 = k == 1 ? i : (k == 0 ? ia : ib);
     const int c2 = k == 2 ? i : ib;
     return ((c2 / A.tz) * A.ntile[1] + c1 / TY) * A.ntile[0] + c0 / TX;
-}
-
-// Subset of event q (events are subset-contiguous).
-__device__ __forceinline__ int subset_of(const int64_t* sub_off, int n, int64_t q)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sub_off[mid] <= q) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
 }
 
 __device__ __forceinline__ void load_tab(const float* g, float* s)
@@ -75,100 +73,212 @@ __device__ __forceinline__ void load_tab(const float* g, float* s)
     for (int k = threadIdx.x; k <= lmh::TOF_TAB_N; k += blockDim.x) s[k] = g[k];
 }
 
-// Per event: traversal parameters, (P^LM 1)_e = c_e sum of sample weights,
-// number of segments, and per (subset, tile) segment counts.
-template <bool TWO_D>
-__global__ void __launch_bounds__(256) tl_count_kernel(const TileArgs A, int64_t N, unsigned* nseg_out,
-                                                       unsigned* tile_cnt)
+// Shuffled copy of lane src's stored traversal.
+struct Trav {
+    float ua0, sa, ub0, sb, tau0, dtau, step;
+    int info;
+};
+
+__device__ __forceinline__ Trav shfl_trav(const float4& e0, const float4& e1, int src)
 {
-    extern __shared__ float s_tab[];
-    load_tab(A.tof_tab, s_tab);
+    Trav t;
+    t.ua0 = __shfl_sync(FULL, e0.x, src);
+    t.sa = __shfl_sync(FULL, e0.y, src);
+    t.ub0 = __shfl_sync(FULL, e0.z, src);
+    t.sb = __shfl_sync(FULL, e0.w, src);
+    t.tau0 = __shfl_sync(FULL, e1.x, src);
+    t.dtau = __shfl_sync(FULL, e1.y, src);
+    t.step = __shfl_sync(FULL, e1.z, src);
+    t.info = __shfl_sync(FULL, __float_as_int(e1.w), src);
+    return t;
+}
+
+// Walks the planes of one traversal with the whole warp (32 planes per pass)
+// and calls seg(s, tile, first_plane, planes) once per segment, from one lane
+// (s is the segment's index within the event).  Returns, on every lane, the
+// number of segments.
+template <class F>
+__device__ __forceinline__ int warp_segments(const TileArgs& A, const Trav& t, bool two_d, F&& seg)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = info_k(t.info), i0 = info_i0(t.info), iend = i0 + info_cnt(t.info);
+    int carry = -1, open_start = -1, open_t = -1, open_s = 0, ns = 0;
+    for (int b = i0; b < iend; b += 32) {
+        const int i = b + lane;
+        const bool in = i < iend;
+        const int tl = in ? tile_of_plane(A, t.ua0, t.sa, t.ub0, t.sb, k, two_d, i) : -2;
+        int prev = __shfl_up_sync(FULL, tl, 1);
+        if (lane == 0) prev = carry;
+        const bool bnd = in && tl != prev;
+        const unsigned mask = __ballot_sync(FULL, bnd);
+        if (mask) {
+            const int first = __ffs(mask) - 1;
+            if (open_start >= 0 && lane == first) seg(open_s, open_t, open_start, i - open_start);
+            if (bnd) {
+                const unsigned above = mask & ~((2u << lane) - 1u);
+                if (above) {
+                    const int end = b + __ffs(above) - 1;
+                    seg(ns + __popc(mask & ((1u << lane) - 1u)), tl, i, end - i);
+                }
+            }
+            const int last = 31 - __clz(mask);
+            open_start = __shfl_sync(FULL, i, last);
+            open_t = __shfl_sync(FULL, tl, last);
+            open_s = ns + __popc(mask) - 1;
+            ns += __popc(mask);
+        }
+        carry = __shfl_sync(FULL, tl, 31);
+    }
+    if (open_start >= 0 && lane == 0) seg(open_s, open_t, open_start, iend - open_start);
+    return ns;
+}
+
+// Per event: traversal parameters and (P^LM 1)_e = c_e sum of sample weights;
+// per binning block: segment counts per tile (block histogram).
+template <bool TWO_D>
+__global__ void __launch_bounds__(256) tl_count_kernel(const TileArgs A, const BinBlock* bb, unsigned* nseg_out,
+                                                       unsigned* bhist)
+{
+    extern __shared__ float smem[];
+    float* tab = smem;
+    unsigned* hist = reinterpret_cast<unsigned*>(smem + lmh::TOF_TAB_N + 4);
+    load_tab(A.tof_tab, tab);
+    for (int k = threadIdx.x; k < A.n_tiles; k += blockDim.x) hist[k] = 0u;
     __syncthreads();
     const Geo& G = A.G;
     const float inv_dt = (float)lmh::TOF_TAB_N / (2.0f * G.W);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        const int d1 = A.det1[q], d2 = A.det2[q];
-        const int m = (int)A.tofb[q];
+    const BinBlock B = bb[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (long long e0 = B.e0 + 32LL * warp; e0 < B.e1; e0 += 32LL * nw) {
+        // lane l sets up event e0 + l
+        const long long q = e0 + lane;
+        const bool have = q < B.e1;
         Lor L;
-        bool ok = d1 >= 0 && d1 < G.n_det && d2 >= 0 && d2 < G.n_det && d1 != d2 && m >= -G.M && m <= G.M;
-        ok = ok && lor_setup(G, d1, d2, m, TOF_BIN, false, L);
-        float4 e0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), e1 = e0;
-        unsigned ns = 0;
-        float wsum_all = 0.0f;
+        bool ok = false;
+        float c = 1.0f;
+        if (have) {
+            const int d1 = A.det1[q], d2 = A.det2[q];
+            const int m = (int)A.tofb[q];
+            if (A.corr) c = A.corr[q];
+            ok = d1 >= 0 && d1 < G.n_det && d2 >= 0 && d2 < G.n_det && d1 != d2 && m >= -G.M && m <= G.M;
+            ok = ok && lor_setup(G, d1, d2, m, TOF_BIN, false, L) && L.cnt < 16384 && L.i0 < 16384;
+        }
+        float4 e0v = make_float4(0.0f, 0.0f, 0.0f, 0.0f), e1v = e0v;
         if (ok) {
-            e0 = make_float4(L.ua0, L.sa, L.ub0, L.sb);
-            e1 = make_float4(L.tau0, L.dtau, L.step, __int_as_float(L.k | 4 | (L.i0 << 3) | (L.cnt << 17)));
-            const int sub = subset_of(A.sub_off, A.n_subsets, q);
-            int cur = -1;
-            for (int i = L.i0; i < L.i0 + L.cnt; ++i) {
+            e0v = make_float4(L.ua0, L.sa, L.ub0, L.sb);
+            e1v = make_float4(L.tau0, L.dtau, L.step, __int_as_float(L.k | 4 | (L.i0 << 3) | (L.cnt << 17)));
+        }
+        if (have) {
+            A.evp[2 * q] = e0v;
+            A.evp[2 * q + 1] = e1v;
+        }
+        const int nev = (int)min(32LL, B.e1 - e0);
+        float my_p1 = 0.0f;
+        unsigned my_ns = 0;
+        for (int r = 0; r < nev; ++r) {
+            const Trav t = shfl_trav(e0v, e1v, r);
+            if (!(t.info & 4)) continue;  // warp-uniform
+            // sample weights of this lane's planes (the direct kernel's per-sample weights)
+            const int k = info_k(t.info), i0 = info_i0(t.info), iend = i0 + info_cnt(t.info);
+            const int nA = k == 0 ? G.n[1] : G.n[0];
+            const int nB = k == 2 ? G.n[1] : G.n[2];
+            float ws = 0.0f;
+            for (int i = i0 + lane; i < iend; i += 32) {
                 const float fi = (float)i;
-                const float wt = L.step * lmh::tof_weight_tab(G, s_tab, inv_dt, fmaf(fi, L.dtau, L.tau0));
-                if (wt != 0.0f) {
-                    const float ua = fmaf(fi, L.sa, L.ua0);
-                    const float fla = floorf(ua);
-                    const int ia = (int)fla;
-                    const float fa = ua - fla;
-                    const float wa0 = (ia >= 0 && ia < L.nA) ? (1.0f - fa) : 0.0f;
-                    const float wa1 = (ia + 1 >= 0 && ia + 1 < L.nA) ? fa : 0.0f;
-                    if (TWO_D) {
-                        wsum_all += wt * wa0 + wt * wa1;
-                    } else {
-                        const float ub = fmaf(fi, L.sb, L.ub0);
-                        const float flb = floorf(ub);
-                        const int ib = (int)flb;
-                        const float fb = ub - flb;
-                        const float wb0 = (ib >= 0 && ib < L.nB) ? (1.0f - fb) : 0.0f;
-                        const float wb1 = (ib + 1 >= 0 && ib + 1 < L.nB) ? fb : 0.0f;
-                        const float wA0 = wt * wa0, wA1 = wt * wa1;
-                        wsum_all += (wA0 * wb0 + wA1 * wb0) + (wA0 * wb1 + wA1 * wb1);
-                    }
-                }
-                const int t = tile_of_plane(A, e0, L.k, TWO_D, i);
-                if (t != cur) {
-                    atomicAdd(tile_cnt + (size_t)sub * A.n_tiles + t, 1u);
-                    ++ns;
-                    cur = t;
+                const float wt = t.step * lmh::tof_weight_tab(G, tab, inv_dt, fmaf(fi, t.dtau, t.tau0));
+                if (wt == 0.0f) continue;
+                const float ua = fmaf(fi, t.sa, t.ua0);
+                const float fla = floorf(ua);
+                const int ia = (int)fla;
+                const float fa = ua - fla;
+                const float wa0 = (ia >= 0 && ia < nA) ? (1.0f - fa) : 0.0f;
+                const float wa1 = (ia + 1 >= 0 && ia + 1 < nA) ? fa : 0.0f;
+                if (TWO_D) {
+                    ws += wt * wa0 + wt * wa1;
+                } else {
+                    const float ub = fmaf(fi, t.sb, t.ub0);
+                    const float flb = floorf(ub);
+                    const int ib = (int)flb;
+                    const float fb = ub - flb;
+                    const float wb0 = (ib >= 0 && ib < nB) ? (1.0f - fb) : 0.0f;
+                    const float wb1 = (ib + 1 >= 0 && ib + 1 < nB) ? fb : 0.0f;
+                    const float wA0 = wt * wa0, wA1 = wt * wa1;
+                    ws += (wA0 * wb0 + wA1 * wb0) + (wA0 * wb1 + wA1 * wb1);
                 }
             }
+            ws = warp_sum(ws);
+            const int ns = warp_segments(A, t, TWO_D, [&](int, int tl, int, int) { atomicAdd(hist + tl, 1u); });
+            if (lane == r) {
+                my_p1 = ws;
+                my_ns = (unsigned)ns;
+            }
         }
-        A.evp[2 * q] = e0;
-        A.evp[2 * q + 1] = e1;
-        A.p1[q] = ok ? (A.corr ? A.corr[q] : 1.0f) * wsum_all : 0.0f;
-        nseg_out[q] = ns;
+        if (have) {
+            A.p1[q] = ok ? c * my_p1 : 0.0f;
+            nseg_out[q] = ok ? my_ns : 0u;
+        }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < A.n_tiles; k += blockDim.x) bhist[(size_t)blockIdx.x * A.n_tiles + k] = hist[k];
+}
+
+// Offsets of every binning block within its subset's tile ranges: for each
+// (subset, tile), blocks in order.  Also the per-(subset, tile) totals.
+__global__ void tl_block_offsets(const int* bsub_off, int n, int64_t n_tiles, unsigned* bhist, unsigned* tile_cnt)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)n * n_tiles) return;
+    const int sub = (int)(id / n_tiles);
+    const int64_t t = id - (int64_t)sub * n_tiles;
+    unsigned run = 0;
+    for (int b = bsub_off[sub]; b < bsub_off[sub + 1]; ++b) {
+        unsigned* h = bhist + (size_t)b * n_tiles + t;
+        const unsigned c = *h;
+        *h = run;  // becomes the block's offset
+        run += c;
+    }
+    tile_cnt[id] = run;
 }
 
 // Segment records at their tile-sorted positions.
 template <bool TWO_D>
-__global__ void __launch_bounds__(256) tl_fill_kernel(const TileArgs A, int64_t N, const unsigned* tile_off,
-                                                      unsigned* tile_fill, unsigned total)
+__global__ void __launch_bounds__(256) tl_fill_kernel(const TileArgs A, const BinBlock* bb, const unsigned* bhist,
+                                                      const unsigned* tile_off, unsigned total)
 {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        const float4 e1 = A.evp[2 * q + 1];
-        const int info = __float_as_int(e1.w);
-        if (!(info & 4)) continue;
-        const float4 e0 = A.evp[2 * q];
-        const int k = info_k(info), i0 = info_i0(info), iend = i0 + info_cnt(info);
-        const int sub = subset_of(A.sub_off, A.n_subsets, q);
-        const unsigned base = A.seg_off[q], lim = A.seg_off[q + 1];
-        unsigned s = 0;
-        int cur = -1, start = i0;
-        for (int i = i0; i <= iend; ++i) {
-            const int t = i < iend ? tile_of_plane(A, e0, k, TWO_D, i) : -2;
-            if (t != cur) {
-                if (cur >= 0) {
-                    const size_t ti = (size_t)sub * A.n_tiles + cur;
-                    const unsigned pos = tile_off[ti] + atomicAdd(tile_fill + ti, 1u);
-                    // the enumeration is the count pass's; the checks only guard the buffers
-                    if (pos < total && base + s < lim) {
-                        A.seg[pos] = make_uint2((unsigned)q, (unsigned)start | ((unsigned)(i - start) << 16));
-                        A.seg_pos[base + s] = pos;
-                    }
-                    ++s;
+    extern __shared__ unsigned s_u[];
+    unsigned* base = s_u;
+    unsigned* cnt = s_u + A.n_tiles;
+    const BinBlock B = bb[blockIdx.x];
+    for (int k = threadIdx.x; k < A.n_tiles; k += blockDim.x) {
+        base[k] = tile_off[(size_t)B.sub * A.n_tiles + k] + bhist[(size_t)blockIdx.x * A.n_tiles + k];
+        cnt[k] = 0u;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (long long e0 = B.e0 + 32LL * warp; e0 < B.e1; e0 += 32LL * nw) {
+        const long long q = e0 + lane;
+        float4 e0v = make_float4(0.0f, 0.0f, 0.0f, 0.0f), e1v = e0v;
+        unsigned sbase = 0, slim = 0;
+        if (q < B.e1) {
+            e0v = A.evp[2 * q];
+            e1v = A.evp[2 * q + 1];
+            sbase = A.seg_off[q];
+            slim = A.seg_off[q + 1];
+        }
+        const int nev = (int)min(32LL, B.e1 - e0);
+        for (int r = 0; r < nev; ++r) {
+            const Trav t = shfl_trav(e0v, e1v, r);
+            const unsigned qb = __shfl_sync(FULL, sbase, r), ql = __shfl_sync(FULL, slim, r);
+            if (!(t.info & 4)) continue;  // warp-uniform
+            const unsigned qe = (unsigned)(e0 + r);
+            warp_segments(A, t, TWO_D, [&](int s, int tl, int start, int len) {
+                const unsigned pos = base[tl] + atomicAdd(cnt + tl, 1u);
+                // the enumeration is the count pass's; the checks only guard the buffers
+                if (pos < total && qb + (unsigned)s < ql) {
+                    A.seg[pos] = make_uint2(qe, (unsigned)start | ((unsigned)len << 16));
+                    A.seg_pos[qb + s] = pos;
                 }
-                cur = t;
-                start = i;
-            }
+            });
         }
     }
 }
@@ -291,13 +401,13 @@ struct TSmp {
 };
 
 template <bool TWO_D>
-__device__ __forceinline__ bool tile_sample(const Geo& G, const float* tab, float inv_dt, const float4& e0,
-                                            const float4& e1, const SegFrame& f, int i, TSmp& s)
+__device__ __forceinline__ bool tile_sample(const Geo& G, const float* tab, float inv_dt, const Trav& t,
+                                            const SegFrame& f, int i, TSmp& s)
 {
     const float fi = (float)i;
-    const float wt = e1.z * lmh::tof_weight_tab(G, tab, inv_dt, fmaf(fi, e1.y, e1.x));
+    const float wt = t.step * lmh::tof_weight_tab(G, tab, inv_dt, fmaf(fi, t.dtau, t.tau0));
     if (wt == 0.0f) return false;
-    const float ua = fmaf(fi, e0.y, e0.x);
+    const float ua = fmaf(fi, t.sa, t.ua0);
     const float fla = floorf(ua);
     const int ia = (int)fla;
     const float fa = ua - fla;
@@ -310,7 +420,7 @@ __device__ __forceinline__ bool tile_sample(const Geo& G, const float* tab, floa
         s.w2 = s.w3 = 0.0f;
         return (wa0 != 0.0f) || (wa1 != 0.0f);
     }
-    const float ub = fmaf(fi, e0.w, e0.z);
+    const float ub = fmaf(fi, t.sb, t.ub0);
     const float flb = floorf(ub);
     const int ib = (int)flb;
     const float fb = ub - flb;
@@ -325,60 +435,64 @@ __device__ __forceinline__ bool tile_sample(const Geo& G, const float* tab, floa
     return (s.w0 != 0.0f) || (s.w1 != 0.0f) || (s.w2 != 0.0f) || (s.w3 != 0.0f);
 }
 
-constexpr int GL = 16;  // lanes per segment
-
+// The segments of one work item: each warp takes batches of 32 (one record
+// per lane, loaded together), its two halves process two segments at a time.
 template <bool TWO_D, bool BACK>
 __device__ __forceinline__ void tile_segments(const TileArgs& A, const TileItem& I, const TileBox& b, float* box,
                                               const float* tab, float inv_dt)
 {
     const Geo& G = A.G;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % GL;
-    const int grp = threadIdx.x / GL, ngrp = blockDim.x / GL;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int half = lane / GL, sub = lane % GL;
     const unsigned end = I.start + (unsigned)I.count;
-    // every group runs the same number of rounds so the shuffles stay full-warp
-    const int rounds = (I.count + ngrp - 1) / ngrp;
-    for (int r = 0; r < rounds; ++r) {
-        const unsigned j = I.start + (unsigned)(r * ngrp + grp);
-        const bool have = j < end;
-        uint2 sg = make_uint2(0u, 0u);
-        if (have) sg = __ldg(A.seg + j);
-        const unsigned q = sg.x;
-        const int i_a = (int)(sg.y & 0xFFFFu), len = have ? (int)(sg.y >> 16) : 0;
+    for (unsigned j0 = I.start + 32u * warp; j0 < end; j0 += 32u * nw) {
+        const unsigned jl = j0 + lane;
         float4 e0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), e1 = e0;
+        unsigned sy = 0;
         float bv = 0.0f;
-        if (have) {
-            e0 = __ldg(A.evp + 2 * (size_t)q);
-            e1 = __ldg(A.evp + 2 * (size_t)q + 1);
-            if (BACK) bv = A.v[q];
+        if (jl < end) {
+            const uint2 sg = __ldg(A.seg + jl);
+            sy = sg.y;
+            e0 = __ldg(A.evp + 2 * (size_t)sg.x);
+            e1 = __ldg(A.evp + 2 * (size_t)sg.x + 1);
+            if (BACK) bv = A.v[sg.x];
         }
-        const SegFrame f = seg_frame(G, b, __float_as_int(e1.w) & 3);
-        float acc = 0.0f;
-        if (!BACK || bv != 0.0f) {
-            for (int p = sub; p < len; p += GL) {
-                TSmp s;
-                if (!tile_sample<TWO_D>(G, tab, inv_dt, e0, e1, f, i_a + p, s)) continue;
-                if (BACK) {
-                    if (s.w0 != 0.0f) atomicAdd(box + s.base, s.w0 * bv);
-                    if (s.w1 != 0.0f) atomicAdd(box + s.base + f.sA, s.w1 * bv);
-                    if (!TWO_D) {
-                        if (s.w2 != 0.0f) atomicAdd(box + s.base + f.sB, s.w2 * bv);
-                        if (s.w3 != 0.0f) atomicAdd(box + s.base + f.sA + f.sB, s.w3 * bv);
-                    }
-                } else {
-                    if (s.w0 != 0.0f) acc = fmaf(s.w0, box[s.base], acc);
-                    if (s.w1 != 0.0f) acc = fmaf(s.w1, box[s.base + f.sA], acc);
-                    if (!TWO_D) {
-                        if (s.w2 != 0.0f) acc = fmaf(s.w2, box[s.base + f.sB], acc);
-                        if (s.w3 != 0.0f) acc = fmaf(s.w3, box[s.base + f.sA + f.sB], acc);
+        const int nseg = (int)min(32u, end - j0);
+        for (int r = 0; 2 * r < nseg; ++r) {
+            const int src = 2 * r + half;
+            const Trav t = shfl_trav(e0, e1, src);
+            const unsigned sys = __shfl_sync(FULL, sy, src);
+            const float bvs = BACK ? __shfl_sync(FULL, bv, src) : 0.0f;
+            const bool valid = src < nseg;
+            const int i_a = (int)(sys & 0xFFFFu), len = valid ? (int)(sys >> 16) : 0;
+            const SegFrame f = seg_frame(G, b, info_k(t.info));
+            float acc = 0.0f;
+            if (!BACK || bvs != 0.0f) {
+                for (int p = sub; p < len; p += GL) {
+                    TSmp s;
+                    if (!tile_sample<TWO_D>(G, tab, inv_dt, t, f, i_a + p, s)) continue;
+                    if (BACK) {
+                        if (s.w0 != 0.0f) atomicAdd(box + s.base, s.w0 * bvs);
+                        if (s.w1 != 0.0f) atomicAdd(box + s.base + f.sA, s.w1 * bvs);
+                        if (!TWO_D) {
+                            if (s.w2 != 0.0f) atomicAdd(box + s.base + f.sB, s.w2 * bvs);
+                            if (s.w3 != 0.0f) atomicAdd(box + s.base + f.sA + f.sB, s.w3 * bvs);
+                        }
+                    } else {
+                        if (s.w0 != 0.0f) acc = fmaf(s.w0, box[s.base], acc);
+                        if (s.w1 != 0.0f) acc = fmaf(s.w1, box[s.base + f.sA], acc);
+                        if (!TWO_D) {
+                            if (s.w2 != 0.0f) acc = fmaf(s.w2, box[s.base + f.sB], acc);
+                            if (s.w3 != 0.0f) acc = fmaf(s.w3, box[s.base + f.sA + f.sB], acc);
+                        }
                     }
                 }
             }
-        }
-        if (!BACK) {
+            if (!BACK) {
 #pragma unroll
-            for (int o = GL / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, GL);
-            if (have && sub == 0) A.part[j] = acc;
+                for (int o = GL / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, GL);
+                if (valid && sub == 0) A.part[j0 + src] = acc;
+            }
         }
     }
 }
@@ -468,8 +582,8 @@ __global__ void __launch_bounds__(256) tl_back_kernel(const TileArgs A)
     }
 }
 
-size_t tab_bytes() { return (size_t)(lmh::TOF_TAB_N + 1) * sizeof(float); }
 size_t tile_smem(int bz) { return (size_t)(lmh::TOF_TAB_N + 4) * 4 + (size_t)BXW * BYH * bz * 4; }
+size_t count_smem(int64_t n_tiles) { return (size_t)(lmh::TOF_TAB_N + 4) * 4 + (size_t)n_tiles * 4; }
 
 }  // namespace
 
@@ -499,6 +613,7 @@ TileLayout tile_layout(const lm_grid* g, int64_t N, int n_subsets)
     };
     L.cap = cap;
     L.max_items = (int64_t)n_subsets * ntiles + cap / TL_CH + n_subsets + 1;
+    L.max_bblocks = N / TL_EPB + n_subsets + 1;
     L.evp = take((size_t)std::max<int64_t>(N, 1) * 32);
     L.p1 = take((size_t)std::max<int64_t>(N, 1) * 4);
     L.seg_off = take((size_t)(N + 1) * 4);
@@ -506,10 +621,12 @@ TileLayout tile_layout(const lm_grid* g, int64_t N, int n_subsets)
     L.seg = take((size_t)cap * 8);
     L.seg_pos = take((size_t)cap * 4);
     L.part = take((size_t)cap * 4);
-    L.tiles = take((size_t)n_subsets * ntiles * 4 * 3);
+    L.tiles = take((size_t)n_subsets * ntiles * 4 * 2);
     L.items = take((size_t)L.max_items * sizeof(TileItem));
     L.item_off = take((size_t)(n_subsets + 1) * 4);
     L.bsums = take((size_t)((N + SB) / SB + 1) * 8);
+    L.bblocks = take((size_t)L.max_bblocks * sizeof(BinBlock) + (size_t)(n_subsets + 1) * 4);
+    L.bhist = take((size_t)L.max_bblocks * ntiles * 4);
     L.total = off + 256;
     return L;
 }
@@ -519,40 +636,67 @@ int tile_build(TileArgs& A, const TileLayout& Lt, char* base, int64_t N, const s
 {
     const int n = A.n_subsets;
     const int64_t nt = A.n_tiles;
+    *n_segments = 0;
+    LM_CHECK(nt <= TL_MAX_TILES, LM_ERR_NOMEM, "tile grid of %lld tiles exceeds %d", (long long)nt, TL_MAX_TILES);
     unsigned* tile_cnt = (unsigned*)(base + Lt.tiles);
     unsigned* tile_off = tile_cnt + (size_t)n * nt;
-    unsigned* tile_fill = tile_off + (size_t)n * nt;
     unsigned* nseg = (unsigned*)(base + Lt.nseg);
     unsigned long long* bsums = (unsigned long long*)(base + Lt.bsums);
-    *n_segments = 0;
-    LM_CUDA(cudaMemsetAsync(tile_cnt, 0, (size_t)n * nt * 4 * 3, st));
-    if (N == 0) {
+    BinBlock* bb = (BinBlock*)(base + Lt.bblocks);
+    int* bsub_off = (int*)(base + Lt.bblocks + (size_t)Lt.max_bblocks * sizeof(BinBlock));
+    unsigned* bhist = (unsigned*)(base + Lt.bhist);
+    // binning blocks: contiguous event ranges of at most TL_EPB inside one subset
+    std::vector<BinBlock> hb;
+    std::vector<int> hbo(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        hbo[k] = (int)hb.size();
+        for (int64_t e = sub_off_h[k]; e < sub_off_h[k + 1]; e += TL_EPB) {
+            BinBlock b;
+            b.e0 = e;
+            b.e1 = std::min<int64_t>(sub_off_h[k + 1], e + TL_EPB);
+            b.sub = k;
+            b.pad = 0;
+            hb.push_back(b);
+        }
+    }
+    hbo[n] = (int)hb.size();
+    LM_CHECK((int64_t)hb.size() <= Lt.max_bblocks, LM_ERR_NOMEM, "binning blocks exceed capacity");
+    const int nbb = (int)hb.size();
+    if (N == 0 || nbb == 0) {
         std::vector<int> io(n + 1, 0);
         LM_CUDA(cudaMemcpyAsync(A.item_off, io.data(), io.size() * 4, cudaMemcpyHostToDevice, st));
         LM_CUDA(cudaMemsetAsync(A.seg_off, 0, 4, st));
+        A.max_items = 0;
         LM_CUDA(cudaStreamSynchronize(st));
         return LM_OK;
     }
-    const int grid = (int)std::min<int64_t>((N + 255) / 256, (int64_t)num_sms() * 16);
-    if (two_d) tl_count_kernel<true><<<grid, 256, tab_bytes(), st>>>(A, N, nseg, tile_cnt);
-    else tl_count_kernel<false><<<grid, 256, tab_bytes(), st>>>(A, N, nseg, tile_cnt);
-    count_launch();
+    LM_CUDA(cudaMemcpyAsync(bb, hb.data(), hb.size() * sizeof(BinBlock), cudaMemcpyHostToDevice, st));
+    LM_CUDA(cudaMemcpyAsync(bsub_off, hbo.data(), hbo.size() * 4, cudaMemcpyHostToDevice, st));
+    const size_t csm = count_smem(nt);
+    if (csm > 48 * 1024) {
+        cudaFuncSetAttribute(tl_count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+        cudaFuncSetAttribute(tl_count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    }
+    if (two_d) tl_count_kernel<true><<<nbb, 256, csm, st>>>(A, bb, nseg, bhist);
+    else tl_count_kernel<false><<<nbb, 256, csm, st>>>(A, bb, nseg, bhist);
+    const int64_t nbo = (int64_t)n * nt;
+    tl_block_offsets<<<(int)((nbo + 255) / 256), 256, 0, st>>>(bsub_off, n, nt, bhist, tile_cnt);
     const int64_t nb = (N + SB - 1) / SB;
     tl_block_sums<<<(int)nb, 256, 0, st>>>(nseg, N, bsums);
-    count_launch();
-    std::vector<unsigned long long> hb((size_t)nb);
-    LM_CUDA(cudaMemcpyAsync(hb.data(), bsums, (size_t)nb * 8, cudaMemcpyDeviceToHost, st));
+    count_launch(3);
+    std::vector<unsigned long long> hs((size_t)nb);
+    LM_CUDA(cudaMemcpyAsync(hs.data(), bsums, (size_t)nb * 8, cudaMemcpyDeviceToHost, st));
     LM_CUDA(cudaStreamSynchronize(st));
     unsigned long long run = 0;
     for (int64_t b = 0; b < nb; ++b) {
-        const unsigned long long x = hb[b];
-        hb[b] = run;
+        const unsigned long long x = hs[b];
+        hs[b] = run;
         run += x;
     }
     *n_segments = (int64_t)run;
     LM_CHECK(run <= (unsigned long long)Lt.cap && run < (1ull << 32), LM_ERR_NOMEM,
              "tile binning needs %llu segments, capacity %lld", run, (long long)Lt.cap);
-    LM_CUDA(cudaMemcpyAsync(bsums, hb.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, st));
+    LM_CUDA(cudaMemcpyAsync(bsums, hs.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, st));
     tl_block_scan<<<(int)nb, 256, 0, st>>>(nseg, N, bsums, A.seg_off);
     count_launch();
     const unsigned total = (unsigned)run;
@@ -582,16 +726,21 @@ int tile_build(TileArgs& A, const TileLayout& Lt, char* base, int64_t N, const s
             }
             pos += c;
         }
+        LM_CHECK(pos == base_k[k + 1], LM_ERR_CUDA, "tile counts of subset %d do not add up", k);
     }
     io[n] = (int)items.size();
     LM_CHECK((int64_t)items.size() <= Lt.max_items, LM_ERR_NOMEM, "tile work items exceed capacity");
     LM_CUDA(cudaMemcpyAsync(tile_off, ho.data(), ho.size() * 4, cudaMemcpyHostToDevice, st));
     if (!items.empty())
-        LM_CUDA(cudaMemcpyAsync(A.items, items.data(), items.size() * sizeof(TileItem), cudaMemcpyHostToDevice,
-                                st));
+        LM_CUDA(cudaMemcpyAsync(A.items, items.data(), items.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st));
     LM_CUDA(cudaMemcpyAsync(A.item_off, io.data(), io.size() * 4, cudaMemcpyHostToDevice, st));
-    if (two_d) tl_fill_kernel<true><<<grid, 256, 0, st>>>(A, N, tile_off, tile_fill, total);
-    else tl_fill_kernel<false><<<grid, 256, 0, st>>>(A, N, tile_off, tile_fill, total);
+    const size_t fsm = (size_t)nt * 8;
+    if (fsm > 48 * 1024) {
+        cudaFuncSetAttribute(tl_fill_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+        cudaFuncSetAttribute(tl_fill_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    }
+    if (two_d) tl_fill_kernel<true><<<nbb, 256, fsm, st>>>(A, bb, bhist, tile_off, total);
+    else tl_fill_kernel<false><<<nbb, 256, fsm, st>>>(A, bb, bhist, tile_off, total);
     count_launch();
     int max_items = 0;
     for (int k = 0; k < n; ++k) max_items = std::max(max_items, io[k + 1] - io[k]);
