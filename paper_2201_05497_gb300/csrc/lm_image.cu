@@ -814,11 +814,20 @@ __global__ void __launch_bounds__(256, 2) image_tma_batch_kernel(const lmh::Batc
     __shared__ int abort_flag;
     tma_block_init(sm, &abort_flag);
     Pipe p{(uint64_t*)(sm + TmaLayout::bars), 0u, &abort_flag};
+    // the frame's arguments in shared memory: the item code reads them in its inner loops
+    __shared__ lmh::ImgArgs sA;
+    int cur = -1;
     const int par = B.u & 1;
     for (int64_t t = blockIdx.x; t < (int64_t)B.cap * B.tiles_per_slot; t += gridDim.x) {
         const int s = (int)(t / B.tiles_per_slot);
         if (!B.active[s]) continue;
-        const lmh::ImgArgs& A = B.slots[s];
+        if (s != cur) {
+            __syncthreads();  // no thread still reads the previous frame's arguments
+            if (threadIdx.x == 0) sA = B.slots[s];
+            __syncthreads();
+            cur = s;
+        }
+        const lmh::ImgArgs& A = sA;
         const int64_t lt = t - (int64_t)s * B.tiles_per_slot;
         const PassMode m = pass_mode(A, B.u);
         if (lt == 0 && threadIdx.x == 0) reset_next_slot(A, B.u);

@@ -280,6 +280,8 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
 
 // Alg. 2 steps 3-5 and the first primal step for the state's current events:
 // gamma, T, y = Eq. (yinit), z = P^T 1 + (P^LM)^T((y-1)/mu), w = 0, x from x0.
+int chunk_for(int64_t count, int grid);
+
 int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
 {
     const size_t V = (size_t)st->V;
@@ -315,6 +317,7 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     }
     a.e_begin = 0;
     a.e_end = st->N;
+    a.chunk = chunk_for(st->N, st->grid_ev);  // all N events, not one subset
     if (st->N > 0) {
         if (!st->det) {
             a.acc_std = st->acc_std;
@@ -328,6 +331,7 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
                 EvArgs b = base_ev_args(st);
                 b.e_begin = 0;
                 b.e_end = st->N;
+                b.chunk = chunk_for(st->N, st->grid_fx);
                 b.vin = st->scr;
                 b.acci_std = st->acci_std;
                 b.acci_yf = st->acci_yf;
@@ -399,6 +403,15 @@ int autotune_group(lm_state* st, cudaStream_t s)
     cudaEventDestroy(e1);
     st->group = best_g;
     return LM_OK;
+}
+
+// Events per work item for a launch over `count` events on `grid` blocks of
+// 8 warps: about four items per warp, between 1 and 32 (a whole warp's
+// per-lane set-up).
+int chunk_for(int64_t count, int grid)
+{
+    const int64_t ch = count / std::max<int64_t>(1, (int64_t)grid * 8 * 4);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(32, ch));
 }
 
 int choose_chunk(const lm_state* st)
@@ -936,6 +949,9 @@ void fill_slot(lm_batch* b, int s, lm_state* st)
     EvArgs a = base_ev_args(st);
     a.queue = nullptr;
     a.done = nullptr;
+    // work items of a batched update span every frame: whole-warp chunks keep the
+    // shared work counter's traffic low even when the frames are small
+    a.chunk = 32;
     a.seq = b->d_seqs + (size_t)s * 2 * b->n;
     a.xb[0] = st->x[0];
     a.xb[1] = st->x[1];
