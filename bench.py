@@ -412,10 +412,12 @@ def run_gpu(args):
     if fused:
         # TMA-staged passes: the prior's dual step runs inside the image pass; the event
         # kernel launched for a prior update only reads the selection and returns
-        rows = [("event_kernel_prior_update_idle", 1, 0), ("image_pass_data_tma", 2, 48),
+        # data pass: float accumulators are z pairs (8 B read + 8 B cleared per layout) unless deterministic
+        rows = [("event_kernel_prior_update_idle", 1, 0), ("image_pass_data_tma", 2, 48 if args.deterministic else 64),
                 ("prior_update_fused_tma", 3, 32 + 8 * nd)]
     else:
-        rows = [("prior_dual", 1, 4 + 8 * nd), ("image_pass_data", 2, 48), ("image_pass_prior", 3, 32 + 8 * nd)]
+        rows = [("prior_dual", 1, 4 + 8 * nd), ("image_pass_data", 2, 48 if args.deterministic else 64),
+                ("image_pass_prior", 3, 32 + 8 * nd)]
     for key, idx, bpv in rows:
         ms, n = prof[list(prof.keys())[idx]]
         if n:

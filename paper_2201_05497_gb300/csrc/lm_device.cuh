@@ -223,6 +223,35 @@ __device__ __forceinline__ void scatter(float* img, const Lor& L, const Smp& s, 
     }
 }
 
+// Scatter into a z-paired accumulator: element 2j holds voxel j, element
+// 2j + 1 voxel j + nx*ny.  For principal axes x and y the second secondary
+// axis is z, so a sample's two z-neighbours share one 8-byte pair and one
+// vector atomic instead of two scattered scalar ones (half the L2 sector
+// operations); z-principal and 2D traversals add to the first elements.
+template <bool TWO_D>
+__device__ __forceinline__ void scatter_pairs(float* ap, const Lor& L, const Smp& s, float val)
+{
+    if (TWO_D || L.k == 2) {
+        if (s.w0 != 0.0f) atomicAdd(ap + 2 * (int64_t)s.base, s.w0 * val);
+        if (s.w1 != 0.0f) atomicAdd(ap + 2 * ((int64_t)s.base + L.sA), s.w1 * val);
+        if (!TWO_D) {
+            if (s.w2 != 0.0f) atomicAdd(ap + 2 * ((int64_t)s.base + L.sB), s.w2 * val);
+            if (s.w3 != 0.0f) atomicAdd(ap + 2 * ((int64_t)s.base + L.sA + L.sB), s.w3 * val);
+        }
+        return;
+    }
+    float2* p2 = reinterpret_cast<float2*>(ap);
+    if (s.w0 != 0.0f || s.w1 != 0.0f) {
+        // the base slice is inside the grid (its z weight is non-zero)
+        if (s.w0 != 0.0f || s.w2 != 0.0f) atomicAdd(p2 + s.base, make_float2(s.w0 * val, s.w2 * val));
+        if (s.w1 != 0.0f || s.w3 != 0.0f) atomicAdd(p2 + s.base + L.sA, make_float2(s.w1 * val, s.w3 * val));
+    } else {
+        // base slice -1: only the neighbours in slice 0
+        if (s.w2 != 0.0f) atomicAdd(ap + 2 * ((int64_t)s.base + L.sB), s.w2 * val);
+        if (s.w3 != 0.0f) atomicAdd(ap + 2 * ((int64_t)s.base + L.sA + L.sB), s.w3 * val);
+    }
+}
+
 // Fixed-point scatter: value * weight * 2^E rounded to the nearest integer,
 // added with 64-bit integer atomics (order-independent, exact).
 __device__ __forceinline__ void fx_add(unsigned long long* p, float q)

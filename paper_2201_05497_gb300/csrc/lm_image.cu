@@ -240,6 +240,10 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
     float* __restrict__ acc_yf = A.acc_yf;
     unsigned long long* __restrict__ acci_std = A.acci_std;
     unsigned long long* __restrict__ acci_yf = A.acci_yf;
+    // float accumulators hold z pairs: voxel k is element 2k plus element
+    // 2(k - nx*ny) + 1 of the slice below; each half is cleared by its reader
+    const int64_t sz = (int64_t)nx * ny;
+    const bool below = Tl.z > 0;
     if (m.data && have_yf) {
         float vf[RPT];
         long long vi[RPT];
@@ -252,6 +256,7 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
             if (xx < nx && yy < ny) {
                 const int64_t k = ((int64_t)Tl.z * nx + xx) * ny + yy;
                 if (det) vi[q] = (long long)acci_yf[k];
+                else if (A.acc_pairs) vf[q] = acc_yf[2 * k] + (below ? acc_yf[2 * (k - sz) + 1] : 0.0f);
                 else vf[q] = acc_yf[k];
             }
         }
@@ -266,7 +271,12 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
                     acci_yf[k] = 0ULL;
                 } else {
                     sm.f[r][tx] = vf[q];
-                    acc_yf[k] = 0.0f;
+                    if (A.acc_pairs) {
+                        acc_yf[2 * k] = 0.0f;
+                        if (below) acc_yf[2 * (k - sz) + 1] = 0.0f;
+                    } else {
+                        acc_yf[k] = 0.0f;
+                    }
                 }
             }
         }
@@ -293,7 +303,7 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
                     if (have_yf) s += sm.i[tx][ty + q * TR];
                     dz[q] = (float)((double)s * m.fx);
                 } else {
-                    dz[q] = acc_std[j];
+                    dz[q] = A.acc_pairs ? acc_std[2 * j] + (below ? acc_std[2 * (j - sz) + 1] : 0.0f) : acc_std[j];
                     if (have_yf) dz[q] += sm.f[tx][ty + q * TR];
                 }
             } else {
@@ -308,8 +318,14 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
         if (xx < nx && yy < ny) {
             const int64_t j = ((int64_t)Tl.z * ny + yy) * nx + xx;
             if (m.data) {
-                if (det) acci_std[j] = 0ULL;
-                else acc_std[j] = 0.0f;
+                if (det) {
+                    acci_std[j] = 0ULL;
+                } else if (A.acc_pairs) {
+                    acc_std[2 * j] = 0.0f;
+                    if (below) acc_std[2 * (j - sz) + 1] = 0.0f;
+                } else {
+                    acc_std[j] = 0.0f;
+                }
             }
             float zh, zl = 0.0f, xn;
             if (m.init) {
@@ -558,10 +574,19 @@ __device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, i
             if (A.kahan) tma_load_3d(st + TmaLayout::p_zc, &M->zc, I.x0, I.y0, z, bar + s);
         }
     } else {
-        const uint32_t acc = A.det ? 2 * tile : tile;
+        // accumulator tiles: u64 (deterministic) or float z pairs, 8 KB each
+        const uint32_t acc = (A.det || A.acc_pairs) ? 2 * tile : tile;
+        const int ax = A.acc_pairs && !A.det ? 2 : 1;  // pair tensors are (2n, ., .)
+        if (z < I.zb) {
+            // halo slice below the run: only the upper halves of its accumulator pairs are needed
+            mbar_expect_tx(bar + s, 2 * acc);
+            tma_load_3d(st + TmaLayout::d_as, &M->acc_std, ax * I.x0, I.y0, z, bar + s);
+            tma_load_3d(st + TmaLayout::d_ay, &M->acc_yf, ax * I.y0, I.x0, z, bar + s);
+            return;
+        }
         mbar_expect_tx(bar + s, 2 * acc + 3 * tile + (A.kahan ? tile : 0u));
-        tma_load_3d(st + TmaLayout::d_as, &M->acc_std, I.x0, I.y0, z, bar + s);
-        tma_load_3d(st + TmaLayout::d_ay, &M->acc_yf, I.y0, I.x0, z, bar + s);
+        tma_load_3d(st + TmaLayout::d_as, &M->acc_std, ax * I.x0, I.y0, z, bar + s);
+        tma_load_3d(st + TmaLayout::d_ay, &M->acc_yf, ax * I.y0, I.x0, z, bar + s);
         tma_load_3d(st + TmaLayout::d_x, &M->xt[xcur], I.x0, I.y0, z, bar + s);
         tma_load_3d(st + TmaLayout::d_T, &M->T, I.x0, I.y0, z, bar + s);
         tma_load_3d(st + TmaLayout::d_z, &M->z, I.x0, I.y0, z, bar + s);
@@ -699,28 +724,59 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
     }
 }
 
-// Data update merge for slice z of item I.
+// Data update merge for slice z of item I.  Float accumulators are z pairs:
+// a voxel's value is the first half of its own pair plus the second half of
+// the pair below, which the thread carries from the previous slice in
+// prev_s (its 4 x-fastest points) and prev_y (its 4 y-fastest points).  A run
+// starting above z = 0 first reads the slice below (z < I.zb) for these only.
 __device__ __forceinline__ void data_slice(const lmh::ImgArgs& A, const PassMode& m, uint8_t* sm, int s, int z,
-                                           const Item& I, float* x_nxt_std, float* x_nxt_yf)
+                                           const Item& I, float* x_nxt_std, float* x_nxt_yf, float* prev_s,
+                                           float* prev_y)
 {
     const int nx = A.n[0], ny = A.n[1];
+    const int64_t sz = (int64_t)nx * ny;
     const bool det = A.det != 0;
+    const bool pairs = A.acc_pairs && !det;
     const uint8_t* st = sm + TmaLayout::stage + s * TmaLayout::stage_sz;
     const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
     float* AYT = (float*)(sm + TmaLayout::dbuf);
     long long* AYT64 = (long long*)(sm + TmaLayout::dbuf);
     float* XO = (float*)(sm + TmaLayout::xo);
+    const float* AYp = (const float*)(st + TmaLayout::d_ay);
+    const float* ASp = (const float*)(st + TmaLayout::d_as);
+    if (z < I.zb) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int r = wrow + 8 * k;
+            prev_y[k] = AYp[r * 2 * TD + 2 * lane + 1];
+            prev_s[k] = ASp[r * 2 * TD + 2 * lane + 1];
+        }
+        return;
+    }
+    const bool below = z > 0;
     // acc_yf tile (rows x, columns y) -> transposed buffer [y][x]; clear it in memory
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int r = wrow + 8 * k, c = lane;
         const int ix = I.x0 + r, iy = I.y0 + c;
-        if (det) AYT64[c * TP + r] = ((const long long*)(st + TmaLayout::d_ay))[r * TD + c];
-        else AYT[c * TP + r] = ((const float*)(st + TmaLayout::d_ay))[r * TD + c];
+        if (det) {
+            AYT64[c * TP + r] = ((const long long*)(st + TmaLayout::d_ay))[r * TD + c];
+        } else if (pairs) {
+            AYT[c * TP + r] = AYp[r * 2 * TD + 2 * c] + prev_y[k];
+            prev_y[k] = AYp[r * 2 * TD + 2 * c + 1];
+        } else {
+            AYT[c * TP + r] = AYp[r * TD + c];
+        }
         if (ix < nx && iy < ny) {
             const int64_t k2 = ((int64_t)z * nx + ix) * ny + iy;
-            if (det) A.acci_yf[k2] = 0ULL;
-            else A.acc_yf[k2] = 0.0f;
+            if (det) {
+                A.acci_yf[k2] = 0ULL;
+            } else if (pairs) {
+                A.acc_yf[2 * k2] = 0.0f;
+                if (below) A.acc_yf[2 * (k2 - sz) + 1] = 0.0f;
+            } else {
+                A.acc_yf[k2] = 0.0f;
+            }
         }
     }
     __syncthreads();
@@ -741,8 +797,13 @@ __device__ __forceinline__ void data_slice(const lmh::ImgArgs& A, const PassMode
                 sacc += AYT64[ty * TP + tx];
                 dz = (float)((double)sacc * m.fx);
                 A.acci_std[j] = 0ULL;
+            } else if (pairs) {
+                dz = ASp[ty * 2 * TD + 2 * tx] + prev_s[k];
+                dz += AYT[ty * TP + tx];
+                A.acc_std[2 * j] = 0.0f;
+                if (below) A.acc_std[2 * (j - sz) + 1] = 0.0f;
             } else {
-                dz = ((const float*)(st + TmaLayout::d_as))[t];
+                dz = ASp[t];
                 dz += AYT[ty * TP + tx];
                 A.acc_std[j] = 0.0f;
             }
@@ -754,6 +815,7 @@ __device__ __forceinline__ void data_slice(const lmh::ImgArgs& A, const PassMode
             x_nxt_std[j] = xn;
             XO[ty * TP + tx] = xn;
         }
+        if (pairs) prev_s[k] = ASp[ty * 2 * TD + 2 * tx + 1];
     }
     __syncthreads();
     store_x_yf(A, XO, x_nxt_yf, I, z);
@@ -767,15 +829,18 @@ __device__ bool tma_item(const lmh::ImgArgs& A, const PassMode& m, int u, int64_
     const Item I = item_of(A, it);
     const bool prior = m.prior;
     const int wp = prior ? A.wpar[u] : 0;
-    const int zs = (prior && I.zb > 0) ? I.zb - 1 : I.zb;
+    // a halo slice below the run: the prior needs its w+, paired accumulators their upper halves
+    const bool halo = I.zb > 0 && (prior || (A.acc_pairs && !A.det));
+    const int zs = halo ? I.zb - 1 : I.zb;
     float dprev[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float prev_y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (threadIdx.x == 0) issue_slice(A, prior, xcur, wp, sm, 0, zs, zs, I, true, p.bar);
     for (int z = zs, i = 0; z < I.ze; ++z, ++i) {
         const int s = i & 1;
         if (threadIdx.x == 0 && z + 1 < I.ze) issue_slice(A, prior, xcur, wp, sm, s ^ 1, z + 1, zs, I, false, p.bar);
         if (!stage_wait(p, s, A.err)) return false;
         if (prior) prior_slice(A, wp, sm, s, z, zs, I, dprev, x_nxt_std, x_nxt_yf);
-        else data_slice(A, m, sm, s, z, I, x_nxt_std, x_nxt_yf);
+        else data_slice(A, m, sm, s, z, I, x_nxt_std, x_nxt_yf, dprev, prev_y);
         __syncthreads();
     }
     return true;
@@ -1295,12 +1360,21 @@ int encode_tma_maps(const lm_grid* g, float* const x[2], float* const w[2], int 
     if ((rc = encode_one(&out->T, F32, 3, T, dims, strides, box_t))) return rc;
     if ((rc = encode_one(&out->z, F32, 3, z, dims, strides, box_t))) return rc;
     if ((rc = encode_one(&out->zc, F32, 3, zc, dims, strides, box_t))) return rc;
-    const cuuint64_t es = det ? 8 : 4;
-    const CUtensorMapDataType at = det ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : F32;
-    const cuuint64_t s_std[2] = {nx * es, nx * ny * es};
-    if ((rc = encode_one(&out->acc_std, at, 3, acc_std, dims, s_std, box_t))) return rc;
-    const cuuint64_t d_yf[3] = {ny, nx, nz}, s_yf[2] = {ny * es, nx * ny * es};
-    if ((rc = encode_one(&out->acc_yf, at, 3, acc_yf, d_yf, s_yf, box_t))) return rc;
+    if (det) {
+        // 64-bit fixed-point accumulators, one per voxel
+        const CUtensorMapDataType at = CU_TENSOR_MAP_DATA_TYPE_UINT64;
+        const cuuint64_t s_std[2] = {nx * 8, nx * ny * 8};
+        if ((rc = encode_one(&out->acc_std, at, 3, acc_std, dims, s_std, box_t))) return rc;
+        const cuuint64_t d_yf[3] = {ny, nx, nz}, s_yf[2] = {ny * 8, nx * ny * 8};
+        if ((rc = encode_one(&out->acc_yf, at, 3, acc_yf, d_yf, s_yf, box_t))) return rc;
+    } else {
+        // float z pairs: a row of n voxels is 2n floats; a tile box covers 32 pairs
+        const cuuint32_t box_p[3] = {2 * TD, TD, 1};
+        const cuuint64_t d_std[3] = {2 * nx, ny, nz}, s_std[2] = {2 * nx * 4, 2 * nx * ny * 4};
+        if ((rc = encode_one(&out->acc_std, F32, 3, acc_std, d_std, s_std, box_p))) return rc;
+        const cuuint64_t d_yf[3] = {2 * ny, nx, nz}, s_yf[2] = {2 * ny * 4, 2 * nx * ny * 4};
+        if ((rc = encode_one(&out->acc_yf, F32, 3, acc_yf, d_yf, s_yf, box_p))) return rc;
+    }
     return LM_OK;
 }
 

@@ -128,6 +128,7 @@ struct EvArgs {
     unsigned* maxbits_base;
     int prior_fused;            // 1: the prior's dual step runs inside the TMA image pass instead
     int prior_only;             // 1: data selections are left to the tile-binned projector
+    int acc_pairs;              // 1: acc_std / acc_yf hold (voxel j, voxel j + nx*ny) float pairs
 };
 
 // Batched multi-frame epochs: per-frame argument tables in device memory.
@@ -228,8 +229,8 @@ struct alignas(128) TmaMaps {
     CUtensorMap xt[2];     // x (std), box {32, 32, 1}
     CUtensorMap w[2];      // w, (nx, ny, nz, ndim), box {36, 33, 1, ndim}
     CUtensorMap T, z, zc;  // box {32, 32, 1}
-    CUtensorMap acc_std;   // f32 (or u64 when deterministic), box {32, 32, 1}
-    CUtensorMap acc_yf;    // y-fastest layout (ny, nx, nz), box {32, 32, 1}
+    CUtensorMap acc_std;   // float z pairs (2nx, ny, nz), box {64, 32, 1}; u64 (nx, ny, nz) when deterministic
+    CUtensorMap acc_yf;    // the same in the y-fastest layout (2ny, nx, nz) / (ny, nx, nz)
 };
 bool tma_capable(const lm_grid* g);
 int encode_tma_maps(const lm_grid* g, float* const x[2], float* const w[2], int ndim, float* T, float* z, float* zc,
@@ -279,6 +280,7 @@ struct ImgArgs {
     int* wpar_w;
     int* wbase;
     // TMA-staged passes
+    int acc_pairs;         // 1: float accumulators hold (j, j + nx*ny) pairs (see EvArgs)
     const TmaMaps* tm;     // device copy of the state's maps, or nullptr
     int xcur;              // index of x_cur among the two x buffers
     int zlen;              // z slices per work item

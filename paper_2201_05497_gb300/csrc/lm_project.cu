@@ -362,6 +362,7 @@ __device__ __forceinline__ void event_chunk(const EvArgs& A, const float* __rest
         const bool valid = r < R && (grp * R + r) < nev;
         if (!valid) E.cnt = 0;
         lor_strides(Gm, k, has_yf, E);
+        E.k = k;
         const int npass = (E.cnt + G - 1) / G;
         const int iend = E.i0 + E.cnt;
         float acc = 0.0f, acc1 = 0.0f;
@@ -433,22 +434,24 @@ __device__ __forceinline__ void event_chunk(const EvArgs& A, const float* __rest
         }
         if (T::back_float && bval != 0.0f) {
             float* acc_img = E.yf ? A.acc_yf : A.acc_std;
+            auto put = [&](const Smp& s) {
+                if (A.acc_pairs) scatter_pairs<TWO_D>(acc_img, E, s, bval);
+                else scatter<TWO_D>(acc_img, E, s, bval);
+            };
             if (T::gather) {
 #pragma unroll
                 for (int p = 0; p < PC; ++p)
-                    if (p < npass) scatter<TWO_D>(acc_img, E, cs[p], bval);
+                    if (p < npass) put(cs[p]);
                 for (int p = PC; p < npass; ++p) {
                     const int i = E.i0 + p * G + sub;
                     Smp s;
-                    if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s))
-                        scatter<TWO_D>(acc_img, E, s, bval);
+                    if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s)) put(s);
                 }
             } else {
                 for (int p = 0; p < npass; ++p) {
                     const int i = E.i0 + p * G + sub;
                     Smp s;
-                    if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s))
-                        scatter<TWO_D>(acc_img, E, s, bval);
+                    if (i < iend && sample_any<TWO_D>(Gm, E, tofmode, tab, inv_dt, i, s)) put(s);
                 }
             }
         }

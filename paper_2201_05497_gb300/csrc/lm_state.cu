@@ -103,8 +103,9 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
     float* T = F(V);
     float* w0 = F(nd * V);
     float* w1 = F(nd * V);
-    float* acc_std = det ? nullptr : F(V);
-    float* acc_yf = (!det && yf) ? F(V) : nullptr;
+    // float accumulators hold (voxel j, voxel j + nx*ny) pairs (scatter_pairs)
+    float* acc_std = det ? nullptr : F(2 * V);
+    float* acc_yf = (!det && yf) ? F(2 * V) : nullptr;
     unsigned long long* ai_std = det ? c.take<unsigned long long>(V * 8) : nullptr;
     unsigned long long* ai_yf = (det && yf) ? c.take<unsigned long long>(V * 8) : nullptr;
     float* y = F((size_t)std::max<int64_t>(N, 1));
@@ -166,6 +167,7 @@ EvArgs base_ev_args(const lm_state* st)
     a.tof_tab = st->tof.n_bins > 0 ? st->tof_tab : nullptr;
     a.group = st->group;
     a.prior_fused = st->tma ? 1 : 0;
+    a.acc_pairs = st->det ? 0 : 1;
     return a;
 }
 
@@ -200,6 +202,7 @@ ImgArgs base_img_args(const lm_state* st)
     a.inv_p_prior = 2.0f;
     a.s_prior = (float)(st->gamma * (double)st->P.rho / st->knorm);
     a.beta = st->P.beta;
+    a.acc_pairs = st->det ? 0 : 1;
     a.tm = st->tma ? st->tmaps : nullptr;
     a.err = st->err;
     a.zlen = st->zlen;
@@ -289,8 +292,8 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     LM_CUDA(cudaMemsetAsync(st->zc, 0, V * 4, s));
     LM_CUDA(cudaMemsetAsync(st->w[0], 0, (size_t)std::max(1, st->ndim) * V * 4, s));
     LM_CUDA(cudaMemsetAsync(st->w[1], 0, (size_t)std::max(1, st->ndim) * V * 4, s));
-    if (st->acc_std) LM_CUDA(cudaMemsetAsync(st->acc_std, 0, V * 4, s));
-    if (st->acc_yf) LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, V * 4, s));
+    if (st->acc_std) LM_CUDA(cudaMemsetAsync(st->acc_std, 0, 2 * V * 4, s));
+    if (st->acc_yf) LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, 2 * V * 4, s));
     if (st->acci_std) LM_CUDA(cudaMemsetAsync(st->acci_std, 0, V * 8, s));
     if (st->acci_yf) LM_CUDA(cudaMemsetAsync(st->acci_yf, 0, V * 8, s));
     LM_CUDA(cudaMemsetAsync(st->wbase, 0, 16, s));

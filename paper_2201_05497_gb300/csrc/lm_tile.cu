@@ -576,7 +576,8 @@ __global__ void __launch_bounds__(256) tl_back_kernel(const TileArgs A)
             for (int lx = threadIdx.x & 31; lx < BYH; lx += 32) {
                 const int gx = b.o0 + lx;
                 const float val = box[(lz * BYH + ly) * BXW + lx];
-                if (gx < nx && val != 0.0f) atomicAdd(A.acc + ((int64_t)gz * ny + gy) * nx + gx, val);
+                // the accumulator holds z pairs: voxel j is element 2j
+                if (gx < nx && val != 0.0f) atomicAdd(A.acc + 2 * (((int64_t)gz * ny + gy) * nx + gx), val);
             }
         }
     }
