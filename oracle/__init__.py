@@ -8,7 +8,9 @@ The arithmetic lives in ``lmoracle.c`` (plain double precision C, built with
 gcc on first use); this module only marshals numpy arrays.  Functions follow
 the paper's notation: ``fwd`` is P^LM (Eq. lmop), ``back`` its adjoint,
 ``sens`` is P^T 1, ``lm_init``/``lm_update`` are Alg. 2, ``sino_*`` are
-Alg. 1 on a full TOF sinogram.
+Alg. 1 on a full TOF sinogram, ``EMTV``/``emtv_denoise`` are Alg. 3 (the
+listmode EM-TV warm start).  The denoiser's iterate path at a fixed iteration
+count (its extrapolation step) is parity unpinned; its limit is pinned.
 """
 from __future__ import annotations
 
@@ -116,6 +118,10 @@ def lib():
             L.or_sino_update.argtypes = [P(SinoProblem), P(LmState), C.c_int32, P(C.c_double), P(C.c_double)]
             L.or_sino_objective.argtypes = [P(SinoProblem), P(C.c_double)]
             L.or_sino_objective.restype = C.c_double
+            L.or_emtv_em_step.argtypes = [P(LmProblem), P(C.c_double), P(C.c_double), C.c_int32, P(C.c_double)]
+            L.or_emtv_denoise.argtypes = [P(Grid), P(C.c_double), P(C.c_double), P(C.c_uint8), C.c_int,
+                                          C.c_double, P(C.c_double), P(C.c_double)]
+            L.or_emtv_epoch.argtypes = [P(LmProblem), P(C.c_double), P(C.c_double), C.c_int]
             _lib = L
     return _lib
 
@@ -328,6 +334,46 @@ class LM:
     def objective(self, x: np.ndarray | None = None) -> float:
         xx = np.ascontiguousarray(self.x if x is None else x, dtype=np.float64)
         return float(lib().or_lm_objective(C.byref(self.prob), _p(xx, C.c_double), _p(self._sens, C.c_double)))
+
+
+class EMTV:
+    """Listmode EM-TV (Alg. 3) in FP64: the subset EM step, the weighted TV
+    denoising by accelerated PDHG, and one pass over the subsets."""
+
+    def __init__(self, geo: Geometry, ev: EventArrays, n_subsets: int, beta: float, knorm: float):
+        self.geo, self.ev = geo, ev
+        self._mu = np.ones(max(ev.n, 1), dtype=np.int32)
+        self.prob = LmProblem(C.pointer(geo.sc), C.pointer(geo.g), C.pointer(geo.tof),
+                              _p(ev.det1, C.c_int32), _p(ev.det2, C.c_int32), _p(ev.tof, C.c_int16),
+                              _p(ev.corr, C.c_float), _p(ev.contam, C.c_float), _p(self._mu, C.c_int32),
+                              ev.n, n_subsets, beta, 0.0, 0.0, knorm)
+
+    def em_step(self, x: np.ndarray, sens_img: np.ndarray, i: int) -> np.ndarray:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        ss = np.ascontiguousarray(sens_img, dtype=np.float64)
+        z = np.zeros(self.geo.V)
+        lib().or_emtv_em_step(C.byref(self.prob), _p(ss, C.c_double), _p(xx, C.c_double), int(i),
+                              _p(z, C.c_double))
+        return z
+
+    def epoch(self, x: np.ndarray, sens_img: np.ndarray, pdhg_iters: int = 20) -> np.ndarray:
+        xx = np.array(x, dtype=np.float64)
+        ss = np.ascontiguousarray(sens_img, dtype=np.float64)
+        lib().or_emtv_epoch(C.byref(self.prob), _p(ss, C.c_double), _p(xx, C.c_double), int(pdhg_iters))
+        return xx
+
+
+def emtv_denoise(geo: Geometry, z: np.ndarray, w: np.ndarray, free: np.ndarray, iters: int, knorm: float):
+    """argmin_{u>=0} sum w/2 (u-z)^2 + ||Ku||_{2,1} by accelerated PDHG;
+    returns (u, q) with q the dual variable."""
+    zz = np.ascontiguousarray(z, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    ff = np.ascontiguousarray(free, dtype=np.uint8)
+    u = np.zeros(geo.V)
+    q = np.zeros(max(geo.ndim, 1) * geo.V)
+    lib().or_emtv_denoise(C.byref(geo.g), _p(zz, C.c_double), _p(ww, C.c_double), _p(ff, C.c_uint8), int(iters),
+                          float(knorm), _p(u, C.c_double), _p(q, C.c_double))
+    return u, q
 
 
 class Sino:

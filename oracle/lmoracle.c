@@ -34,9 +34,17 @@
  *   The detectors lie outside the image, so the infinite line and the
  *   detector-to-detector segment cross the same voxels.
  *
+ *   - Alg. 3       listmode EM-TV (the warm start x0): subset EM step and
+ *                  weighted TV denoising by accelerated primal-dual iterations
+ *
  * parity pinned: adjoint, TOF sum, closed-form chords, brute force on tiny
- * grids, prox fixed points, TV adjoint and norm, LM == sinogram SPDHG (see the
- * CPU tests).
+ * grids, prox fixed points, TV adjoint and norm, LM == sinogram SPDHG; EM-TV:
+ * the EM step as a scaled log-likelihood gradient step (finite differences),
+ * the denoiser's closed form (two voxels), an independent dual solve,
+ * optimality conditions, Chambolle-Pock's rate bound and limits (see the CPU
+ * tests).  The denoiser's extrapolation ubar = u+ + theta (u+ - u) is pinned
+ * only through these: leaving it out reaches the same limit, so the iterate
+ * path at a fixed iteration count is parity unpinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -560,6 +568,107 @@ double or_lm_objective(const or_lm_problem* P, const double* x, const double* se
         c += P->beta * r;
     }
     return c;
+}
+
+/* ------------------------------------------------------------------------
+ * Listmode EM-TV (Alg. 3), the initialisation of x0 used in the paper's
+ * experiments (one pass over the n subsets, Sec. "Numerical experiments").
+ * Per subset i:
+ *   z = x n / g * (P^LM_{N_i})^T (1 / (P^LM_{N_i} x + s_{N_i}))  (subset EM step;
+ *       the printed step has no x inside P^LM_{N_i}: read as the current x)
+ *   w = g / (beta x)
+ *   x = argmin_{u >= 0} sum_j w_j/2 (u_j - z_j)^2 + ||K u||_{2,1}
+ * The last problem is solved by the accelerated primal-dual algorithm of
+ * Chambolle & Pock (2011, their Alg. 2), which the paper names, with
+ * G(u) = sum_j w_j/2 (u_j - z_j)^2 + i_{u >= 0} (uniformly convex with modulus
+ * gam = min_j w_j over the free voxels) and F^* the indicator of the unit
+ * 2-norm balls.  Readings (the paper gives no parameters): voxels with
+ * x_j = 0 or g_j = 0 are held at 0; u_0 = ubar_0 = z, q_0 = 0,
+ * tau_0 = sigma_0 = 0.99 / ||K||; per iteration
+ *   q <- proj(q + sigma K ubar);  u+ = prox_{tau G}(u - tau K^T q);
+ *   theta = 1/sqrt(1 + 2 gam tau);  tau <- theta tau;  sigma <- sigma/theta;
+ *   ubar = u+ + theta (u+ - u).
+ * ------------------------------------------------------------------------ */
+
+/* Subset EM step: z_j = x_j n / g_j * sum_{e in N_i} c_e J_e^T / (c_e J_e x + s_e)
+ * (z_j = 0 where g_j = 0).  Event e belongs to subset e mod n. */
+void or_emtv_em_step(const or_lm_problem* P, const double* sens, const double* x, int32_t i, double* z)
+{
+    const int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    for (int64_t j = 0; j < V; ++j) z[j] = 0.0;
+    for (int64_t e = i; e < P->n_ev; e += P->n_subsets) {
+        const double u = ev_fwd(P, e, x) + (double)P->contam[e];
+        ev_back(P, e, 1.0 / u, z);
+    }
+    for (int64_t j = 0; j < V; ++j) z[j] = sens[j] > 0.0 ? x[j] * (double)P->n_subsets / sens[j] * z[j] : 0.0;
+}
+
+/* Weighted TV denoising by the accelerated primal-dual algorithm (see
+ * above).  free_[j] = 0 holds u_j at 0.  q: dual variable (ndim*V), output. */
+void or_emtv_denoise(const or_grid* g, const double* z, const double* w, const unsigned char* free_, int iters,
+                     double knorm, double* u, double* q)
+{
+    const int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    const int nd = or_tv_ndim(g) > 0 ? or_tv_ndim(g) : 1;
+    double gam = INFINITY;
+    for (int64_t j = 0; j < V; ++j)
+        if (free_[j] && w[j] < gam) gam = w[j];
+    if (!(gam < INFINITY)) gam = 0.0;
+    double* ubar = (double*)malloc(sizeof(double) * V);
+    double* kt = (double*)malloc(sizeof(double) * V);
+    double* gr = (double*)malloc(sizeof(double) * nd * V);
+    for (int64_t j = 0; j < V; ++j) u[j] = ubar[j] = free_[j] ? z[j] : 0.0;
+    for (int64_t j = 0; j < (int64_t)nd * V; ++j) q[j] = 0.0;
+    double tau = 0.99 / knorm, sigma = 0.99 / knorm;
+    for (int it = 0; it < iters; ++it) {
+        or_tv_grad(g, ubar, gr);
+        for (int64_t j = 0; j < (int64_t)nd * V; ++j) q[j] += sigma * gr[j];
+        or_tv_prox(g, q, 1.0); /* projection onto the unit balls */
+        or_tv_adj(g, q, kt);
+        const double theta = 1.0 / sqrt(1.0 + 2.0 * gam * tau);
+        for (int64_t j = 0; j < V; ++j) {
+            double un = 0.0;
+            if (free_[j]) {
+                const double v = u[j] - tau * kt[j];
+                un = fmax(0.0, (v + tau * w[j] * z[j]) / (1.0 + tau * w[j]));
+            }
+            ubar[j] = un + theta * (un - u[j]);
+            u[j] = un;
+        }
+        tau *= theta;
+        sigma /= theta;
+    }
+    free(ubar);
+    free(kt);
+    free(gr);
+}
+
+/* One EM-TV pass over the subsets 0..n-1 in order; x (in/out). */
+void or_emtv_epoch(const or_lm_problem* P, const double* sens, double* x, int pdhg_iters)
+{
+    const int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    const int nd = or_tv_ndim(P->g) > 0 ? or_tv_ndim(P->g) : 1;
+    double* z = (double*)malloc(sizeof(double) * V);
+    double* w = (double*)malloc(sizeof(double) * V);
+    double* q = (double*)malloc(sizeof(double) * nd * V);
+    unsigned char* fr = (unsigned char*)malloc(V);
+    for (int32_t i = 0; i < P->n_subsets; ++i) {
+        or_emtv_em_step(P, sens, x, i, z);
+        if (!(P->beta > 0.0)) {
+            /* no prior: the weight is infinite and the update is the EM step */
+            for (int64_t j = 0; j < V; ++j) x[j] = z[j];
+            continue;
+        }
+        for (int64_t j = 0; j < V; ++j) {
+            fr[j] = (x[j] > 0.0 && sens[j] > 0.0) ? 1 : 0;
+            w[j] = fr[j] ? sens[j] / (P->beta * x[j]) : 0.0;
+        }
+        or_emtv_denoise(P->g, z, w, fr, pdhg_iters, P->knorm, x, q);
+    }
+    free(z);
+    free(w);
+    free(q);
+    free(fr);
 }
 
 /* ------------------------------------------------------------------------
