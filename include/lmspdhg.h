@@ -175,7 +175,7 @@ size_t lm_knorm_workspace_bytes(const lm_grid* grid);
 int lm_knorm_fp64(const lm_grid* grid, int32_t iters, void* ws, size_t ws_bytes, double* out_host,
                   void* stream);
 
-/* ---- event set-up (Alg. 2 steps 2 and 6) -------------------------------- */
+/* ---- event set-up (Alg. 2: event counts, sub lists) --------------------- */
 /* Validates the events (0 <= det < n_det, det1 != det2, |tof| <= (n_bins-1)/2,
  * corr > 0, contam > 0), counts mu_e = number of events of the whole list in
  * the event's data bin (its unordered detector pair and TOF bin; footnote of
@@ -233,13 +233,13 @@ size_t lmspdhg_tile_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subse
 size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets,
                            int32_t deterministic);
 
-/* Initialise Alg. 2 (steps 3-6) on events already in subset-contiguous
+/* Initialise Alg. 2 (duals, z, step sizes) on events already in subset-contiguous
  * order (from lm_event_setup; the arrays are referenced, not copied, and
  * must outlive the state):
  *   y_e = 1 - mu_e / ((P^LM x0)_e + s_e)                      (Eq. yinit)
  *   z = zbar = P^T 1 + (P^LM)^T((y - 1)/mu) + K^T w, w = 0
  *     (= P^T applied to the sinogram that is 1 on empty bins and Eq. yinit
- *      elsewhere; the printed minus sign of step 5 is read as this plus)
+ *      elsewhere; the printed minus sign of the z initialisation is read as this plus)
  *   T = min_k T_k with T_k = gamma^-1 rho p_k / (P^T 1 / n) for data subsets
  *   and T_{n+1} = gamma^-1 p_{n+1} rho / ||K||;  S_e = gamma rho / (P^LM 1)_e
  *   (Eq. lm_stepsizes), S_{n+1} = gamma rho / ||K||; p_k = 1/(2n), p_{n+1} = 1/2.
@@ -286,7 +286,7 @@ int lmspdhg_info(lm_state* st, int64_t* n_updates, double* gamma, double* knorm)
  * forward-projection times of subset 0 (ms) for widths 8, 16, 32 (else 0). */
 int lmspdhg_tuning(lm_state* st, int32_t* group, double* ms3);
 
-/* Re-initialise the state (Alg. 2 steps 3-5 as in lmspdhg_create) for the
+/* Re-initialise the state (as lmspdhg_create initialises Alg. 2) for the
  * current contents of the referenced event arrays and a new x0, keeping the
  * buffers and the captured epoch graph: the events may have been overwritten
  * with another frame of the same size and subset split.  Synchronous. */
@@ -310,6 +310,49 @@ int lmspdhg_image_kernel(lm_state* st, int32_t* kind);
 int lmspdhg_projector(lm_state* st, int32_t* kind, int64_t* n_segments);
 
 int lmspdhg_destroy(lm_state* st);
+
+/* ---- listmode EM-TV: the warm start x0 (Alg. 3) ------------------------- */
+/* The listmode experiments start LM-SPDHG from one pass of listmode EM-TV
+ * over the n subsets (Alg. 3, Sec. "Numerical experiments").  For subsets
+ * i = 0, 1, ..., n-1 in turn, with g = P^T 1 (sens):
+ *   z = x n / g * (P^LM_{N_i})^T (1 / (P^LM_{N_i} x + s_{N_i}))   (EM step)
+ *   w = g / (beta x)
+ *   x = argmin_{u >= 0} sum_j w_j/2 (u_j - z_j)^2 + ||K u||_{2,1}  (weighted TV denoising)
+ * Readings (the paper leaves them open): the EM step's forward projection
+ * uses the current x; z_j = 0 where g_j = 0; voxels with x_j = 0 or g_j = 0
+ * are held at 0 (w_j = 0); the denoising problem is solved by `pdhg_iters`
+ * iterations of the accelerated primal-dual algorithm of Chambolle & Pock
+ * (2011, their Alg. 2) from u = z, q = 0, tau_0 = sigma_0 = 0.99/knorm,
+ * with the uniform convexity gam = min w_j over the free voxels:
+ *   q <- q / max(1, |q|) after q += sigma K ubar;  u+ = max(0, (u - tau K^T q
+ *   + tau w z) / (1 + tau w));  theta = 1/sqrt(1 + 2 gam tau);  tau *= theta;
+ *   sigma /= theta;  ubar = u+ + theta (u+ - u).
+ * beta = 0 makes x = z (listmode OSEM).  float32 images and float atomics
+ * (the back-projection's order of additions varies between runs).
+ *
+ * lm_emtv_epoch: ev_perm holds the events in subset-contiguous order
+ * (lm_event_setup's det/tof/corr/contam output; mu unused) with host int64
+ * offsets sub_off_host[n_subsets+1] (0 .. n, non-decreasing).  sens, x:
+ * device float images; x (in/out) >= 0.  beta >= 0; pdhg_iters in
+ * [0, 10000]; knorm = ||K|| (lm_knorm_fp64) or an upper bound, > 0.
+ * ws: device workspace of lm_emtv_workspace_bytes(grid) bytes, 256-byte
+ * aligned.  Asynchronous on `stream`; LM_ERR_NOMEM for a short workspace,
+ * LM_ERR_INVALID_ARG for the other argument errors (nothing is queued). */
+size_t lm_emtv_workspace_bytes(const lm_grid* grid);
+int lm_emtv_epoch(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev_perm,
+                  const int64_t* sub_off_host, int32_t n_subsets, const float* sens, float* x, float beta,
+                  int32_t pdhg_iters, double knorm, void* ws, size_t ws_bytes, void* stream);
+/* The EM step alone over the events of ev (one subset):
+ * z = x n_subsets / sens * (P^LM)^T (1 / (P^LM x + s)), z overwritten
+ * (device float image, 0 where sens = 0).  Same workspace. */
+int lm_emtv_em_step(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev,
+                    int32_t n_subsets, const float* sens, const float* x, float* z, void* ws, size_t ws_bytes,
+                    void* stream);
+/* The weighted TV denoising alone: u (device float image, overwritten) after
+ * `iters` iterations from u = z; voxels with w_j <= 0 are held at 0.  Same
+ * workspace. */
+int lm_emtv_denoise(const lm_grid* grid, const float* z, const float* w, float* u, int32_t iters, double knorm,
+                    void* ws, size_t ws_bytes, void* stream);
 
 /* ---- batched epochs of several frames ----------------------------------- */
 /* A batch advances every occupied slot (an lm_state) by one epoch of Alg. 2

@@ -472,7 +472,7 @@ static void ev_back(const or_lm_problem* P, int64_t e, double v, double* img)
     or_lor_visit(P->sc, P->g, P->tof, P->det1[e], P->det2[e], P->tbin[e], ev_mode(P->tof), back_visit, &c);
 }
 
-/* Initialisation, Alg. 2 steps 3-5 plus the first primal step's inputs:
+/* Initialisation of Alg. 2 (duals, z, step sizes) plus the first primal step's inputs:
  *   y_e = 1 - mu_e / ((P^LM x0)_e + s_e)                    (Eq. yinit)
  *   z = zbar = P^T 1 + (P^LM)^T ((y - 1)/mu) + K^T w, w = 0
  *     (the sign reading: the first part equals P^T applied to a sinogram that

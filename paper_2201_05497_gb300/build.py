@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblmspdhg.so")
-SOURCES = ["lm_project.cu", "lm_image.cu", "lm_setup.cu", "lm_state.cu", "lm_noalloc.cu", "lm_server.cu", "lm_tile.cu"]
+SOURCES = ["lm_project.cu", "lm_image.cu", "lm_setup.cu", "lm_state.cu", "lm_noalloc.cu", "lm_server.cu", "lm_tile.cu",
+           "lm_emtv.cu"]
 HEADERS = ["lm_device.cuh", "lm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

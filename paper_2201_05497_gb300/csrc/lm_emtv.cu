@@ -1,0 +1,399 @@
+// Listmode EM-TV (Alg. 3): the warm start of the listmode experiments.  One
+// pass over the n subsets; per subset a listmode EM step on the subset's
+// events (the event kernel in its EM mode, scattering c_e / (c_e J_e x + s_e))
+// followed by a weighted TV denoising problem
+//   x = argmin_{u >= 0} sum_j w_j/2 (u_j - z_j)^2 + ||K u||_{2,1},  w = g / (beta x),
+// solved by the accelerated primal-dual algorithm of Chambolle & Pock (2011,
+// their Alg. 2) with G(u) = sum_j w_j/2 (u_j - z_j)^2 + i_{u >= 0}, uniformly
+// convex with modulus gam = min_j w_j over the free voxels, and F^* the
+// indicator of the unit 2-norm balls.
+//
+// The inner iteration is two voxel-parallel passes: the dual step needs the
+// forward neighbours of ubar, the primal step the backward neighbours of q,
+// so one pass cannot finish before the other starts.  The step-size schedule
+// (tau_k, sigma_k, theta_k) depends only on gam and ||K||; one thread computes
+// it in FP64 on the device once gam is known, so the whole epoch is queued
+// on the stream without a host round trip.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "lm_internal.h"
+
+using namespace lmk;
+using namespace lmh;
+
+namespace {
+
+constexpr int EMTV_MAX_ITERS = 10000;
+
+struct Sched {
+    // ~(float bits) of min w over the free voxels: non-negative floats order
+    // as unsigned integers, so the minimum is an atomic maximum of the
+    // complements and a cleared word (0) means "no free voxel"
+    unsigned gam_nbits;
+    unsigned pad[63];
+    float tau[EMTV_MAX_ITERS];
+    float sigma[EMTV_MAX_ITERS];
+    float theta[EMTV_MAX_ITERS];
+};
+
+struct Ws {
+    float* z;
+    float* w;
+    float* ubar;
+    float* q;      // [ndim][V]
+    float* acc_yf; // y-fastest accumulator of the EM back-projection
+    float* x_yf;   // y-fastest copy of x for the EM gathers
+    Sched* sc;
+};
+
+struct Axes {
+    int nd;
+    int n[3];
+    int64_t st[3];  // strides of the TV components' axes
+    int dim[3];     // grid dimension of component c
+};
+
+Axes axes_of(const lm_grid* g)
+{
+    Axes a;
+    std::memset(&a, 0, sizeof(a));
+    const int64_t stride[3] = {1, g->n[0], (int64_t)g->n[0] * g->n[1]};
+    for (int d = 0; d < 3; ++d)
+        if (g->n[d] > 1) {
+            a.n[a.nd] = g->n[d];
+            a.st[a.nd] = stride[d];
+            a.dim[a.nd] = d;
+            ++a.nd;
+        }
+    return a;
+}
+
+size_t ws_layout(const lm_grid* g, Ws* w, void* base)
+{
+    const size_t V = (size_t)nvox(g);
+    const int nd = std::max(1, axes_of(g).nd);
+    char* p = (char*)base;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* r = p ? p + off : nullptr;
+        off += align_up(bytes);
+        return r;
+    };
+    Ws t;
+    t.z = (float*)take(V * 4);
+    t.w = (float*)take(V * 4);
+    t.ubar = (float*)take(V * 4);
+    t.q = (float*)take((size_t)nd * V * 4);
+    t.acc_yf = (float*)take(V * 4);
+    t.x_yf = (float*)take(V * 4);
+    t.sc = (Sched*)take(sizeof(Sched));
+    if (w) *w = t;
+    return off;
+}
+
+__device__ __forceinline__ int coord(int64_t j, int d, int nx, int ny)
+{
+    return d == 0 ? (int)(j % nx) : d == 1 ? (int)((j / nx) % ny) : (int)(j / ((int64_t)nx * ny));
+}
+
+// z_j = x_j n / g_j * b_j (0 where g_j = 0), b = the EM back-projection.
+// With a prior (beta > 0) also the weights and the start of the inner
+// problem: free_j = x_j > 0 and g_j > 0; w_j = g_j / (beta x_j) (0 = held);
+// u = ubar = z on free voxels, 0 elsewhere (u written to x); q = 0; gam.
+// Without a prior x = z.
+__global__ void __launch_bounds__(256) em_fold_kernel(float* __restrict__ x, float* __restrict__ z,
+                                                      const float* __restrict__ sens, float* __restrict__ w,
+                                                      float* __restrict__ ubar, float* __restrict__ q, int nd,
+                                                      int64_t V, float n_sub, float beta, Sched* sc)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const float xj = x[j], gj = sens[j];
+        const float zj = gj > 0.0f ? xj * n_sub / gj * z[j] : 0.0f;
+        if (!(beta > 0.0f)) {
+            x[j] = zj;
+            continue;
+        }
+        z[j] = zj;
+        const bool fr = xj > 0.0f && gj > 0.0f;
+        const float wj = fr ? gj / (beta * xj) : 0.0f;
+        w[j] = wj;
+        const float u0 = fr ? zj : 0.0f;
+        x[j] = u0;
+        ubar[j] = u0;
+        for (int c = 0; c < nd; ++c) q[c * V + j] = 0.0f;
+        if (fr) atomicMax(&sc->gam_nbits, ~__float_as_uint(wj));
+    }
+}
+
+// Start of a standalone denoising call: free_j = w_j > 0.
+__global__ void __launch_bounds__(256) denoise_init_kernel(const float* __restrict__ z, const float* __restrict__ w,
+                                                           float* __restrict__ u, float* __restrict__ ubar,
+                                                           float* __restrict__ q, int nd, int64_t V, Sched* sc)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const float wj = w[j];
+        const bool fr = wj > 0.0f;
+        const float u0 = fr ? z[j] : 0.0f;
+        u[j] = u0;
+        ubar[j] = u0;
+        for (int c = 0; c < nd; ++c) q[c * V + j] = 0.0f;
+        if (fr) atomicMax(&sc->gam_nbits, ~__float_as_uint(wj));
+    }
+}
+
+// Step sizes of the accelerated algorithm: tau_0 = sigma_0 = 0.99 / ||K||;
+// theta_k = 1 / sqrt(1 + 2 gam tau_k); tau_{k+1} = theta_k tau_k;
+// sigma_{k+1} = sigma_k / theta_k (so tau_k sigma_k ||K||^2 stays 0.99^2).
+__global__ void sched_kernel(Sched* sc, int iters, double knorm)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const unsigned nb = sc->gam_nbits;
+    const double gam = nb == 0u ? 0.0 : (double)__uint_as_float(~nb);
+    double tau = 0.99 / knorm, sigma = 0.99 / knorm;
+    for (int k = 0; k < iters; ++k) {
+        const double th = 1.0 / sqrt(1.0 + 2.0 * gam * tau);
+        sc->tau[k] = (float)tau;
+        sc->sigma[k] = (float)sigma;
+        sc->theta[k] = (float)th;
+        tau *= th;
+        sigma /= th;
+    }
+}
+
+// q <- proj_{|.| <= 1}(q + sigma_k K ubar), per voxel over the components.
+__global__ void __launch_bounds__(256) dual_kernel(const float* __restrict__ ubar, float* __restrict__ q, Axes ax,
+                                                   int nx, int ny, int64_t V, const Sched* __restrict__ sc, int k)
+{
+    const float sg = sc->sigma[k];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const float uj = ubar[j];
+        float v[3];
+        float n2 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c < ax.nd) {
+                const float gr = coord(j, ax.dim[c], nx, ny) < ax.n[c] - 1 ? ubar[j + ax.st[c]] - uj : 0.0f;
+                v[c] = fmaf(sg, gr, q[c * V + j]);
+                n2 = fmaf(v[c], v[c], n2);
+            }
+        }
+        const float s = tv_ball_scale(n2, 1.0f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < ax.nd) q[c * V + j] = __fmul_rn(v[c], s);
+    }
+}
+
+// u+ = prox_{tau G}(u - tau K^T q) = max(0, (v + tau w z) / (1 + tau w)) on
+// free voxels (0 on held ones); ubar = u+ + theta (u+ - u); u = u+.
+__global__ void __launch_bounds__(256) primal_kernel(float* __restrict__ u, float* __restrict__ ubar,
+                                                     const float* __restrict__ q, const float* __restrict__ z,
+                                                     const float* __restrict__ w, Axes ax, int nx, int ny,
+                                                     int64_t V, const Sched* __restrict__ sc, int k)
+{
+    const float tau = sc->tau[k], th = sc->theta[k];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        float kt = 0.0f;  // (K^T q)_j
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c < ax.nd) {
+                const int cj = coord(j, ax.dim[c], nx, ny);
+                if (cj < ax.n[c] - 1) kt -= q[c * V + j];
+                if (cj >= 1) kt += q[c * V + j - ax.st[c]];
+            }
+        }
+        const float wj = w[j], uj = u[j];
+        float un = 0.0f;
+        if (wj > 0.0f) {
+            const float v = fmaf(-tau, kt, uj);
+            const float tw = tau * wj;
+            un = fmaxf(0.0f, fmaf(tw, z[j], v) / (1.0f + tw));
+        }
+        ubar[j] = fmaf(th, un - uj, un);
+        u[j] = un;
+    }
+}
+
+int voxel_grid(int64_t V)
+{
+    const int64_t want = (V + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
+}
+
+// The schedule from gam, then the inner iterations on (u, ubar, q) with z, w.
+int run_pdhg(const lm_grid* g, const Ws& W, float* u, int iters, double knorm, cudaStream_t st)
+{
+    const Axes ax = axes_of(g);
+    const int64_t V = nvox(g);
+    const int gv = voxel_grid(V);
+    sched_kernel<<<1, 32, 0, st>>>(W.sc, iters, knorm);
+    count_launch();
+    for (int k = 0; k < iters; ++k) {
+        dual_kernel<<<gv, 256, 0, st>>>(W.ubar, W.q, ax, g->n[0], g->n[1], V, W.sc, k);
+        primal_kernel<<<gv, 256, 0, st>>>(u, W.ubar, W.q, W.z, W.w, ax, g->n[0], g->n[1], V, W.sc, k);
+    }
+    count_launch(2 * (int64_t)iters);
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int check_common(const lm_grid* grid, void* ws, size_t ws_bytes, int iters, double knorm)
+{
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(ws != nullptr && ws_bytes >= ws_layout(grid, nullptr, nullptr), LM_ERR_NOMEM,
+             "EM-TV needs %zu workspace bytes", ws_layout(grid, nullptr, nullptr));
+    LM_CHECK(((uintptr_t)ws & 255) == 0, LM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    LM_CHECK(iters >= 0 && iters <= EMTV_MAX_ITERS, LM_ERR_INVALID_ARG, "pdhg_iters must be in [0, %d]",
+             EMTV_MAX_ITERS);
+    LM_CHECK(std::isfinite(knorm) && knorm > 0.0, LM_ERR_INVALID_ARG, "knorm must be positive");
+    return LM_OK;
+}
+
+// Back-projection of c_e / (c_e J_e x + s_e) over events [e0, e1) into W.z
+// (overwritten), then the fold of em_fold_kernel.
+int em_step(const lm_scanner* sc, const lm_grid* grid, const Geo& G, const lm_events* ev, int64_t e0, int64_t e1,
+            int n_subsets, const float* sens, float* x, float beta, const Ws& W, cudaStream_t st)
+{
+    const size_t V = (size_t)nvox(grid);
+    const bool two_d = grid->n[2] == 1 && sc->n_rings == 1;  // single-ring scanner in the image plane
+    const bool use_yf = grid->n[1] > 1;
+    LM_CUDA(cudaMemsetAsync(W.z, 0, V * 4, st));
+    if (beta > 0.0f) LM_CUDA(cudaMemsetAsync(&W.sc->gam_nbits, 0, 4, st));
+    if (e1 > e0) {
+        EvArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.G = G;
+        a.x_std = x;
+        a.det1 = ev->det1;
+        a.det2 = ev->det2;
+        a.tof = ev->tof;
+        a.corr = ev->corr;
+        a.contam = ev->contam;
+        a.acc_std = W.z;
+        if (use_yf) {
+            launch_transpose_to_yf(grid, x, W.x_yf, st);
+            a.x_yf = W.x_yf;
+            a.acc_yf = W.acc_yf;
+            LM_CUDA(cudaMemsetAsync(W.acc_yf, 0, V * 4, st));
+        }
+        a.e_begin = e0;
+        a.e_end = e1;
+        a.chunk = 32;
+        a.stepmax = 2.0f * std::fmax(grid->h[0], std::fmax(grid->h[1], grid->h[2]));
+        int rc = launch_events(EV_EM, two_d, a, ev_grid(EV_EM, two_d), st);
+        LM_CHECK(rc == LM_OK, rc, "EM back-projection launch failed");
+        if (use_yf) launch_add_yf_to_std(grid, W.z, W.acc_yf, st);
+    }
+    const Axes ax = axes_of(grid);
+    em_fold_kernel<<<voxel_grid((int64_t)V), 256, 0, st>>>(x, W.z, sens, W.w, W.ubar, W.q, std::max(1, ax.nd),
+                                                          (int64_t)V, (float)n_subsets, beta, W.sc);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+// Same checks as the projector's entry points.
+int check_events_em(const lm_tof* tof, const lm_events* ev)
+{
+    LM_CHECK(ev != nullptr && ev->n >= 0, LM_ERR_INVALID_ARG, "events NULL or negative count");
+    if (ev->n == 0) return LM_OK;
+    LM_CHECK(ev->det1 && ev->det2, LM_ERR_INVALID_ARG, "event detector arrays are NULL");
+    LM_CHECK(ev->contam != nullptr, LM_ERR_INVALID_ARG, "event contamination is NULL");
+    LM_CHECK(tof->n_bins == 0 || ev->tof != nullptr, LM_ERR_INVALID_ARG, "TOF bins NULL for a TOF scanner");
+    return LM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lm_emtv_workspace_bytes(const lm_grid* grid)
+{
+    if (check_grid(grid)) return 0;
+    return ws_layout(grid, nullptr, nullptr);
+}
+
+int lm_emtv_em_step(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev,
+                    int32_t n_subsets, const float* sens, const float* x, float* z, void* ws, size_t ws_bytes,
+                    void* stream)
+{
+    clear_error();
+    Geo G;
+    int rc = make_geo(sc, grid, tof, G, true);
+    if (rc) return rc;
+    rc = check_common(grid, ws, ws_bytes, 0, 1.0);
+    if (rc) return rc;
+    rc = check_events_em(tof, ev);
+    if (rc) return rc;
+    LM_CHECK(sens && x && z, LM_ERR_INVALID_ARG, "sens, x or z is NULL");
+    LM_CHECK(n_subsets >= 1, LM_ERR_INVALID_ARG, "n_subsets must be >= 1");
+    Ws W;
+    ws_layout(grid, &W, ws);
+    cudaStream_t st = S(stream);
+    const size_t V = (size_t)nvox(grid);
+    // work on a copy of x so that the fold (which writes x = z without a prior) leaves x untouched
+    LM_CUDA(cudaMemcpyAsync(z, x, V * 4, cudaMemcpyDeviceToDevice, st));
+    rc = em_step(sc, grid, G, ev, 0, ev->n, n_subsets, sens, z, 0.0f, W, st);
+    if (rc) return rc;
+    return LM_OK;
+}
+
+int lm_emtv_denoise(const lm_grid* grid, const float* z, const float* w, float* u, int32_t iters, double knorm,
+                    void* ws, size_t ws_bytes, void* stream)
+{
+    clear_error();
+    int rc = check_common(grid, ws, ws_bytes, iters, knorm);
+    if (rc) return rc;
+    LM_CHECK(z && w && u, LM_ERR_INVALID_ARG, "z, w or u is NULL");
+    Ws W;
+    ws_layout(grid, &W, ws);
+    cudaStream_t st = S(stream);
+    const size_t V = (size_t)nvox(grid);
+    const Axes ax = axes_of(grid);
+    LM_CUDA(cudaMemcpyAsync(W.z, z, V * 4, cudaMemcpyDeviceToDevice, st));
+    LM_CUDA(cudaMemcpyAsync(W.w, w, V * 4, cudaMemcpyDeviceToDevice, st));
+    LM_CUDA(cudaMemsetAsync(&W.sc->gam_nbits, 0, 4, st));
+    denoise_init_kernel<<<voxel_grid((int64_t)V), 256, 0, st>>>(W.z, W.w, u, W.ubar, W.q, std::max(1, ax.nd),
+                                                                (int64_t)V, W.sc);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return run_pdhg(grid, W, u, iters, knorm, st);
+}
+
+int lm_emtv_epoch(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev_perm,
+                  const int64_t* sub_off_host, int32_t n_subsets, const float* sens, float* x, float beta,
+                  int32_t pdhg_iters, double knorm, void* ws, size_t ws_bytes, void* stream)
+{
+    clear_error();
+    Geo G;
+    int rc = make_geo(sc, grid, tof, G, true);
+    if (rc) return rc;
+    rc = check_common(grid, ws, ws_bytes, pdhg_iters, knorm);
+    if (rc) return rc;
+    rc = check_events_em(tof, ev_perm);
+    if (rc) return rc;
+    LM_CHECK(sens && x, LM_ERR_INVALID_ARG, "sens or x is NULL");
+    LM_CHECK(n_subsets >= 1 && sub_off_host != nullptr, LM_ERR_INVALID_ARG, "bad subset split");
+    LM_CHECK(beta >= 0.0f && std::isfinite(beta), LM_ERR_INVALID_ARG, "beta must be finite and >= 0");
+    LM_CHECK(sub_off_host[0] == 0 && sub_off_host[n_subsets] == ev_perm->n, LM_ERR_INVALID_ARG,
+             "subset offsets must span [0, n)");
+    for (int i = 0; i < n_subsets; ++i)
+        LM_CHECK(sub_off_host[i + 1] >= sub_off_host[i], LM_ERR_INVALID_ARG, "subset offsets must not decrease");
+    Ws W;
+    ws_layout(grid, &W, ws);
+    cudaStream_t st = S(stream);
+    for (int i = 0; i < n_subsets; ++i) {
+        rc = em_step(sc, grid, G, ev_perm, sub_off_host[i], sub_off_host[i + 1], n_subsets, sens, x, beta, W, st);
+        if (rc) return rc;
+        if (beta > 0.0f) {
+            rc = run_pdhg(grid, W, x, pdhg_iters, knorm, st);
+            if (rc) return rc;
+        }
+    }
+    return LM_OK;
+}
+
+}  // extern "C"

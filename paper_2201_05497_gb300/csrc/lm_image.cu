@@ -1,7 +1,8 @@
 // Image-space kernels of LM-SPDHG (Alg. 2): the per-update image pass that
 // merges the back-projected dual change into z (compensated float32
 // summation), forms zbar = z + dz/p_i and applies the next primal step
-// x <- proj_{>=0}(x - T zbar) (Alg. 2 line 8 of the following update); the
+// x <- proj_{>=0}(x - T zbar) (the primal step that opens the following
+// update of Alg. 2); the
 // TV operator K (forward differences, Neumann boundary), its adjoint and the
 // prox of R^* (Sec. "Numerical experiments"); the FP64 power iteration for
 // ||K||; the step sizes T (Eq. lm_stepsizes) and FP64 reductions of the
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(256) image_batch_kernel(const lmh::BatchImgArg
 // two-stage shared-memory ring (one thread issues the copies, an mbarrier
 // counts their bytes), so each block keeps a whole slice of loads in flight
 // without holding them in registers.  Data updates merge the accumulators
-// into z; prior updates fuse the prior's dual step (Alg. 2 line 15: w+ from
+// into z; prior updates fuse the prior's dual step (Alg. 2: w+ from
 // x over the tile and a one-voxel halo), dz = K^T(w+ - w) and the primal
 // step into the same pass, and the event kernel does nothing for them.
 // Needs rows of a multiple of 4 floats (16-byte tensor strides) and

@@ -78,7 +78,8 @@ enum EvMode {
     EV_YINIT = 5,      // y = 1 - mu/(corr*J(x)+s); acc += corr*(y-1)/mu*J^T
     EV_YINIT_FX1 = 6,  // y init, out[e] = corr*(y-1)/mu, max|.|
     EV_ABSMAX = 7,     // max |corr*v[e]|
-    EV_COUNT = 8       // traversal statistics: samples and neighbour touches
+    EV_COUNT = 8,      // traversal statistics: samples and neighbour touches
+    EV_EM = 9          // subset EM step (Alg. 3): acc += corr * J^T / (corr*J(x) + s)
 };
 
 struct EvArgs {

@@ -114,7 +114,7 @@ using lmh::EvArgs;
 
 namespace {
 
-// Dual step of the prior at voxel j (Alg. 2 line 15):
+// Dual step of the prior at voxel j (prior update of Alg. 2):
 // w+ = v / max(1, |v|/beta), v = w + S_{n+1} K x.
 __device__ __forceinline__ void prior_voxel(const EvArgs& A, const float* __restrict__ x,
                                             const float* __restrict__ wc, float* __restrict__ wn, int j)
@@ -206,13 +206,14 @@ __device__ __noinline__ void prior_dual(const EvArgs& A)
 template <int MODE>
 struct ModeTraits {
     static constexpr bool gather = MODE == lmh::EV_FWD || MODE == lmh::EV_DATA || MODE == lmh::EV_DATA_FX1 ||
-                                   MODE == lmh::EV_YINIT || MODE == lmh::EV_YINIT_FX1;
-    static constexpr bool back_float = MODE == lmh::EV_BACK || MODE == lmh::EV_DATA || MODE == lmh::EV_YINIT;
+                                   MODE == lmh::EV_YINIT || MODE == lmh::EV_YINIT_FX1 || MODE == lmh::EV_EM;
+    static constexpr bool back_float =
+        MODE == lmh::EV_BACK || MODE == lmh::EV_DATA || MODE == lmh::EV_YINIT || MODE == lmh::EV_EM;
     static constexpr bool back_fx = MODE == lmh::EV_BACK_FX;
     static constexpr bool needs_y = MODE == lmh::EV_DATA || MODE == lmh::EV_DATA_FX1;
     static constexpr bool needs_mu = MODE == lmh::EV_DATA || MODE == lmh::EV_DATA_FX1 || MODE == lmh::EV_YINIT ||
                                      MODE == lmh::EV_YINIT_FX1;
-    static constexpr bool needs_s = needs_mu;
+    static constexpr bool needs_s = needs_mu || MODE == lmh::EV_EM;
     static constexpr bool needs_vin = MODE == lmh::EV_BACK || MODE == lmh::EV_BACK_FX || MODE == lmh::EV_ABSMAX;
     static constexpr bool traverse = MODE != lmh::EV_ABSMAX;
     static constexpr bool count = MODE == lmh::EV_COUNT;
@@ -427,6 +428,11 @@ __device__ __forceinline__ void event_chunk(const EvArgs& A, const float* __rest
             }
             if (MODE == lmh::EV_YINIT) bval = valid ? cj * v : 0.0f;
             else if (valid) wmax = fmaxf(wmax, fabsf(cj * v));
+        } else if (MODE == lmh::EV_EM) {
+            // subset EM step of Alg. 3: back-project c_e / (c_e J_e x + s_e)
+            const float sj = __shfl_sync(FULL, ms, src);
+            const float u = fmaf(cj, acc, sj);
+            bval = (valid && u > 0.0f) ? cj / u : 0.0f;
         } else if (MODE == lmh::EV_BACK || MODE == lmh::EV_BACK_FX) {
             // every lane takes part in the shuffle; groups without an event discard the value
             const float vj = __shfl_sync(FULL, mv, src);
@@ -781,6 +787,7 @@ int launch_events(int mode, bool two_d, const EvArgs& a, int grid, cudaStream_t 
         LM_CASE(EV_YINIT_FX1)
         LM_CASE(EV_ABSMAX)
         LM_CASE(EV_COUNT)
+        LM_CASE(EV_EM)
         default:
             return LM_ERR_INVALID_ARG;
     }
@@ -887,6 +894,7 @@ int ev_grid_g(int mode, bool two_d, int group)
         LM_CASE(EV_YINIT_FX1)
         LM_CASE(EV_ABSMAX)
         LM_CASE(EV_COUNT)
+        LM_CASE(EV_EM)
         default:
             return num_sms();
     }
@@ -908,6 +916,7 @@ int ev_grid(int mode, bool two_d)
         LM_CASE(EV_YINIT_FX1)
         LM_CASE(EV_ABSMAX)
         LM_CASE(EV_COUNT)
+        LM_CASE(EV_EM)
         default:
             return num_sms();
     }

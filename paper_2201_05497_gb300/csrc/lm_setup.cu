@@ -1,5 +1,5 @@
-// Event set-up of Alg. 2: validation, event counts mu_e (step 2) and the
-// split of the list into n sub lists, event e to subset e mod n (step 6).
+// Event set-up of Alg. 2: validation, the event counts mu_e and the split
+// of the list into n sub lists, event e to subset e mod n.
 //
 // mu_e counts the events of the whole list in e's data bin (unordered
 // detector pair + TOF bin signed toward the larger detector id).  The count

@@ -281,7 +281,7 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
     return LM_OK;
 }
 
-// Alg. 2 steps 3-5 and the first primal step for the state's current events:
+// Initialisation of Alg. 2 and the first primal step for the state's current events:
 // gamma, T, y = Eq. (yinit), z = P^T 1 + (P^LM)^T((y-1)/mu), w = 0, x from x0.
 int chunk_for(int64_t count, int grid);
 

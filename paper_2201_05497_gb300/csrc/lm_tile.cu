@@ -1,4 +1,5 @@
-// Tile-binned projector for the data updates of Alg. 2 (lines 10-13).
+// Tile-binned projector for the data updates of Alg. 2 (forward projection,
+// dual step, back-projection of the dual change).
 //
 // The direct event kernel gathers and scatters each event's samples straight
 // from/to L2; its atomics land on scattered sectors (a 32-lane request covers

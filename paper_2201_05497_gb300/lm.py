@@ -125,6 +125,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lm_server_wait": ([V, I64, V, P(D), P(D), I32], C.c_int),
         "lm_server_stats": ([V, P(I64), P(I64), P(I64), P(SZ), P(I64)], C.c_int),
         "lm_server_destroy": ([V], C.c_int),
+        "lm_emtv_workspace_bytes": ([P(lm_grid)], SZ),
+        "lm_emtv_epoch": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), P(I64), I32, V, V, F, I32, D, V,
+                           SZ, V], C.c_int),
+        "lm_emtv_em_step": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), I32, V, V, V, V, SZ, V],
+                            C.c_int),
+        "lm_emtv_denoise": ([P(lm_grid), V, V, V, I32, D, V, SZ, V], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -354,6 +360,55 @@ def event_setup(geo: Geometry, ev: DeviceEvents, n_subsets: int, stream=None, in
                             _ptr(out.det2), _ptr(out.tof), _ptr(out.corr), _ptr(out.contam), _ptr(mu),
                             off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(ws), ws.numel(), _stream(stream)))
     return PermutedEvents(out, mu, off)
+
+
+# --------------------------------------------------------------------------
+# listmode EM-TV warm start (Alg. 3)
+# --------------------------------------------------------------------------
+def _emtv_ws(geo: Geometry, ws, dev):
+    nb = int(load_library().lm_emtv_workspace_bytes(C.byref(geo.g)))
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    return ws
+
+
+def emtv_epoch(geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x: torch.Tensor, *, beta: float,
+               pdhg_iters: int, knorm: float, ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """One listmode EM-TV pass over the subsets (Alg. 3), x updated in place."""
+    L = load_library()
+    ws = _emtv_ws(geo, ws, x.device)
+    d = pe.events.desc()
+    off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
+    _check(L.lm_emtv_epoch(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d),
+                           off.ctypes.data_as(C.POINTER(C.c_int64)), int(off.shape[0] - 1), _ptr(sens_img), _ptr(x),
+                           float(beta), int(pdhg_iters), float(knorm), _ptr(ws), ws.numel(), _stream(stream)))
+    return x
+
+
+def emtv_em_step(geo: Geometry, ev: DeviceEvents, n_subsets: int, sens_img: torch.Tensor, x: torch.Tensor,
+                 out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """z = x n / g * (P^LM)^T (1 / (P^LM x + s)) over the events of ev."""
+    L = load_library()
+    ws = _emtv_ws(geo, ws, x.device)
+    if out is None:
+        out = torch.empty(geo.V, dtype=torch.float32, device=x.device)
+    d = ev.desc()
+    _check(L.lm_emtv_em_step(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d), int(n_subsets),
+                             _ptr(sens_img), _ptr(x), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def emtv_denoise(geo: Geometry, z: torch.Tensor, w: torch.Tensor, iters: int, knorm: float,
+                 out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """argmin_{u >= 0} sum w/2 (u - z)^2 + ||K u||_{2,1} by `iters` accelerated
+    primal-dual iterations; voxels with w <= 0 held at 0."""
+    L = load_library()
+    ws = _emtv_ws(geo, ws, z.device)
+    if out is None:
+        out = torch.empty(geo.V, dtype=torch.float32, device=z.device)
+    _check(L.lm_emtv_denoise(C.byref(geo.g), _ptr(z), _ptr(w), _ptr(out), int(iters), float(knorm), _ptr(ws),
+                             ws.numel(), _stream(stream)))
+    return out
 
 
 class LMSPDHG:
