@@ -8,7 +8,8 @@ The arithmetic lives in ``lmoracle.c`` (plain double precision C, built with
 gcc on first use); this module only marshals numpy arrays.  Functions follow
 the paper's notation: ``fwd`` is P^LM (Eq. lmop), ``back`` its adjoint,
 ``sens`` is P^T 1, ``lm_init``/``lm_update`` are Alg. 2, ``sino_*`` are
-Alg. 1 on a full TOF sinogram, ``EMTV``/``emtv_denoise`` are Alg. 3 (the
+Alg. 1 on a full TOF sinogram, ``dtv_*`` the directional TV operator (the
+paper's second prior; ``xi`` of ``LM``/``Sino``), ``EMTV``/``emtv_denoise`` are Alg. 3 (the
 listmode EM-TV warm start).  The denoiser's iterate path at a fixed iteration
 count (its extrapolation step) is parity unpinned; its limit is pinned.
 """
@@ -55,7 +56,8 @@ class LmProblem(C.Structure):
                 ("tbin", C.POINTER(C.c_int16)), ("corr", C.POINTER(C.c_float)),
                 ("contam", C.POINTER(C.c_float)), ("mu", C.POINTER(C.c_int32)),
                 ("n_ev", C.c_int64), ("n_subsets", C.c_int32),
-                ("beta", C.c_double), ("gamma", C.c_double), ("rho", C.c_double), ("knorm", C.c_double)]
+                ("beta", C.c_double), ("gamma", C.c_double), ("rho", C.c_double), ("knorm", C.c_double),
+                ("xi", C.POINTER(C.c_double))]
 
 
 class LmState(C.Structure):
@@ -69,7 +71,8 @@ class SinoProblem(C.Structure):
                 ("lor_factor", C.POINTER(C.c_float)), ("d", C.POINTER(C.c_double)),
                 ("s", C.POINTER(C.c_double)), ("sub", C.POINTER(C.c_int32)),
                 ("n_subsets", C.c_int32),
-                ("beta", C.c_double), ("gamma", C.c_double), ("rho", C.c_double), ("knorm", C.c_double)]
+                ("beta", C.c_double), ("gamma", C.c_double), ("rho", C.c_double), ("knorm", C.c_double),
+                ("xi", C.POINTER(C.c_double))]
 
 
 def _p(a, ct):
@@ -99,6 +102,9 @@ def lib():
             L.or_tv_grad.argtypes = [P(Grid), P(C.c_double), P(C.c_double)]
             L.or_tv_adj.argtypes = [P(Grid), P(C.c_double), P(C.c_double)]
             L.or_tv_prox.argtypes = [P(Grid), P(C.c_double), C.c_double]
+            L.or_dtv_grad.argtypes = [P(Grid), P(C.c_double), P(C.c_double), P(C.c_double)]
+            L.or_dtv_adj.argtypes = [P(Grid), P(C.c_double), P(C.c_double), P(C.c_double)]
+            L.or_dtv_xi.argtypes = [P(Grid), P(C.c_double), C.c_double, P(C.c_double)]
             L.or_knorm_power.argtypes = [P(Grid), C.c_int]
             L.or_knorm_power.restype = C.c_double
             L.or_prox_dstar.argtypes = [C.c_double, C.c_double, C.c_double]
@@ -280,6 +286,36 @@ def tv_adj(geo: Geometry, q: np.ndarray) -> np.ndarray:
     return out
 
 
+def _xi_ptr(xi):
+    return None if xi is None else _p(xi, C.c_double)
+
+
+def dtv_xi(geo: Geometry, v: np.ndarray, eta: float) -> np.ndarray:
+    """Directional-TV field xi = grad v / sqrt(|grad v|^2 + eta^2), [ndim][V]."""
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    out = np.zeros(geo.ndim * geo.V, dtype=np.float64)
+    lib().or_dtv_xi(C.byref(geo.g), _p(v, C.c_double), float(eta), _p(out, C.c_double))
+    return out
+
+
+def dtv_grad(geo: Geometry, xi: np.ndarray | None, x: np.ndarray) -> np.ndarray:
+    """K x = P grad x (DTV; xi None = TV)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    xi = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
+    out = np.zeros(geo.ndim * geo.V, dtype=np.float64)
+    lib().or_dtv_grad(C.byref(geo.g), _xi_ptr(xi), _p(x, C.c_double), _p(out, C.c_double))
+    return out
+
+
+def dtv_adj(geo: Geometry, xi: np.ndarray | None, q: np.ndarray) -> np.ndarray:
+    """K^T q = grad^T (P q)."""
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    xi = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
+    out = np.zeros(geo.V, dtype=np.float64)
+    lib().or_dtv_adj(C.byref(geo.g), _xi_ptr(xi), _p(q, C.c_double), _p(out, C.c_double))
+    return out
+
+
 def tv_prox(geo: Geometry, w: np.ndarray, beta: float) -> np.ndarray:
     w = np.array(w, dtype=np.float64).reshape(-1)
     lib().or_tv_prox(C.byref(geo.g), _p(w, C.c_double), float(beta))
@@ -298,9 +334,10 @@ class LM:
     """Alg. 2 state in FP64: ``init`` then ``update(i)`` for each selection."""
 
     def __init__(self, geo: Geometry, ev: EventArrays, mu: np.ndarray, n_subsets: int,
-                 beta: float, gamma: float, rho: float, knorm: float):
+                 beta: float, gamma: float, rho: float, knorm: float, xi: np.ndarray | None = None):
         self.geo, self.ev = geo, ev
         self.mu = np.ascontiguousarray(mu, dtype=np.int32)
+        self.xi = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
         V, nd = geo.V, geo.ndim
         self.x = np.zeros(V)
         self.z = np.zeros(V)
@@ -313,7 +350,7 @@ class LM:
         self.prob = LmProblem(C.pointer(geo.sc), C.pointer(geo.g), C.pointer(geo.tof),
                               _p(ev.det1, C.c_int32), _p(ev.det2, C.c_int32), _p(ev.tof, C.c_int16),
                               _p(ev.corr, C.c_float), _p(ev.contam, C.c_float), _p(self.mu, C.c_int32),
-                              ev.n, n_subsets, beta, gamma, rho, knorm)
+                              ev.n, n_subsets, beta, gamma, rho, knorm, _xi_ptr(self.xi))
         self.state = LmState(_p(self.x, C.c_double), _p(self.z, C.c_double), _p(self.zbar, C.c_double),
                              _p(self.w, C.c_double), _p(self.y, C.c_double), _p(self.T, C.c_double))
 
@@ -380,8 +417,10 @@ class Sino:
     """Alg. 1 on the full TOF sinogram (every LOR and TOF bin)."""
 
     def __init__(self, geo: Geometry, lor_factor: np.ndarray, d: np.ndarray, s: np.ndarray,
-                 sub: np.ndarray, n_subsets: int, beta: float, gamma: float, rho: float, knorm: float):
+                 sub: np.ndarray, n_subsets: int, beta: float, gamma: float, rho: float, knorm: float,
+                 xi: np.ndarray | None = None):
         self.geo = geo
+        self.xi = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
         self.lf = np.ascontiguousarray(lor_factor, dtype=np.float32)
         self.d = np.ascontiguousarray(d, dtype=np.float64)
         self.s = np.ascontiguousarray(s, dtype=np.float64)
@@ -397,7 +436,7 @@ class Sino:
         self._gw = np.zeros(max(nd, 1) * V)
         self.prob = SinoProblem(C.pointer(geo.sc), C.pointer(geo.g), C.pointer(geo.tof),
                                 _p(self.lf, C.c_float), _p(self.d, C.c_double), _p(self.s, C.c_double),
-                                _p(self.sub, C.c_int32), n_subsets, beta, gamma, rho, knorm)
+                                _p(self.sub, C.c_int32), n_subsets, beta, gamma, rho, knorm, _xi_ptr(self.xi))
         self.state = LmState(_p(self.x, C.c_double), _p(self.z, C.c_double), _p(self.zbar, C.c_double),
                              _p(self.w, C.c_double), _p(self.y, C.c_double), _p(self.T, C.c_double))
         assert lib().or_sino_nbins(C.byref(self.prob)) == self.d.shape[0]

@@ -16,7 +16,8 @@
  *   - Alg. 2       LM-SPDHG loop; Alg. 1 (SPDHG on a sinogram) for the
  *                  equivalence check of the appendix
  *   - Eq. (lm_stepsizes) step sizes S_k, T_k; S_{n+1}, T_{n+1} of Sec. 1
- *   - Sec. "Numerical experiments": TV prior ||Kx||_{2,1}, prox of R^*
+ *   - Sec. "Numerical experiments": TV prior ||Kx||_{2,1}, prox of R^*, and the
+ *                  directional TV prior (K = P grad with a structural field)
  *
  * The projector: the paper cites Joseph (1982) and a Gaussian TOF kernel but
  * prints no formula.  The reading implemented here:
@@ -386,6 +387,61 @@ void or_tv_prox(const or_grid* g, double* w, double beta)
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Directional TV (Sec. "Numerical experiments", after Ehrhardt & Betcke 2016):
+ * only the part of the forward-difference vector perpendicular to the
+ * gradient of a structural image counts,
+ *   (K x)_j = P_j (grad x)_j,   P_j = I - xi_j xi_j^T,
+ * with the per-voxel vector field xi ([nd][V], |xi_j| <= 1; NULL = TV).
+ * K^T q = grad^T (P q) (P_j is symmetric).  The field of a structural image
+ * v is xi_j = (grad v)_j / sqrt(|(grad v)_j|^2 + eta^2) (0 where both vanish);
+ * eta = 0 makes P_j the orthogonal projection perpendicular to (grad v)_j.
+ * ------------------------------------------------------------------------ */
+static void dtv_project(const or_grid* g, const double* xi, double* q)
+{
+    int nd = or_tv_ndim(g);
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    for (int64_t j = 0; j < V; ++j) {
+        double s = 0.0;
+        for (int c = 0; c < nd; ++c) s += xi[c * V + j] * q[c * V + j];
+        for (int c = 0; c < nd; ++c) q[c * V + j] -= xi[c * V + j] * s;
+    }
+}
+
+void or_dtv_grad(const or_grid* g, const double* xi, const double* x, double* out)
+{
+    or_tv_grad(g, x, out);
+    if (xi) dtv_project(g, xi, out);
+}
+
+void or_dtv_adj(const or_grid* g, const double* xi, const double* q, double* out)
+{
+    if (!xi) {
+        or_tv_adj(g, q, out);
+        return;
+    }
+    int nd = or_tv_ndim(g);
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    double* t = (double*)malloc(sizeof(double) * V * (nd > 0 ? nd : 1));
+    memcpy(t, q, sizeof(double) * V * nd);
+    dtv_project(g, xi, t);
+    or_tv_adj(g, t, out);
+    free(t);
+}
+
+void or_dtv_xi(const or_grid* g, const double* v, double eta, double* xi)
+{
+    int nd = or_tv_ndim(g);
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    or_tv_grad(g, v, xi);
+    for (int64_t j = 0; j < V; ++j) {
+        double s = eta * eta;
+        for (int c = 0; c < nd; ++c) s += xi[c * V + j] * xi[c * V + j];
+        double r = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+        for (int c = 0; c < nd; ++c) xi[c * V + j] *= r;
+    }
+}
+
 /* ||K|| by power iteration on K^T K from the checkerboard (-1)^(ix+iy+iz);
  * returns sqrt of the last Rayleigh quotient <v, K^T K v>/<v, v>. */
 double or_knorm_power(const or_grid* g, int iters)
@@ -446,6 +502,7 @@ typedef struct {
     int64_t n_ev;
     int32_t n_subsets;
     double beta, gamma, rho, knorm;
+    const double* xi; /* DTV field [nd][V]; NULL = TV */
 } or_lm_problem;
 
 typedef struct {
@@ -530,7 +587,7 @@ void or_lm_update(const or_lm_problem* P, or_lm_state* S, int32_t i, double* dz,
     } else {
         p_i = 0.5;
         double Sp = P->gamma * P->rho / P->knorm; /* S_{n+1} */
-        or_tv_grad(P->g, S->x, gw);
+        or_dtv_grad(P->g, P->xi, S->x, gw);
         for (int64_t j = 0; j < (int64_t)nd * V; ++j) gw[j] = S->w[j] + Sp * gw[j];
         or_tv_prox(P->g, gw, P->beta);                 /* gw = w^+ */
         for (int64_t j = 0; j < (int64_t)nd * V; ++j) {
@@ -538,7 +595,7 @@ void or_lm_update(const or_lm_problem* P, or_lm_state* S, int32_t i, double* dz,
             gw[j] = t - S->w[j];                       /* w^+ - w */
             S->w[j] = t;
         }
-        or_tv_adj(P->g, gw, dz);                       /* dz = K^T (w^+ - w) */
+        or_dtv_adj(P->g, P->xi, gw, dz);               /* dz = K^T (w^+ - w) */
     }
     for (int64_t j = 0; j < V; ++j) {
         S->z[j] += dz[j];
@@ -557,7 +614,7 @@ double or_lm_objective(const or_lm_problem* P, const double* x, const double* se
     for (int64_t e = 0; e < P->n_ev; ++e) c -= log(ev_fwd(P, e, x) + (double)P->contam[e]);
     if (P->beta > 0.0) {
         double* gr = (double*)malloc(sizeof(double) * V * (nd > 0 ? nd : 1));
-        or_tv_grad(P->g, x, gr);
+        or_dtv_grad(P->g, P->xi, x, gr);
         double r = 0.0;
         for (int64_t j = 0; j < V; ++j) {
             double s = 0.0;
@@ -690,6 +747,7 @@ typedef struct {
     const int32_t* sub;      /* subset of each bin */
     int32_t n_subsets;
     double beta, gamma, rho, knorm;
+    const double* xi; /* DTV field [nd][V]; NULL = TV */
 } or_sino_problem;
 
 static void bin_dets(const or_sino_problem* P, int64_t b, int32_t* d1, int32_t* d2, int32_t* m)
@@ -778,7 +836,7 @@ void or_sino_update(const or_sino_problem* P, or_lm_state* S, int32_t i, double*
     } else {
         p_i = 0.5;
         double Sp = P->gamma * P->rho / P->knorm;
-        or_tv_grad(P->g, S->x, gw);
+        or_dtv_grad(P->g, P->xi, S->x, gw);
         for (int64_t j = 0; j < (int64_t)nd * V; ++j) gw[j] = S->w[j] + Sp * gw[j];
         or_tv_prox(P->g, gw, P->beta);
         for (int64_t j = 0; j < (int64_t)nd * V; ++j) {
@@ -786,7 +844,7 @@ void or_sino_update(const or_sino_problem* P, or_lm_state* S, int32_t i, double*
             gw[j] = t - S->w[j];
             S->w[j] = t;
         }
-        or_tv_adj(P->g, gw, dz);
+        or_dtv_adj(P->g, P->xi, gw, dz);
     }
     for (int64_t j = 0; j < V; ++j) {
         S->z[j] += dz[j];
@@ -808,7 +866,7 @@ double or_sino_objective(const or_sino_problem* P, const double* x)
     }
     if (P->beta > 0.0) {
         double* gr = (double*)malloc(sizeof(double) * V * (nd > 0 ? nd : 1));
-        or_tv_grad(P->g, x, gr);
+        or_dtv_grad(P->g, P->xi, x, gr);
         double r = 0.0;
         for (int64_t j = 0; j < V; ++j) {
             double s = 0.0;

@@ -75,11 +75,23 @@ def _dense_lm_matrix(O, geo, E):
     return A
 
 
-def test_lmpdhg_reaches_independent_minimiser(oracle_mod):
+def _dtv_field(O, geo, n, seed=21, eta=0.3):
+    """A structural image (smooth blob plus noise) and its DTV field."""
+    rng = np.random.default_rng(seed)
+    ix, iy, iz = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    v = np.exp(-((ix - 1.5) ** 2 + (iy - 2.0) ** 2) / 3.0) + 0.1 * rng.uniform(size=ix.shape)
+    v = np.transpose(v, (2, 1, 0)).reshape(-1)  # x fastest
+    return O.dtv_xi(geo, v, eta)
+
+
+@pytest.mark.parametrize("prior", ["tv", "dtv"])
+def test_lmpdhg_reaches_independent_minimiser(oracle_mod, prior):
     """Brute force on a tiny grid: the dense P^LM is built column by column;
     L-BFGS-B on Eq. (1) with a smoothed TV (eps = 1e-9) gives the minimiser
     independently of Alg. 2.  LM-SPDHG (n = 1) must approach it: the objective
-    gap and the KKT residual of x >= 0 become small."""
+    gap and the KKT residual of x >= 0 become small.  For DTV the dense K is
+    the dense TV matrix with P_j = I - xi_j xi_j^T applied to each voxel's
+    rows, written here from the definition."""
     O = oracle_mod
     sc, g, tof, ev = tiny_problem(n=(5, 4, 1), n_events=250, seed=5)
     geo = _geometry(O, sc, g, tof)
@@ -96,6 +108,13 @@ def test_lmpdhg_reaches_independent_minimiser(oracle_mod):
         e = np.zeros(V)
         e[j] = 1
         Km[:, j] = O.tv_grad(geo, e)
+    xi = None
+    if prior == "dtv":
+        xi = _dtv_field(O, geo, g.n)
+        Kr = Km.reshape(geo.ndim, V, V)
+        X = xi.reshape(geo.ndim, V)
+        par = np.einsum("cj,cjk->jk", X, Kr)
+        Km = (Kr - X[:, :, None] * par[None]).reshape(geo.ndim * V, V)
     eps = 1e-9
 
     def f(x):
@@ -114,7 +133,7 @@ def test_lmpdhg_reaches_independent_minimiser(oracle_mod):
 
     x0 = np.full(V, np.float32(1.0))
     knorm = _knorm(g.n)
-    lm = O.LM(geo, E, mu, 1, beta=beta, gamma=3.0 / float(x0.max()), rho=0.999, knorm=knorm)
+    lm = O.LM(geo, E, mu, 1, beta=beta, gamma=3.0 / float(x0.max()), rho=0.999, knorm=knorm, xi=xi)
     lm.init(x0, sens)
     seq = S.selection_sequence(1, 60000, seed=3)
     lm.run(seq)
@@ -149,8 +168,8 @@ def _sino_setup(O, geo, sc, tof, ev, n_subsets, lm_subset_of_event):
     return d, s, sub, b
 
 
-@pytest.mark.parametrize("n_subsets,dup_free", [(1, False), (3, True)])
-def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free):
+@pytest.mark.parametrize("n_subsets,dup_free,prior", [(1, False, "tv"), (3, True, "tv"), (3, True, "dtv")])
+def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free, prior):
     """Appendix: LM-SPDHG is SPDHG on the listmode reformulation.  With the
     same selection sequence (n = 1 with duplicated events, or n = 3 on
     duplicate-free data with the sinogram subset of a bin = the listmode
@@ -175,10 +194,11 @@ def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free):
     knorm = _knorm(g.n)
     x0 = np.random.default_rng(4).uniform(0.5, 1.5, geo.V).astype(np.float32)
     gamma = 3.0 / float(x0.max())
-    lm = O.LM(geo, E, mu, n_subsets, beta=0.2, gamma=gamma, rho=0.999, knorm=knorm)
+    xi = _dtv_field(O, geo, g.n) if prior == "dtv" else None
+    lm = O.LM(geo, E, mu, n_subsets, beta=0.2, gamma=gamma, rho=0.999, knorm=knorm, xi=xi)
     lm.init(x0, sens)
     d, s, sub, b_of_e = _sino_setup(O, geo, sc, tof, ev, n_subsets, np.arange(ev.n) % n_subsets)
-    sino = O.Sino(geo, lf, d, s, sub, n_subsets, beta=0.2, gamma=gamma, rho=0.999, knorm=knorm)
+    sino = O.Sino(geo, lf, d, s, sub, n_subsets, beta=0.2, gamma=gamma, rho=0.999, knorm=knorm, xi=xi)
     sino.init(x0, sens)
     np.testing.assert_allclose(lm.z, sino.z, rtol=1e-12, atol=1e-12 * np.abs(sino.z).max())
     seq = S.selection_sequence(n_subsets, 120, seed=3)
