@@ -57,7 +57,7 @@ class LmProblem(C.Structure):
                 ("contam", C.POINTER(C.c_float)), ("mu", C.POINTER(C.c_int32)),
                 ("n_ev", C.c_int64), ("n_subsets", C.c_int32),
                 ("beta", C.c_double), ("gamma", C.c_double), ("rho", C.c_double), ("knorm", C.c_double),
-                ("xi", C.POINTER(C.c_double))]
+                ("xi", C.POINTER(C.c_double)), ("res_fwhm", C.c_double)]
 
 
 class LmState(C.Structure):
@@ -105,6 +105,7 @@ def lib():
             L.or_dtv_grad.argtypes = [P(Grid), P(C.c_double), P(C.c_double), P(C.c_double)]
             L.or_dtv_adj.argtypes = [P(Grid), P(C.c_double), P(C.c_double), P(C.c_double)]
             L.or_dtv_xi.argtypes = [P(Grid), P(C.c_double), C.c_double, P(C.c_double)]
+            L.or_res_apply.argtypes = [P(Grid), C.c_double, P(C.c_double), P(C.c_double)]
             L.or_knorm_power.argtypes = [P(Grid), C.c_int]
             L.or_knorm_power.restype = C.c_double
             L.or_prox_dstar.argtypes = [C.c_double, C.c_double, C.c_double]
@@ -316,6 +317,14 @@ def dtv_adj(geo: Geometry, xi: np.ndarray | None, q: np.ndarray) -> np.ndarray:
     return out
 
 
+def res_apply(geo: Geometry, fwhm: float, x: np.ndarray) -> np.ndarray:
+    """G x: the separable Gaussian resolution model (mirrored faces)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    out = np.zeros(geo.V, dtype=np.float64)
+    lib().or_res_apply(C.byref(geo.g), float(fwhm), _p(x, C.c_double), _p(out, C.c_double))
+    return out
+
+
 def tv_prox(geo: Geometry, w: np.ndarray, beta: float) -> np.ndarray:
     w = np.array(w, dtype=np.float64).reshape(-1)
     lib().or_tv_prox(C.byref(geo.g), _p(w, C.c_double), float(beta))
@@ -334,7 +343,8 @@ class LM:
     """Alg. 2 state in FP64: ``init`` then ``update(i)`` for each selection."""
 
     def __init__(self, geo: Geometry, ev: EventArrays, mu: np.ndarray, n_subsets: int,
-                 beta: float, gamma: float, rho: float, knorm: float, xi: np.ndarray | None = None):
+                 beta: float, gamma: float, rho: float, knorm: float, xi: np.ndarray | None = None,
+                 res_fwhm: float = 0.0):
         self.geo, self.ev = geo, ev
         self.mu = np.ascontiguousarray(mu, dtype=np.int32)
         self.xi = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
@@ -350,7 +360,7 @@ class LM:
         self.prob = LmProblem(C.pointer(geo.sc), C.pointer(geo.g), C.pointer(geo.tof),
                               _p(ev.det1, C.c_int32), _p(ev.det2, C.c_int32), _p(ev.tof, C.c_int16),
                               _p(ev.corr, C.c_float), _p(ev.contam, C.c_float), _p(self.mu, C.c_int32),
-                              ev.n, n_subsets, beta, gamma, rho, knorm, _xi_ptr(self.xi))
+                              ev.n, n_subsets, beta, gamma, rho, knorm, _xi_ptr(self.xi), float(res_fwhm))
         self.state = LmState(_p(self.x, C.c_double), _p(self.z, C.c_double), _p(self.zbar, C.c_double),
                              _p(self.w, C.c_double), _p(self.y, C.c_double), _p(self.T, C.c_double))
 
@@ -377,13 +387,14 @@ class EMTV:
     """Listmode EM-TV (Alg. 3) in FP64: the subset EM step, the weighted TV
     denoising by accelerated PDHG, and one pass over the subsets."""
 
-    def __init__(self, geo: Geometry, ev: EventArrays, n_subsets: int, beta: float, knorm: float):
+    def __init__(self, geo: Geometry, ev: EventArrays, n_subsets: int, beta: float, knorm: float,
+                 res_fwhm: float = 0.0):
         self.geo, self.ev = geo, ev
         self._mu = np.ones(max(ev.n, 1), dtype=np.int32)
         self.prob = LmProblem(C.pointer(geo.sc), C.pointer(geo.g), C.pointer(geo.tof),
                               _p(ev.det1, C.c_int32), _p(ev.det2, C.c_int32), _p(ev.tof, C.c_int16),
                               _p(ev.corr, C.c_float), _p(ev.contam, C.c_float), _p(self._mu, C.c_int32),
-                              ev.n, n_subsets, beta, 0.0, 0.0, knorm)
+                              ev.n, n_subsets, beta, 0.0, 0.0, knorm, None, float(res_fwhm))
 
     def em_step(self, x: np.ndarray, sens_img: np.ndarray, i: int) -> np.ndarray:
         xx = np.ascontiguousarray(x, dtype=np.float64)

@@ -18,6 +18,7 @@
  *   - Eq. (lm_stepsizes) step sizes S_k, T_k; S_{n+1}, T_{n+1} of Sec. 1
  *   - Sec. "Numerical experiments": TV prior ||Kx||_{2,1}, prox of R^*, and the
  *                  directional TV prior (K = P grad with a structural field)
+ *   - Eq. (1)      P with an image-space resolution model: P = A G (or_res_apply)
  *
  * The projector: the paper cites Joseph (1982) and a Gaussian TOF kernel but
  * prints no formula.  The reading implemented here:
@@ -442,6 +443,54 @@ void or_dtv_xi(const or_grid* g, const double* v, double eta, double* xi)
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Image-space resolution model.  Eq. (1)'s P includes the scanner's limited
+ * spatial resolution; the paper gives no kernel.  Reading: P = A G with A the
+ * TOF Joseph projector and G a separable Gaussian blur of full width at half
+ * maximum fwhm (mm) on every axis with n_d > 1: sigma_d = fwhm / (2 sqrt(2 ln 2))
+ * / h_d voxels, taps k = -r..r with r = floor(3 sigma_d + 1/2) (at most
+ * n_d - 1), weights exp(-k^2 / (2 sigma_d^2)) normalised to sum 1, and the
+ * image mirrored about its outer faces (index -1 reads 0, index n reads
+ * n - 1).  That G is symmetric and its rows sum to 1, so P^T = G A^T and
+ * P 1 = A 1.  fwhm <= 0: G = identity.
+ * ------------------------------------------------------------------------ */
+void or_res_apply(const or_grid* g, double fwhm, const double* x, double* out)
+{
+    int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    memcpy(out, x, sizeof(double) * V);
+    if (!(fwhm > 0.0)) return;
+    double* tmp = (double*)malloc(sizeof(double) * V);
+    for (int d = 0; d < 3; ++d) {
+        const int n = g->n[d];
+        if (n < 2) continue;
+        const double sig = fwhm / (2.0 * sqrt(2.0 * log(2.0))) / (double)g->h[d];
+        int r = (int)floor(3.0 * sig + 0.5);
+        if (r > n - 1) r = n - 1;
+        double* w = (double*)malloc(sizeof(double) * (2 * r + 1));
+        double sum = 0.0;
+        for (int k = -r; k <= r; ++k) {
+            w[k + r] = exp(-(double)k * k / (2.0 * sig * sig));
+            sum += w[k + r];
+        }
+        for (int k = 0; k <= 2 * r; ++k) w[k] /= sum;
+        const int64_t st = stride_of(g, d);
+        for (int64_t j = 0; j < V; ++j) {
+            const int c = coord_of(g, j, d);
+            double acc = 0.0;
+            for (int k = -r; k <= r; ++k) {
+                int m = c + k;
+                if (m < 0) m = -m - 1;
+                if (m >= n) m = 2 * n - m - 1;
+                acc += w[k + r] * out[j + (int64_t)(m - c) * st];
+            }
+            tmp[j] = acc;
+        }
+        memcpy(out, tmp, sizeof(double) * V);
+        free(w);
+    }
+    free(tmp);
+}
+
 /* ||K|| by power iteration on K^T K from the checkerboard (-1)^(ix+iy+iz);
  * returns sqrt of the last Rayleigh quotient <v, K^T K v>/<v, v>. */
 double or_knorm_power(const or_grid* g, int iters)
@@ -503,6 +552,7 @@ typedef struct {
     int32_t n_subsets;
     double beta, gamma, rho, knorm;
     const double* xi; /* DTV field [nd][V]; NULL = TV */
+    double res_fwhm;  /* resolution model G (mm, <= 0: none): P = A G */
 } or_lm_problem;
 
 typedef struct {
@@ -529,6 +579,34 @@ static void ev_back(const or_lm_problem* P, int64_t e, double v, double* img)
     or_lor_visit(P->sc, P->g, P->tof, P->det1[e], P->det2[e], P->tbin[e], ev_mode(P->tof), back_visit, &c);
 }
 
+/* The image the projector A reads: G x with the resolution model (a new
+ * array in *buf), x itself without (*buf = NULL). */
+static const double* res_in(const or_lm_problem* P, const double* x, double** buf)
+{
+    *buf = NULL;
+    if (!(P->res_fwhm > 0.0)) return x;
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    *buf = (double*)malloc(sizeof(double) * V);
+    or_res_apply(P->g, P->res_fwhm, x, *buf);
+    return *buf;
+}
+
+/* img += G b (the transpose of the resolution model after a back-projection b). */
+static void res_add(const or_lm_problem* P, const double* b, double* img)
+{
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    double* t = (double*)malloc(sizeof(double) * V);
+    or_res_apply(P->g, P->res_fwhm, b, t);
+    for (int64_t j = 0; j < V; ++j) img[j] += t[j];
+    free(t);
+}
+
+/* (P^LM 1)_e = corr_e J_e(G 1) */
+static double ev_fwd_one_img(const or_lm_problem* P, int64_t e, const double* g1)
+{
+    return g1 ? ev_fwd(P, e, g1) : ev_fwd_ones(P, e);
+}
+
 /* Initialisation of Alg. 2 (duals, z, step sizes) plus the first primal step's inputs:
  *   y_e = 1 - mu_e / ((P^LM x0)_e + s_e)                    (Eq. yinit)
  *   z = zbar = P^T 1 + (P^LM)^T ((y - 1)/mu) + K^T w, w = 0
@@ -543,10 +621,18 @@ void or_lm_init(const or_lm_problem* P, const float* x0, const double* sens, or_
     double* x0d = S->x;
     for (int64_t j = 0; j < V; ++j) x0d[j] = (double)x0[j];
     for (int64_t j = 0; j < V; ++j) S->z[j] = sens[j];
+    double* gbuf;
+    const double* gx = res_in(P, x0d, &gbuf);
+    double* bz = gbuf ? (double*)calloc(V, sizeof(double)) : S->z;
     for (int64_t e = 0; e < P->n_ev; ++e) {
-        double u = ev_fwd(P, e, x0d) + (double)P->contam[e];
+        double u = ev_fwd(P, e, gx) + (double)P->contam[e];
         S->y[e] = 1.0 - (double)P->mu[e] / u;
-        ev_back(P, e, (S->y[e] - 1.0) / (double)P->mu[e], S->z);
+        ev_back(P, e, (S->y[e] - 1.0) / (double)P->mu[e], bz);
+    }
+    if (gbuf) {
+        res_add(P, bz, S->z);
+        free(bz);
+        free(gbuf);
     }
     for (int64_t j = 0; j < (int64_t)nd * V; ++j) S->w[j] = 0.0;
     for (int64_t j = 0; j < V; ++j) S->zbar[j] = S->z[j];
@@ -575,14 +661,30 @@ void or_lm_update(const or_lm_problem* P, or_lm_state* S, int32_t i, double* dz,
     double p_i;
     if (i < P->n_subsets) {
         p_i = 1.0 / (2.0 * n);
+        double *gbuf, *g1 = NULL;
+        const double* gx = res_in(P, S->x, &gbuf);
+        if (gbuf) {
+            double* ones = (double*)malloc(sizeof(double) * V);
+            for (int64_t j = 0; j < V; ++j) ones[j] = 1.0;
+            g1 = (double*)malloc(sizeof(double) * V);
+            or_res_apply(P->g, P->res_fwhm, ones, g1);
+            free(ones);
+        }
+        double* bz = gbuf ? (double*)calloc(V, sizeof(double)) : dz;
         for (int64_t e = i; e < P->n_ev; e += P->n_subsets) {
-            double p1 = ev_fwd_ones(P, e);
+            double p1 = ev_fwd_one_img(P, e, g1);
             double Se = p1 > 0.0 ? P->gamma * P->rho / p1 : 0.0; /* S_k = gamma rho / P^LM_{N_k} 1 */
-            double a = S->y[e] + Se * (ev_fwd(P, e, S->x) + (double)P->contam[e]);
+            double a = S->y[e] + Se * (ev_fwd(P, e, gx) + (double)P->contam[e]);
             double mu = (double)P->mu[e];
             double yp = or_prox_dstar(a, mu * Se, 1.0);
-            ev_back(P, e, (yp - S->y[e]) / mu, dz);
+            ev_back(P, e, (yp - S->y[e]) / mu, bz);
             S->y[e] = yp;
+        }
+        if (gbuf) {
+            res_add(P, bz, dz);
+            free(bz);
+            free(gbuf);
+            free(g1);
         }
     } else {
         p_i = 0.5;
@@ -611,7 +713,10 @@ double or_lm_objective(const or_lm_problem* P, const double* x, const double* se
     int nd = or_tv_ndim(P->g);
     double c = 0.0;
     for (int64_t j = 0; j < V; ++j) c += sens[j] * x[j];
-    for (int64_t e = 0; e < P->n_ev; ++e) c -= log(ev_fwd(P, e, x) + (double)P->contam[e]);
+    double* gbuf;
+    const double* gx = res_in(P, x, &gbuf);
+    for (int64_t e = 0; e < P->n_ev; ++e) c -= log(ev_fwd(P, e, gx) + (double)P->contam[e]);
+    free(gbuf);
     if (P->beta > 0.0) {
         double* gr = (double*)malloc(sizeof(double) * V * (nd > 0 ? nd : 1));
         or_dtv_grad(P->g, P->xi, x, gr);
@@ -653,9 +758,17 @@ void or_emtv_em_step(const or_lm_problem* P, const double* sens, const double* x
 {
     const int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
     for (int64_t j = 0; j < V; ++j) z[j] = 0.0;
+    double* gbuf;
+    const double* gx = res_in(P, x, &gbuf);
+    double* bz = gbuf ? (double*)calloc(V, sizeof(double)) : z;
     for (int64_t e = i; e < P->n_ev; e += P->n_subsets) {
-        const double u = ev_fwd(P, e, x) + (double)P->contam[e];
-        ev_back(P, e, 1.0 / u, z);
+        const double u = ev_fwd(P, e, gx) + (double)P->contam[e];
+        ev_back(P, e, 1.0 / u, bz);
+    }
+    if (gbuf) {
+        res_add(P, bz, z);
+        free(bz);
+        free(gbuf);
     }
     for (int64_t j = 0; j < V; ++j) z[j] = sens[j] > 0.0 ? x[j] * (double)P->n_subsets / sens[j] * z[j] : 0.0;
 }

@@ -84,14 +84,15 @@ def _dtv_field(O, geo, n, seed=21, eta=0.3):
     return O.dtv_xi(geo, v, eta)
 
 
-@pytest.mark.parametrize("prior", ["tv", "dtv"])
+@pytest.mark.parametrize("prior", ["tv", "dtv", "tv+res"])
 def test_lmpdhg_reaches_independent_minimiser(oracle_mod, prior):
     """Brute force on a tiny grid: the dense P^LM is built column by column;
     L-BFGS-B on Eq. (1) with a smoothed TV (eps = 1e-9) gives the minimiser
     independently of Alg. 2.  LM-SPDHG (n = 1) must approach it: the objective
     gap and the KKT residual of x >= 0 become small.  For DTV the dense K is
     the dense TV matrix with P_j = I - xi_j xi_j^T applied to each voxel's
-    rows, written here from the definition."""
+    rows, written here from the definition; with the resolution model the
+    dense forward model is A G (G from its columns) and P^T 1 = G A^T 1."""
     O = oracle_mod
     sc, g, tof, ev = tiny_problem(n=(5, 4, 1), n_events=250, seed=5)
     geo = _geometry(O, sc, g, tof)
@@ -99,6 +100,15 @@ def test_lmpdhg_reaches_independent_minimiser(oracle_mod, prior):
     mu = O.event_counts(ev.det1, ev.det2, ev.tof)
     sens = O.sens(geo, np.ones(sc.n_lor, np.float32))
     A = _dense_lm_matrix(O, geo, E)
+    fwhm = 6.0 if prior == "tv+res" else 0.0
+    if fwhm > 0:
+        G = np.zeros((geo.V, geo.V))
+        for j in range(geo.V):
+            e = np.zeros(geo.V)
+            e[j] = 1.0
+            G[:, j] = O.res_apply(geo, fwhm, e)
+        A = A @ G
+        sens = G @ sens
     s = ev.contam.astype(np.float64)
     beta = 0.5
     V = geo.V
@@ -133,7 +143,8 @@ def test_lmpdhg_reaches_independent_minimiser(oracle_mod, prior):
 
     x0 = np.full(V, np.float32(1.0))
     knorm = _knorm(g.n)
-    lm = O.LM(geo, E, mu, 1, beta=beta, gamma=3.0 / float(x0.max()), rho=0.999, knorm=knorm, xi=xi)
+    lm = O.LM(geo, E, mu, 1, beta=beta, gamma=3.0 / float(x0.max()), rho=0.999, knorm=knorm, xi=xi,
+              res_fwhm=fwhm)
     lm.init(x0, sens)
     seq = S.selection_sequence(1, 60000, seed=3)
     lm.run(seq)
