@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="events in the oracle's timed sample")
     ap.add_argument("--knorm-iters", type=int, default=1000)
+    ap.add_argument("--prior", default="tv", choices=["tv", "dtv"],
+                    help="tv: the TV prior; dtv: the directional TV prior with the flipped-contrast phantom "
+                         "as structural image")
+    ap.add_argument("--beta", type=float, default=-1.0, help="override the workload's prior weight")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the (untimed-region) measurement of the listmode EM-TV warm start")
     ap.add_argument("--pdhg-iters", type=int, default=20, help="inner iterations of the EM-TV denoising")
@@ -187,9 +191,10 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # the oracle's timed sample (CPU baseline and reference arm)
 # --------------------------------------------------------------------------
-def oracle_sample_step(wl, ev_np, n_sample, seq_epoch):
+def oracle_sample_step(wl, ev_np, n_sample, seq_epoch, beta=None, xi=None):
     """One oracle run on a bounded sample of the frame: the first n_sample
-    events, full image grid, initialisation + one epoch (2n updates).
+    events, full image grid, initialisation + one epoch (2n updates), with
+    the TV prior or (xi given) the directional TV.
     Returns (events fwd+back projected, seconds)."""
     import oracle as O
     n = min(n_sample, ev_np.n)
@@ -203,7 +208,8 @@ def oracle_sample_step(wl, ev_np, n_sample, seq_epoch):
     sens = np.full(V, 1.0)
     kn = math.sqrt(sum(4.0 * math.sin(math.pi * (m - 1) / (2.0 * m)) ** 2 for m in wl.grid.n if m > 1))
     x0 = np.full(V, np.float32(0.8 * n / V))
-    lm = O.LM(geo, E, mu, wl.n_subsets, beta=wl.beta, gamma=3.0 / float(x0.max()), rho=0.999, knorm=kn)
+    lm = O.LM(geo, E, mu, wl.n_subsets, beta=wl.beta if beta is None else beta, gamma=3.0 / float(x0.max()),
+              rho=0.999, knorm=kn, xi=xi)
     t0 = time.perf_counter()
     lm.init(x0, sens)
     lm.run(seq_epoch)
@@ -285,8 +291,12 @@ def run_gpu(args):
     x0 = torch.full((geo.V,), kappa, dtype=torch.float32, device=dev)
     setup_ws = torch.empty(L.load_library().lm_setup_workspace_bytes(N), dtype=torch.uint8, device=dev)
     pe = L.event_setup(geo, raw_dev, n_sub, ws=setup_ws)
-    st = L.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=n_sub, rho=0.999, knorm=kn,
-                   deterministic=args.deterministic, kahan=True, projector=args.projector)
+    beta = wl.beta if args.beta < 0 else args.beta
+    xi = None
+    if args.prior == "dtv":
+        xi = dtv_structure(L, wl, geo, dev)
+    st = L.LMSPDHG(geo, pe, sens, x0, beta=beta, n_subsets=n_sub, rho=0.999, knorm=kn,
+                   deterministic=args.deterministic, kahan=True, projector=args.projector, xi=xi)
     E = args.epochs
     seq = S.selection_sequence(n_sub, 2 * n_sub * E, seed=3)
     seqs = [seq[2 * n_sub * e:2 * n_sub * (e + 1)] for e in range(E)]
@@ -419,8 +429,10 @@ def run_gpu(args):
         rows = [("event_kernel_prior_update_idle", 1, 0), ("image_pass_data_tma", 2, 48 if args.deterministic else 64),
                 ("prior_update_fused_tma", 3, 32 + 8 * nd)]
     else:
-        rows = [("prior_dual", 1, 4 + 8 * nd), ("image_pass_data", 2, 48 if args.deterministic else 64),
-                ("image_pass_prior", 3, 32 + 8 * nd)]
+        # the directional TV also reads its field (nd floats per voxel) in both prior kernels
+        fb = 4 * nd if xi is not None else 0
+        rows = [("prior_dual", 1, 4 + 8 * nd + fb), ("image_pass_data", 2, 48 if args.deterministic else 64),
+                ("image_pass_prior", 3, 32 + 8 * nd + fb)]
     for key, idx, bpv in rows:
         ms, n = prof[list(prof.keys())[idx]]
         if n:
@@ -462,7 +474,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ev_np = S.Events(*(getattr(raw, k)[:args.cpu_sample].cpu().numpy() for k in
                            ("det1", "det2", "tof", "corr", "contam")))
-        e_cpu, s_cpu = oracle_sample_step(wl, ev_np, args.cpu_sample, seqs[0])
+        xi_np = None if xi is None else xi.cpu().numpy().astype(np.float64)
+        e_cpu, s_cpu = oracle_sample_step(wl, ev_np, args.cpu_sample, seqs[0], beta=beta, xi=xi_np)
         cpu = {"value": e_cpu / s_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {min(args.cpu_sample, N)} events of the frame on the full grid: FP64 init + "
                          f"one epoch ({2 * n_sub} updates), {s_cpu:.1f} s"}
@@ -474,7 +487,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl.scanner.n_rings} rings x {wl.scanner.n_xtal} crystals, "
                                    f"{wl.grid.n[0]}x{wl.grid.n[1]}x{wl.grid.n[2]} image @{wl.grid.h[0]} mm, "
-                                   f"{N} events, {n_sub} subsets, TV beta={wl.beta}, {E} epochs per frame, "
+                                   f"{N} events, {n_sub} subsets, {args.prior.upper()} beta={beta}, {E} epochs per frame, "
                                    f"{'deterministic' if args.deterministic else 'atomic'} back-projection",
                        "n_events": N, "n_subsets": n_sub, "epochs_per_step": E,
                        "events_per_step": events_per_step, "parallelism": f"replicas x{world}",
@@ -492,6 +505,18 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def dtv_structure(L, wl, geo, dev):
+    """Directional-TV field of the flipped-contrast phantom (the paper's DTV
+    runs use the image itself with flipped contrast as structural image),
+    eta = 1 % of its largest gradient magnitude."""
+    import torch
+    act = torch.from_numpy(wl.phantom.voxelised(wl.grid, supersample=1)).to(dev)
+    v = (act.max() - act).contiguous()
+    g = L.tv_grad(geo, v).view(geo.ndim, geo.V)
+    eta = 0.01 * float(torch.sqrt((g.double() ** 2).sum(0)).max().item())
+    return L.dtv_field(geo, v, eta)
 
 
 def warm_start_measure(L, geo, pe, sens, x0, wl, kn, iters, stream, hbm_peak, peak_src, dev):

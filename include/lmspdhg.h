@@ -167,6 +167,35 @@ int lm_tv_div(const lm_grid* grid, const float* g, float* d, void* stream);
 /* w <- beta prox_{R^*}(w / beta) = w / max(1, |w|/beta), per voxel over the
  * components (in place); beta = 0 sets w = 0. */
 int lm_tv_prox(const lm_grid* grid, float* w, float beta, void* stream);
+/* ---- image-space resolution model (Eq. (1): P includes the limited
+ * spatial resolution) -------------------------------------------------- */
+/* P = A G with A the projector above and G a separable Gaussian blur of full
+ * width at half maximum fwhm (mm) on every axis with n_d > 1 (the paper gives
+ * no kernel; this is the implemented one): sigma_d = fwhm/(2 sqrt(2 ln 2))/h_d
+ * voxels, taps k = -r..r with r = floor(3 sigma_d + 1/2) (at most n_d - 1,
+ * at most 31), weights exp(-k^2/(2 sigma_d^2)) normalised to sum 1, the
+ * image mirrored about its outer faces.  G is symmetric with unit row sums,
+ * so P^T = G A^T and P 1 = A 1; P^T 1 = G (lm_sens).  out = G x (out may
+ * equal x); fwhm = 0 copies.  ws: device workspace of
+ * lm_res_workspace_bytes(grid) bytes.  LM_ERR_INVALID_ARG for a kernel
+ * wider than 31 taps per side. */
+size_t lm_res_workspace_bytes(const lm_grid* grid);
+int lm_res_apply(const lm_grid* grid, float fwhm, const float* x, float* out, void* ws, size_t ws_bytes,
+                 void* stream);
+
+/* ---- directional TV (the paper's second prior, Sec. "Numerical experiments") */
+/* Only the part of the forward-difference vector perpendicular to the
+ * gradient of a structural image v counts (after Ehrhardt & Betcke 2016):
+ *   (K x)_j = P_j (grad x)_j,  P_j = I - xi_j xi_j^T,
+ *   xi_j = (grad v)_j / sqrt(|(grad v)_j|^2 + eta^2)   (0 where both vanish),
+ * so eta = 0 makes P_j the orthogonal projection perpendicular to (grad v)_j.
+ * xi: device float [ndim][V] in the layout of lm_tv_grad (|xi_j| <= 1).
+ * K^T q = grad^T (P q); ||K|| <= ||K_TV||.  lm_params.xi selects this prior
+ * for LM-SPDHG.  lm_dtv_field: xi of v (eta >= 0); lm_dtv_grad: g = K x;
+ * lm_dtv_div: d = -K^T g. */
+int lm_dtv_field(const lm_grid* grid, const float* v, float eta, float* xi, void* stream);
+int lm_dtv_grad(const lm_grid* grid, const float* xi, const float* x, float* g, void* stream);
+int lm_dtv_div(const lm_grid* grid, const float* xi, const float* g, float* d, void* stream);
 /* ||K|| by FP64 power iteration on K^T K from the checkerboard
  * (-1)^(ix+iy+iz), `iters` iterations; *out_host = sqrt of the last Rayleigh
  * quotient (never above ||K||).  Synchronous.  ws: device workspace of
@@ -223,6 +252,16 @@ typedef struct {
                           /* per-sample arithmetic, sums in another order.  If the*/
                           /* events need more segments than the buffer holds     */
                           /* (6 per event), the direct kernel is used.            */
+    const float* xi;      /* directional TV prior (lm_dtv_field): device field    */
+                          /* [ndim][V], referenced, must outlive the state; NULL  */
+                          /* = TV.  Runs the plain-load image passes (auto picks */
+                          /* them; image_kernel = 2 is rejected).  knorm may be  */
+                          /* the TV norm: ||K_DTV|| <= ||K_TV||.                  */
+    float res_fwhm;       /* image-space resolution model P = A G (lm_res_apply): */
+                          /* FWHM in mm, 0 = none.  sens must then be G (lm_sens).*/
+                          /* Float-atomic mode only (deterministic is rejected);  */
+                          /* plain image passes, direct projector, no y-fastest   */
+                          /* image copies; not for batches.                      */
 } lm_params;
 
 /* Bytes of the optional tile-binned projector buffer (lm_params.tile_buf):

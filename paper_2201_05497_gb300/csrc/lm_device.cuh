@@ -280,6 +280,17 @@ __device__ __forceinline__ float tv_ball_scale(float n2, float beta)
     return n2 > beta * beta ? beta * rsqrtf(n2) : 1.0f;
 }
 
+// Directional TV (Sec. "Numerical experiments"): the part of a difference
+// vector (gx, gy, gz) perpendicular to the structural field (fx, fy, fz) of
+// the voxel, g - f (f . g); components of axes of length 1 are 0 in both.
+__device__ __forceinline__ void dtv_perp(float fx, float fy, float fz, float& gx, float& gy, float& gz)
+{
+    const float s = fmaf(fx, gx, fmaf(fy, gy, fz * gz));
+    gx = fmaf(-fx, s, gx);
+    gy = fmaf(-fy, s, gy);
+    gz = fmaf(-fz, s, gz);
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

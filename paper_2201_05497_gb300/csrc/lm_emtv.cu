@@ -8,9 +8,7 @@
 // convex with modulus gam = min_j w_j over the free voxels, and F^* the
 // indicator of the unit 2-norm balls.
 //
-// The inner iteration is two voxel-parallel passes: the dual step needs the
-// forward neighbours of ubar, the primal step the backward neighbours of q,
-// so one pass cannot finish before the other starts.  The step-size schedule
+// One inner iteration is two voxel passes (dual, primal).  The step-size schedule
 // (tau_k, sigma_k, theta_k) depends only on gam and ||K||; one thread computes
 // it in FP64 on the device once gam is known, so the whole epoch is queued
 // on the stream without a host round trip.
@@ -32,7 +30,9 @@ struct Sched {
     // as unsigned integers, so the minimum is an atomic maximum of the
     // complements and a cleared word (0) means "no free voxel"
     unsigned gam_nbits;
-    unsigned pad[63];
+    unsigned done;             // the event kernel's self-resetting work counters
+    unsigned long long queue;
+    unsigned pad[60];
     float tau[EMTV_MAX_ITERS];
     float sigma[EMTV_MAX_ITERS];
     float theta[EMTV_MAX_ITERS];
@@ -41,10 +41,11 @@ struct Sched {
 struct Ws {
     float* z;
     float* w;
-    float* ubar;
-    float* q;      // [ndim][V]
+    float* ubar;   // extrapolated primal iterate
+    float* q;      // dual iterate [ndim][V]
     float* acc_yf; // y-fastest accumulator of the EM back-projection
     float* x_yf;   // y-fastest copy of x for the EM gathers
+    float* tof_tab; // the TOF kernel tabulated for the event kernel (TOF_TAB_N + 1 floats)
     Sched* sc;
 };
 
@@ -88,14 +89,10 @@ size_t ws_layout(const lm_grid* g, Ws* w, void* base)
     t.q = (float*)take((size_t)nd * V * 4);
     t.acc_yf = (float*)take(V * 4);
     t.x_yf = (float*)take(V * 4);
+    t.tof_tab = (float*)take((size_t)(TOF_TAB_N + 1) * 4);
     t.sc = (Sched*)take(sizeof(Sched));
     if (w) *w = t;
     return off;
-}
-
-__device__ __forceinline__ int coord(int64_t j, int d, int nx, int ny)
-{
-    return d == 0 ? (int)(j % nx) : d == 1 ? (int)((j / nx) % ny) : (int)(j / ((int64_t)nx * ny));
 }
 
 // z_j = x_j n / g_j * b_j (0 where g_j = 0), b = the EM back-projection.
@@ -143,6 +140,30 @@ __global__ void __launch_bounds__(256) denoise_init_kernel(const float* __restri
     }
 }
 
+// The bin-integrated Gaussian TOF weight w(tau) on TOF_TAB_N intervals of
+// [-W, W] (the table the event kernel interpolates), evaluated in FP64.
+__global__ void tof_tab_kernel(float* tab, double W, double D, double s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > TOF_TAB_N) return;
+    const double tau = -W + 2.0 * W * k / TOF_TAB_N;
+    tab[k] = (float)(0.5 * (erf((tau + 0.5 * D) / s) - erf((tau - 0.5 * D) / s)));
+}
+
+// Clears the work counters and tabulates the TOF kernel for the EM steps.
+int em_prepare(const lm_tof* tof, const Ws& W, cudaStream_t st)
+{
+    LM_CUDA(cudaMemsetAsync(W.sc, 0, 16, st));
+    if (tof->n_bins > 0) {
+        const double sig = tof->sigma_mm;
+        tof_tab_kernel<<<(TOF_TAB_N + 256) / 256, 256, 0, st>>>(W.tof_tab, (double)tof->n_sigma * sig,
+                                                                (double)tof->bin_mm, std::sqrt(2.0) * sig);
+        count_launch();
+        LM_CUDA(cudaGetLastError());
+    }
+    return LM_OK;
+}
+
 // Step sizes of the accelerated algorithm: tau_0 = sigma_0 = 0.99 / ||K||;
 // theta_k = 1 / sqrt(1 + 2 gam tau_k); tau_{k+1} = theta_k tau_k;
 // sigma_{k+1} = sigma_k / theta_k (so tau_k sigma_k ||K||^2 stays 0.99^2).
@@ -162,58 +183,184 @@ __global__ void sched_kernel(Sched* sc, int iters, double knorm)
     }
 }
 
-// q <- proj_{|.| <= 1}(q + sigma_k K ubar), per voxel over the components.
-__global__ void __launch_bounds__(256) dual_kernel(const float* __restrict__ ubar, float* __restrict__ q, Axes ax,
-                                                   int nx, int ny, int64_t V, const Sched* __restrict__ sc, int k)
+// One inner iteration is two voxel passes: the dual step needs the forward
+// neighbours of ubar, the primal step the backward neighbours of the new q,
+// so the second pass starts when the first has finished.  Each thread takes
+// four consecutive voxels of one image row with 16-byte loads when rows are
+// a multiple of 4 long (all loads issued before any arithmetic), else one
+// voxel.  Indices are 32-bit (grids have fewer than 2^31 voxels).
+struct PdArgs {
+    float* ubar;
+    float* q;            // [ndim][V]
+    float* u;
+    const float* z;
+    const float* w;
+    int nx, ny, nz;
+    int cx, cy, cz;      // component of the x, y, z difference (-1: axis of length 1)
+    int V;
+    const Sched* sc;
+    int k;
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float f4(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ void st4(float* p, const float* v) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+
+// q <- proj_{|.| <= 1}(q + sigma_k K ubar) at voxel j (components in axis
+// order), from ubar_j and its forward neighbours.
+__device__ __forceinline__ void dual_point(const PdArgs& A, float sg, float u0, float ux, float uy, float uz, bool inx,
+                                           bool iny, bool inz, float q0, float q1, float q2, float& o0, float& o1,
+                                           float& o2)
 {
-    const float sg = sc->sigma[k];
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
-        const float uj = ubar[j];
-        float v[3];
-        float n2 = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (c < ax.nd) {
-                const float gr = coord(j, ax.dim[c], nx, ny) < ax.n[c] - 1 ? ubar[j + ax.st[c]] - uj : 0.0f;
-                v[c] = fmaf(sg, gr, q[c * V + j]);
-                n2 = fmaf(v[c], v[c], n2);
-            }
-        }
-        const float s = tv_ball_scale(n2, 1.0f);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (c < ax.nd) q[c * V + j] = __fmul_rn(v[c], s);
+    float vx = 0.0f, vy = 0.0f, vz = 0.0f, n2 = 0.0f;
+    if (A.cx >= 0) {
+        vx = fmaf(sg, inx ? ux - u0 : 0.0f, q0);
+        n2 = fmaf(vx, vx, n2);
     }
+    if (A.cy >= 0) {
+        vy = fmaf(sg, iny ? uy - u0 : 0.0f, q1);
+        n2 = fmaf(vy, vy, n2);
+    }
+    if (A.cz >= 0) {
+        vz = fmaf(sg, inz ? uz - u0 : 0.0f, q2);
+        n2 = fmaf(vz, vz, n2);
+    }
+    const float s = tv_ball_scale(n2, 1.0f);
+    o0 = __fmul_rn(vx, s);
+    o1 = __fmul_rn(vy, s);
+    o2 = __fmul_rn(vz, s);
 }
 
 // u+ = prox_{tau G}(u - tau K^T q) = max(0, (v + tau w z) / (1 + tau w)) on
-// free voxels (0 on held ones); ubar = u+ + theta (u+ - u); u = u+.
-__global__ void __launch_bounds__(256) primal_kernel(float* __restrict__ u, float* __restrict__ ubar,
-                                                     const float* __restrict__ q, const float* __restrict__ z,
-                                                     const float* __restrict__ w, Axes ax, int nx, int ny,
-                                                     int64_t V, const Sched* __restrict__ sc, int k)
+// free voxels (0 on held ones); returns u+, ubar+ = u+ + theta (u+ - u).
+__device__ __forceinline__ float primal_point(float tau, float th, float kt, float uj, float wj, float zj, float& ub)
 {
-    const float tau = sc->tau[k], th = sc->theta[k];
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
-        float kt = 0.0f;  // (K^T q)_j
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (c < ax.nd) {
-                const int cj = coord(j, ax.dim[c], nx, ny);
-                if (cj < ax.n[c] - 1) kt -= q[c * V + j];
-                if (cj >= 1) kt += q[c * V + j - ax.st[c]];
-            }
-        }
-        const float wj = w[j], uj = u[j];
-        float un = 0.0f;
-        if (wj > 0.0f) {
-            const float v = fmaf(-tau, kt, uj);
-            const float tw = tau * wj;
-            un = fmaxf(0.0f, fmaf(tw, z[j], v) / (1.0f + tw));
-        }
-        ubar[j] = fmaf(th, un - uj, un);
-        u[j] = un;
+    float un = 0.0f;
+    if (wj > 0.0f) {
+        const float v = fmaf(-tau, kt, uj);
+        const float tw = tau * wj;
+        un = fmaxf(0.0f, fmaf(tw, zj, v) / (1.0f + tw));
     }
+    ub = fmaf(th, un - uj, un);
+    return un;
+}
+
+__global__ void __launch_bounds__(256) dual_quad_kernel(const PdArgs A)
+{
+    const int nq = A.nx >> 2;
+    const int nquads = A.V >> 2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nquads) return;
+    const float sg = A.sc->sigma[A.k];
+    const int nx = A.nx, ny = A.ny, nz = A.nz, V = A.V;
+    const int ix = (t % nq) * 4, r = t / nq, iy = r % ny, iz = r / ny;
+    const int j = r * nx + ix;
+    const bool iny = iy < ny - 1, inz = iz < nz - 1;
+    const float4 uc = ld4(A.ubar + j);
+    const float ur = (A.cx >= 0 && ix + 4 < nx) ? A.ubar[j + 4] : 0.0f;
+    const float4 uy = (A.cy >= 0 && iny) ? ld4(A.ubar + j + nx) : uc;
+    const float4 uz = (A.cz >= 0 && inz) ? ld4(A.ubar + j + nx * ny) : uc;
+    const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4 qx = A.cx >= 0 ? ld4(A.q + A.cx * V + j) : zero;
+    const float4 qy = A.cy >= 0 ? ld4(A.q + A.cy * V + j) : zero;
+    const float4 qz = A.cz >= 0 ? ld4(A.q + A.cz * V + j) : zero;
+    float ox[4], oy[4], oz[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        dual_point(A, sg, f4(uc, i), i < 3 ? f4(uc, i + 1) : ur, f4(uy, i), f4(uz, i), ix + i < nx - 1, iny, inz,
+                   f4(qx, i), f4(qy, i), f4(qz, i), ox[i], oy[i], oz[i]);
+    if (A.cx >= 0) st4(A.q + A.cx * V + j, ox);
+    if (A.cy >= 0) st4(A.q + A.cy * V + j, oy);
+    if (A.cz >= 0) st4(A.q + A.cz * V + j, oz);
+}
+
+__global__ void __launch_bounds__(256) primal_quad_kernel(const PdArgs A)
+{
+    const int nq = A.nx >> 2;
+    const int nquads = A.V >> 2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nquads) return;
+    const float tau = A.sc->tau[A.k], th = A.sc->theta[A.k];
+    const int nx = A.nx, ny = A.ny, nz = A.nz, V = A.V;
+    const int ix = (t % nq) * 4, r = t / nq, iy = r % ny, iz = r / ny;
+    const int j = r * nx + ix;
+    const int sz = nx * ny;
+    const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4 qx = A.cx >= 0 ? ld4(A.q + A.cx * V + j) : zero;
+    const float qxl = (A.cx >= 0 && ix >= 1) ? A.q[A.cx * V + j - 1] : 0.0f;
+    const float4 qy = A.cy >= 0 ? ld4(A.q + A.cy * V + j) : zero;
+    const float4 qyb = (A.cy >= 0 && iy >= 1) ? ld4(A.q + A.cy * V + j - nx) : zero;
+    const float4 qz = A.cz >= 0 ? ld4(A.q + A.cz * V + j) : zero;
+    const float4 qzb = (A.cz >= 0 && iz >= 1) ? ld4(A.q + A.cz * V + j - sz) : zero;
+    const float4 u4 = ld4(A.u + j), w4 = ld4(A.w + j), z4 = ld4(A.z + j);
+    float uo[4], bo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float kt = 0.0f;  // (K^T q)_j, components in axis order
+        if (A.cx >= 0) {
+            if (ix + i < nx - 1) kt -= f4(qx, i);
+            if (ix + i >= 1) kt += i > 0 ? f4(qx, i - 1) : qxl;
+        }
+        if (A.cy >= 0) {
+            if (iy < ny - 1) kt -= f4(qy, i);
+            if (iy >= 1) kt += f4(qyb, i);
+        }
+        if (A.cz >= 0) {
+            if (iz < nz - 1) kt -= f4(qz, i);
+            if (iz >= 1) kt += f4(qzb, i);
+        }
+        uo[i] = primal_point(tau, th, kt, f4(u4, i), f4(w4, i), f4(z4, i), bo[i]);
+    }
+    st4(A.u + j, uo);
+    st4(A.ubar + j, bo);
+}
+
+// One voxel per thread (rows not a multiple of 4 long).
+__global__ void __launch_bounds__(256) dual_point_kernel(const PdArgs A)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.V) return;
+    const float sg = A.sc->sigma[A.k];
+    const int nx = A.nx, ny = A.ny, nz = A.nz, V = A.V;
+    const int ix = j % nx, r = j / nx, iy = r % ny, iz = r / ny;
+    const bool inx = ix < nx - 1, iny = iy < ny - 1, inz = iz < nz - 1;
+    const float u0 = A.ubar[j];
+    const float ux = (A.cx >= 0 && inx) ? A.ubar[j + 1] : u0;
+    const float uy = (A.cy >= 0 && iny) ? A.ubar[j + nx] : u0;
+    const float uz = (A.cz >= 0 && inz) ? A.ubar[j + nx * ny] : u0;
+    const float q0 = A.cx >= 0 ? A.q[A.cx * V + j] : 0.0f;
+    const float q1 = A.cy >= 0 ? A.q[A.cy * V + j] : 0.0f;
+    const float q2 = A.cz >= 0 ? A.q[A.cz * V + j] : 0.0f;
+    float o0, o1, o2;
+    dual_point(A, sg, u0, ux, uy, uz, inx, iny, inz, q0, q1, q2, o0, o1, o2);
+    if (A.cx >= 0) A.q[A.cx * V + j] = o0;
+    if (A.cy >= 0) A.q[A.cy * V + j] = o1;
+    if (A.cz >= 0) A.q[A.cz * V + j] = o2;
+}
+
+__global__ void __launch_bounds__(256) primal_point_kernel(const PdArgs A)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.V) return;
+    const float tau = A.sc->tau[A.k], th = A.sc->theta[A.k];
+    const int nx = A.nx, ny = A.ny, nz = A.nz, V = A.V;
+    const int ix = j % nx, r = j / nx, iy = r % ny, iz = r / ny;
+    float kt = 0.0f;
+    if (A.cx >= 0) {
+        if (ix < nx - 1) kt -= A.q[A.cx * V + j];
+        if (ix >= 1) kt += A.q[A.cx * V + j - 1];
+    }
+    if (A.cy >= 0) {
+        if (iy < ny - 1) kt -= A.q[A.cy * V + j];
+        if (iy >= 1) kt += A.q[A.cy * V + j - nx];
+    }
+    if (A.cz >= 0) {
+        if (iz < nz - 1) kt -= A.q[A.cz * V + j];
+        if (iz >= 1) kt += A.q[A.cz * V + j - nx * ny];
+    }
+    float ub;
+    A.u[j] = primal_point(tau, th, kt, A.u[j], A.w[j], A.z[j], ub);
+    A.ubar[j] = ub;
 }
 
 int voxel_grid(int64_t V)
@@ -225,14 +372,35 @@ int voxel_grid(int64_t V)
 // The schedule from gam, then the inner iterations on (u, ubar, q) with z, w.
 int run_pdhg(const lm_grid* g, const Ws& W, float* u, int iters, double knorm, cudaStream_t st)
 {
-    const Axes ax = axes_of(g);
-    const int64_t V = nvox(g);
-    const int gv = voxel_grid(V);
     sched_kernel<<<1, 32, 0, st>>>(W.sc, iters, knorm);
     count_launch();
+    PdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = g->n[0];
+    a.ny = g->n[1];
+    a.nz = g->n[2];
+    int c = 0;
+    a.cx = a.nx > 1 ? c++ : -1;
+    a.cy = a.ny > 1 ? c++ : -1;
+    a.cz = a.nz > 1 ? c++ : -1;
+    a.V = (int)nvox(g);
+    a.ubar = W.ubar;
+    a.q = W.q;
+    a.u = u;
+    a.z = W.z;
+    a.w = W.w;
+    a.sc = W.sc;
+    const bool quad = (a.nx & 3) == 0;
+    const int blocks = quad ? (a.V / 4 + 255) / 256 : (a.V + 255) / 256;
     for (int k = 0; k < iters; ++k) {
-        dual_kernel<<<gv, 256, 0, st>>>(W.ubar, W.q, ax, g->n[0], g->n[1], V, W.sc, k);
-        primal_kernel<<<gv, 256, 0, st>>>(u, W.ubar, W.q, W.z, W.w, ax, g->n[0], g->n[1], V, W.sc, k);
+        a.k = k;
+        if (quad) {
+            dual_quad_kernel<<<blocks, 256, 0, st>>>(a);
+            primal_quad_kernel<<<blocks, 256, 0, st>>>(a);
+        } else {
+            dual_point_kernel<<<blocks, 256, 0, st>>>(a);
+            primal_point_kernel<<<blocks, 256, 0, st>>>(a);
+        }
     }
     count_launch(2 * (int64_t)iters);
     LM_CUDA(cudaGetLastError());
@@ -282,8 +450,12 @@ int em_step(const lm_scanner* sc, const lm_grid* grid, const Geo& G, const lm_ev
         a.e_begin = e0;
         a.e_end = e1;
         a.chunk = 32;
+        a.queue = &W.sc->queue;
+        a.done = &W.sc->done;
+        a.tof_tab = G.tof_on ? W.tof_tab : nullptr;
+        a.group = two_d ? 16 : 32;  // the widths the autotuner picks on the 2D and 3D frames
         a.stepmax = 2.0f * std::fmax(grid->h[0], std::fmax(grid->h[1], grid->h[2]));
-        int rc = launch_events(EV_EM, two_d, a, ev_grid(EV_EM, two_d), st);
+        int rc = launch_events(EV_EM, two_d, a, ev_grid_g(EV_EM, two_d, a.group), st);
         LM_CHECK(rc == LM_OK, rc, "EM back-projection launch failed");
         if (use_yf) launch_add_yf_to_std(grid, W.z, W.acc_yf, st);
     }
@@ -336,6 +508,8 @@ int lm_emtv_em_step(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof
     const size_t V = (size_t)nvox(grid);
     // work on a copy of x so that the fold (which writes x = z without a prior) leaves x untouched
     LM_CUDA(cudaMemcpyAsync(z, x, V * 4, cudaMemcpyDeviceToDevice, st));
+    rc = em_prepare(tof, W, st);
+    if (rc) return rc;
     rc = em_step(sc, grid, G, ev, 0, ev->n, n_subsets, sens, z, 0.0f, W, st);
     if (rc) return rc;
     return LM_OK;
@@ -385,6 +559,8 @@ int lm_emtv_epoch(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, 
     Ws W;
     ws_layout(grid, &W, ws);
     cudaStream_t st = S(stream);
+    rc = em_prepare(tof, W, st);
+    if (rc) return rc;
     for (int i = 0; i < n_subsets; ++i) {
         rc = em_step(sc, grid, G, ev_perm, sub_off_host[i], sub_off_host[i + 1], n_subsets, sens, x, beta, W, st);
         if (rc) return rc;

@@ -138,10 +138,61 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Directional TV: (P d) at voxel m for d = w+ - w, P = I - xi xi^T of the
+// voxel (components of axes of length 1 are 0).
+__device__ __forceinline__ void dtv_pd(const lmh::ImgArgs& A, const float* wc, const float* wn, int64_t m, int cx,
+                                       int cy, int cz, float& px, float& py, float& pz)
+{
+    const int64_t V = A.V;
+    const float* f = A.xi;
+    px = cx >= 0 ? wn[cx * V + m] - wc[cx * V + m] : 0.0f;
+    py = cy >= 0 ? wn[cy * V + m] - wc[cy * V + m] : 0.0f;
+    pz = cz >= 0 ? wn[cz * V + m] - wc[cz * V + m] : 0.0f;
+    dtv_perp(cx >= 0 ? f[cx * V + m] : 0.0f, cy >= 0 ? f[cy * V + m] : 0.0f, cz >= 0 ? f[cz * V + m] : 0.0f, px, py,
+             pz);
+}
+
+// dz_j = (K^T (w+ - w))_j = (grad^T P (w+ - w))_j for the directional TV
+__device__ __noinline__ float prior_dz_dtv(const lmh::ImgArgs& A, const float* wc, const float* wn, int xx, int yy,
+                                           int zz, int64_t j)
+{
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    int c = 0;
+    const int cx = nx > 1 ? c++ : -1;
+    const int cy = ny > 1 ? c++ : -1;
+    const int cz = nz > 1 ? c++ : -1;
+    float px, py, pz, qx, qy, qz;
+    dtv_pd(A, wc, wn, j, cx, cy, cz, px, py, pz);
+    float dz = 0.0f;
+    if (cx >= 0) {
+        if (xx < nx - 1) dz -= px;
+        if (xx >= 1) {
+            dtv_pd(A, wc, wn, j - 1, cx, cy, cz, qx, qy, qz);
+            dz += qx;
+        }
+    }
+    if (cy >= 0) {
+        if (yy < ny - 1) dz -= py;
+        if (yy >= 1) {
+            dtv_pd(A, wc, wn, j - nx, cx, cy, cz, qx, qy, qz);
+            dz += qy;
+        }
+    }
+    if (cz >= 0) {
+        if (zz < nz - 1) dz -= pz;
+        if (zz >= 1) {
+            dtv_pd(A, wc, wn, j - (int64_t)nx * ny, cx, cy, cz, qx, qy, qz);
+            dz += qz;
+        }
+    }
+    return dz;
+}
+
 // dz_j = (K^T (w+ - w))_j, components in axis order for axes with n > 1
 __device__ __forceinline__ float prior_dz(const lmh::ImgArgs& A, const float* wc, const float* wn, int xx, int yy,
                                           int zz, int64_t j)
 {
+    if (A.xi != nullptr) return prior_dz_dtv(A, wc, wn, xx, yy, zz, j);
     const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
     const int64_t V = A.V;
     float dz = 0.0f;
@@ -231,7 +282,9 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
     constexpr int RPT = TD / TR;  // rows per thread in a tile
     const int nx = A.n[0], ny = A.n[1];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const bool have_yf = ny > 1;
+    // y-fastest accumulators and x copy (absent with the resolution model, whose projections read one layout)
+    const bool have_yf = ny > 1 && (A.det ? A.acci_yf != nullptr : A.acc_yf != nullptr);
+    const bool x_yf = ny > 1 && x_nxt_yf != nullptr;
     const bool kahan = A.kahan != 0;
     const bool det = A.det != 0;
     const float* __restrict__ Tm = A.T;
@@ -354,7 +407,7 @@ __device__ __forceinline__ void image_tile(const lmh::ImgArgs& A, const PassMode
         }
     }
     __syncthreads();
-    if (have_yf) {
+    if (x_yf) {
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
             const int r = ty + q * TR;
@@ -1011,9 +1064,11 @@ __device__ __forceinline__ double block_sum_d(double v, double* sm)
     return r;
 }
 
-// objective parts over voxels: <sens, x> and ||Kx||_{2,1} (FP64)
+// objective parts over voxels: <sens, x> and ||Kx||_{2,1} (FP64); K is the
+// forward difference, or its part perpendicular to the field xi (DTV)
 __global__ void __launch_bounds__(256) obj_img_partial(const float* __restrict__ sens, const float* __restrict__ x,
-                                                       int nx, int ny, int nz, double* part)
+                                                       const float* __restrict__ xi, int nx, int ny, int nz,
+                                                       double* part)
 {
     __shared__ double sm[256];
     const int64_t V = (int64_t)nx * ny * nz;
@@ -1022,11 +1077,29 @@ __global__ void __launch_bounds__(256) obj_img_partial(const float* __restrict__
         const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / ((int64_t)nx * ny));
         const double xj = (double)x[j];
         s1 += (double)sens[j] * xj;
-        double g2 = 0.0, g;
-        if (nx > 1 && ix < nx - 1) { g = (double)x[j + 1] - xj; g2 += g * g; }
-        if (ny > 1 && iy < ny - 1) { g = (double)x[j + nx] - xj; g2 += g * g; }
-        if (nz > 1 && iz < nz - 1) { g = (double)x[j + (int64_t)nx * ny] - xj; g2 += g * g; }
-        s2 += sqrt(g2);
+        double gx = 0.0, gy = 0.0, gz = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+        int c = 0;
+        if (nx > 1) {
+            if (ix < nx - 1) gx = (double)x[j + 1] - xj;
+            if (xi) fx = xi[c * V + j];
+            ++c;
+        }
+        if (ny > 1) {
+            if (iy < ny - 1) gy = (double)x[j + nx] - xj;
+            if (xi) fy = xi[c * V + j];
+            ++c;
+        }
+        if (nz > 1) {
+            if (iz < nz - 1) gz = (double)x[j + (int64_t)nx * ny] - xj;
+            if (xi) fz = xi[c * V + j];
+        }
+        if (xi) {
+            const double t = fx * gx + fy * gy + fz * gz;
+            gx -= fx * t;
+            gy -= fy * t;
+            gz -= fz * t;
+        }
+        s2 += sqrt(gx * gx + gy * gy + gz * gz);
     }
     s1 = block_sum_d(s1, sm);
     s2 = block_sum_d(s2, sm);
@@ -1056,6 +1129,111 @@ __global__ void __launch_bounds__(256) obj_final(double* part)
         for (int i = threadIdx.x; i < RB; i += 256) acc += part[q * RB + i];
         acc = block_sum_d(acc, sm);
         if (threadIdx.x == 0) part[3 * RB + q] = acc;
+    }
+}
+
+// ---- directional TV (standalone calls) ----
+// Difference vector of x at voxel j (0 for boundary differences), axis order.
+__device__ __forceinline__ void fwd_diff(const float* x, int64_t j, int ix, int iy, int iz, int nx, int ny, int nz,
+                                         float& gx, float& gy, float& gz)
+{
+    const float xj = x[j];
+    gx = (nx > 1 && ix < nx - 1) ? x[j + 1] - xj : 0.0f;
+    gy = (ny > 1 && iy < ny - 1) ? x[j + nx] - xj : 0.0f;
+    gz = (nz > 1 && iz < nz - 1) ? x[j + (int64_t)nx * ny] - xj : 0.0f;
+}
+
+// Field components of voxel j per axis (0 for axes of length 1).
+__device__ __forceinline__ void field_at(const float* xi, int64_t V, int64_t j, int nx, int ny, int nz, float& fx,
+                                         float& fy, float& fz)
+{
+    int c = 0;
+    fx = nx > 1 ? xi[(c++) * V + j] : 0.0f;
+    fy = ny > 1 ? xi[(c++) * V + j] : 0.0f;
+    fz = nz > 1 ? xi[(c++) * V + j] : 0.0f;
+}
+
+__device__ __forceinline__ void store_comps(float* g, int64_t V, int64_t j, int nx, int ny, int nz, float gx, float gy,
+                                            float gz)
+{
+    int c = 0;
+    if (nx > 1) g[(c++) * V + j] = gx;
+    if (ny > 1) g[(c++) * V + j] = gy;
+    if (nz > 1) g[(c++) * V + j] = gz;
+}
+
+// xi_j = (grad v)_j / sqrt(|(grad v)_j|^2 + eta^2), 0 where both vanish
+__global__ void dtv_field_kernel(const float* __restrict__ v, float eta2, float* __restrict__ xi, int nx, int ny,
+                                 int nz)
+{
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / ((int64_t)nx * ny));
+        float gx, gy, gz;
+        fwd_diff(v, j, ix, iy, iz, nx, ny, nz, gx, gy, gz);
+        const float n2 = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, eta2)));
+        const float r = n2 > 0.0f ? 1.0f / sqrtf(n2) : 0.0f;
+        store_comps(xi, V, j, nx, ny, nz, gx * r, gy * r, gz * r);
+    }
+}
+
+// g = K x = P grad x
+__global__ void dtv_grad_kernel(const float* __restrict__ x, const float* __restrict__ xi, float* __restrict__ g,
+                                int nx, int ny, int nz)
+{
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / ((int64_t)nx * ny));
+        float gx, gy, gz, fx, fy, fz;
+        fwd_diff(x, j, ix, iy, iz, nx, ny, nz, gx, gy, gz);
+        field_at(xi, V, j, nx, ny, nz, fx, fy, fz);
+        dtv_perp(fx, fy, fz, gx, gy, gz);
+        store_comps(g, V, j, nx, ny, nz, gx, gy, gz);
+    }
+}
+
+// (P g) at voxel m
+__device__ __forceinline__ void pg_at(const float* g, const float* xi, int64_t V, int64_t m, int nx, int ny, int nz,
+                                      float& px, float& py, float& pz)
+{
+    float fx, fy, fz;
+    field_at(g, V, m, nx, ny, nz, px, py, pz);
+    field_at(xi, V, m, nx, ny, nz, fx, fy, fz);
+    dtv_perp(fx, fy, fz, px, py, pz);
+}
+
+// d = -K^T g = div (P g)
+__global__ void dtv_div_kernel(const float* __restrict__ g, const float* __restrict__ xi, float* __restrict__ d,
+                               int nx, int ny, int nz)
+{
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % nx), iy = (int)((j / nx) % ny), iz = (int)(j / ((int64_t)nx * ny));
+        float px, py, pz, qx, qy, qz;
+        pg_at(g, xi, V, j, nx, ny, nz, px, py, pz);
+        float s = 0.0f;
+        if (nx > 1) {
+            if (ix < nx - 1) s += px;
+            if (ix >= 1) {
+                pg_at(g, xi, V, j - 1, nx, ny, nz, qx, qy, qz);
+                s -= qx;
+            }
+        }
+        if (ny > 1) {
+            if (iy < ny - 1) s += py;
+            if (iy >= 1) {
+                pg_at(g, xi, V, j - nx, nx, ny, nz, qx, qy, qz);
+                s -= qy;
+            }
+        }
+        if (nz > 1) {
+            if (iz < nz - 1) s += pz;
+            if (iz >= 1) {
+                pg_at(g, xi, V, j - (int64_t)nx * ny, nx, ny, nz, qx, qy, qz);
+                s -= qz;
+            }
+        }
+        d[j] = s;
     }
 }
 
@@ -1475,10 +1653,10 @@ int reduce_minmax(const float* x, int64_t n, float* dev_scratch, float* mn, floa
 
 size_t objective_scratch_bytes() { return align_up((3 * RB + 4) * sizeof(double)); }
 
-int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* p, const float* contam,
-                    int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st)
+int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* xi, const float* p,
+                    const float* contam, int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st)
 {
-    obj_img_partial<<<RB, 256, 0, st>>>(sens, x, g->n[0], g->n[1], g->n[2], scratch);
+    obj_img_partial<<<RB, 256, 0, st>>>(sens, x, xi, g->n[0], g->n[1], g->n[2], scratch);
     obj_ev_partial<<<RB, 256, 0, st>>>(p, contam, n_ev, scratch);
     obj_final<<<1, 256, 0, st>>>(scratch);
     count_launch(3);
@@ -1533,6 +1711,46 @@ int lm_tv_div(const lm_grid* grid, const float* g, float* d, void* stream)
     LM_CHECK(g && d, LM_ERR_INVALID_ARG, "g or d is NULL");
     const int64_t V = nvox(grid);
     tv_div_kernel<<<flat_grid(V), 256, 0, S(stream)>>>(g, d, grid->n[0], grid->n[1], grid->n[2]);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_dtv_field(const lm_grid* grid, const float* v, float eta, float* xi, void* stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(v && xi, LM_ERR_INVALID_ARG, "v or xi is NULL");
+    LM_CHECK(eta >= 0.0f && std::isfinite(eta), LM_ERR_INVALID_ARG, "eta must be finite and >= 0");
+    const int64_t V = nvox(grid);
+    dtv_field_kernel<<<flat_grid(V), 256, 0, S(stream)>>>(v, eta * eta, xi, grid->n[0], grid->n[1], grid->n[2]);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_dtv_grad(const lm_grid* grid, const float* xi, const float* x, float* g, void* stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(xi && x && g, LM_ERR_INVALID_ARG, "xi, x or g is NULL");
+    const int64_t V = nvox(grid);
+    dtv_grad_kernel<<<flat_grid(V), 256, 0, S(stream)>>>(x, xi, g, grid->n[0], grid->n[1], grid->n[2]);
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_dtv_div(const lm_grid* grid, const float* xi, const float* g, float* d, void* stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    LM_CHECK(xi && g && d, LM_ERR_INVALID_ARG, "xi, g or d is NULL");
+    const int64_t V = nvox(grid);
+    dtv_div_kernel<<<flat_grid(V), 256, 0, S(stream)>>>(g, xi, d, grid->n[0], grid->n[1], grid->n[2]);
     count_launch();
     LM_CUDA(cudaGetLastError());
     return LM_OK;

@@ -130,6 +130,7 @@ struct EvArgs {
     int prior_fused;            // 1: the prior's dual step runs inside the TMA image pass instead
     int prior_only;             // 1: data selections are left to the tile-binned projector
     int acc_pairs;              // 1: acc_std / acc_yf hold (voxel j, voxel j + nx*ny) float pairs
+    const float* xi;            // directional TV field [ndim][V], or nullptr (TV)
 };
 
 // Batched multi-frame epochs: per-frame argument tables in device memory.
@@ -286,6 +287,7 @@ struct ImgArgs {
     int xcur;              // index of x_cur among the two x buffers
     int zlen;              // z slices per work item
     unsigned* err;         // set when a bounded wait gave up
+    const float* xi;       // directional TV field [ndim][V], or nullptr (TV; plain passes only)
 };
 
 struct BatchImgArgs {
@@ -311,8 +313,24 @@ void launch_step_T(const lm_grid* g, const float* sens, float* T, float rho, flo
                    cudaStream_t st);
 int reduce_minmax(const float* x, int64_t n, float* dev_scratch, float* mn, float* mx, cudaStream_t st);
 void launch_zadd(const lm_grid* g, const float* z, const float* zc, float* out, cudaStream_t st);
-int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* p, const float* contam,
-                    int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st);
+// Image-space resolution model G (separable Gaussian, mirrored faces).
+constexpr int RES_MAX_R = 31;  // taps per side
+struct ResAxis {
+    int r;
+    float w[2 * RES_MAX_R + 1];  // w[k + r], k = -r..r
+};
+struct ResPlan {
+    int n_axes;       // 0: G is the identity
+    int axis[3];
+    ResAxis ax[3];
+};
+int res_plan(const lm_grid* g, float fwhm, ResPlan& p);
+// dst = G src via temporaries t1, t2; skipped when seq[u] >= n_subsets (seq set)
+int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* t1, float* t2,
+               const uint16_t* seq, int u, int n_subsets, cudaStream_t st);
+
+int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* xi, const float* p,
+                    const float* contam, int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st);
 size_t objective_scratch_bytes();
 
 }  // namespace lmh

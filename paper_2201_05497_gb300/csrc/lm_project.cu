@@ -115,7 +115,9 @@ using lmh::EvArgs;
 namespace {
 
 // Dual step of the prior at voxel j (prior update of Alg. 2):
-// w+ = v / max(1, |v|/beta), v = w + S_{n+1} K x.
+// w+ = v / max(1, |v|/beta), v = w + S_{n+1} K x; K x is the forward
+// difference vector, or (directional TV, A.xi set) its part perpendicular to
+// the structural field.
 __device__ __forceinline__ void prior_voxel(const EvArgs& A, const float* __restrict__ x,
                                             const float* __restrict__ wc, float* __restrict__ wn, int j)
 {
@@ -126,11 +128,20 @@ __device__ __forceinline__ void prior_voxel(const EvArgs& A, const float* __rest
     const int iz = j / (nx * ny);
     const float x0 = x[j];
     int c = 0;
-    float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
     int cx = -1, cy = -1, cz = -1;
-    if (nx > 1) { cx = c++; vx = fmaf(A.s_prior, ix < nx - 1 ? x[j + 1] - x0 : 0.0f, wc[(int64_t)cx * V + j]); }
-    if (ny > 1) { cy = c++; vy = fmaf(A.s_prior, iy < ny - 1 ? x[j + nx] - x0 : 0.0f, wc[(int64_t)cy * V + j]); }
-    if (nz > 1) { cz = c++; vz = fmaf(A.s_prior, iz < nz - 1 ? x[j + nx * ny] - x0 : 0.0f, wc[(int64_t)cz * V + j]); }
+    if (nx > 1) { cx = c++; gx = ix < nx - 1 ? x[j + 1] - x0 : 0.0f; }
+    if (ny > 1) { cy = c++; gy = iy < ny - 1 ? x[j + nx] - x0 : 0.0f; }
+    if (nz > 1) { cz = c++; gz = iz < nz - 1 ? x[j + nx * ny] - x0 : 0.0f; }
+    if (A.xi != nullptr) {
+        const float* f = A.xi;
+        dtv_perp(cx >= 0 ? f[(int64_t)cx * V + j] : 0.0f, cy >= 0 ? f[(int64_t)cy * V + j] : 0.0f,
+                 cz >= 0 ? f[(int64_t)cz * V + j] : 0.0f, gx, gy, gz);
+    }
+    float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+    if (cx >= 0) vx = fmaf(A.s_prior, gx, wc[(int64_t)cx * V + j]);
+    if (cy >= 0) vy = fmaf(A.s_prior, gy, wc[(int64_t)cy * V + j]);
+    if (cz >= 0) vz = fmaf(A.s_prior, gz, wc[(int64_t)cz * V + j]);
     const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), A.beta);
     if (cx >= 0) wn[(int64_t)cx * V + j] = __fmul_rn(vx, sc);
     if (cy >= 0) wn[(int64_t)cy * V + j] = __fmul_rn(vy, sc);
@@ -164,14 +175,22 @@ __device__ __forceinline__ void prior_quad(const EvArgs& A, const float* __restr
     const float4 wx = hx ? ld4(wc + j) : z4;
     const float4 wy = hy ? ld4(wc + (int64_t)cy * V + j) : z4;
     const float4 wz = hz ? ld4(wc + (int64_t)cz * V + j) : z4;
+    const bool dtv = A.xi != nullptr;
+    const float4 fx = (dtv && hx) ? ld4(A.xi + j) : z4;
+    const float4 fy = (dtv && hy) ? ld4(A.xi + (int64_t)cy * V + j) : z4;
+    const float4 fz = (dtv && hz) ? ld4(A.xi + (int64_t)cz * V + j) : z4;
     float ox[4], oy[4], oz[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float x0 = f4(xc, k);
         const float xn = k < 3 ? f4(xc, k + 1) : xr;
-        const float vx = hx ? fmaf(A.s_prior, ix + k < nx - 1 ? xn - x0 : 0.0f, f4(wx, k)) : 0.0f;
-        const float vy = hy ? fmaf(A.s_prior, iny ? f4(xy, k) - x0 : 0.0f, f4(wy, k)) : 0.0f;
-        const float vz = hz ? fmaf(A.s_prior, inz ? f4(xz, k) - x0 : 0.0f, f4(wz, k)) : 0.0f;
+        float gx = hx ? (ix + k < nx - 1 ? xn - x0 : 0.0f) : 0.0f;
+        float gy = hy ? (iny ? f4(xy, k) - x0 : 0.0f) : 0.0f;
+        float gz = hz ? (inz ? f4(xz, k) - x0 : 0.0f) : 0.0f;
+        if (dtv) dtv_perp(f4(fx, k), f4(fy, k), f4(fz, k), gx, gy, gz);
+        const float vx = hx ? fmaf(A.s_prior, gx, f4(wx, k)) : 0.0f;
+        const float vy = hy ? fmaf(A.s_prior, gy, f4(wy, k)) : 0.0f;
+        const float vz = hz ? fmaf(A.s_prior, gz, f4(wz, k)) : 0.0f;
         const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), A.beta);
         ox[k] = __fmul_rn(vx, sc);
         oy[k] = __fmul_rn(vy, sc);

@@ -54,6 +54,8 @@ struct lm_state_s {
     TmaMaps* tmaps;   // device copy of the tensor maps (TMA-staged image passes)
     unsigned* err;    // set by a bounded device wait that gave up
     bool tma;         // image passes staged by TMA (grid permitting, unless disabled)
+    bool has_res;     // resolution model P = A G: the event kernels read G x from xyf[0]
+    ResPlan res;
     int zlen;         // z slices per TMA work item
     bool tiled;       // data updates by the tile-binned projector
     TileArgs ta;      // its per-frame tables (pointers into the caller's tile buffer)
@@ -167,7 +169,8 @@ EvArgs base_ev_args(const lm_state* st)
     a.tof_tab = st->tof.n_bins > 0 ? st->tof_tab : nullptr;
     a.group = st->group;
     a.prior_fused = st->tma ? 1 : 0;
-    a.acc_pairs = st->det ? 0 : 1;
+    a.acc_pairs = (st->det || st->has_res) ? 0 : 1;
+    a.xi = st->P.xi;
     return a;
 }
 
@@ -202,10 +205,12 @@ ImgArgs base_img_args(const lm_state* st)
     a.inv_p_prior = 2.0f;
     a.s_prior = (float)(st->gamma * (double)st->P.rho / st->knorm);
     a.beta = st->P.beta;
-    a.acc_pairs = st->det ? 0 : 1;
+    a.acc_pairs = (st->det || st->has_res) ? 0 : 1;
+    if (st->has_res) a.acc_yf = nullptr;  // scratch of the resolution model; the events use one layout
     a.tm = st->tma ? st->tmaps : nullptr;
     a.err = st->err;
     a.zlen = st->zlen;
+    a.xi = st->P.xi;
     return a;
 }
 
@@ -223,8 +228,8 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         EvArgs a = base_ev_args(st);
         a.seq = st->seq;
         a.u = u;
-        a.x_std = st->x[cur];
-        a.x_yf = st->xyf[cur];
+        a.x_std = st->has_res ? st->xyf[0] : st->x[cur];  // G x with the resolution model
+        a.x_yf = st->has_res ? nullptr : st->xyf[cur];
         a.px = st->x[cur];
         a.maxbits = st->maxbits + slot;
         if (st->tiled) {
@@ -245,9 +250,15 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
             }
         } else if (!st->det) {
             a.acc_std = st->acc_std;
-            a.acc_yf = st->acc_yf;
+            a.acc_yf = st->has_res ? nullptr : st->acc_yf;
             int rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
             LM_CHECK(rc == LM_OK, rc, "data update launch failed");
+            if (st->has_res) {
+                // dz = G (A^T v): blur the back-projection in place (nothing for a prior selection)
+                rc = launch_res(&st->g, st->res, st->acc_std, st->acc_std, st->xyf[1], st->acc_yf, st->seq, u, st->n,
+                                s);
+                if (rc) return rc;
+            }
         } else {
             a.out = st->scr;
             int rc = launch_events(EV_DATA_FX1, st->two_d, a, st->grid_ev, s);
@@ -269,12 +280,17 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         im.u = u;
         im.x_cur = st->x[cur];
         im.x_nxt_std = st->x[nxt];
-        im.x_nxt_yf = st->xyf[nxt];
+        im.x_nxt_yf = st->has_res ? nullptr : st->xyf[nxt];
         // scale slots: update u reads slot (slot0 + u) & 1, its pass clears the other one
         im.slot0 = slot0;
         im.xcur = cur;
         if (st->tma) launch_image_tma(im, s);
         else launch_image_pass(im, s);
+        if (st->has_res) {
+            // the next update's projections read G x
+            int rc = launch_res(&st->g, st->res, st->x[nxt], st->xyf[0], st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
+            if (rc) return rc;
+        }
         if (ev) LM_CUDA(cudaEventRecord(ev[3 * u + 2], s));
     }
     LM_CUDA(cudaGetLastError());
@@ -314,7 +330,11 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     launch_step_T(&st->g, st->sens, st->T, st->P.rho, (float)st->gamma, st->knorm, st->n, s);
     EvArgs a = base_ev_args(st);
     a.x_std = x0;
-    if (yf) {
+    if (st->has_res) {
+        rc = launch_res(&st->g, st->res, x0, st->xyf[0], st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
+        if (rc) return rc;
+        a.x_std = st->xyf[0];
+    } else if (yf) {
         launch_transpose_to_yf(&st->g, x0, st->xyf[1], s);
         a.x_yf = st->xyf[1];
     }
@@ -324,8 +344,10 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     if (st->N > 0) {
         if (!st->det) {
             a.acc_std = st->acc_std;
-            a.acc_yf = st->acc_yf;
+            a.acc_yf = st->has_res ? nullptr : st->acc_yf;
             rc = launch_events(EV_YINIT, st->two_d, a, st->grid_ev, s);
+            if (!rc && st->has_res)
+                rc = launch_res(&st->g, st->res, st->acc_std, st->acc_std, st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
         } else {
             a.out = st->scr;
             a.maxbits = st->maxbits + 1;
@@ -349,8 +371,12 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     im.x_cur = x0;
     im.x_keep = st->x[1];
     im.x_nxt_std = st->x[0];
-    im.x_nxt_yf = st->xyf[0];
+    im.x_nxt_yf = st->has_res ? nullptr : st->xyf[0];
     launch_image_pass(im, s);
+    if (st->has_res) {
+        rc = launch_res(&st->g, st->res, st->x[0], st->xyf[0], st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
+        if (rc) return rc;
+    }
     LM_CUDA(cudaGetLastError());
     st->xpar = 0;
     st->n_updates = 0;
@@ -524,7 +550,20 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         set_error("the TMA-staged image pass needs nx, ny multiples of 4 with nx >= 40, ny >= 36");
         return fail(LM_ERR_INVALID_ARG);
     }
-    if (P.image_kernel != 1 && tma_capable(grid)) {
+    if (P.image_kernel == 2 && P.xi != nullptr) {
+        set_error("the TMA-staged image pass implements the TV prior only (xi must be NULL)");
+        return fail(LM_ERR_INVALID_ARG);
+    }
+    st->has_res = P.res_fwhm > 0.0f;
+    if (st->has_res) {
+        if (st->det || P.image_kernel == 2) {
+            set_error("the resolution model runs in float-atomic mode with the plain image passes");
+            return fail(LM_ERR_INVALID_ARG);
+        }
+        rc = res_plan(grid, P.res_fwhm, st->res);
+        if (rc) return fail(rc);
+    }
+    if (P.image_kernel != 1 && P.xi == nullptr && !st->has_res && tma_capable(grid)) {
         TmaMaps h;
         rc = encode_tma_maps(grid, st->x, st->w, std::max(1, st->ndim), st->T, st->z, st->zc,
                              st->det ? (void*)st->acci_std : (void*)st->acc_std,
@@ -544,7 +583,7 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->tiled = false;
     st->n_segments = 0;
     st->tile_base = nullptr;
-    if (P.tile_buf != nullptr && tof->n_bins > 0 && !st->det && grid->n[0] < 16384 && grid->n[1] < 16384 &&
+    if (P.tile_buf != nullptr && tof->n_bins > 0 && !st->det && !st->has_res && grid->n[0] < 16384 && grid->n[1] < 16384 &&
         grid->n[2] < 16384) {
         st->tl = tile_layout(grid, ev->n, st->n);
         if (P.tile_bytes < st->tl.total) {
@@ -794,6 +833,14 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
         EvArgs a = base_ev_args(st);
         a.x_std = st->x[xb];
         a.x_yf = st->xyf[xb];
+        if (st->has_res) {
+            // G x into scratch that the next update does not read
+            int rc = launch_res(&st->g, st->res, st->x[xb], st->xyf[1], st->acc_yf, st->acc_yf + st->V, nullptr, 0,
+                                0, s);
+            if (rc) return rc;
+            a.x_std = st->xyf[1];
+            a.x_yf = nullptr;
+        }
         a.out = p;
         a.e_begin = 0;
         a.e_end = st->N;
@@ -804,7 +851,7 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
         LM_CHECK(rc == LM_OK, rc, "objective projection failed");
     }
     double parts[3];
-    int rc = objective_parts(&st->g, st->sens, st->x[xb], p, st->contam, st->N, st->P.beta, st->redd, parts, s);
+    int rc = objective_parts(&st->g, st->sens, st->x[xb], st->P.xi, p, st->contam, st->N, st->P.beta, st->redd, parts, s);
     if (rc) return rc;
     unsigned err = 0;
     LM_CUDA(cudaMemcpyAsync(&err, st->err, sizeof(err), cudaMemcpyDeviceToHost, s));
@@ -1081,6 +1128,7 @@ int lmspdhg_batch_set(lm_batch* b, int32_t slot, lm_state* st, void* stream)
     cudaStream_t s = S(stream);
     if (st != nullptr) {
         LM_CHECK(st->n == b->n, LM_ERR_INVALID_ARG, "state has %d subsets, batch %d", st->n, b->n);
+        LM_CHECK(!st->has_res, LM_ERR_INVALID_ARG, "states with the resolution model do not run in batches");
         LM_CHECK(!b->have_cfg || same_config(b->cfg, st), LM_ERR_INVALID_ARG,
                  "state differs from the batch's grid, TOF kernel or mode");
         LM_CHECK(st->xpar == 0 && (st->n_updates & 1) == 0, LM_ERR_INVALID_ARG,

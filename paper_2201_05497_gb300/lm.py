@@ -51,7 +51,8 @@ class lm_params(C.Structure):
     _fields_ = [("beta", C.c_float), ("gamma", C.c_float), ("rho", C.c_float), ("knorm", C.c_double),
                 ("knorm_iters", C.c_int32), ("n_subsets", C.c_int32), ("deterministic", C.c_int32),
                 ("kahan", C.c_int32), ("group", C.c_int32), ("image_kernel", C.c_int32),
-                ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t)]
+                ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t), ("xi", C.c_void_p),
+                ("res_fwhm", C.c_float)]
 
 
 _lib = None
@@ -86,6 +87,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lm_tv_grad": ([P(lm_grid), V, V, V], C.c_int),
         "lm_tv_div": ([P(lm_grid), V, V, V], C.c_int),
         "lm_tv_prox": ([P(lm_grid), V, F, V], C.c_int),
+        "lm_dtv_field": ([P(lm_grid), V, F, V, V], C.c_int),
+        "lm_res_workspace_bytes": ([P(lm_grid)], SZ),
+        "lm_res_apply": ([P(lm_grid), F, V, V, V, SZ, V], C.c_int),
+        "lm_dtv_grad": ([P(lm_grid), V, V, V, V], C.c_int),
+        "lm_dtv_div": ([P(lm_grid), V, V, V, V], C.c_int),
         "lm_knorm_workspace_bytes": ([P(lm_grid)], SZ),
         "lm_knorm_fp64": ([P(lm_grid), I32, V, SZ, P(D), V], C.c_int),
         "lm_setup_workspace_bytes": ([I64], SZ),
@@ -295,6 +301,42 @@ def tv_prox(geo: Geometry, w: torch.Tensor, beta: float, stream=None) -> torch.T
     return w
 
 
+def res_apply(geo: Geometry, fwhm: float, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """G x: the image-space resolution model (separable Gaussian, mirrored faces)."""
+    L = load_library()
+    if out is None:
+        out = torch.empty(geo.V, dtype=torch.float32, device=x.device)
+    ws = _ws(L.lm_res_workspace_bytes(C.byref(geo.g)), x.device)
+    _check(L.lm_res_apply(C.byref(geo.g), float(fwhm), _ptr(x), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def dtv_field(geo: Geometry, v: torch.Tensor, eta: float, out=None, stream=None) -> torch.Tensor:
+    """Directional-TV field of the structural image v: [ndim * V]."""
+    L = load_library()
+    if out is None:
+        out = torch.empty(geo.ndim * geo.V, dtype=torch.float32, device=v.device)
+    _check(L.lm_dtv_field(C.byref(geo.g), _ptr(v), float(eta), _ptr(out), _stream(stream)))
+    return out
+
+
+def dtv_grad(geo: Geometry, xi: torch.Tensor, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    L = load_library()
+    if out is None:
+        out = torch.empty(geo.ndim * geo.V, dtype=torch.float32, device=x.device)
+    _check(L.lm_dtv_grad(C.byref(geo.g), _ptr(xi), _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def dtv_div(geo: Geometry, xi: torch.Tensor, g: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """-K^T g for the directional TV."""
+    L = load_library()
+    if out is None:
+        out = torch.empty(geo.V, dtype=torch.float32, device=g.device)
+    _check(L.lm_dtv_div(C.byref(geo.g), _ptr(xi), _ptr(g), _ptr(out), _stream(stream)))
+    return out
+
+
 def knorm_fp64(geo: Geometry, iters: int, stream=None) -> float:
     L = load_library()
     ws = _ws(L.lm_knorm_workspace_bytes(C.byref(geo.g)), geo.xtal.device)
@@ -417,9 +459,11 @@ class LMSPDHG:
     def __init__(self, geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x0: torch.Tensor, *,
                  beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
-                 image_kernel: int = 0, projector: str = "direct", stream=None):
+                 image_kernel: int = 0, projector: str = "direct", xi: Optional[torch.Tensor] = None,
+                 res_fwhm: float = 0.0, stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
+        self.xi = xi  # directional TV field (referenced by the state), None = TV
         self.n_subsets = n_subsets
         nbytes = L.lmspdhg_state_bytes(C.byref(geo.g), pe.events.n, int(n_subsets), int(deterministic))
         if nbytes == 0:
@@ -437,7 +481,7 @@ class LMSPDHG:
                 self.tile = torch.empty(tb, dtype=torch.uint8, device=x0.device)
         self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan),
                                 int(group), int(image_kernel), None if self.tile is None else self.tile.data_ptr(),
-                                0 if self.tile is None else self.tile.numel())
+                                0 if self.tile is None else self.tile.numel(), _ptr(xi), float(res_fwhm))
         self._ev = pe.events.desc()
         self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
         h = C.c_void_p()
