@@ -61,6 +61,10 @@ def parse_args():
                     help="tv: the TV prior; dtv: the directional TV prior with the flipped-contrast phantom "
                          "as structural image")
     ap.add_argument("--beta", type=float, default=-1.0, help="override the workload's prior weight")
+    ap.add_argument("--res-fwhm", type=float, default=0.0,
+                    help="image-space resolution model P = A G with a Gaussian of this FWHM (mm); 0 = none")
+    ap.add_argument("--sino-compare", action="store_true",
+                    help="also time sinogram SPDHG (Alg. 1) epochs on the frame's sinogram (outside the timed region)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the (untimed-region) measurement of the listmode EM-TV warm start")
     ap.add_argument("--pdhg-iters", type=int, default=20, help="inner iterations of the EM-TV denoising")
@@ -285,7 +289,6 @@ def run_gpu(args):
         return r, a.elapsed_time(b)
 
     sens, sens_ms = timed(lambda: L.sens(geo, lor_att))
-    del lor_att
     kn, knorm_ms = timed(lambda: L.knorm_fp64(geo, args.knorm_iters))
     kappa = 0.8 * N / float(sens.double().sum().item())
     x0 = torch.full((geo.V,), kappa, dtype=torch.float32, device=dev)
@@ -295,8 +298,11 @@ def run_gpu(args):
     xi = None
     if args.prior == "dtv":
         xi = dtv_structure(L, wl, geo, dev)
+    if args.res_fwhm > 0:
+        sens = L.res_apply(geo, args.res_fwhm, sens)  # P^T 1 = G A^T 1
     st = L.LMSPDHG(geo, pe, sens, x0, beta=beta, n_subsets=n_sub, rho=0.999, knorm=kn,
-                   deterministic=args.deterministic, kahan=True, projector=args.projector, xi=xi)
+                   deterministic=args.deterministic, kahan=True, projector=args.projector, xi=xi,
+                   res_fwhm=args.res_fwhm)
     E = args.epochs
     seq = S.selection_sequence(n_sub, 2 * n_sub * E, seed=3)
     seqs = [seq[2 * n_sub * e:2 * n_sub * (e + 1)] for e in range(E)]
@@ -464,6 +470,13 @@ def run_gpu(args):
                     "frac": d["frac"], "traffic": None, "kernel": dom, "peak_source": peak_src}
     roofline["kernel_time_shares"] = {k: v / sum(shares.values()) for k, v in shares.items()}
 
+    # ---- sinogram SPDHG (Alg. 1) on the same frame, outside the timed region ----
+    sino = None
+    if args.sino_compare:
+        sino = sino_compare(L, S, wl, geo, raw, lor_att, sens, x0, beta, kn, seqs, n_sub, stream, dev,
+                            statistics.median(epoch_ms) if epoch_ms else None)
+    del lor_att
+
     # ---- the listmode EM-TV warm start (Alg. 3), measured outside the timed region ----
     warm = None
     if not args.no_warm_start:
@@ -488,7 +501,8 @@ def run_gpu(args):
             "config": {"workload": f"{args.workload}: {wl.scanner.n_rings} rings x {wl.scanner.n_xtal} crystals, "
                                    f"{wl.grid.n[0]}x{wl.grid.n[1]}x{wl.grid.n[2]} image @{wl.grid.h[0]} mm, "
                                    f"{N} events, {n_sub} subsets, {args.prior.upper()} beta={beta}, {E} epochs per frame, "
-                                   f"{'deterministic' if args.deterministic else 'atomic'} back-projection",
+                                   + (f"resolution model FWHM {args.res_fwhm} mm, " if args.res_fwhm > 0 else "")
+                                   + f"{'deterministic' if args.deterministic else 'atomic'} back-projection",
                        "n_events": N, "n_subsets": n_sub, "epochs_per_step": E,
                        "events_per_step": events_per_step, "parallelism": f"replicas x{world}",
                        "l2": "256 MiB write between steps; per-step inputs (0.42 GB of events, 0.2 GB of images) "
@@ -498,6 +512,7 @@ def run_gpu(args):
             "sens_ms": sens_ms, "knorm_ms": knorm_ms, "generate_s": gen_s, "wall_s": wall,
             "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks, "tuning": st.tuning(), "warm_start": warm,
+            "sinogram_spdhg": sino,
             "objective_last": f_last,
         }
         print(json.dumps(out))
@@ -505,6 +520,45 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def sino_compare(L, S, wl, geo, raw, lor_att, sens, x0, beta, kn, seqs, n_sub, stream, dev, lm_epoch_ms):
+    """Sinogram SPDHG (Alg. 1) on the histogram of the frame's events: every
+    (LOR, TOF bin) of the scanner, empty bins included, view-based subsets,
+    the same selection sequences; epoch times by CUDA events."""
+    import torch
+    nb_tot = int(L.load_library().lm_sino_n_bins(L.C.byref(geo.sc), L.C.byref(geo.tof)))
+    need = nb_tot * 26 + (64 << 20)  # bin list (det1, det2, tof, corr, contam, counts, y) and scratch
+    free = torch.cuda.mem_get_info(dev)[0]
+    if need > 0.6 * free:
+        return {"skipped": f"the sinogram has {nb_tot} bins ({need / 1e9:.1f} GB); {free / 1e9:.1f} GB free"}
+    b = S.sinogram_bins_torch(wl.scanner, wl.tof, raw.det1, raw.det2, raw.tof)
+    d = torch.bincount(b, minlength=nb_tot)
+    if int(d.max().item()) > 65535:
+        return {"skipped": "a bin holds more than 65535 counts"}
+    d16 = d.to(torch.int32).to(torch.int16).view(torch.uint16)  # counts < 2^16: the bit pattern is kept
+    s = torch.full((nb_tot,), float(raw.contam[0].item()), dtype=torch.float32, device=dev)
+    pe = L.sino_setup(geo, d16, s, n_sub, lor_att)
+    st = L.LMSPDHG(geo, pe, sens, x0, beta=beta, n_subsets=n_sub, rho=0.999, knorm=kn, kahan=True,
+                   projector="direct", sinogram=True)
+    for sq in seqs[:2]:
+        st.epoch(sq)  # warm-up (graph capture)
+    st.reinit(x0)
+    ms = []
+    for sq in seqs:
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.epoch(sq)
+        e.record(stream)
+        e.synchronize()
+        ms.append(a.elapsed_time(e))
+    obj = st.objective()
+    st.close()
+    med = statistics.median(ms)
+    return {"bins": nb_tot, "nonempty_bins": int((d > 0).sum().item()), "events": int(raw.det1.numel()),
+            "epoch_ms": med, "lm_epoch_ms": lm_epoch_ms,
+            "lm_speedup": (med / lm_epoch_ms) if lm_epoch_ms else None, "objective": obj,
+            "subsets": "views (c1 + c2) mod n_xtal, view v in subset v mod n"}
 
 
 def dtv_structure(L, wl, geo, dev):

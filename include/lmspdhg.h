@@ -222,6 +222,28 @@ int lm_event_setup(const lm_scanner* sc, const lm_tof* tof, const lm_events* ev,
                    float* contam_out, uint16_t* mu_out, int64_t* sub_off_host, void* ws,
                    size_t ws_bytes, void* stream);
 
+/* ---- sinogram SPDHG (Alg. 1) ---------------------------------------------- */
+/* The comparison method of the paper: SPDHG over every bin of the TOF
+ * sinogram, empty bins included (Sec. "Memory-efficient SPDHG": y = 1 on
+ * empty bins, Eq. (yinit) elsewhere).  lm_sino_setup lays the sinogram out as
+ * an event list for lmspdhg_create with lm_params.sinogram = 1: bin b =
+ * l * nb + (m + (nb-1)/2) of canonical LOR l (lm_sens's order) and signed TOF
+ * bin m (nb = max(n_bins, 1)) becomes an event with det1/det2 of l's
+ * canonical orientation, tof m, corr = lor_factor[l] (NULL = 1), contam =
+ * s[b] (> 0, else LM_ERR_DOMAIN), and d_out = d[b] (the bin's count).  Bins
+ * are grouped by view-based subsets: transaxial pair (c1, c2) has view
+ * (c1 + c2) mod n_xtal (parallel LORs share it) and view v goes to subset
+ * v mod n_subsets; inside a subset bins keep canonical order.
+ * sub_off_host (host int64[n_subsets+1]) receives the offsets.  d, s:
+ * device arrays of lm_sino_n_bins entries; outputs: device arrays of the
+ * same length.  ws: device workspace of lm_sino_workspace_bytes bytes.
+ * Synchronous. */
+int64_t lm_sino_n_bins(const lm_scanner* sc, const lm_tof* tof);
+size_t lm_sino_workspace_bytes(const lm_scanner* sc, int32_t n_subsets);
+int lm_sino_setup(const lm_scanner* sc, const lm_tof* tof, int32_t n_subsets, const uint16_t* d, const float* s,
+                  const float* lor_factor, int32_t* det1_out, int32_t* det2_out, int16_t* tof_out, float* corr_out,
+                  float* contam_out, uint16_t* d_out, int64_t* sub_off_host, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- LM-SPDHG state (Alg. 2) --------------------------------------------- */
 typedef struct lm_state_s lm_state;
 
@@ -262,6 +284,11 @@ typedef struct {
                           /* Float-atomic mode only (deterministic is rejected);  */
                           /* plain image passes, direct projector, no y-fastest   */
                           /* image copies; not for batches.                      */
+    int32_t sinogram;     /* 1: Alg. 1 (sinogram SPDHG): the events are the bins */
+                          /* of lm_sino_setup and mu their counts d_b (0 allowed);*/
+                          /* the dual step uses prox with S_b d_b and back-       */
+                          /* projects y+ - y; the objective is Eq. (1) with the   */
+                          /* sum of s.  0: Alg. 2 (listmode).                     */
 } lm_params;
 
 /* Bytes of the optional tile-binned projector buffer (lm_params.tile_buf):

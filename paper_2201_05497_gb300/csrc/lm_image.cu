@@ -1109,26 +1109,36 @@ __global__ void __launch_bounds__(256) obj_img_partial(const float* __restrict__
     }
 }
 
-// sum_e log(p_e + s_e) (FP64)
+// sum_e w_e log(p_e + s_e) and, with weights (sinogram bins: w = d_b), sum_e s_e (FP64)
 __global__ void __launch_bounds__(256) obj_ev_partial(const float* __restrict__ p, const float* __restrict__ s,
-                                                      int64_t n, double* part)
+                                                      const uint16_t* __restrict__ w, int64_t n, double* part)
 {
     __shared__ double sm[256];
-    double acc = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)RB * 256)
-        acc += log((double)p[e] + (double)s[e]);
+    double acc = 0.0, acs = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)RB * 256) {
+        if (w) {
+            if (w[e]) acc += (double)w[e] * log((double)p[e] + (double)s[e]);
+            acs += (double)s[e];
+        } else {
+            acc += log((double)p[e] + (double)s[e]);
+        }
+    }
     acc = block_sum_d(acc, sm);
-    if (threadIdx.x == 0) part[2 * RB + blockIdx.x] = acc;
+    acs = block_sum_d(acs, sm);
+    if (threadIdx.x == 0) {
+        part[2 * RB + blockIdx.x] = acc;
+        part[3 * RB + blockIdx.x] = acs;
+    }
 }
 
 __global__ void __launch_bounds__(256) obj_final(double* part)
 {
     __shared__ double sm[256];
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 4; ++q) {
         double acc = 0.0;
         for (int i = threadIdx.x; i < RB; i += 256) acc += part[q * RB + i];
         acc = block_sum_d(acc, sm);
-        if (threadIdx.x == 0) part[3 * RB + q] = acc;
+        if (threadIdx.x == 0) part[4 * RB + q] = acc;
     }
 }
 
@@ -1651,23 +1661,19 @@ int reduce_minmax(const float* x, int64_t n, float* dev_scratch, float* mn, floa
     return LM_OK;
 }
 
-size_t objective_scratch_bytes() { return align_up((3 * RB + 4) * sizeof(double)); }
+size_t objective_scratch_bytes() { return align_up((4 * RB + 4) * sizeof(double)); }
 
 int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* xi, const float* p,
-                    const float* contam, int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st)
+                    const float* contam, const uint16_t* w, int64_t n_ev, double* scratch, double* out4,
+                    cudaStream_t st)
 {
     obj_img_partial<<<RB, 256, 0, st>>>(sens, x, xi, g->n[0], g->n[1], g->n[2], scratch);
-    obj_ev_partial<<<RB, 256, 0, st>>>(p, contam, n_ev, scratch);
+    obj_ev_partial<<<RB, 256, 0, st>>>(p, contam, w, n_ev, scratch);
     obj_final<<<1, 256, 0, st>>>(scratch);
     count_launch(3);
     LM_CUDA(cudaGetLastError());
-    double h[3];
-    LM_CUDA(cudaMemcpyAsync(h, scratch + 3 * RB, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaMemcpyAsync(out4, scratch + 4 * RB, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     LM_CUDA(cudaStreamSynchronize(st));
-    out3[0] = h[0];
-    out3[1] = h[1];
-    out3[2] = h[2];
-    (void)beta;
     return LM_OK;
 }
 

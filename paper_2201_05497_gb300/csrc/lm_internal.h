@@ -131,6 +131,7 @@ struct EvArgs {
     int prior_only;             // 1: data selections are left to the tile-binned projector
     int acc_pairs;              // 1: acc_std / acc_yf hold (voxel j, voxel j + nx*ny) float pairs
     const float* xi;            // directional TV field [ndim][V], or nullptr (TV)
+    int sino;                   // 1: the events are sinogram bins, mu their counts d_b (Alg. 1)
 };
 
 // Batched multi-frame epochs: per-frame argument tables in device memory.
@@ -329,8 +330,10 @@ int res_plan(const lm_grid* g, float fwhm, ResPlan& p);
 int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* t1, float* t2,
                const uint16_t* seq, int u, int n_subsets, cudaStream_t st);
 
+// out4: <sens, x>, ||Kx||_{2,1}, sum_e w_e log(p_e + s_e) (w = 1 if NULL), sum_e s_e if w is set (else 0)
 int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* xi, const float* p,
-                    const float* contam, int64_t n_ev, float beta, double* scratch, double* out3, cudaStream_t st);
+                    const float* contam, const uint16_t* w, int64_t n_ev, double* scratch, double* out4,
+                    cudaStream_t st);
 size_t objective_scratch_bytes();
 
 }  // namespace lmh

@@ -428,7 +428,8 @@ __device__ __forceinline__ void event_chunk(const EvArgs& A, const float* __rest
             const float Se = p1 > 0.0f ? A.gamma_rho / p1 : 0.0f;  // S_k = gamma rho / P^LM_{N_k} 1
             const float a = fmaf(Se, fmaf(cj, acc, sj), yj);       // y + S (P^LM x + s)
             const float yp = prox_dstar(a, muj * Se);
-            const float v = (yp - yj) / muj;
+            // Alg. 2 back-projects (y+ - y)/mu; Alg. 1 on sinogram bins (mu = d_b) y+ - y
+            const float v = A.sino ? yp - yj : (yp - yj) / muj;
             if (lane == src) {
                 r_y = yp;
                 r_out = v;
@@ -439,8 +440,8 @@ __device__ __forceinline__ void event_chunk(const EvArgs& A, const float* __rest
             const float sj = __shfl_sync(FULL, ms, src);
             const float muj = __shfl_sync(FULL, mmu, src);
             const float u = fmaf(cj, acc, sj);
-            const float yv = 1.0f - muj / u;    // Eq. (yinit) with d -> mu
-            const float v = (yv - 1.0f) / muj;  // = -1/u
+            const float yv = 1.0f - muj / u;                       // Eq. (yinit) with d -> mu
+            const float v = A.sino ? yv - 1.0f : (yv - 1.0f) / muj;  // listmode: -1/u
             if (lane == src) {
                 r_y = yv;
                 r_out = v;

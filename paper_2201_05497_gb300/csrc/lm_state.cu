@@ -171,6 +171,7 @@ EvArgs base_ev_args(const lm_state* st)
     a.prior_fused = st->tma ? 1 : 0;
     a.acc_pairs = (st->det || st->has_res) ? 0 : 1;
     a.xi = st->P.xi;
+    a.sino = st->P.sinogram ? 1 : 0;
     return a;
 }
 
@@ -583,7 +584,7 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->tiled = false;
     st->n_segments = 0;
     st->tile_base = nullptr;
-    if (P.tile_buf != nullptr && tof->n_bins > 0 && !st->det && !st->has_res && grid->n[0] < 16384 && grid->n[1] < 16384 &&
+    if (P.tile_buf != nullptr && tof->n_bins > 0 && !st->det && !st->has_res && !P.sinogram && grid->n[0] < 16384 && grid->n[1] < 16384 &&
         grid->n[2] < 16384) {
         st->tl = tile_layout(grid, ev->n, st->n);
         if (P.tile_bytes < st->tl.total) {
@@ -850,14 +851,17 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
         int rc = launch_events(EV_FWD, st->two_d, a, ev_grid_g(EV_FWD, st->two_d, st->group), s);
         LM_CHECK(rc == LM_OK, rc, "objective projection failed");
     }
-    double parts[3];
-    int rc = objective_parts(&st->g, st->sens, st->x[xb], st->P.xi, p, st->contam, st->N, st->P.beta, st->redd, parts, s);
+    double parts[4];
+    int rc = objective_parts(&st->g, st->sens, st->x[xb], st->P.xi, p, st->contam, st->P.sinogram ? st->mu : nullptr,
+                             st->N, st->redd, parts, s);
     if (rc) return rc;
     unsigned err = 0;
     LM_CUDA(cudaMemcpyAsync(&err, st->err, sizeof(err), cudaMemcpyDeviceToHost, s));
     LM_CUDA(cudaStreamSynchronize(s));
     LM_CHECK(err == 0, LM_ERR_TIMEOUT, "a bounded wait of the image pass gave up; the iterate is not valid");
-    *out_host = parts[0] - parts[2] + (double)st->P.beta * parts[1];
+    // listmode: <P^T 1, x> - sum_e log(...) + beta R (Eq. (1) without the constant sum of s);
+    // sinogram bins: Eq. (1) itself, sum_b (Px + s)_b - d_b log(Px + s)_b + beta R
+    *out_host = parts[0] - parts[2] + (double)st->P.beta * parts[1] + parts[3];
     return LM_OK;
 }
 

@@ -52,7 +52,7 @@ class lm_params(C.Structure):
                 ("knorm_iters", C.c_int32), ("n_subsets", C.c_int32), ("deterministic", C.c_int32),
                 ("kahan", C.c_int32), ("group", C.c_int32), ("image_kernel", C.c_int32),
                 ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t), ("xi", C.c_void_p),
-                ("res_fwhm", C.c_float)]
+                ("res_fwhm", C.c_float), ("sinogram", C.c_int32)]
 
 
 _lib = None
@@ -89,6 +89,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lm_tv_prox": ([P(lm_grid), V, F, V], C.c_int),
         "lm_dtv_field": ([P(lm_grid), V, F, V, V], C.c_int),
         "lm_res_workspace_bytes": ([P(lm_grid)], SZ),
+        "lm_sino_n_bins": ([P(lm_scanner), P(lm_tof)], I64),
+        "lm_sino_workspace_bytes": ([P(lm_scanner), I32], SZ),
+        "lm_sino_setup": ([P(lm_scanner), P(lm_tof), I32, V, V, V, V, V, V, V, V, V, P(I64), V, SZ, V], C.c_int),
         "lm_res_apply": ([P(lm_grid), F, V, V, V, SZ, V], C.c_int),
         "lm_dtv_grad": ([P(lm_grid), V, V, V, V], C.c_int),
         "lm_dtv_div": ([P(lm_grid), V, V, V, V], C.c_int),
@@ -453,6 +456,28 @@ def emtv_denoise(geo: Geometry, z: torch.Tensor, w: torch.Tensor, iters: int, kn
     return out
 
 
+def sino_setup(geo: Geometry, d: torch.Tensor, s: torch.Tensor, n_subsets: int,
+               lor_factor: Optional[torch.Tensor] = None, stream=None) -> PermutedEvents:
+    """The bins of a TOF sinogram (counts d uint16, contamination s float32, both
+    in canonical bin order) as an event list for sinogram SPDHG (Alg. 1):
+    view-based subsets; ``mu`` holds the counts."""
+    L = load_library()
+    dev = d.device
+    nb = int(L.lm_sino_n_bins(C.byref(geo.sc), C.byref(geo.tof)))
+    if d.numel() != nb or s.numel() != nb:
+        raise ValueError(f"the sinogram has {nb} bins")
+    ev = DeviceEvents(torch.empty(nb, dtype=torch.int32, device=dev), torch.empty(nb, dtype=torch.int32, device=dev),
+                      torch.empty(nb, dtype=torch.int16, device=dev), torch.empty(nb, dtype=torch.float32, device=dev),
+                      torch.empty(nb, dtype=torch.float32, device=dev))
+    mu = torch.empty(nb, dtype=torch.uint16, device=dev)
+    off = np.zeros(n_subsets + 1, dtype=np.int64)
+    ws = _ws(L.lm_sino_workspace_bytes(C.byref(geo.sc), int(n_subsets)), dev)
+    _check(L.lm_sino_setup(C.byref(geo.sc), C.byref(geo.tof), int(n_subsets), _ptr(d), _ptr(s), _ptr(lor_factor),
+                           _ptr(ev.det1), _ptr(ev.det2), _ptr(ev.tof), _ptr(ev.corr), _ptr(ev.contam), _ptr(mu),
+                           off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(ws), ws.numel(), _stream(stream)))
+    return PermutedEvents(ev, mu, off)
+
+
 class LMSPDHG:
     """Alg. 2 on the device.  Holds the state buffer and the library handle."""
 
@@ -460,7 +485,7 @@ class LMSPDHG:
                  beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
                  image_kernel: int = 0, projector: str = "direct", xi: Optional[torch.Tensor] = None,
-                 res_fwhm: float = 0.0, stream=None):
+                 res_fwhm: float = 0.0, sinogram: bool = False, stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.xi = xi  # directional TV field (referenced by the state), None = TV
@@ -481,7 +506,8 @@ class LMSPDHG:
                 self.tile = torch.empty(tb, dtype=torch.uint8, device=x0.device)
         self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan),
                                 int(group), int(image_kernel), None if self.tile is None else self.tile.data_ptr(),
-                                0 if self.tile is None else self.tile.numel(), _ptr(xi), float(res_fwhm))
+                                0 if self.tile is None else self.tile.numel(), _ptr(xi), float(res_fwhm),
+                                int(sinogram))
         self._ev = pe.events.desc()
         self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
         h = C.c_void_p()

@@ -596,6 +596,27 @@ def monte_carlo_events_torch(sc: Scanner, ph: Phantom, tof: Tof, n_events: int, 
                   torch.full((n_events,), s_flat, dtype=torch.float32, device=device))
 
 
+def sinogram_bins(sc: Scanner, tof: Tof, det1: np.ndarray, det2: np.ndarray, tb: np.ndarray) -> np.ndarray:
+    """Canonical sinogram bin of each event: b = l * nb + (m + M) with l the
+    canonical LOR and m the TOF bin signed toward the canonical det2
+    (nb = max(n_bins, 1), M = (nb - 1) / 2)."""
+    r1, c1 = np.divmod(det1.astype(np.int64), sc.n_xtal)
+    r2, c2 = np.divmod(det2.astype(np.int64), sc.n_xtal)
+    _, sw = q_of_pair(c1, c2, sc.n_xtal)
+    nb = max(tof.n_bins, 1)
+    m = np.where(sw, -tb.astype(np.int64), tb.astype(np.int64)) if tof.n_bins > 0 else np.zeros(det1.shape, np.int64)
+    return lor_of_events(sc, det1, det2) * nb + m + (nb - 1) // 2
+
+
+def sinogram_counts(sc: Scanner, tof: Tof, ev: "Events") -> np.ndarray:
+    """Counts d_b of the events in every canonical sinogram bin (uint16)."""
+    nb = max(tof.n_bins, 1)
+    d = np.bincount(sinogram_bins(sc, tof, ev.det1, ev.det2, ev.tof), minlength=sc.n_lor * nb)
+    if d.max(initial=0) > 65535:
+        raise ValueError("a sinogram bin holds more than 65535 counts")
+    return d.astype(np.uint16)
+
+
 def lor_of_events_torch(sc: Scanner, det1, det2):
     """Canonical LOR index of events (torch tensors), as lor_of_events."""
     import torch
@@ -615,6 +636,22 @@ def lor_of_events_torch(sc: Scanner, det1, det2):
     ra = torch.where(sw, r2, r1)
     rb = torch.where(sw, r1, r2)
     return (q * sc.n_rings + ra) * sc.n_rings + rb
+
+
+def sinogram_bins_torch(sc: Scanner, tof: Tof, det1, det2, tb):
+    """sinogram_bins for torch tensors (int64 canonical bin per event)."""
+    import torch
+    n = sc.n_xtal
+    c1 = torch.remainder(det1.long(), n)
+    c2 = torch.remainder(det2.long(), n)
+    off = torch.remainder(c2 - c1, n)
+    half = (n - 1) // 2
+    direct = (off >= 1) & (off <= half)
+    even_mid = (off == n // 2) & (n % 2 == 0)
+    sw = torch.where(even_mid, c1 > c2, ~direct)
+    nb = max(tof.n_bins, 1)
+    m = torch.where(sw, -tb.long(), tb.long()) if tof.n_bins > 0 else torch.zeros_like(c1)
+    return lor_of_events_torch(sc, det1, det2) * nb + m + (nb - 1) // 2
 
 
 def lor_attenuation_torch(sc: Scanner, ph: Phantom, device="cuda"):
