@@ -112,16 +112,18 @@ def test_epochs_match_oracle(lm, name, epochs):
     for k in range(epochs):
         s = seq[2 * c.n_sub * k:2 * c.n_sub * (k + 1)]
         g.epoch(s)
-        o.run(s)
+        for i in s:
+            o.update(int(i))
     err = H.rel_l2(g.x().cpu().numpy(), o.x)
     assert err < H.REL_L2_IMAGE, err
     f_g, f_o = g.objective(), o.objective()
     assert abs(f_g - f_o) <= 1e-5 * abs(f_o)
-    # empty bins keep y = 1; y of the others matches the oracle's
+    # empty bins keep y = 1 (exact in real arithmetic; (a + 1) - sqrt((a - 1)^2) rounds within a few
+    # float32 ulps of 2); y of the others matches the oracle's
     b = _canonical_index(c, pe)
     y = g.y().cpu().numpy()
     empty = c.d[b] == 0
-    assert empty.any() and np.all(y[empty] == 1.0)
+    assert empty.any() and np.abs(y[empty] - 1.0).max() <= 1e-6
     assert H.rel_l2(y[~empty], o.y[b[~empty]]) < H.REL_L2_IMAGE
 
 
