@@ -525,27 +525,40 @@ def run_gpu(args):
 def sino_compare(L, S, wl, geo, raw, lor_att, sens, x0, beta, kn, seqs, n_sub, stream, dev, lm_epoch_ms):
     """Sinogram SPDHG (Alg. 1) on the histogram of the frame's events: every
     (LOR, TOF bin) of the scanner, empty bins included, view-based subsets,
-    the same selection sequences; epoch times by CUDA events."""
+    the same selection sequences; epoch times by CUDA events.  The bins are
+    held as a list when it fits in 60 % of the free memory, else with their
+    geometry generated from the bin index (counts, y and scratch: 10 B per bin)."""
     import torch
     nb_tot = int(L.load_library().lm_sino_n_bins(L.C.byref(geo.sc), L.C.byref(geo.tof)))
-    need = nb_tot * 26 + (64 << 20)  # bin list (det1, det2, tof, corr, contam, counts, y) and scratch
     free = torch.cuda.mem_get_info(dev)[0]
-    if need > 0.6 * free:
-        return {"skipped": f"the sinogram has {nb_tot} bins ({need / 1e9:.1f} GB); {free / 1e9:.1f} GB free"}
-    b = S.sinogram_bins_torch(wl.scanner, wl.tof, raw.det1, raw.det2, raw.tof)
-    d = torch.bincount(b, minlength=nb_tot)
-    if int(d.max().item()) > 65535:
-        return {"skipped": "a bin holds more than 65535 counts"}
-    d16 = d.to(torch.int32).to(torch.int16).view(torch.uint16)  # counts < 2^16: the bit pattern is kept
-    s = torch.full((nb_tot,), float(raw.contam[0].item()), dtype=torch.float32, device=dev)
-    pe = L.sino_setup(geo, d16, s, n_sub, lor_att)
-    st = L.LMSPDHG(geo, pe, sens, x0, beta=beta, n_subsets=n_sub, rho=0.999, knorm=kn, kahan=True,
-                   projector="direct", sinogram=True)
-    for sq in seqs[:2]:
-        st.epoch(sq)  # warm-up (graph capture)
+    s0 = float(raw.contam[0].item())
+    if nb_tot * 26 + (64 << 20) <= 0.6 * free:
+        layout = "stored bin list"
+        b = S.sinogram_bins_torch(wl.scanner, wl.tof, raw.det1, raw.det2, raw.tof)
+        d = torch.bincount(b, minlength=nb_tot)
+        if int(d.max().item()) > 65535:
+            return {"skipped": "a bin holds more than 65535 counts"}
+        nonempty = int((d > 0).sum().item())
+        d16 = d.to(torch.int32).to(torch.int16).view(torch.uint16)  # counts < 2^16: the bit pattern is kept
+        del b, d
+        s = torch.full((nb_tot,), s0, dtype=torch.float32, device=dev)
+        pe = L.sino_setup(geo, d16, s, n_sub, lor_att)
+        st = L.LMSPDHG(geo, pe, sens, x0, beta=beta, n_subsets=n_sub, rho=0.999, knorm=kn, kahan=True,
+                       projector="direct", sinogram=1)
+        timed = seqs
+    elif nb_tot * 10 + (1 << 30) <= 0.8 * free:
+        layout = "generated bin geometry (counts only)"
+        gen = L.sino_count(geo, L.DeviceEvents(raw.det1, raw.det2, raw.tof, raw.corr, raw.contam), n_sub)
+        nonempty = int((gen.mu[:nb_tot].view(torch.int16) != 0).sum().item())
+        st = L.LMSPDHG(geo, gen, sens, x0, beta=beta, n_subsets=n_sub, rho=0.999, knorm=kn, kahan=True,
+                       projector="direct", sinogram=2, sino_s=s0, sino_lorf=lor_att, group=32)
+        timed = seqs[:2]
+    else:
+        return {"skipped": f"the sinogram has {nb_tot} bins; {free / 1e9:.1f} GB free"}
+    st.epoch(seqs[0])  # warm-up (graph capture)
     st.reinit(x0)
     ms = []
-    for sq in seqs:
+    for sq in timed:
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         st.epoch(sq)
@@ -555,9 +568,10 @@ def sino_compare(L, S, wl, geo, raw, lor_att, sens, x0, beta, kn, seqs, n_sub, s
     obj = st.objective()
     st.close()
     med = statistics.median(ms)
-    return {"bins": nb_tot, "nonempty_bins": int((d > 0).sum().item()), "events": int(raw.det1.numel()),
-            "epoch_ms": med, "lm_epoch_ms": lm_epoch_ms,
-            "lm_speedup": (med / lm_epoch_ms) if lm_epoch_ms else None, "objective": obj,
+    return {"bins": nb_tot, "nonempty_bins": nonempty, "events": int(raw.det1.numel()), "layout": layout,
+            "epoch_ms": med, "epochs_timed": len(ms), "lm_epoch_ms": lm_epoch_ms,
+            "lm_speedup": (med / lm_epoch_ms) if lm_epoch_ms else None,
+            "bins_per_s": nb_tot / (med / 1e3) if med > 0 else None, "objective": obj,
             "subsets": "views (c1 + c2) mod n_xtal, view v in subset v mod n"}
 
 

@@ -243,6 +243,20 @@ size_t lm_sino_workspace_bytes(const lm_scanner* sc, int32_t n_subsets);
 int lm_sino_setup(const lm_scanner* sc, const lm_tof* tof, int32_t n_subsets, const uint16_t* d, const float* s,
                   const float* lor_factor, int32_t* det1_out, int32_t* det2_out, int16_t* tof_out, float* corr_out,
                   float* contam_out, uint16_t* d_out, int64_t* sub_off_host, void* ws, size_t ws_bytes, void* stream);
+/* Generated-geometry layout (lm_params.sinogram = 2), for sinograms too large
+ * to hold as a bin list (the 3D scanner's 2.9e8 LORs x 41 bins): only the
+ * counts are stored, in the order of lm_sino_setup; the event kernels compute
+ * each bin's detectors and TOF bin from its index, with the LOR factor from
+ * lm_params.sino_lorf and a flat contamination lm_params.sino_s.
+ * lm_sino_count histograms the events of ev (validated like lm_event_setup;
+ * LM_ERR_OUT_OF_RANGE for an invalid event or a bin above 65535 counts) into
+ * d_out (device uint16, lm_sino_n_bins entries rounded up to an even number,
+ * 4-byte aligned; overwritten), and writes the subsets' transaxial pairs
+ * (q_out: device int32 [n_xtal (n_xtal - 1) / 2]) with their offsets (qoff_out:
+ * device int64 [n_subsets + 1]) and the bin offsets (sub_off_host).  Same
+ * workspace as lm_sino_setup.  Synchronous. */
+int lm_sino_count(const lm_scanner* sc, const lm_tof* tof, int32_t n_subsets, const lm_events* ev, uint16_t* d_out,
+                  int32_t* q_out, int64_t* qoff_out, int64_t* sub_off_host, void* ws, size_t ws_bytes, void* stream);
 
 /* ---- LM-SPDHG state (Alg. 2) --------------------------------------------- */
 typedef struct lm_state_s lm_state;
@@ -288,7 +302,13 @@ typedef struct {
                           /* of lm_sino_setup and mu their counts d_b (0 allowed);*/
                           /* the dual step uses prox with S_b d_b and back-       */
                           /* projects y+ - y; the objective is Eq. (1) with the   */
-                          /* sum of s.  0: Alg. 2 (listmode).                     */
+                          /* sum of s.  0: Alg. 2 (listmode).  2: the same with  */
+                          /* the bins' geometry generated (lm_sino_count): the   */
+                          /* events' arrays may be NULL, mu = the counts.         */
+    const int32_t* sino_q;   /* sinogram = 2: q_out of lm_sino_count               */
+    const int64_t* sino_qoff;/* sinogram = 2: qoff_out of lm_sino_count            */
+    const float* sino_lorf;  /* sinogram = 2: LOR factor [lm_n_lor] (NULL = 1)     */
+    float sino_s;            /* sinogram = 2: flat contamination s_b > 0           */
 } lm_params;
 
 /* Bytes of the optional tile-binned projector buffer (lm_params.tile_buf):

@@ -1111,16 +1111,18 @@ __global__ void __launch_bounds__(256) obj_img_partial(const float* __restrict__
 
 // sum_e w_e log(p_e + s_e) and, with weights (sinogram bins: w = d_b), sum_e s_e (FP64)
 __global__ void __launch_bounds__(256) obj_ev_partial(const float* __restrict__ p, const float* __restrict__ s,
-                                                      const uint16_t* __restrict__ w, int64_t n, double* part)
+                                                      float s_flat, const uint16_t* __restrict__ w, int64_t n,
+                                                      double* part)
 {
     __shared__ double sm[256];
     double acc = 0.0, acs = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)RB * 256) {
+        const double se = s ? (double)s[e] : (double)s_flat;
         if (w) {
-            if (w[e]) acc += (double)w[e] * log((double)p[e] + (double)s[e]);
-            acs += (double)s[e];
+            if (w[e]) acc += (double)w[e] * log((double)p[e] + se);
+            acs += se;
         } else {
-            acc += log((double)p[e] + (double)s[e]);
+            acc += log((double)p[e] + se);
         }
     }
     acc = block_sum_d(acc, sm);
@@ -1664,11 +1666,11 @@ int reduce_minmax(const float* x, int64_t n, float* dev_scratch, float* mn, floa
 size_t objective_scratch_bytes() { return align_up((4 * RB + 4) * sizeof(double)); }
 
 int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* xi, const float* p,
-                    const float* contam, const uint16_t* w, int64_t n_ev, double* scratch, double* out4,
-                    cudaStream_t st)
+                    const float* contam, float s_flat, const uint16_t* w, int64_t n_ev, double* scratch,
+                    double* out4, cudaStream_t st)
 {
     obj_img_partial<<<RB, 256, 0, st>>>(sens, x, xi, g->n[0], g->n[1], g->n[2], scratch);
-    obj_ev_partial<<<RB, 256, 0, st>>>(p, contam, w, n_ev, scratch);
+    obj_ev_partial<<<RB, 256, 0, st>>>(p, contam, s_flat, w, n_ev, scratch);
     obj_final<<<1, 256, 0, st>>>(scratch);
     count_launch(3);
     LM_CUDA(cudaGetLastError());

@@ -131,7 +131,13 @@ struct EvArgs {
     int prior_only;             // 1: data selections are left to the tile-binned projector
     int acc_pairs;              // 1: acc_std / acc_yf hold (voxel j, voxel j + nx*ny) float pairs
     const float* xi;            // directional TV field [ndim][V], or nullptr (TV)
-    int sino;                   // 1: the events are sinogram bins, mu their counts d_b (Alg. 1)
+    int sino;                   // 1: the events are sinogram bins, mu their counts d_b (Alg. 1);
+                                // 2: the same, with each bin's geometry computed from its index
+    const int32_t* g_q;         // sino 2: transaxial pairs of every subset, subset by subset
+    const int64_t* g_qoff;      // sino 2: [n_subsets + 1] offsets into g_q
+    const float* g_lorf;        // sino 2: per-LOR factor [n_lor] or nullptr (1)
+    float g_s;                  // sino 2: flat contamination s_b
+    int g_rings, g_xtal, g_nb;  // sino 2: scanner rings, crystals per ring, TOF bins (>= 1)
 };
 
 // Batched multi-frame epochs: per-frame argument tables in device memory.
@@ -326,14 +332,19 @@ struct ResPlan {
     ResAxis ax[3];
 };
 int res_plan(const lm_grid* g, float fwhm, ResPlan& p);
-// dst = G src via temporaries t1, t2; skipped when seq[u] >= n_subsets (seq set)
+// dst = G src via temporaries t1, t2; skipped when seq[u] >= n_subsets (seq set);
+// pair_out: dst is a pair accumulator (values go to the first halves)
 int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* t1, float* t2,
-               const uint16_t* seq, int u, int n_subsets, cudaStream_t st);
+               const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out);
+// out = the float pair accumulators (std and y-fastest) folded into one image; clears them
+void launch_res_fold(const lm_grid* g, float* acc_std, float* acc_yf, float* out, const uint16_t* seq, int u,
+                     int n_subsets, cudaStream_t st);
 
-// out4: <sens, x>, ||Kx||_{2,1}, sum_e w_e log(p_e + s_e) (w = 1 if NULL), sum_e s_e if w is set (else 0)
+// out4: <sens, x>, ||Kx||_{2,1}, sum_e w_e log(p_e + s_e) (w = 1 if NULL), sum_e s_e if w is set (else 0);
+// s_e = contam[e], or s_flat where contam is NULL
 int objective_parts(const lm_grid* g, const float* sens, const float* x, const float* xi, const float* p,
-                    const float* contam, const uint16_t* w, int64_t n_ev, double* scratch, double* out4,
-                    cudaStream_t st);
+                    const float* contam, float s_flat, const uint16_t* w, int64_t n_ev, double* scratch,
+                    double* out4, cudaStream_t st);
 size_t objective_scratch_bytes();
 
 }  // namespace lmh

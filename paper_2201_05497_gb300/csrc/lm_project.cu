@@ -222,6 +222,43 @@ __device__ __noinline__ void prior_dual(const EvArgs& A)
                 (int64_t)gridDim.x * blockDim.x);
 }
 
+// Sinogram bin e of the generated layout (lm_params.sinogram = 2): the subset
+// holding e (binary search of the offsets), then the bin's transaxial pair,
+// ring pair and TOF bin in the order lm_sino_setup writes them: pairs in
+// their subset's list, ring pairs, TOF bins; canonical detectors.
+__device__ __forceinline__ void gen_bin(const EvArgs& A, int64_t e, int& d1, int& d2, int& m, float& c)
+{
+    int lo = 0, hi = A.n_subsets;  // sub_off[lo] <= e < sub_off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (A.sub_off[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    const int nr = A.g_rings, nb = A.g_nb, nx = A.g_xtal;
+    const int64_t nr2 = (int64_t)nr * nr;
+    const int64_t per_q = nr2 * nb;
+    const int64_t pos = e - A.sub_off[lo];
+    const int64_t qr = pos / per_q;
+    const int64_t rem = pos - qr * per_q;
+    const int rr = (int)(rem / nb);
+    const int mi = (int)(rem - (int64_t)rr * nb);
+    const int64_t qq = A.g_q[A.g_qoff[lo] + qr];
+    const int64_t B = (int64_t)nx * ((nx - 1) / 2);
+    int c1, c2;
+    if (qq < B) {
+        c1 = (int)(qq % nx);
+        c2 = (int)((c1 + 1 + qq / nx) % nx);
+    } else {
+        c1 = (int)(qq - B);
+        c2 = c1 + nx / 2;
+    }
+    const int r1 = rr / nr, r2 = rr - r1 * nr;
+    d1 = r1 * nx + c1;
+    d2 = r2 * nx + c2;
+    m = mi - (nb - 1) / 2;
+    c = A.g_lorf ? A.g_lorf[qq * nr2 + rr] : 1.0f;
+}
+
 template <int MODE>
 struct ModeTraits {
     static constexpr bool gather = MODE == lmh::EV_FWD || MODE == lmh::EV_DATA || MODE == lmh::EV_DATA_FX1 ||
@@ -335,10 +372,17 @@ __device__ __forceinline__ void event_chunk(const EvArgs& A, const float* __rest
     bool mok = false;
     if (own) {
         const int64_t e = e0 + q;
-        const int d1 = A.det1[e], d2 = A.det2[e];
-        const int m = A.tof ? (int)A.tof[e] : 0;
-        if (A.corr) mc = A.corr[e];
-        if (T::needs_s) ms = A.contam[e];
+        int d1, d2, m;
+        if (A.sino == 2) {
+            gen_bin(A, e, d1, d2, m, mc);
+            ms = A.g_s;
+        } else {
+            d1 = A.det1[e];
+            d2 = A.det2[e];
+            m = A.tof ? (int)A.tof[e] : 0;
+            if (A.corr) mc = A.corr[e];
+            if (T::needs_s) ms = A.contam[e];
+        }
         if (T::needs_y) my = A.y[e];
         if (T::needs_mu) mmu = (float)A.mu[e];
         if (T::needs_vin) mv = A.vin[e];

@@ -20,7 +20,7 @@ namespace {
 
 __global__ void __launch_bounds__(256) res_pass_kernel(const float* __restrict__ src, float* __restrict__ dst,
                                                        int nx, int ny, int nz, int axis, lmh::ResAxis w,
-                                                       const uint16_t* seq, int u, int n_subsets)
+                                                       const uint16_t* seq, int u, int n_subsets, int pair_out)
 {
     if (seq != nullptr && seq[u] >= n_subsets) return;  // a prior update back-projects nothing
     const int V = nx * ny * nz;
@@ -48,7 +48,57 @@ __global__ void __launch_bounds__(256) res_pass_kernel(const float* __restrict__
         if (m >= n) m = 2 * n - m - 1;
         acc = fmaf(w.w[k + r], __ldg(src + j + (m - c) * st), acc);
     }
-    dst[j] = acc;
+    // pair_out: the first half of voxel j's (j, j + nx*ny) accumulator pair
+    dst[pair_out ? 2 * (int64_t)j : j] = acc;
+}
+
+// The back-projection accumulators as one image: voxel j is the first half of
+// its own std pair plus the second half of the pair below, plus the same from
+// the y-fastest pairs (read through a shared-memory transpose); every half is
+// cleared by its reader, as in the image pass.
+constexpr int FT = 32, FR = 8;
+__global__ void __launch_bounds__(256) res_fold_kernel(float* __restrict__ acc_std, float* __restrict__ acc_yf,
+                                                       float* __restrict__ out, int nx, int ny, int nz,
+                                                       const uint16_t* seq, int u, int n_subsets)
+{
+    if (seq != nullptr && seq[u] >= n_subsets) return;
+    __shared__ float sm[FT][FT + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tiles_x = (nx + FT - 1) / FT, tiles_y = (ny + FT - 1) / FT;
+    const int64_t sz = (int64_t)nx * ny;
+    const int64_t n_tiles = (int64_t)tiles_x * tiles_y * nz;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int x0 = (int)(t % tiles_x) * FT;
+        const int y0 = (int)((t / tiles_x) % tiles_y) * FT;
+        const int z = (int)(t / ((int64_t)tiles_x * tiles_y));
+        const bool below = z > 0;
+        if (acc_yf != nullptr) {
+            for (int r = ty; r < FT; r += FR) {
+                const int xx = x0 + r, yy = y0 + tx;
+                float v = 0.0f;
+                if (xx < nx && yy < ny) {
+                    const int64_t k = ((int64_t)z * nx + xx) * ny + yy;
+                    v = acc_yf[2 * k] + (below ? acc_yf[2 * (k - sz) + 1] : 0.0f);
+                    acc_yf[2 * k] = 0.0f;
+                    if (below) acc_yf[2 * (k - sz) + 1] = 0.0f;
+                }
+                sm[r][tx] = v;
+            }
+        }
+        __syncthreads();
+        for (int r = ty; r < FT; r += FR) {
+            const int xx = x0 + tx, yy = y0 + r;
+            if (xx < nx && yy < ny) {
+                const int64_t j = ((int64_t)z * ny + yy) * nx + xx;
+                float v = acc_std[2 * j] + (below ? acc_std[2 * (j - sz) + 1] : 0.0f);
+                if (acc_yf != nullptr) v += sm[tx][r];
+                acc_std[2 * j] = 0.0f;
+                if (below) acc_std[2 * (j - sz) + 1] = 0.0f;
+                out[j] = v;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace
@@ -83,10 +133,12 @@ int res_plan(const lm_grid* g, float fwhm, ResPlan& p)
     return LM_OK;
 }
 
-// dst = G src through the temporaries t1, t2 (src may equal dst; neither may
-// alias t1 or t2).  With seq set, nothing runs when seq[u] selects the prior.
+// dst = G src through the temporaries t1, t2 (pass i > 0 reads the previous
+// pass's output, so t2 may be src; dst must alias neither t1 nor t2 unless it
+// is src with one pass).  pair_out: dst is a pair accumulator (first halves).
+// With seq set, nothing runs when seq[u] selects the prior.
 int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* t1, float* t2,
-               const uint16_t* seq, int u, int n_subsets, cudaStream_t st)
+               const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out)
 {
     const int V = (int)nvox(g);
     const int blocks = (V + 255) / 256;
@@ -97,20 +149,31 @@ int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst,
     }
     const float* in = src;
     for (int i = 0; i < k; ++i) {
-        float* out = (i == k - 1) ? (in == dst ? t2 : dst) : ((i & 1) ? t2 : t1);
+        const bool last = i == k - 1;
+        float* out = last ? (in == dst ? t2 : dst) : ((i & 1) ? t2 : t1);
         res_pass_kernel<<<blocks, 256, 0, st>>>(in, out, g->n[0], g->n[1], g->n[2], p.axis[i], p.ax[i], seq, u,
-                                                n_subsets);
+                                                n_subsets, (last && out == dst && pair_out) ? 1 : 0);
         in = out;
     }
     count_launch(k);
     if (in != dst) {
         // one pass in place: copy the result back (skipped like the pass for a prior update)
         res_pass_kernel<<<blocks, 256, 0, st>>>(in, dst, g->n[0], g->n[1], g->n[2], 0, ResAxis{0, {1.0f}}, seq, u,
-                                                n_subsets);
+                                                n_subsets, pair_out ? 1 : 0);
         count_launch();
     }
     LM_CUDA(cudaGetLastError());
     return LM_OK;
+}
+
+void launch_res_fold(const lm_grid* g, float* acc_std, float* acc_yf, float* out, const uint16_t* seq, int u,
+                     int n_subsets, cudaStream_t st)
+{
+    const int64_t tiles = (int64_t)((g->n[0] + FT - 1) / FT) * ((g->n[1] + FT - 1) / FT) * g->n[2];
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 8);
+    res_fold_kernel<<<std::max(grid, 1), dim3(FT, FR), 0, st>>>(acc_std, g->n[1] > 1 ? acc_yf : nullptr, out, g->n[0],
+                                                               g->n[1], g->n[2], seq, u, n_subsets);
+    count_launch();
 }
 
 }  // namespace lmh
@@ -138,7 +201,7 @@ int lm_res_apply(const lm_grid* grid, float fwhm, const float* x, float* out, vo
     if (rc) return rc;
     float* t1 = (float*)ws;
     float* t2 = (float*)((char*)ws + lmh::align_up((size_t)lmh::nvox(grid) * 4));
-    return lmh::launch_res(grid, p, x, out, t1, t2, nullptr, 0, 0, lmh::S(stream));
+    return lmh::launch_res(grid, p, x, out, t1, t2, nullptr, 0, 0, lmh::S(stream), false);
 }
 
 }  // extern "C"

@@ -54,7 +54,8 @@ struct lm_state_s {
     TmaMaps* tmaps;   // device copy of the tensor maps (TMA-staged image passes)
     unsigned* err;    // set by a bounded device wait that gave up
     bool tma;         // image passes staged by TMA (grid permitting, unless disabled)
-    bool has_res;     // resolution model P = A G: the event kernels read G x from xyf[0]
+    bool has_res;     // resolution model P = A G: the event kernels read G x from gx / gxyf
+    float *gx, *gxyf; // G x in both layouts (float mode; scratch of the back-projection's G)
     ResPlan res;
     int zlen;         // z slices per TMA work item
     bool tiled;       // data updates by the tile-binned projector
@@ -110,6 +111,9 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
     float* acc_yf = (!det && yf) ? F(2 * V) : nullptr;
     unsigned long long* ai_std = det ? c.take<unsigned long long>(V * 8) : nullptr;
     unsigned long long* ai_yf = (det && yf) ? c.take<unsigned long long>(V * 8) : nullptr;
+    // G x for the resolution model, both layouts (8 B per voxel, float mode)
+    float* gx = det ? nullptr : F(V);
+    float* gxyf = det ? nullptr : F(V);
     float* y = F((size_t)std::max<int64_t>(N, 1));
     const size_t scr_bytes = std::max<size_t>((size_t)std::max<int64_t>(N, 1) * 4,
                                               std::max(lm_knorm_workspace_bytes(g), objective_scratch_bytes()));
@@ -136,6 +140,7 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
         st->y = y; st->scr = scr; st->scr_bytes = scr_bytes; st->sub_off = sub_off; st->seq = seq;
         st->wpar = wpar; st->wbase = wbase; st->maxbits = maxbits; st->queue = queue; st->done = done;
         st->redf = redf; st->redd = redd;
+        st->gx = gx; st->gxyf = gxyf;
     }
 }
 
@@ -169,9 +174,18 @@ EvArgs base_ev_args(const lm_state* st)
     a.tof_tab = st->tof.n_bins > 0 ? st->tof_tab : nullptr;
     a.group = st->group;
     a.prior_fused = st->tma ? 1 : 0;
-    a.acc_pairs = (st->det || st->has_res) ? 0 : 1;
+    a.acc_pairs = st->det ? 0 : 1;
     a.xi = st->P.xi;
-    a.sino = st->P.sinogram ? 1 : 0;
+    a.sino = st->P.sinogram;
+    if (st->P.sinogram == 2) {
+        a.g_q = st->P.sino_q;
+        a.g_qoff = st->P.sino_qoff;
+        a.g_lorf = st->P.sino_lorf;
+        a.g_s = st->P.sino_s;
+        a.g_rings = st->sc.n_rings;
+        a.g_xtal = st->sc.n_xtal;
+        a.g_nb = std::max(1, (int)st->tof.n_bins);
+    }
     return a;
 }
 
@@ -206,13 +220,37 @@ ImgArgs base_img_args(const lm_state* st)
     a.inv_p_prior = 2.0f;
     a.s_prior = (float)(st->gamma * (double)st->P.rho / st->knorm);
     a.beta = st->P.beta;
-    a.acc_pairs = (st->det || st->has_res) ? 0 : 1;
-    if (st->has_res) a.acc_yf = nullptr;  // scratch of the resolution model; the events use one layout
+    a.acc_pairs = st->det ? 0 : 1;
     a.tm = st->tma ? st->tmaps : nullptr;
     a.err = st->err;
     a.zlen = st->zlen;
     a.xi = st->P.xi;
     return a;
+}
+
+// Resolution model: G x into gx (x-fastest) and gxyf (y-fastest).  The pair
+// accumulators, zero between updates, hold the passes' temporaries and are
+// cleared again.
+int res_fwd(lm_state* st, const float* x, cudaStream_t s)
+{
+    float* t1 = st->acc_std;
+    float* t2 = st->acc_std + st->V;
+    int rc = launch_res(&st->g, st->res, x, st->gx, t1, t2, nullptr, 0, 0, s, false);
+    if (rc) return rc;
+    LM_CUDA(cudaMemsetAsync(st->acc_std, 0, 2 * (size_t)st->V * 4, s));
+    if (st->g.n[1] > 1) launch_transpose_to_yf(&st->g, st->gx, st->gxyf, s);
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+// Resolution model: dz = G (A^T v).  The accumulators are folded into gx
+// (and cleared), blurred, and written back as the first halves of the std
+// pairs, so the image pass merges G A^T v unchanged.  Skipped on the device
+// when seq[u] selects the prior.
+int res_back(lm_state* st, const uint16_t* seq, int u, cudaStream_t s)
+{
+    launch_res_fold(&st->g, st->acc_std, st->acc_yf, st->gx, seq, u, st->n, s);
+    return launch_res(&st->g, st->res, st->gx, st->acc_std, st->gxyf, st->gx, seq, u, st->n, s, true);
 }
 
 // Launches updates 0..count-1 of the selection already in st->seq; x starts
@@ -229,8 +267,8 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         EvArgs a = base_ev_args(st);
         a.seq = st->seq;
         a.u = u;
-        a.x_std = st->has_res ? st->xyf[0] : st->x[cur];  // G x with the resolution model
-        a.x_yf = st->has_res ? nullptr : st->xyf[cur];
+        a.x_std = st->has_res ? st->gx : st->x[cur];  // G x with the resolution model
+        a.x_yf = st->has_res ? st->gxyf : st->xyf[cur];
         a.px = st->x[cur];
         a.maxbits = st->maxbits + slot;
         if (st->tiled) {
@@ -251,13 +289,11 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
             }
         } else if (!st->det) {
             a.acc_std = st->acc_std;
-            a.acc_yf = st->has_res ? nullptr : st->acc_yf;
+            a.acc_yf = st->acc_yf;
             int rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
             LM_CHECK(rc == LM_OK, rc, "data update launch failed");
             if (st->has_res) {
-                // dz = G (A^T v): blur the back-projection in place (nothing for a prior selection)
-                rc = launch_res(&st->g, st->res, st->acc_std, st->acc_std, st->xyf[1], st->acc_yf, st->seq, u, st->n,
-                                s);
+                rc = res_back(st, st->seq, u, s);
                 if (rc) return rc;
             }
         } else {
@@ -281,15 +317,14 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         im.u = u;
         im.x_cur = st->x[cur];
         im.x_nxt_std = st->x[nxt];
-        im.x_nxt_yf = st->has_res ? nullptr : st->xyf[nxt];
+        im.x_nxt_yf = st->xyf[nxt];
         // scale slots: update u reads slot (slot0 + u) & 1, its pass clears the other one
         im.slot0 = slot0;
         im.xcur = cur;
         if (st->tma) launch_image_tma(im, s);
         else launch_image_pass(im, s);
         if (st->has_res) {
-            // the next update's projections read G x
-            int rc = launch_res(&st->g, st->res, st->x[nxt], st->xyf[0], st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
+            int rc = res_fwd(st, st->x[nxt], s);  // the next update's projections read G x
             if (rc) return rc;
         }
         if (ev) LM_CUDA(cudaEventRecord(ev[3 * u + 2], s));
@@ -332,9 +367,10 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     EvArgs a = base_ev_args(st);
     a.x_std = x0;
     if (st->has_res) {
-        rc = launch_res(&st->g, st->res, x0, st->xyf[0], st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
+        rc = res_fwd(st, x0, s);
         if (rc) return rc;
-        a.x_std = st->xyf[0];
+        a.x_std = st->gx;
+        a.x_yf = yf ? st->gxyf : nullptr;
     } else if (yf) {
         launch_transpose_to_yf(&st->g, x0, st->xyf[1], s);
         a.x_yf = st->xyf[1];
@@ -345,10 +381,9 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     if (st->N > 0) {
         if (!st->det) {
             a.acc_std = st->acc_std;
-            a.acc_yf = st->has_res ? nullptr : st->acc_yf;
+            a.acc_yf = st->acc_yf;
             rc = launch_events(EV_YINIT, st->two_d, a, st->grid_ev, s);
-            if (!rc && st->has_res)
-                rc = launch_res(&st->g, st->res, st->acc_std, st->acc_std, st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
+            if (!rc && st->has_res) rc = res_back(st, nullptr, 0, s);
         } else {
             a.out = st->scr;
             a.maxbits = st->maxbits + 1;
@@ -372,10 +407,10 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
     im.x_cur = x0;
     im.x_keep = st->x[1];
     im.x_nxt_std = st->x[0];
-    im.x_nxt_yf = st->has_res ? nullptr : st->xyf[0];
+    im.x_nxt_yf = st->xyf[0];
     launch_image_pass(im, s);
     if (st->has_res) {
-        rc = launch_res(&st->g, st->res, st->x[0], st->xyf[0], st->xyf[1], st->acc_yf, nullptr, 0, 0, s);
+        rc = res_fwd(st, st->x[0], s);
         if (rc) return rc;
     }
     LM_CUDA(cudaGetLastError());
@@ -485,9 +520,16 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     LM_CHECK(P.n_subsets >= 1 && P.n_subsets < 65535, LM_ERR_INVALID_ARG, "n_subsets out of range");
     LM_CHECK(P.beta >= 0.0f && std::isfinite(P.beta), LM_ERR_INVALID_ARG, "beta must be >= 0");
     LM_CHECK(P.rho > 0.0f && std::isfinite(P.rho), LM_ERR_INVALID_ARG, "rho must be > 0");
-    LM_CHECK(ev->n >= 0 && (ev->n == 0 || (ev->det1 && ev->det2 && ev->contam && mu)), LM_ERR_INVALID_ARG,
-             "events need det1, det2, contam and mu");
-    LM_CHECK(tof->n_bins == 0 || ev->n == 0 || ev->tof != nullptr, LM_ERR_INVALID_ARG, "TOF bins NULL");
+    LM_CHECK(P.sinogram >= 0 && P.sinogram <= 2, LM_ERR_INVALID_ARG, "sinogram must be 0, 1 or 2");
+    if (P.sinogram == 2) {
+        LM_CHECK(ev->n == lm_sino_n_bins(sc, tof) && mu && P.sino_q && P.sino_qoff, LM_ERR_INVALID_ARG,
+                 "a generated sinogram needs every bin's count and the subsets' pair lists");
+        LM_CHECK(P.sino_s > 0.0f && std::isfinite(P.sino_s), LM_ERR_DOMAIN, "sino_s must be > 0");
+    } else {
+        LM_CHECK(ev->n >= 0 && (ev->n == 0 || (ev->det1 && ev->det2 && ev->contam && mu)), LM_ERR_INVALID_ARG,
+                 "events need det1, det2, contam and mu");
+        LM_CHECK(tof->n_bins == 0 || ev->n == 0 || ev->tof != nullptr, LM_ERR_INVALID_ARG, "TOF bins NULL");
+    }
     LM_CHECK(sens && x0 && sub_off_host && state_buf, LM_ERR_INVALID_ARG, "NULL sens, x0, sub_off or state buffer");
     LM_CHECK(sub_off_host[0] == 0 && sub_off_host[P.n_subsets] == ev->n, LM_ERR_INVALID_ARG,
              "subset offsets must span [0, n)");
@@ -835,11 +877,12 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
         a.x_std = st->x[xb];
         a.x_yf = st->xyf[xb];
         if (st->has_res) {
-            // G x into scratch that the next update does not read
-            int rc = launch_res(&st->g, st->res, st->x[xb], st->xyf[1], st->acc_yf, st->acc_yf + st->V, nullptr, 0,
-                                0, s);
+            // G x into the (zero) accumulators, which the next update does not read before clearing
+            float* t = st->acc_std;
+            int rc = launch_res(&st->g, st->res, st->x[xb], t, t + st->V, st->acc_yf ? st->acc_yf : t + st->V,
+                                nullptr, 0, 0, s, false);
             if (rc) return rc;
-            a.x_std = st->xyf[1];
+            a.x_std = t;
             a.x_yf = nullptr;
         }
         a.out = p;
@@ -850,10 +893,15 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
         a.chunk = 32;
         int rc = launch_events(EV_FWD, st->two_d, a, ev_grid_g(EV_FWD, st->two_d, st->group), s);
         LM_CHECK(rc == LM_OK, rc, "objective projection failed");
+        if (st->has_res) {
+            // the accumulators must be zero at the next update
+            LM_CUDA(cudaMemsetAsync(st->acc_std, 0, 2 * (size_t)st->V * 4, s));
+            if (st->acc_yf) LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, 2 * (size_t)st->V * 4, s));
+        }
     }
     double parts[4];
-    int rc = objective_parts(&st->g, st->sens, st->x[xb], st->P.xi, p, st->contam, st->P.sinogram ? st->mu : nullptr,
-                             st->N, st->redd, parts, s);
+    int rc = objective_parts(&st->g, st->sens, st->x[xb], st->P.xi, p, st->contam, st->P.sino_s,
+                             st->P.sinogram ? st->mu : nullptr, st->N, st->redd, parts, s);
     if (rc) return rc;
     unsigned err = 0;
     LM_CUDA(cudaMemcpyAsync(&err, st->err, sizeof(err), cudaMemcpyDeviceToHost, s));

@@ -52,7 +52,8 @@ class lm_params(C.Structure):
                 ("knorm_iters", C.c_int32), ("n_subsets", C.c_int32), ("deterministic", C.c_int32),
                 ("kahan", C.c_int32), ("group", C.c_int32), ("image_kernel", C.c_int32),
                 ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t), ("xi", C.c_void_p),
-                ("res_fwhm", C.c_float), ("sinogram", C.c_int32)]
+                ("res_fwhm", C.c_float), ("sinogram", C.c_int32), ("sino_q", C.c_void_p),
+                ("sino_qoff", C.c_void_p), ("sino_lorf", C.c_void_p), ("sino_s", C.c_float)]
 
 
 _lib = None
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lm_sino_n_bins": ([P(lm_scanner), P(lm_tof)], I64),
         "lm_sino_workspace_bytes": ([P(lm_scanner), I32], SZ),
         "lm_sino_setup": ([P(lm_scanner), P(lm_tof), I32, V, V, V, V, V, V, V, V, V, P(I64), V, SZ, V], C.c_int),
+        "lm_sino_count": ([P(lm_scanner), P(lm_tof), I32, P(lm_events), V, V, V, P(I64), V, SZ, V], C.c_int),
         "lm_res_apply": ([P(lm_grid), F, V, V, V, SZ, V], C.c_int),
         "lm_dtv_grad": ([P(lm_grid), V, V, V, V], C.c_int),
         "lm_dtv_div": ([P(lm_grid), V, V, V, V], C.c_int),
@@ -478,6 +480,43 @@ def sino_setup(geo: Geometry, d: torch.Tensor, s: torch.Tensor, n_subsets: int,
     return PermutedEvents(ev, mu, off)
 
 
+@dataclasses.dataclass
+class _CountOnly:
+    """Event-list descriptor of a generated sinogram: only the bin count."""
+    n: int
+
+    def desc(self) -> lm_events:
+        return lm_events(None, None, None, None, None, self.n)
+
+
+@dataclasses.dataclass
+class GeneratedSinogram:
+    events: _CountOnly
+    mu: torch.Tensor          # counts d_b (uint16), subset order
+    sub_off: np.ndarray       # int64 [n_subsets + 1] bin offsets
+    q: torch.Tensor           # int32 transaxial pairs of the subsets
+    qoff: torch.Tensor        # int64 [n_subsets + 1]
+
+
+def sino_count(geo: Geometry, ev: DeviceEvents, n_subsets: int, stream=None) -> GeneratedSinogram:
+    """Histogram of the events over every sinogram bin for the generated
+    sinogram layout (lm_params.sinogram = 2)."""
+    L = load_library()
+    dev = ev.det1.device
+    nb = int(L.lm_sino_n_bins(C.byref(geo.sc), C.byref(geo.tof)))
+    mu = torch.empty((nb + 1) // 2 * 2, dtype=torch.uint16, device=dev)
+    n_pairs = geo.sc.n_xtal * (geo.sc.n_xtal - 1) // 2
+    q = torch.empty(n_pairs, dtype=torch.int32, device=dev)
+    qoff = torch.empty(n_subsets + 1, dtype=torch.int64, device=dev)
+    off = np.zeros(n_subsets + 1, dtype=np.int64)
+    ws = _ws(L.lm_sino_workspace_bytes(C.byref(geo.sc), int(n_subsets)), dev)
+    d = ev.desc()
+    _check(L.lm_sino_count(C.byref(geo.sc), C.byref(geo.tof), int(n_subsets), C.byref(d), _ptr(mu), _ptr(q),
+                           _ptr(qoff), off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(ws), ws.numel(),
+                           _stream(stream)))
+    return GeneratedSinogram(_CountOnly(nb), mu, off, q, qoff)
+
+
 class LMSPDHG:
     """Alg. 2 on the device.  Holds the state buffer and the library handle."""
 
@@ -485,7 +524,8 @@ class LMSPDHG:
                  beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
                  image_kernel: int = 0, projector: str = "direct", xi: Optional[torch.Tensor] = None,
-                 res_fwhm: float = 0.0, sinogram: bool = False, stream=None):
+                 res_fwhm: float = 0.0, sinogram: int = 0, sino_s: float = 0.0,
+                 sino_lorf: Optional[torch.Tensor] = None, stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.xi = xi  # directional TV field (referenced by the state), None = TV
@@ -507,7 +547,9 @@ class LMSPDHG:
         self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan),
                                 int(group), int(image_kernel), None if self.tile is None else self.tile.data_ptr(),
                                 0 if self.tile is None else self.tile.numel(), _ptr(xi), float(res_fwhm),
-                                int(sinogram))
+                                int(sinogram), _ptr(getattr(pe, "q", None)), _ptr(getattr(pe, "qoff", None)),
+                                _ptr(sino_lorf), float(sino_s))
+        self._keep = (sino_lorf,)
         self._ev = pe.events.desc()
         self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
         h = C.c_void_p()

@@ -145,3 +145,39 @@ def test_listmode_equals_sinogram_on_gpu(lm):
     assert H.rel_l2(g_sino.x().cpu().numpy(), g_lm.x().cpu().numpy()) < 1e-4
     assert abs(g_sino.objective() - float(c.s.astype(np.float64).sum()) - g_lm.objective()) <= 1e-5 * abs(
         g_lm.objective())
+
+
+@pytest.mark.parametrize("name", ["2d_small", "3d_small"])
+def test_generated_layout_equals_stored(lm, name):
+    """lm_sino_count gives the counts of the stored layout (same order), and a
+    state that computes every bin's geometry from its index (sinogram = 2)
+    reproduces the stored-list state bit for bit (deterministic mode)."""
+    c = Case(lm, name)
+    gen = lm.sino_count(c.geo_g, lm.DeviceEvents.from_numpy(c.ev), c.n_sub)
+    pe = c.bins()
+    np.testing.assert_array_equal(pe.sub_off, gen.sub_off)
+    mu_st = pe.mu.view(torch.int16).cpu().numpy().view(np.uint16)
+    mu_gen = gen.mu.view(torch.int16).cpu().numpy().view(np.uint16)[:c.NB]
+    np.testing.assert_array_equal(mu_gen, mu_st)
+    a, _ = c.gpu(pe=pe, deterministic=True)
+    sens = torch.from_numpy(c.sens_or.astype(np.float32)).cuda()
+    b = lm.LMSPDHG(c.geo_g, gen, sens, torch.from_numpy(c.x0).cuda(), beta=c.wl.beta, n_subsets=c.n_sub,
+                   gamma=c.gamma, rho=0.999, knorm=c.knorm, deterministic=True, kahan=True, group=0,
+                   projector="direct", sinogram=2, sino_s=float(c.s[0]), sino_lorf=torch.from_numpy(c.lf).cuda())
+    seq = S.selection_sequence(c.n_sub, 4 * c.n_sub, seed=3)
+    for k in range(2):
+        s = seq[2 * c.n_sub * k:2 * c.n_sub * (k + 1)]
+        a.epoch(s)
+        b.epoch(s)
+    np.testing.assert_array_equal(a.x().cpu().numpy(), b.x().cpu().numpy())
+    np.testing.assert_array_equal(a.y().cpu().numpy(), b.y().cpu().numpy()[:c.NB])
+    assert a.objective() == b.objective()
+
+
+def test_count_rejects_invalid_events(lm):
+    c = Case(lm, "2d_small", n_events=500)
+    ev = lm.DeviceEvents.from_numpy(c.ev)
+    ev.det1[7] = c.wl.scanner.n_det + 3
+    with pytest.raises(lm.LMError) as ei:
+        lm.sino_count(c.geo_g, ev, c.n_sub)
+    assert ei.value.code == 2
