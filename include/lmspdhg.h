@@ -290,14 +290,14 @@ typedef struct {
                           /* (6 per event), the direct kernel is used.            */
     const float* xi;      /* directional TV prior (lm_dtv_field): device field    */
                           /* [ndim][V], referenced, must outlive the state; NULL  */
-                          /* = TV.  Runs the plain-load image passes (auto picks */
-                          /* them; image_kernel = 2 is rejected).  knorm may be  */
+                          /* = TV.  Prior updates run the plain-load image pass  */
+                          /* (the TMA pass fuses the TV prior only); data updates */
+                          /* the TMA pass where the grid allows.  knorm may be    */
                           /* the TV norm: ||K_DTV|| <= ||K_TV||.                  */
     float res_fwhm;       /* image-space resolution model P = A G (lm_res_apply): */
                           /* FWHM in mm, 0 = none.  sens must then be G (lm_sens).*/
                           /* Float-atomic mode only (deterministic is rejected);  */
-                          /* plain image passes, direct projector, no y-fastest   */
-                          /* image copies; not for batches.                      */
+                          /* direct projector; not for batches.                   */
     int32_t sinogram;     /* 1: Alg. 1 (sinogram SPDHG): the events are the bins */
                           /* of lm_sino_setup and mu their counts d_b (0 allowed);*/
                           /* the dual step uses prox with S_b d_b and back-       */
@@ -387,7 +387,8 @@ int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, doubl
                     void* stream);
 
 /* Which image-pass kernel the state uses: 1 plain loads, 2 TMA-staged with
- * the prior's dual step fused in (lm_params.image_kernel). */
+ * the prior's dual step fused in (lm_params.image_kernel), 3 TMA-staged data
+ * passes with plain prior passes (the directional TV prior). */
 int lmspdhg_image_kernel(lm_state* st, int32_t* kind);
 
 /* Which projector the data updates use: 1 direct event kernel, 2 tile-binned

@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(256) image_pass_kernel(const lmh::ImgArgs A)
     __shared__ TileSmem sm;
     const int u = A.u;
     const PassMode m = pass_mode(A, u);
+    if ((m.prior && A.skip_prior) || (m.data && !m.init && A.skip_data)) return;  // the other pass serves it
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) reset_next_slot(A, u);
     for (int64_t t = blockIdx.x; t < n_tiles(A.n[0], A.n[1], A.n[2]); t += gridDim.x)
         image_tile(A, m, u, tile_of(t, A.n[0], A.n[1]), A.x_cur, A.x_nxt_std, A.x_nxt_yf, sm);
@@ -920,6 +921,7 @@ __global__ void __launch_bounds__(256, 2) image_tma_kernel(const lmh::ImgArgs A)
     Pipe p{(uint64_t*)(sm + TmaLayout::bars), 0u, &abort_flag};
     const int u = A.u;
     const PassMode m = pass_mode(A, u);
+    if ((m.prior && A.skip_prior) || (m.data && !m.init && A.skip_data)) return;  // the other pass serves it
     if (blockIdx.x == 0 && threadIdx.x == 0) reset_next_slot(A, u);
     const int64_t n = tma_items(A);
     for (int64_t it = blockIdx.x; it < n; it += gridDim.x)

@@ -10,6 +10,8 @@
 // One pass per axis; a thread computes one output voxel from the 2r + 1
 // inputs along the axis (consecutive threads take consecutive x, so every
 // tap's loads are coalesced and neighbouring outputs share them in L1/L2).
+// Blocks cover row segments (grid.x along x, grid.y the (y, z) rows), so no
+// thread divides its voxel index; taps mirror only near the faces.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -23,33 +25,99 @@ __global__ void __launch_bounds__(256) res_pass_kernel(const float* __restrict__
                                                        const uint16_t* seq, int u, int n_subsets, int pair_out)
 {
     if (seq != nullptr && seq[u] >= n_subsets) return;  // a prior update back-projects nothing
-    const int V = nx * ny * nz;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= V) return;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ix >= nx) return;
+    const int row = blockIdx.y + gridDim.y * blockIdx.z;  // row = iz * ny + iy
+    if (row >= ny * nz) return;
+    const int j = row * nx + ix;
     int c, n, st;
     if (axis == 0) {
-        c = j % nx;
+        c = ix;
         n = nx;
         st = 1;
     } else if (axis == 1) {
-        c = (j / nx) % ny;
+        c = row % ny;
         n = ny;
         st = nx;
     } else {
-        c = j / (nx * ny);
+        c = row / ny;
         n = nz;
         st = nx * ny;
     }
     const int r = w.r;
+    const float* s0 = src + j;
     float acc = 0.0f;
-    for (int k = -r; k <= r; ++k) {
-        int m = c + k;
-        if (m < 0) m = -m - 1;
-        if (m >= n) m = 2 * n - m - 1;
-        acc = fmaf(w.w[k + r], __ldg(src + j + (m - c) * st), acc);
+    if (c >= r && c + r < n) {
+        for (int k = -r; k <= r; ++k) acc = fmaf(w.w[k + r], __ldg(s0 + k * st), acc);
+    } else {
+        for (int k = -r; k <= r; ++k) {
+            int m = c + k;
+            if (m < 0) m = -m - 1;
+            if (m >= n) m = 2 * n - m - 1;
+            acc = fmaf(w.w[k + r], __ldg(s0 + (m - c) * st), acc);
+        }
     }
     // pair_out: the first half of voxel j's (j, j + nx*ny) accumulator pair
     dst[pair_out ? 2 * (int64_t)j : j] = acc;
+}
+
+// The y and z passes with up to 8 taps per side march along their axis: a
+// thread owns one x of one line and a segment of RES_SEG outputs, keeps the
+// 2R + 1 inputs of the current output in registers and loads each input
+// once (the window's first 2R on entry).  Same products in the same order as
+// res_pass_kernel, so the results are identical.
+constexpr int RES_SEG = 32;
+
+__device__ __forceinline__ int mirror(int m, int n) { return m < 0 ? -m - 1 : (m >= n ? 2 * n - m - 1 : m); }
+
+template <int R>
+__global__ void __launch_bounds__(256) res_march_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                                        int nx, int ny, int nz, int axis, lmh::ResAxis w,
+                                                        const uint16_t* seq, int u, int n_subsets, int pair_out)
+{
+    if (seq != nullptr && seq[u] >= n_subsets) return;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ix >= nx) return;
+    const int o = blockIdx.y;  // z of a y line, y of a z line
+    int n, st, base;
+    if (axis == 1) {
+        n = ny;
+        st = nx;
+        base = o * nx * ny + ix;
+    } else {
+        n = nz;
+        st = nx * ny;
+        base = o * nx + ix;
+    }
+    const int c0 = blockIdx.z * RES_SEG;
+    if (c0 >= n) return;
+    const int c1 = min(n, c0 + RES_SEG);
+    float wr[2 * R + 1], v[2 * R + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) wr[k] = w.w[k];
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) v[k + 1] = __ldg(src + base + mirror(c0 - R + k, n) * st);
+    for (int c = c0; c < c1; ++c) {
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) v[k] = v[k + 1];
+        v[2 * R] = __ldg(src + base + mirror(c + R, n) * st);
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wr[k], v[k], acc);
+        const int64_t j = (int64_t)base + (int64_t)c * st;
+        dst[pair_out ? 2 * j : j] = acc;
+    }
+}
+
+// Threads per block: a whole row rounded up to a warp, at most 256.
+int res_block(const lm_grid* g) { return std::min(256, (g->n[0] + 31) / 32 * 32); }
+
+dim3 res_grid(const lm_grid* g)
+{
+    const int rows = g->n[1] * g->n[2];
+    const int gy = std::min(rows, 65535);
+    const int bx = res_block(g);
+    return dim3((g->n[0] + bx - 1) / bx, gy, (rows + gy - 1) / gy);
 }
 
 // The back-projection accumulators as one image: voxel j is the first half of
@@ -72,29 +140,50 @@ __global__ void __launch_bounds__(256) res_fold_kernel(float* __restrict__ acc_s
         const int y0 = (int)((t / tiles_x) % tiles_y) * FT;
         const int z = (int)(t / ((int64_t)tiles_x * tiles_y));
         const bool below = z > 0;
+        // all loads of the thread's rows first (memory-level parallelism), then the clears
+        constexpr int RPT = FT / FR;
         if (acc_yf != nullptr) {
-            for (int r = ty; r < FT; r += FR) {
-                const int xx = x0 + r, yy = y0 + tx;
-                float v = 0.0f;
+            float v[RPT];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int xx = x0 + ty + q * FR, yy = y0 + tx;
+                v[q] = 0.0f;
                 if (xx < nx && yy < ny) {
                     const int64_t k = ((int64_t)z * nx + xx) * ny + yy;
-                    v = acc_yf[2 * k] + (below ? acc_yf[2 * (k - sz) + 1] : 0.0f);
+                    v[q] = acc_yf[2 * k] + (below ? acc_yf[2 * (k - sz) + 1] : 0.0f);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int xx = x0 + ty + q * FR, yy = y0 + tx;
+                if (xx < nx && yy < ny) {
+                    const int64_t k = ((int64_t)z * nx + xx) * ny + yy;
                     acc_yf[2 * k] = 0.0f;
                     if (below) acc_yf[2 * (k - sz) + 1] = 0.0f;
                 }
-                sm[r][tx] = v;
+                sm[ty + q * FR][tx] = v[q];
             }
         }
         __syncthreads();
-        for (int r = ty; r < FT; r += FR) {
+        float v[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int xx = x0 + tx, yy = y0 + ty + q * FR;
+            v[q] = 0.0f;
+            if (xx < nx && yy < ny) {
+                const int64_t j = ((int64_t)z * ny + yy) * nx + xx;
+                v[q] = acc_std[2 * j] + (below ? acc_std[2 * (j - sz) + 1] : 0.0f);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int r = ty + q * FR;
             const int xx = x0 + tx, yy = y0 + r;
             if (xx < nx && yy < ny) {
                 const int64_t j = ((int64_t)z * ny + yy) * nx + xx;
-                float v = acc_std[2 * j] + (below ? acc_std[2 * (j - sz) + 1] : 0.0f);
-                if (acc_yf != nullptr) v += sm[tx][r];
                 acc_std[2 * j] = 0.0f;
                 if (below) acc_std[2 * (j - sz) + 1] = 0.0f;
-                out[j] = v;
+                out[j] = v[q] + (acc_yf != nullptr ? sm[tx][r] : 0.0f);
             }
         }
         __syncthreads();
@@ -141,7 +230,7 @@ int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst,
                const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out)
 {
     const int V = (int)nvox(g);
-    const int blocks = (V + 255) / 256;
+    const dim3 blocks = res_grid(g);
     const int k = p.n_axes;
     if (k == 0) {
         if (src != dst) LM_CUDA(cudaMemcpyAsync(dst, src, (size_t)V * 4, cudaMemcpyDeviceToDevice, st));
@@ -151,15 +240,32 @@ int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst,
     for (int i = 0; i < k; ++i) {
         const bool last = i == k - 1;
         float* out = last ? (in == dst ? t2 : dst) : ((i & 1) ? t2 : t1);
-        res_pass_kernel<<<blocks, 256, 0, st>>>(in, out, g->n[0], g->n[1], g->n[2], p.axis[i], p.ax[i], seq, u,
-                                                n_subsets, (last && out == dst && pair_out) ? 1 : 0);
+        const int po = (last && out == dst && pair_out) ? 1 : 0;
+        const int ax = p.axis[i], r = p.ax[i].r;
+        const int lines = ax == 1 ? g->n[2] : g->n[1];
+        if (ax > 0 && r >= 1 && r <= 8 && lines <= 65535) {
+            const int n = g->n[ax];
+            const dim3 mg((g->n[0] + res_block(g) - 1) / res_block(g), lines, (n + RES_SEG - 1) / RES_SEG);
+#define LM_MARCH(RR)                                                                                             \
+    case RR:                                                                                                     \
+        res_march_kernel<RR><<<mg, res_block(g), 0, st>>>(in, out, g->n[0], g->n[1], g->n[2], ax, p.ax[i], seq, u, \
+                                                          n_subsets, po);                                        \
+        break;
+            switch (r) {
+                LM_MARCH(1) LM_MARCH(2) LM_MARCH(3) LM_MARCH(4) LM_MARCH(5) LM_MARCH(6) LM_MARCH(7) LM_MARCH(8)
+            }
+#undef LM_MARCH
+        } else {
+            res_pass_kernel<<<blocks, res_block(g), 0, st>>>(in, out, g->n[0], g->n[1], g->n[2], ax, p.ax[i], seq, u,
+                                                             n_subsets, po);
+        }
         in = out;
     }
     count_launch(k);
     if (in != dst) {
         // one pass in place: copy the result back (skipped like the pass for a prior update)
-        res_pass_kernel<<<blocks, 256, 0, st>>>(in, dst, g->n[0], g->n[1], g->n[2], 0, ResAxis{0, {1.0f}}, seq, u,
-                                                n_subsets, pair_out ? 1 : 0);
+        res_pass_kernel<<<blocks, res_block(g), 0, st>>>(in, dst, g->n[0], g->n[1], g->n[2], 0, ResAxis{0, {1.0f}}, seq,
+                                                         u, n_subsets, pair_out ? 1 : 0);
         count_launch();
     }
     LM_CUDA(cudaGetLastError());

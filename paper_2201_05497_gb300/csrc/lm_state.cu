@@ -54,6 +54,7 @@ struct lm_state_s {
     TmaMaps* tmaps;   // device copy of the tensor maps (TMA-staged image passes)
     unsigned* err;    // set by a bounded device wait that gave up
     bool tma;         // image passes staged by TMA (grid permitting, unless disabled)
+    bool tma_data;    // directional TV: TMA-staged data passes, plain prior passes
     bool has_res;     // resolution model P = A G: the event kernels read G x from gx / gxyf
     float *gx, *gxyf; // G x in both layouts (float mode; scratch of the back-projection's G)
     ResPlan res;
@@ -221,7 +222,7 @@ ImgArgs base_img_args(const lm_state* st)
     a.s_prior = (float)(st->gamma * (double)st->P.rho / st->knorm);
     a.beta = st->P.beta;
     a.acc_pairs = st->det ? 0 : 1;
-    a.tm = st->tma ? st->tmaps : nullptr;
+    a.tm = (st->tma || st->tma_data) ? st->tmaps : nullptr;
     a.err = st->err;
     a.zlen = st->zlen;
     a.xi = st->P.xi;
@@ -321,8 +322,18 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         // scale slots: update u reads slot (slot0 + u) & 1, its pass clears the other one
         im.slot0 = slot0;
         im.xcur = cur;
-        if (st->tma) launch_image_tma(im, s);
-        else launch_image_pass(im, s);
+        if (st->tma) {
+            launch_image_tma(im, s);
+        } else if (st->tma_data) {
+            // the TMA pass fuses the TV prior only: prior updates of the directional TV take the plain pass
+            ImgArgs d = im, q = im;
+            d.skip_prior = 1;
+            q.skip_data = 1;
+            launch_image_tma(d, s);
+            launch_image_pass(q, s);
+        } else {
+            launch_image_pass(im, s);
+        }
         if (st->has_res) {
             int rc = res_fwd(st, st->x[nxt], s);  // the next update's projections read G x
             if (rc) return rc;
@@ -588,25 +599,22 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     LM_TRY(cudaMemcpyAsync(st->sub_off, sub_off_host, (size_t)(st->n + 1) * 8, cudaMemcpyHostToDevice, s));
     LM_TRY(cudaMemsetAsync(st->err, 0, 16, s));
     st->tma = false;
+    st->tma_data = false;
     st->zlen = 1;
     if (P.image_kernel == 2 && !tma_capable(grid)) {
         set_error("the TMA-staged image pass needs nx, ny multiples of 4 with nx >= 40, ny >= 36");
         return fail(LM_ERR_INVALID_ARG);
     }
-    if (P.image_kernel == 2 && P.xi != nullptr) {
-        set_error("the TMA-staged image pass implements the TV prior only (xi must be NULL)");
-        return fail(LM_ERR_INVALID_ARG);
-    }
     st->has_res = P.res_fwhm > 0.0f;
     if (st->has_res) {
-        if (st->det || P.image_kernel == 2) {
-            set_error("the resolution model runs in float-atomic mode with the plain image passes");
+        if (st->det) {
+            set_error("the resolution model runs in float-atomic mode");
             return fail(LM_ERR_INVALID_ARG);
         }
         rc = res_plan(grid, P.res_fwhm, st->res);
         if (rc) return fail(rc);
     }
-    if (P.image_kernel != 1 && P.xi == nullptr && !st->has_res && tma_capable(grid)) {
+    if (P.image_kernel != 1 && tma_capable(grid)) {
         TmaMaps h;
         rc = encode_tma_maps(grid, st->x, st->w, std::max(1, st->ndim), st->T, st->z, st->zc,
                              st->det ? (void*)st->acci_std : (void*)st->acc_std,
@@ -614,7 +622,8 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         if (rc) return fail(rc);
         LM_TRY(cudaMemcpyAsync(st->tmaps, &h, sizeof(h), cudaMemcpyHostToDevice, s));
         LM_TRY(cudaStreamSynchronize(s));
-        st->tma = true;
+        st->tma = P.xi == nullptr;
+        st->tma_data = P.xi != nullptr;
         st->zlen = tma_zlen(grid);
     }
     if (tof->n_bins > 0) {
@@ -927,7 +936,7 @@ int lmspdhg_image_kernel(lm_state* st, int32_t* kind)
 {
     clear_error();
     LM_CHECK(st && kind, LM_ERR_INVALID_ARG, "NULL argument");
-    *kind = st->tma ? 2 : 1;
+    *kind = st->tma ? 2 : (st->tma_data ? 3 : 1);
     return LM_OK;
 }
 

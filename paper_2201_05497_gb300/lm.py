@@ -625,7 +625,7 @@ class LMSPDHG:
         pk, nseg = C.c_int32(), C.c_int64()
         _check(load_library().lmspdhg_projector(self.h, C.byref(pk), C.byref(nseg)))
         return dict(group=g.value, ms_g8=ms[0], ms_g16=ms[1], ms_g32=ms[2],
-                    image_kernel={1: "plain", 2: "tma"}[kind.value],
+                    image_kernel={1: "plain", 2: "tma", 3: "tma_data"}[kind.value],
                     projector={1: "direct", 2: "tiled"}[pk.value], tile_segments=nseg.value)
 
     def close(self):

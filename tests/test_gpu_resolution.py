@@ -1,7 +1,7 @@
 """GPU parity of the image-space resolution model (P = A G, Eq. (1)'s limited
 spatial resolution) against the FP64 oracle: G itself, and LM-SPDHG (Alg. 2)
-with P = A G for single updates and whole epochs; the modes that do not
-support it refuse it."""
+with P = A G for single updates and whole epochs (TMA-staged and plain image
+passes); the modes that do not support it refuse it."""
 import numpy as np
 import pytest
 
@@ -83,14 +83,15 @@ def test_single_update_matches_oracle(lm, name, sel):
     assert H.rel_l2(g.x().cpu().numpy(), o.x) < 1e-5
     assert H.rel_l2(g.z().cpu().numpy(), o.z) < 1e-5
     assert H.rel_l2(g.w().cpu().numpy(), o.w) < H.REL_L2_IMAGE
-    assert g.tuning()["image_kernel"] == "plain"
+    assert g.tuning()["image_kernel"] == ("tma" if name == "3d_quad" else "plain")
 
 
-@pytest.mark.parametrize("name,epochs", [("2d_small", 3), ("3d_small", 2), ("3d_quad", 2)])
-def test_epochs_match_oracle(lm, name, epochs):
+@pytest.mark.parametrize("name,epochs,image_kernel", [("2d_small", 3, 0), ("3d_small", 2, 0), ("3d_quad", 2, 2),
+                                                       ("3d_quad", 2, 1)])
+def test_epochs_match_oracle(lm, name, epochs, image_kernel):
     c = Case(lm, name)
     o = c.oracle()
-    g = c.gpu()
+    g = c.gpu(image_kernel=image_kernel)
     seq = S.selection_sequence(c.n_sub, 2 * c.n_sub * epochs, seed=3)
     for k in range(epochs):
         s = seq[2 * c.n_sub * k:2 * c.n_sub * (k + 1)]
@@ -104,10 +105,9 @@ def test_epochs_match_oracle(lm, name, epochs):
 
 def test_unsupported_modes_refuse(lm):
     c = Case(lm, "3d_quad", n_events=3000)
-    for kw in (dict(deterministic=True), dict(image_kernel=2)):
-        with pytest.raises(lm.LMError) as ei:
-            c.gpu(**kw)
-        assert ei.value.code == 1
+    with pytest.raises(lm.LMError) as ei:
+        c.gpu(deterministic=True)
+    assert ei.value.code == 1
     g = c.gpu()
     b = lm.Batch(2, c.n_sub)
     with pytest.raises(lm.LMError) as ei:
