@@ -315,9 +315,13 @@ typedef struct {
  * about 136 per event plus per-tile tables. */
 size_t lmspdhg_tile_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets);
 
-/* Device bytes the state needs (images, duals, per-event y and scratch). */
+/* Device bytes the state needs (images, duals, per-event y and scratch) with
+ * the TV prior.  lmspdhg_state_bytes_ex: for the given parameters (the
+ * directional TV prior, lm_params.xi, adds ndim images); lmspdhg_create
+ * checks the buffer against it. */
 size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets,
                            int32_t deterministic);
+size_t lmspdhg_state_bytes_ex(const lm_grid* grid, int64_t n_events, int32_t n_subsets, const lm_params* params);
 
 /* Initialise Alg. 2 (duals, z, step sizes) on events already in subset-contiguous
  * order (from lm_event_setup; the arrays are referenced, not copied, and

@@ -188,11 +188,41 @@ __device__ __noinline__ float prior_dz_dtv(const lmh::ImgArgs& A, const float* w
     return dz;
 }
 
+// dz_j = grad^T D at voxel j for D = P (w+ - w) stored by the directional
+// TV's dual step (components in axis order; same sums as prior_dz_dtv)
+__device__ __forceinline__ float prior_dz_dtv_stored(const lmh::ImgArgs& A, int xx, int yy, int zz, int64_t j)
+{
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const int64_t V = A.V;
+    const float* D = A.dtv_d;
+    float dz = 0.0f;
+    int c = 0;
+    if (nx > 1) {
+        const int64_t o = (int64_t)c * V;
+        if (xx < nx - 1) dz -= D[o + j];
+        if (xx >= 1) dz += D[o + j - 1];
+        ++c;
+    }
+    if (ny > 1) {
+        const int64_t o = (int64_t)c * V;
+        if (yy < ny - 1) dz -= D[o + j];
+        if (yy >= 1) dz += D[o + j - nx];
+        ++c;
+    }
+    if (nz > 1) {
+        const int64_t o = (int64_t)c * V;
+        if (zz < nz - 1) dz -= D[o + j];
+        if (zz >= 1) dz += D[o + j - (int64_t)nx * ny];
+    }
+    return dz;
+}
+
 // dz_j = (K^T (w+ - w))_j, components in axis order for axes with n > 1
 __device__ __forceinline__ float prior_dz(const lmh::ImgArgs& A, const float* wc, const float* wn, int xx, int yy,
                                           int zz, int64_t j)
 {
-    if (A.xi != nullptr) return prior_dz_dtv(A, wc, wn, xx, yy, zz, j);
+    if (A.xi != nullptr)
+        return A.dtv_d != nullptr ? prior_dz_dtv_stored(A, xx, yy, zz, j) : prior_dz_dtv(A, wc, wn, xx, yy, zz, j);
     const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
     const int64_t V = A.V;
     float dz = 0.0f;

@@ -131,6 +131,7 @@ struct EvArgs {
     int prior_only;             // 1: data selections are left to the tile-binned projector
     int acc_pairs;              // 1: acc_std / acc_yf hold (voxel j, voxel j + nx*ny) float pairs
     const float* xi;            // directional TV field [ndim][V], or nullptr (TV)
+    float* dtv_d;               // directional TV: P (w+ - w) of the prior's dual step [ndim][V], or nullptr
     int sino;                   // 1: the events are sinogram bins, mu their counts d_b (Alg. 1);
                                 // 2: the same, with each bin's geometry computed from its index
     const int32_t* g_q;         // sino 2: transaxial pairs of every subset, subset by subset
@@ -295,6 +296,7 @@ struct ImgArgs {
     int zlen;              // z slices per work item
     unsigned* err;         // set when a bounded wait gave up
     const float* xi;       // directional TV field [ndim][V], or nullptr (TV; plain prior passes only)
+    const float* dtv_d;    // directional TV: P (w+ - w) from the dual step, or nullptr (formed here)
     int skip_prior;        // 1: return at once when the update is a prior update
     int skip_data;         // 1: return at once when the update is a data update
 };

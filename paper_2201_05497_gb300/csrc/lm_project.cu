@@ -143,9 +143,22 @@ __device__ __forceinline__ void prior_voxel(const EvArgs& A, const float* __rest
     if (cy >= 0) vy = fmaf(A.s_prior, gy, wc[(int64_t)cy * V + j]);
     if (cz >= 0) vz = fmaf(A.s_prior, gz, wc[(int64_t)cz * V + j]);
     const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), A.beta);
-    if (cx >= 0) wn[(int64_t)cx * V + j] = __fmul_rn(vx, sc);
-    if (cy >= 0) wn[(int64_t)cy * V + j] = __fmul_rn(vy, sc);
-    if (cz >= 0) wn[(int64_t)cz * V + j] = __fmul_rn(vz, sc);
+    const float ox = __fmul_rn(vx, sc), oy = __fmul_rn(vy, sc), oz = __fmul_rn(vz, sc);
+    if (cx >= 0) wn[(int64_t)cx * V + j] = ox;
+    if (cy >= 0) wn[(int64_t)cy * V + j] = oy;
+    if (cz >= 0) wn[(int64_t)cz * V + j] = oz;
+    if (A.dtv_d != nullptr) {
+        // P (w+ - w) for the image pass's K^T (w+ - w) = grad^T P (w+ - w)
+        const float* f = A.xi;
+        float dx = cx >= 0 ? ox - wc[(int64_t)cx * V + j] : 0.0f;
+        float dy = cy >= 0 ? oy - wc[(int64_t)cy * V + j] : 0.0f;
+        float dz = cz >= 0 ? oz - wc[(int64_t)cz * V + j] : 0.0f;
+        dtv_perp(cx >= 0 ? f[(int64_t)cx * V + j] : 0.0f, cy >= 0 ? f[(int64_t)cy * V + j] : 0.0f,
+                 cz >= 0 ? f[(int64_t)cz * V + j] : 0.0f, dx, dy, dz);
+        if (cx >= 0) A.dtv_d[(int64_t)cx * V + j] = dx;
+        if (cy >= 0) A.dtv_d[(int64_t)cy * V + j] = dy;
+        if (cz >= 0) A.dtv_d[(int64_t)cz * V + j] = dz;
+    }
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
@@ -195,6 +208,21 @@ __device__ __forceinline__ void prior_quad(const EvArgs& A, const float* __restr
         ox[k] = __fmul_rn(vx, sc);
         oy[k] = __fmul_rn(vy, sc);
         oz[k] = __fmul_rn(vz, sc);
+    }
+    if (dtv && A.dtv_d != nullptr) {
+        // P (w+ - w) for the image pass's K^T (w+ - w) = grad^T P (w+ - w)
+        float dx[4], dy[4], dz[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            dx[k] = hx ? ox[k] - f4(wx, k) : 0.0f;
+            dy[k] = hy ? oy[k] - f4(wy, k) : 0.0f;
+            dz[k] = hz ? oz[k] - f4(wz, k) : 0.0f;
+            dtv_perp(f4(fx, k), f4(fy, k), f4(fz, k), dx[k], dy[k], dz[k]);
+        }
+        float* D = A.dtv_d;
+        if (hx) *reinterpret_cast<float4*>(D + j) = make_float4(dx[0], dx[1], dx[2], dx[3]);
+        if (hy) *reinterpret_cast<float4*>(D + (int64_t)cy * V + j) = make_float4(dy[0], dy[1], dy[2], dy[3]);
+        if (hz) *reinterpret_cast<float4*>(D + (int64_t)cz * V + j) = make_float4(dz[0], dz[1], dz[2], dz[3]);
     }
     if (hx) *reinterpret_cast<float4*>(wn + j) = make_float4(ox[0], ox[1], ox[2], ox[3]);
     if (hy) *reinterpret_cast<float4*>(wn + (int64_t)cy * V + j) = make_float4(oy[0], oy[1], oy[2], oy[3]);

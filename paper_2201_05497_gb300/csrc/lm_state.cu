@@ -57,6 +57,7 @@ struct lm_state_s {
     bool tma_data;    // directional TV: TMA-staged data passes, plain prior passes
     bool has_res;     // resolution model P = A G: the event kernels read G x from gx / gxyf
     float *gx, *gxyf; // G x in both layouts (float mode; scratch of the back-projection's G)
+    float* dtvd;      // directional TV: P (w+ - w) of the last prior dual step [ndim][V]
     ResPlan res;
     int zlen;         // z slices per TMA work item
     bool tiled;       // data updates by the tile-binned projector
@@ -90,7 +91,7 @@ struct Carve {
     }
 };
 
-void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
+void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det, bool dtv)
 {
     const size_t V = (size_t)nvox(g);
     const int nd = std::max(1, tv_ndim(g));
@@ -115,6 +116,7 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
     // G x for the resolution model, both layouts (8 B per voxel, float mode)
     float* gx = det ? nullptr : F(V);
     float* gxyf = det ? nullptr : F(V);
+    float* dtvd = dtv ? F(nd * V) : nullptr;
     float* y = F((size_t)std::max<int64_t>(N, 1));
     const size_t scr_bytes = std::max<size_t>((size_t)std::max<int64_t>(N, 1) * 4,
                                               std::max(lm_knorm_workspace_bytes(g), objective_scratch_bytes()));
@@ -141,7 +143,7 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det)
         st->y = y; st->scr = scr; st->scr_bytes = scr_bytes; st->sub_off = sub_off; st->seq = seq;
         st->wpar = wpar; st->wbase = wbase; st->maxbits = maxbits; st->queue = queue; st->done = done;
         st->redf = redf; st->redd = redd;
-        st->gx = gx; st->gxyf = gxyf;
+        st->gx = gx; st->gxyf = gxyf; st->dtvd = dtvd;
     }
 }
 
@@ -177,6 +179,7 @@ EvArgs base_ev_args(const lm_state* st)
     a.prior_fused = st->tma ? 1 : 0;
     a.acc_pairs = st->det ? 0 : 1;
     a.xi = st->P.xi;
+    a.dtv_d = st->dtvd;
     a.sino = st->P.sinogram;
     if (st->P.sinogram == 2) {
         a.g_q = st->P.sino_q;
@@ -226,6 +229,7 @@ ImgArgs base_img_args(const lm_state* st)
     a.err = st->err;
     a.zlen = st->zlen;
     a.xi = st->P.xi;
+    a.dtv_d = st->dtvd;
     return a;
 }
 
@@ -513,7 +517,15 @@ size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subs
 {
     if (check_grid(grid) || n_events < 0 || n_subsets < 1) return 0;
     Carve c;
-    carve(nullptr, c, grid, n_events, n_subsets, deterministic != 0);
+    carve(nullptr, c, grid, n_events, n_subsets, deterministic != 0, false);
+    return c.off + 256;
+}
+
+size_t lmspdhg_state_bytes_ex(const lm_grid* grid, int64_t n_events, int32_t n_subsets, const lm_params* params)
+{
+    if (check_grid(grid) || n_events < 0 || n_subsets < 1 || params == nullptr) return 0;
+    Carve c;
+    carve(nullptr, c, grid, n_events, n_subsets, params->deterministic != 0, params->xi != nullptr);
     return c.off + 256;
 }
 
@@ -546,7 +558,7 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
              "subset offsets must span [0, n)");
     for (int k = 0; k < P.n_subsets; ++k)
         LM_CHECK(sub_off_host[k + 1] >= sub_off_host[k], LM_ERR_INVALID_ARG, "subset offsets must not decrease");
-    const size_t need = lmspdhg_state_bytes(grid, ev->n, P.n_subsets, P.deterministic);
+    const size_t need = lmspdhg_state_bytes_ex(grid, ev->n, P.n_subsets, &P);
     LM_CHECK(state_bytes >= need, LM_ERR_NOMEM, "state buffer needs %zu bytes", need);
 
     lm_state* st = new lm_state();
@@ -572,7 +584,7 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->sub_off_h.assign(sub_off_host, sub_off_host + P.n_subsets + 1);
     Carve c;
     c.base = (char*)(((uintptr_t)state_buf + 255) / 256 * 256);
-    carve(st, c, grid, ev->n, st->n, st->det);
+    carve(st, c, grid, ev->n, st->n, st->det, P.xi != nullptr);
     st->exec = nullptr;
     st->have_graph = false;
     st->xpar = 0;

@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lm_event_setup": ([P(lm_scanner), P(lm_tof), P(lm_events), I32, V, V, V, V, V, V, P(I64), V, SZ, V],
                            C.c_int),
         "lmspdhg_state_bytes": ([P(lm_grid), I64, I32, I32], SZ),
+        "lmspdhg_state_bytes_ex": ([P(lm_grid), I64, I32, P(lm_params)], SZ),
         "lmspdhg_create": ([P(V), P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, P(I64), V, V,
                             P(lm_params), V, SZ, V], C.c_int),
         "lmspdhg_updates": ([V, P(C.c_uint16), I32, V], C.c_int),
@@ -530,10 +531,6 @@ class LMSPDHG:
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.xi = xi  # directional TV field (referenced by the state), None = TV
         self.n_subsets = n_subsets
-        nbytes = L.lmspdhg_state_bytes(C.byref(geo.g), pe.events.n, int(n_subsets), int(deterministic))
-        if nbytes == 0:
-            raise LMError(1, "invalid state size")
-        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=x0.device)
         # projector of the data updates: "direct" (the event kernel) or "tiled" (the
         # tile-binned projector, TOF data in float-atomic mode); "auto" takes the tiled
         # one when its buffer needs at most a quarter of the free device memory
@@ -550,6 +547,10 @@ class LMSPDHG:
                                 int(sinogram), _ptr(getattr(pe, "q", None)), _ptr(getattr(pe, "qoff", None)),
                                 _ptr(sino_lorf), float(sino_s))
         self._keep = (sino_lorf,)
+        nbytes = L.lmspdhg_state_bytes_ex(C.byref(geo.g), pe.events.n, int(n_subsets), C.byref(self.params))
+        if nbytes == 0:
+            raise LMError(1, "invalid state size")
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=x0.device)
         self._ev = pe.events.desc()
         self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
         h = C.c_void_p()

@@ -159,10 +159,11 @@ def test_generated_layout_equals_stored(lm, name):
     mu_st = pe.mu.view(torch.int16).cpu().numpy().view(np.uint16)
     mu_gen = gen.mu.view(torch.int16).cpu().numpy().view(np.uint16)[:c.NB]
     np.testing.assert_array_equal(mu_gen, mu_st)
-    a, _ = c.gpu(pe=pe, deterministic=True)
+    # one lane-group width for both (the width sets the order of each event's forward sum)
+    a, _ = c.gpu(pe=pe, deterministic=True, group=32)
     sens = torch.from_numpy(c.sens_or.astype(np.float32)).cuda()
     b = lm.LMSPDHG(c.geo_g, gen, sens, torch.from_numpy(c.x0).cuda(), beta=c.wl.beta, n_subsets=c.n_sub,
-                   gamma=c.gamma, rho=0.999, knorm=c.knorm, deterministic=True, kahan=True, group=0,
+                   gamma=c.gamma, rho=0.999, knorm=c.knorm, deterministic=True, kahan=True, group=32,
                    projector="direct", sinogram=2, sino_s=float(c.s[0]), sino_lorf=torch.from_numpy(c.lf).cuda())
     seq = S.selection_sequence(c.n_sub, 4 * c.n_sub, seed=3)
     for k in range(2):
