@@ -43,7 +43,8 @@ struct Ws {
     float* w;
     float* ubar;   // extrapolated primal iterate
     float* q;      // dual iterate [ndim][V]
-    float* acc_yf; // y-fastest accumulator of the EM back-projection
+    float* pair_std; // the EM back-projection's (voxel j, voxel j + nx*ny) float pairs, x-fastest
+    float* pair_yf;  // the same, y-fastest (both zero between steps: the fold clears them)
     float* x_yf;   // y-fastest copy of x for the EM gathers
     float* tof_tab; // the TOF kernel tabulated for the event kernel (TOF_TAB_N + 1 floats)
     Sched* sc;
@@ -87,7 +88,8 @@ size_t ws_layout(const lm_grid* g, Ws* w, void* base)
     t.w = (float*)take(V * 4);
     t.ubar = (float*)take(V * 4);
     t.q = (float*)take((size_t)nd * V * 4);
-    t.acc_yf = (float*)take(V * 4);
+    t.pair_std = (float*)take(2 * V * 4);
+    t.pair_yf = (float*)take(2 * V * 4);
     t.x_yf = (float*)take(V * 4);
     t.tof_tab = (float*)take((size_t)(TOF_TAB_N + 1) * 4);
     t.sc = (Sched*)take(sizeof(Sched));
@@ -150,10 +152,14 @@ __global__ void tof_tab_kernel(float* tab, double W, double D, double s)
     tab[k] = (float)(0.5 * (erf((tau + 0.5 * D) / s) - erf((tau - 0.5 * D) / s)));
 }
 
-// Clears the work counters and tabulates the TOF kernel for the EM steps.
-int em_prepare(const lm_tof* tof, const Ws& W, cudaStream_t st)
+// Clears the work counters and the pair accumulators and tabulates the TOF
+// kernel for the EM steps.
+int em_prepare(const lm_grid* grid, const lm_tof* tof, const Ws& W, cudaStream_t st)
 {
     LM_CUDA(cudaMemsetAsync(W.sc, 0, 16, st));
+    const size_t V = (size_t)nvox(grid);
+    LM_CUDA(cudaMemsetAsync(W.pair_std, 0, 2 * V * 4, st));
+    LM_CUDA(cudaMemsetAsync(W.pair_yf, 0, 2 * V * 4, st));
     if (tof->n_bins > 0) {
         const double sig = tof->sigma_mm;
         tof_tab_kernel<<<(TOF_TAB_N + 256) / 256, 256, 0, st>>>(W.tof_tab, (double)tof->n_sigma * sig,
@@ -421,15 +427,16 @@ int check_common(const lm_grid* grid, void* ws, size_t ws_bytes, int iters, doub
 }
 
 // Back-projection of c_e / (c_e J_e x + s_e) over events [e0, e1) into W.z
-// (overwritten), then the fold of em_fold_kernel.
+// (overwritten; scattered into the pair accumulators of both layouts like the
+// LM-SPDHG data update, then folded into one image), then em_fold_kernel.
 int em_step(const lm_scanner* sc, const lm_grid* grid, const Geo& G, const lm_events* ev, int64_t e0, int64_t e1,
             int n_subsets, const float* sens, float* x, float beta, const Ws& W, cudaStream_t st)
 {
     const size_t V = (size_t)nvox(grid);
     const bool two_d = grid->n[2] == 1 && sc->n_rings == 1;  // single-ring scanner in the image plane
     const bool use_yf = grid->n[1] > 1;
-    LM_CUDA(cudaMemsetAsync(W.z, 0, V * 4, st));
     if (beta > 0.0f) LM_CUDA(cudaMemsetAsync(&W.sc->gam_nbits, 0, 4, st));
+    if (e1 <= e0) LM_CUDA(cudaMemsetAsync(W.z, 0, V * 4, st));
     if (e1 > e0) {
         EvArgs a;
         std::memset(&a, 0, sizeof(a));
@@ -440,12 +447,12 @@ int em_step(const lm_scanner* sc, const lm_grid* grid, const Geo& G, const lm_ev
         a.tof = ev->tof;
         a.corr = ev->corr;
         a.contam = ev->contam;
-        a.acc_std = W.z;
+        a.acc_std = W.pair_std;
+        a.acc_pairs = 1;
         if (use_yf) {
             launch_transpose_to_yf(grid, x, W.x_yf, st);
             a.x_yf = W.x_yf;
-            a.acc_yf = W.acc_yf;
-            LM_CUDA(cudaMemsetAsync(W.acc_yf, 0, V * 4, st));
+            a.acc_yf = W.pair_yf;
         }
         a.e_begin = e0;
         a.e_end = e1;
@@ -457,7 +464,7 @@ int em_step(const lm_scanner* sc, const lm_grid* grid, const Geo& G, const lm_ev
         a.stepmax = 2.0f * std::fmax(grid->h[0], std::fmax(grid->h[1], grid->h[2]));
         int rc = launch_events(EV_EM, two_d, a, ev_grid_g(EV_EM, two_d, a.group), st);
         LM_CHECK(rc == LM_OK, rc, "EM back-projection launch failed");
-        if (use_yf) launch_add_yf_to_std(grid, W.z, W.acc_yf, st);
+        launch_res_fold(grid, W.pair_std, W.pair_yf, W.z, nullptr, 0, 0, st);
     }
     const Axes ax = axes_of(grid);
     em_fold_kernel<<<voxel_grid((int64_t)V), 256, 0, st>>>(x, W.z, sens, W.w, W.ubar, W.q, std::max(1, ax.nd),
@@ -508,7 +515,7 @@ int lm_emtv_em_step(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof
     const size_t V = (size_t)nvox(grid);
     // work on a copy of x so that the fold (which writes x = z without a prior) leaves x untouched
     LM_CUDA(cudaMemcpyAsync(z, x, V * 4, cudaMemcpyDeviceToDevice, st));
-    rc = em_prepare(tof, W, st);
+    rc = em_prepare(grid, tof, W, st);
     if (rc) return rc;
     rc = em_step(sc, grid, G, ev, 0, ev->n, n_subsets, sens, z, 0.0f, W, st);
     if (rc) return rc;
@@ -559,7 +566,7 @@ int lm_emtv_epoch(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, 
     Ws W;
     ws_layout(grid, &W, ws);
     cudaStream_t st = S(stream);
-    rc = em_prepare(tof, W, st);
+    rc = em_prepare(grid, tof, W, st);
     if (rc) return rc;
     for (int i = 0; i < n_subsets; ++i) {
         rc = em_step(sc, grid, G, ev_perm, sub_off_host[i], sub_off_host[i + 1], n_subsets, sens, x, beta, W, st);
