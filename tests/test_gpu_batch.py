@@ -121,3 +121,50 @@ def test_batch_outlives_its_first_state(lm):
     for i, k in enumerate((1, 2)):
         np.testing.assert_array_equal(states[k].x().cpu().numpy(), alone[i])
     b.close()
+
+
+@pytest.mark.parametrize("mode", ["dtv", "sinogram"])
+def test_batch_of_prior_and_algorithm_variants(lm, mode):
+    """Frames with the directional TV prior, or sinogram SPDHG frames, run in a
+    batch give each frame's lone result bit for bit (deterministic mode): the
+    batch reads every per-frame option from the frame's own argument tables."""
+    wl, geo, sens, frames = _frames(lm, "3d_quad", [12000, 5000], True)
+    n = wl.n_subsets
+    E = 2
+    seqs = [S.selection_sequence(n, 2 * n * E, seed=7 + k) for k in range(len(frames))]
+    kw = dict(beta=0.1, n_subsets=n, knorm=H.knorm_closed(wl.grid.n), deterministic=True, group=16,
+              projector="direct")
+    extra = []
+    if mode == "dtv":
+        act = torch.from_numpy(wl.phantom.voxelised(wl.grid, supersample=1)).cuda()
+        xi = lm.dtv_field(geo, (act.max() - act).contiguous(), 0.01)
+        kw.update(xi=xi, image_kernel=1)
+        extra.append(xi)
+
+    def make(k):
+        dev, x0 = frames[k]
+        if mode == "sinogram":
+            gen = lm.sino_count(geo, dev, n)
+            lf = torch.from_numpy(S.lor_attenuation(wl.scanner, wl.phantom)).cuda()
+            extra.append((gen, lf))
+            return lm.LMSPDHG(geo, gen, sens, x0, sinogram=2, sino_s=float(dev.contam[0].item()), sino_lorf=lf,
+                              image_kernel=1, **kw)
+        pe = lm.event_setup(geo, dev, n)
+        return lm.LMSPDHG(geo, pe, sens, x0, **kw)
+
+    alone = []
+    for k in range(len(frames)):
+        st = make(k)
+        for e in range(E):
+            st.epoch(seqs[k][2 * n * e:2 * n * (e + 1)])
+        alone.append(st.x().cpu().numpy())
+        st.close()
+    states = [make(k) for k in range(len(frames))]
+    b = lm.Batch(2, n)
+    for k in range(len(frames)):
+        b.set(k, states[k])
+    for e in range(E):
+        b.epoch({k: seqs[k][2 * n * e:2 * n * (e + 1)] for k in range(len(frames))})
+    for k in range(len(frames)):
+        np.testing.assert_array_equal(states[k].x().cpu().numpy(), alone[k])
+    b.close()
