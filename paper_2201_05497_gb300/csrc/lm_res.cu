@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(256) res_march_kernel(const float* __restrict_
     for (int k = 0; k <= 2 * R; ++k) wr[k] = w.w[k];
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) v[k + 1] = __ldg(src + base + mirror(c0 - R + k, n) * st);
+    // unrolled so that several outputs' loads are in flight per thread
+#pragma unroll 4
     for (int c = c0; c < c1; ++c) {
 #pragma unroll
         for (int k = 0; k < 2 * R; ++k) v[k] = v[k + 1];
