@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) res_pass_kernel(const float* __restrict__
 // 2R + 1 inputs of the current output in registers and loads each input
 // once (the window's first 2R on entry).  Same products in the same order as
 // res_pass_kernel, so the results are identical.
-constexpr int RES_SEG = 32;
+constexpr int RES_SEG = 16;
 
 __device__ __forceinline__ int mirror(int m, int n) { return m < 0 ? -m - 1 : (m >= n ? 2 * n - m - 1 : m); }
 
@@ -108,6 +108,48 @@ __global__ void __launch_bounds__(256) res_march_kernel(const float* __restrict_
         for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wr[k], v[k], acc);
         const int64_t j = (int64_t)base + (int64_t)c * st;
         dst[pair_out ? 2 * j : j] = acc;
+    }
+}
+
+// The x pass with up to 8 taps per side: taps unrolled with the weights and
+// the (mirrored) tap offsets in registers, RES_ROWS rows per thread so that
+// their loads are in flight together.  Same products in the same order as
+// res_pass_kernel, so the results are identical.
+constexpr int RES_ROWS = 4;
+
+template <int R>
+__global__ void __launch_bounds__(256) res_row_kernel(const float* __restrict__ src, float* __restrict__ dst, int nx,
+                                                      int rows, lmh::ResAxis w, const uint16_t* seq, int u,
+                                                      int n_subsets, int pair_out)
+{
+    if (seq != nullptr && seq[u] >= n_subsets) return;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ix >= nx) return;
+    const int row0 = (blockIdx.y + gridDim.y * blockIdx.z) * RES_ROWS;
+    if (row0 >= rows) return;
+    float wr[2 * R + 1];
+    int off[2 * R + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) {
+        wr[k] = w.w[k];
+        off[k] = mirror(ix - R + k, nx) - ix;
+    }
+    float acc[RES_ROWS];
+#pragma unroll
+    for (int q = 0; q < RES_ROWS; ++q) {
+        acc[q] = 0.0f;
+        if (row0 + q < rows) {
+            const float* s0 = src + (int64_t)(row0 + q) * nx + ix;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) acc[q] = fmaf(wr[k], __ldg(s0 + off[k]), acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RES_ROWS; ++q) {
+        if (row0 + q < rows) {
+            const int64_t j = (int64_t)(row0 + q) * nx + ix;
+            dst[pair_out ? 2 * j : j] = acc[q];
+        }
     }
 }
 
@@ -245,7 +287,20 @@ int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst,
         const int po = (last && out == dst && pair_out) ? 1 : 0;
         const int ax = p.axis[i], r = p.ax[i].r;
         const int lines = ax == 1 ? g->n[2] : g->n[1];
-        if (ax > 0 && r >= 1 && r <= 8 && lines <= 65535) {
+        if (ax == 0 && r >= 1 && r <= 8) {
+            const int rows = g->n[1] * g->n[2];
+            const int groups = (rows + RES_ROWS - 1) / RES_ROWS;
+            const int gy = std::min(groups, 65535);
+            const dim3 rg((g->n[0] + res_block(g) - 1) / res_block(g), gy, (groups + gy - 1) / gy);
+#define LM_ROW(RR)                                                                                             \
+    case RR:                                                                                                   \
+        res_row_kernel<RR><<<rg, res_block(g), 0, st>>>(in, out, g->n[0], rows, p.ax[i], seq, u, n_subsets, po); \
+        break;
+            switch (r) {
+                LM_ROW(1) LM_ROW(2) LM_ROW(3) LM_ROW(4) LM_ROW(5) LM_ROW(6) LM_ROW(7) LM_ROW(8)
+            }
+#undef LM_ROW
+        } else if (ax > 0 && r >= 1 && r <= 8 && lines <= 65535) {
             const int n = g->n[ax];
             const dim3 mg((g->n[0] + res_block(g) - 1) / res_block(g), lines, (n + RES_SEG - 1) / RES_SEG);
 #define LM_MARCH(RR)                                                                                             \
