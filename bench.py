@@ -427,18 +427,23 @@ def run_gpu(args):
             "achieved_gbs": (b_gather + b_atomic) / t / 1e9, "peak_gbs": eff_peak,
             "frac": ((b_gather + b_atomic) / t / 1e9) / eff_peak,
             "hbm_event_stream_gbs": b_events / t / 1e9, "hbm_frac": b_events / t / 1e9 / hbm_peak}
-    fused = st.tuning()["image_kernel"] == "tma"
+    # the TMA pass fuses the TV's dual step; the directional TV's stays in the event kernel
+    fused = st.tuning()["image_kernel"] == "tma" and xi is None
     if fused:
         # TMA-staged passes: the prior's dual step runs inside the image pass; the event
         # kernel launched for a prior update only reads the selection and returns
         # data pass: float accumulators are z pairs (8 B read + 8 B cleared per layout) unless deterministic
         rows = [("event_kernel_prior_update_idle", 1, 0), ("image_pass_data_tma", 2, 48 if args.deterministic else 64),
                 ("prior_update_fused_tma", 3, 32 + 8 * nd)]
+    elif xi is not None:
+        # directional TV: the dual step reads x, w and the field and writes w+ and D = P(w+ - w);
+        # the prior pass reads D (nd floats per voxel) in place of w and w+
+        tma = st.tuning()["image_kernel"] == "tma"
+        rows = [("prior_dual", 1, 4 + 16 * nd), ("image_pass_data", 2, 48 if args.deterministic else 64),
+                ("image_pass_prior_tma" if tma else "image_pass_prior", 3, 32 + 4 * nd)]
     else:
-        # the directional TV also reads its field (nd floats per voxel) in both prior kernels
-        fb = 4 * nd if xi is not None else 0
-        rows = [("prior_dual", 1, 4 + 8 * nd + fb), ("image_pass_data", 2, 48 if args.deterministic else 64),
-                ("image_pass_prior", 3, 32 + 8 * nd + fb)]
+        rows = [("prior_dual", 1, 4 + 8 * nd), ("image_pass_data", 2, 48 if args.deterministic else 64),
+                ("image_pass_prior", 3, 32 + 8 * nd)]
     for key, idx, bpv in rows:
         ms, n = prof[list(prof.keys())[idx]]
         if n:

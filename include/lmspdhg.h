@@ -275,9 +275,12 @@ typedef struct {
                           /* of subset 0 with each width (autotuner)             */
     int32_t image_kernel; /* image passes: 0 auto (TMA-staged where the grid has */
                           /* nx, ny multiples of 4, nx >= 40, ny >= 36, with the  */
-                          /* prior's dual step fused in; plain loads otherwise),  */
-                          /* 1 plain loads, 2 TMA-staged (LM_ERR_INVALID_ARG if  */
-                          /* the grid does not allow it).  Same results.          */
+                          /* TV's dual step fused in, the directional TV's D =    */
+                          /* P(w+ - w) staged from its dual step; plain loads     */
+                          /* otherwise), 1 plain loads, 2 TMA-staged, 3 TMA-      */
+                          /* staged data passes with plain prior passes (2 and 3: */
+                          /* LM_ERR_INVALID_ARG if the grid does not allow it;    */
+                          /* other values: LM_ERR_INVALID_ARG).  Same results.    */
     void* tile_buf;       /* device buffer of lmspdhg_tile_bytes() bytes for the  */
     size_t tile_bytes;    /* tile-binned projector of the data updates, or NULL:  */
                           /* used for TOF data in float-atomic mode (the batch    */
@@ -390,9 +393,10 @@ int lmspdhg_reinit(lm_state* st, const float* x0, void* stream);
 int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, double* ms4, int64_t* n4,
                     void* stream);
 
-/* Which image-pass kernel the state uses: 1 plain loads, 2 TMA-staged with
- * the prior's dual step fused in (lm_params.image_kernel), 3 TMA-staged data
- * passes with plain prior passes (the directional TV prior). */
+/* Which image-pass kernel the state uses (lm_params.image_kernel): 1 plain
+ * loads, 2 TMA-staged (the TV's dual step fused in; the directional TV's
+ * dual step stays in the event kernel and the pass stages its D), 3
+ * TMA-staged data passes with plain prior passes. */
 int lmspdhg_image_kernel(lm_state* st, int32_t* kind);
 
 /* Which projector the data updates use: 1 direct event kernel, 2 tile-binned

@@ -621,7 +621,8 @@ __device__ __forceinline__ Item item_of(const lmh::ImgArgs& A, int64_t it)
 }
 
 // Copies of one slice (thread 0).  Prior: x slices z (first only) and z+1
-// with halo, w(z) with halo and, for slices the block owns, T, z, zc.
+// with halo, w(z) (the directional TV: D(z)) with halo and, for slices the
+// block owns, T, z, zc.
 // Data: both accumulators, x, T, z, zc of the tile.
 __device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, int xcur, int wp, uint8_t* sm, int s,
                                             int z, int zs, const Item& I, bool first, uint64_t* bar)
@@ -632,7 +633,7 @@ __device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, i
     if (first) {
         if (prior) {
             tmap_acquire(&M->xh[xcur]);
-            tmap_acquire(&M->w[wp]);
+            tmap_acquire(A.dtv_d != nullptr ? &M->dtvd : &M->w[wp]);
         } else {
             tmap_acquire(&M->acc_std);
             tmap_acquire(&M->acc_yf);
@@ -652,7 +653,9 @@ __device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, i
         if (first) tma_load_3d(sm + TmaLayout::xh + ((z - zs) % 3) * TmaLayout::xh_sz, xm, I.x0 - 4, I.y0 - 1, z, bar + s);
         tma_load_3d(sm + TmaLayout::xh + ((z + 1 - zs) % 3) * TmaLayout::xh_sz, xm, I.x0 - 4, I.y0 - 1, z + 1,
                     bar + s);
-        tma_load_4d(st + TmaLayout::p_wc, &M->w[wp], I.x0 - 4, I.y0 - 1, z, 0, bar + s);
+        // the directional TV stages D = P (w+ - w) from its dual step in w's place
+        tma_load_4d(st + TmaLayout::p_wc, A.dtv_d != nullptr ? &M->dtvd : &M->w[wp], I.x0 - 4, I.y0 - 1, z, 0,
+                    bar + s);
         if (own) {
             tma_load_3d(st + TmaLayout::p_T, &M->T, I.x0, I.y0, z, bar + s);
             tma_load_3d(st + TmaLayout::p_z, &M->z, I.x0, I.y0, z, bar + s);
@@ -727,12 +730,19 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
     float* XO = (float*)(sm + TmaLayout::xo);
     float* wn = A.w_nxt[wp];
     const float sp = A.s_prior, beta = A.beta;
+    const bool dtv = A.dtv_d != nullptr;
     // w+ = v / max(1, |v|/beta), v = w + S K x, over the tile (4 points per
-    // thread) and its -1 halo (row y0-1 and column x0-1: 65 points)
+    // thread) and its -1 halo (row y0-1 and column x0-1: 65 points); the
+    // directional TV's dual step has run already and left D = P (w+ - w)
     auto wplus = [&](int ex, int ey, bool tile_pt) {
         const int ix = I.x0 - 1 + ex, iy = I.y0 - 1 + ey;
         float dx = 0.0f, dy = 0.0f, dzc = 0.0f;
-        if (ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
+        if (dtv && ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
+            const int wb = ey * WBW + ex + 3;
+            dx = WC[wb];
+            dy = WC[WBW * WBH + wb];
+            if (hz) dzc = WC[2 * WBW * WBH + wb];
+        } else if (ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
             const int xb = ey * XHW + ex + 3;
             const int wb = ey * WBW + ex + 3;
             const float xc = X0[xb];
@@ -1561,7 +1571,7 @@ static int encode_one(CUtensorMap* m, CUtensorMapDataType t, int rank, void* bas
 }
 
 int encode_tma_maps(const lm_grid* g, float* const x[2], float* const w[2], int ndim, float* T, float* z, float* zc,
-                    void* acc_std, void* acc_yf, bool det, TmaMaps* out)
+                    void* acc_std, void* acc_yf, bool det, float* dtvd, TmaMaps* out)
 {
     LM_CHECK(tma_capable(g), LM_ERR_INVALID_ARG, "grid not supported by the TMA-staged image pass");
     LM_CHECK(encoder() != nullptr, LM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -1579,6 +1589,7 @@ int encode_tma_maps(const lm_grid* g, float* const x[2], float* const w[2], int 
         const cuuint64_t ws[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
         const cuuint32_t wb[4] = {WBW, WBH, 1, (cuuint32_t)ndim};
         if ((rc = encode_one(&out->w[k], F32, 4, w[k], wd, ws, wb))) return rc;
+        if (k == 0 && dtvd != nullptr && (rc = encode_one(&out->dtvd, F32, 4, dtvd, wd, ws, wb))) return rc;
     }
     if ((rc = encode_one(&out->T, F32, 3, T, dims, strides, box_t))) return rc;
     if ((rc = encode_one(&out->z, F32, 3, z, dims, strides, box_t))) return rc;

@@ -241,10 +241,11 @@ struct alignas(128) TmaMaps {
     CUtensorMap T, z, zc;  // box {32, 32, 1}
     CUtensorMap acc_std;   // float z pairs (2nx, ny, nz), box {64, 32, 1}; u64 (nx, ny, nz) when deterministic
     CUtensorMap acc_yf;    // the same in the y-fastest layout (2ny, nx, nz) / (ny, nx, nz)
+    CUtensorMap dtvd;      // directional TV: D = P (w+ - w), shape and box of w (unset without the field)
 };
 bool tma_capable(const lm_grid* g);
 int encode_tma_maps(const lm_grid* g, float* const x[2], float* const w[2], int ndim, float* T, float* z, float* zc,
-                    void* acc_std, void* acc_yf, bool det, TmaMaps* out);
+                    void* acc_std, void* acc_yf, bool det, float* dtvd, TmaMaps* out);
 
 struct ImgArgs {
     int n[3];

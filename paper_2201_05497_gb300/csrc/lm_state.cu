@@ -54,7 +54,7 @@ struct lm_state_s {
     TmaMaps* tmaps;   // device copy of the tensor maps (TMA-staged image passes)
     unsigned* err;    // set by a bounded device wait that gave up
     bool tma;         // image passes staged by TMA (grid permitting, unless disabled)
-    bool tma_data;    // directional TV: TMA-staged data passes, plain prior passes
+    bool tma_data;    // TMA-staged data passes, plain prior passes (image_kernel 3)
     bool has_res;     // resolution model P = A G: the event kernels read G x from gx / gxyf
     float *gx, *gxyf; // G x in both layouts (float mode; scratch of the back-projection's G)
     float* dtvd;      // directional TV: P (w+ - w) of the last prior dual step [ndim][V]
@@ -147,6 +147,11 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det,
     }
 }
 
+// The TMA-staged prior pass computes the TV's dual step itself; the
+// directional TV's dual step (with its field) stays in the event kernel,
+// which stores D = P (w+ - w) for the pass.
+bool tma_fuses_prior(const lm_state* st) { return st->tma && st->dtvd == nullptr; }
+
 EvArgs base_ev_args(const lm_state* st)
 {
     EvArgs a;
@@ -176,7 +181,7 @@ EvArgs base_ev_args(const lm_state* st)
     a.ndim = st->ndim;
     a.tof_tab = st->tof.n_bins > 0 ? st->tof_tab : nullptr;
     a.group = st->group;
-    a.prior_fused = st->tma ? 1 : 0;
+    a.prior_fused = tma_fuses_prior(st) ? 1 : 0;
     a.acc_pairs = st->det ? 0 : 1;
     a.xi = st->P.xi;
     a.dtv_d = st->dtvd;
@@ -286,8 +291,8 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
             t.gamma_rho = (float)(st->gamma * (double)st->P.rho);
             int rc = launch_tile_update(t, st->two_d, s);
             LM_CHECK(rc == LM_OK, rc, "tile data update launch failed");
-            if (!st->tma) {
-                // the plain image pass needs w+ from the event kernel's prior branch
+            if (!tma_fuses_prior(st)) {
+                // the image pass needs w+ (and D) from the event kernel's prior branch
                 a.prior_only = 1;
                 rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
                 LM_CHECK(rc == LM_OK, rc, "prior update launch failed");
@@ -329,7 +334,7 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         if (st->tma) {
             launch_image_tma(im, s);
         } else if (st->tma_data) {
-            // the TMA pass fuses the TV prior only: prior updates of the directional TV take the plain pass
+            // TMA-staged data passes, plain prior passes
             ImgArgs d = im, q = im;
             d.skip_prior = 1;
             q.skip_data = 1;
@@ -613,7 +618,11 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->tma = false;
     st->tma_data = false;
     st->zlen = 1;
-    if (P.image_kernel == 2 && !tma_capable(grid)) {
+    if (P.image_kernel < 0 || P.image_kernel > 3) {
+        set_error("image_kernel must be 0, 1, 2 or 3");
+        return fail(LM_ERR_INVALID_ARG);
+    }
+    if ((P.image_kernel == 2 || P.image_kernel == 3) && !tma_capable(grid)) {
         set_error("the TMA-staged image pass needs nx, ny multiples of 4 with nx >= 40, ny >= 36");
         return fail(LM_ERR_INVALID_ARG);
     }
@@ -630,12 +639,12 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         TmaMaps h;
         rc = encode_tma_maps(grid, st->x, st->w, std::max(1, st->ndim), st->T, st->z, st->zc,
                              st->det ? (void*)st->acci_std : (void*)st->acc_std,
-                             st->det ? (void*)st->acci_yf : (void*)st->acc_yf, st->det, &h);
+                             st->det ? (void*)st->acci_yf : (void*)st->acc_yf, st->det, st->dtvd, &h);
         if (rc) return fail(rc);
         LM_TRY(cudaMemcpyAsync(st->tmaps, &h, sizeof(h), cudaMemcpyHostToDevice, s));
         LM_TRY(cudaStreamSynchronize(s));
-        st->tma = P.xi == nullptr;
-        st->tma_data = P.xi != nullptr;
+        st->tma = P.image_kernel != 3;
+        st->tma_data = P.image_kernel == 3;
         st->zlen = tma_zlen(grid);
     }
     if (tof->n_bins > 0) {

@@ -123,7 +123,7 @@ def test_batch_outlives_its_first_state(lm):
     b.close()
 
 
-@pytest.mark.parametrize("mode", ["dtv", "sinogram"])
+@pytest.mark.parametrize("mode", ["dtv", "dtv_plain", "sinogram"])
 def test_batch_of_prior_and_algorithm_variants(lm, mode):
     """Frames with the directional TV prior, or sinogram SPDHG frames, run in a
     batch give each frame's lone result bit for bit (deterministic mode): the
@@ -135,10 +135,11 @@ def test_batch_of_prior_and_algorithm_variants(lm, mode):
     kw = dict(beta=0.1, n_subsets=n, knorm=H.knorm_closed(wl.grid.n), deterministic=True, group=16,
               projector="direct")
     extra = []
-    if mode == "dtv":
+    if mode.startswith("dtv"):
         act = torch.from_numpy(wl.phantom.voxelised(wl.grid, supersample=1)).cuda()
         xi = lm.dtv_field(geo, (act.max() - act).contiguous(), 0.01)
-        kw.update(xi=xi, image_kernel=1)
+        # TMA-staged passes on this grid unless plain ones are asked for
+        kw.update(xi=xi, image_kernel=1 if mode == "dtv_plain" else 0)
         extra.append(xi)
 
     def make(k):

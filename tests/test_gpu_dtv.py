@@ -115,8 +115,8 @@ def test_single_update_matches_oracle(lm, name, sel):
     assert H.rel_l2(g.x().cpu().numpy(), o.x) < 1e-5
     assert H.rel_l2(g.z().cpu().numpy(), o.z) < 1e-5
     assert H.rel_l2(g.w().cpu().numpy(), o.w) < H.REL_L2_IMAGE
-    # grids the TMA pass takes (3d_quad) stage the data passes; prior passes stay plain
-    assert g.tuning()["image_kernel"] == ("tma_data" if name == "3d_quad" else "plain")
+    # grids the TMA pass takes (3d_quad) stage every pass (the prior's with D from the dual step)
+    assert g.tuning()["image_kernel"] == ("tma" if name == "3d_quad" else "plain")
 
 
 @pytest.mark.parametrize("name,epochs", [("2d_small", 3), ("3d_small", 2), ("3d_quad", 2)])
@@ -156,18 +156,20 @@ def test_zero_field_is_tv_bit_for_bit(lm):
     assert a.objective() == b.objective()
 
 
-def test_tma_data_passes_equal_plain_passes(lm):
-    """TMA-staged data passes with plain prior passes (the DTV layout on grids
-    the TMA pass takes) equal all-plain passes bit for bit (deterministic)."""
+def test_tma_passes_equal_plain_passes(lm):
+    """TMA-staged passes (the prior's staging D = P(w+ - w) of the dual step)
+    and TMA-staged data passes with plain prior passes equal all-plain passes
+    bit for bit (deterministic)."""
     c = Case(lm, "3d_quad")
     seq = S.selection_sequence(c.n_sub, 4 * c.n_sub, seed=3)
-    a = c.gpu(xi=c.xi_g, deterministic=True, image_kernel=2)
-    b = c.gpu(xi=c.xi_g, deterministic=True, image_kernel=1)
-    assert a.tuning()["image_kernel"] == "tma_data" and b.tuning()["image_kernel"] == "plain"
+    g = {k: c.gpu(xi=c.xi_g, deterministic=True, image_kernel=k) for k in (1, 2, 3)}
+    assert [g[k].tuning()["image_kernel"] for k in (1, 2, 3)] == ["plain", "tma", "tma_data"]
     for k in range(2):
         s = seq[2 * c.n_sub * k:2 * c.n_sub * (k + 1)]
-        a.epoch(s)
-        b.epoch(s)
-    np.testing.assert_array_equal(a.x().cpu().numpy(), b.x().cpu().numpy())
-    np.testing.assert_array_equal(a.z().cpu().numpy(), b.z().cpu().numpy())
-    assert a.objective() == b.objective()
+        for st in g.values():
+            st.epoch(s)
+    for k in (2, 3):
+        np.testing.assert_array_equal(g[k].x().cpu().numpy(), g[1].x().cpu().numpy())
+        np.testing.assert_array_equal(g[k].z().cpu().numpy(), g[1].z().cpu().numpy())
+        np.testing.assert_array_equal(g[k].w().cpu().numpy(), g[1].w().cpu().numpy())
+        assert g[k].objective() == g[1].objective()

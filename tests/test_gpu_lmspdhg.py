@@ -203,28 +203,31 @@ def test_x0_negative_rejected(lm):
 @pytest.mark.parametrize("name", ["3d_quad", "2d"])
 @pytest.mark.parametrize("kahan", [True, False])
 def test_tma_and_plain_image_passes_agree(lm, name, kahan):
-    """The TMA-staged image pass (prior dual step fused in) and the
-    plain-load pass compute the same operations in the same order: in
-    deterministic mode x, z, w and y agree bit for bit after two epochs."""
+    """The TMA-staged image pass (prior dual step fused in), TMA-staged data
+    passes with plain prior passes, and the plain-load pass compute the same
+    operations in the same order: in deterministic mode x, z, w and y agree
+    bit for bit after two epochs."""
     c = Case(lm, name, n_events=30000 if name == "2d" else None)
     seq = S.selection_sequence(c.n_sub, 4 * c.n_sub, seed=5)
     out = {}
-    for kind in (1, 2):
+    for kind in (1, 2, 3):
         g = c.gpu(deterministic=True, kahan=kahan, image_kernel=kind, group=16)
-        assert g.tuning()["image_kernel"] == {1: "plain", 2: "tma"}[kind]
+        assert g.tuning()["image_kernel"] == {1: "plain", 2: "tma", 3: "tma_data"}[kind]
         g.epoch(seq[:2 * c.n_sub])
         g.epoch(seq[2 * c.n_sub:])
         out[kind] = [a.cpu().numpy() for a in (g.x(), g.z(), g.w(), g.y())]
         g.close()
-    for a, b in zip(out[1], out[2]):
-        np.testing.assert_array_equal(a, b)
+    for kind in (2, 3):
+        for a, b in zip(out[1], out[kind]):
+            np.testing.assert_array_equal(a, b)
 
 
 def test_image_kernel_choice(lm):
     assert Case(lm, "3d_quad").gpu().tuning()["image_kernel"] == "tma"
     assert Case(lm, "3d_small").gpu().tuning()["image_kernel"] == "plain"
-    with pytest.raises(lm.LMError):
-        Case(lm, "3d_small").gpu(image_kernel=2)
+    for kind in (2, 3, 4):
+        with pytest.raises(lm.LMError):
+            Case(lm, "3d_small").gpu(image_kernel=kind)
 
 
 @pytest.mark.parametrize("name", ["2d_small", "3d_small", "3d_quad", "3d_mid"])
