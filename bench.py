@@ -249,8 +249,8 @@ def run_reference(args):
         "config": {"workload": f"{args.workload}: FP64 CPU oracle, bounded sample of {n_sample} events on the full "
                                f"grid, initialisation + one epoch per step", "events_per_step": tot_ev / args.steps},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"first {n_sample} Monte Carlo events of the frame, full 200x200x96 grid, "
-                                   f"init + {2 * wl.n_subsets} updates"},
+                         "sample": f"first {n_sample} Monte Carlo events of the frame, full "
+                                   f"{'x'.join(str(v) for v in wl.grid.n)} grid, init + {2 * wl.n_subsets} updates"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
