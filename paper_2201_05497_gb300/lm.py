@@ -157,14 +157,26 @@ def _check(rc: int):
         raise LMError(rc, load_library().lm_last_error().decode())
 
 
-def _ptr(t: Optional[torch.Tensor]):
+def _ptr(t: Optional[torch.Tensor], dtype: Optional[torch.dtype] = None, numel: Optional[int] = None,
+         name: str = "tensor"):
+    """Device pointer of t (None passes through).  Raises before any call into
+    the library if t is not a contiguous CUDA tensor, or (when given) has
+    another dtype or fewer than numel elements."""
     if t is None:
         return None
     if not t.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+        raise ValueError(f"{name}: expected a CUDA tensor")
     if not t.is_contiguous():
-        raise ValueError("expected a contiguous tensor")
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {numel} needed")
     return C.c_void_p(t.data_ptr())
+
+
+def _f32(t: Optional[torch.Tensor], numel: int, name: str):
+    return _ptr(t, torch.float32, numel, name)
 
 
 def _stream(stream=None):
@@ -227,8 +239,10 @@ class DeviceEvents:
         return int(self.det1.shape[0])
 
     def desc(self) -> lm_events:
-        return lm_events(_ptr(self.det1), _ptr(self.det2), _ptr(self.tof), _ptr(self.corr), _ptr(self.contam),
-                         self.n)
+        n = self.n
+        return lm_events(_ptr(self.det1, torch.int32, n, "det1"), _ptr(self.det2, torch.int32, n, "det2"),
+                         _ptr(self.tof, torch.int16, n, "tof"), _ptr(self.corr, torch.float32, n, "corr"),
+                         _ptr(self.contam, torch.float32, n, "contam"), n)
 
     @classmethod
     def from_numpy(cls, ev, device="cuda"):
@@ -253,7 +267,8 @@ def fwd(geo: Geometry, x: torch.Tensor, ev: DeviceEvents, out: Optional[torch.Te
         out = torch.empty(ev.n, dtype=torch.float32, device=x.device)
     ws = _ws(L.lm_fwd_workspace_bytes(C.byref(geo.g)), x.device) if use_workspace else None
     d = ev.desc()
-    _check(L.lm_fwd(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _ptr(x), C.byref(d), _ptr(out),
+    _check(L.lm_fwd(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _f32(x, geo.V, "x"), C.byref(d),
+                    _f32(out, ev.n, "out"),
                     _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream)))
     return out
 
@@ -267,7 +282,8 @@ def back(geo: Geometry, v: torch.Tensor, ev: DeviceEvents, img: Optional[torch.T
     nb = L.lm_back_workspace_bytes(C.byref(geo.g), int(deterministic))
     ws = _ws(nb, v.device) if (use_workspace or deterministic) else None
     d = ev.desc()
-    _check(L.lm_back(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d), _ptr(v), _ptr(img),
+    _check(L.lm_back(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d), _f32(v, ev.n, "v"),
+                     _f32(img, geo.V, "img"),
                      int(deterministic), _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream)))
     return img
 
@@ -280,7 +296,8 @@ def sens(geo: Geometry, lor_factor: Optional[torch.Tensor] = None, out: Optional
     if out is None:
         out = torch.empty(geo.V, dtype=torch.float32, device=dev)
     ws = _ws(L.lm_sens_workspace_bytes(C.byref(geo.g)), dev) if use_workspace else None
-    _check(L.lm_sens(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _ptr(lor_factor), _ptr(out), _ptr(ws),
+    _check(L.lm_sens(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _f32(lor_factor, geo.n_lor, "lor_factor"),
+                     _f32(out, geo.V, "out"), _ptr(ws),
                      0 if ws is None else ws.numel(), _stream(stream)))
     return out
 
@@ -289,7 +306,7 @@ def tv_grad(geo: Geometry, x: torch.Tensor, out=None, stream=None) -> torch.Tens
     L = load_library()
     if out is None:
         out = torch.empty(geo.ndim * geo.V, dtype=torch.float32, device=x.device)
-    _check(L.lm_tv_grad(C.byref(geo.g), _ptr(x), _ptr(out), _stream(stream)))
+    _check(L.lm_tv_grad(C.byref(geo.g), _f32(x, geo.V, "x"), _f32(out, geo.ndim * geo.V, "out"), _stream(stream)))
     return out
 
 
@@ -297,13 +314,13 @@ def tv_div(geo: Geometry, g: torch.Tensor, out=None, stream=None) -> torch.Tenso
     L = load_library()
     if out is None:
         out = torch.empty(geo.V, dtype=torch.float32, device=g.device)
-    _check(L.lm_tv_div(C.byref(geo.g), _ptr(g), _ptr(out), _stream(stream)))
+    _check(L.lm_tv_div(C.byref(geo.g), _f32(g, geo.ndim * geo.V, "g"), _f32(out, geo.V, "out"), _stream(stream)))
     return out
 
 
 def tv_prox(geo: Geometry, w: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
     L = load_library()
-    _check(L.lm_tv_prox(C.byref(geo.g), _ptr(w), float(beta), _stream(stream)))
+    _check(L.lm_tv_prox(C.byref(geo.g), _f32(w, geo.ndim * geo.V, "w"), float(beta), _stream(stream)))
     return w
 
 
@@ -313,7 +330,8 @@ def res_apply(geo: Geometry, fwhm: float, x: torch.Tensor, out=None, stream=None
     if out is None:
         out = torch.empty(geo.V, dtype=torch.float32, device=x.device)
     ws = _ws(L.lm_res_workspace_bytes(C.byref(geo.g)), x.device)
-    _check(L.lm_res_apply(C.byref(geo.g), float(fwhm), _ptr(x), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    _check(L.lm_res_apply(C.byref(geo.g), float(fwhm), _f32(x, geo.V, "x"), _f32(out, geo.V, "out"), _ptr(ws),
+                          ws.numel(), _stream(stream)))
     return out
 
 
@@ -322,7 +340,8 @@ def dtv_field(geo: Geometry, v: torch.Tensor, eta: float, out=None, stream=None)
     L = load_library()
     if out is None:
         out = torch.empty(geo.ndim * geo.V, dtype=torch.float32, device=v.device)
-    _check(L.lm_dtv_field(C.byref(geo.g), _ptr(v), float(eta), _ptr(out), _stream(stream)))
+    _check(L.lm_dtv_field(C.byref(geo.g), _f32(v, geo.V, "v"), float(eta), _f32(out, geo.ndim * geo.V, "out"),
+                          _stream(stream)))
     return out
 
 
@@ -330,7 +349,9 @@ def dtv_grad(geo: Geometry, xi: torch.Tensor, x: torch.Tensor, out=None, stream=
     L = load_library()
     if out is None:
         out = torch.empty(geo.ndim * geo.V, dtype=torch.float32, device=x.device)
-    _check(L.lm_dtv_grad(C.byref(geo.g), _ptr(xi), _ptr(x), _ptr(out), _stream(stream)))
+    nv = geo.ndim * geo.V
+    _check(L.lm_dtv_grad(C.byref(geo.g), _f32(xi, nv, "xi"), _f32(x, geo.V, "x"), _f32(out, nv, "out"),
+                         _stream(stream)))
     return out
 
 
@@ -339,7 +360,9 @@ def dtv_div(geo: Geometry, xi: torch.Tensor, g: torch.Tensor, out=None, stream=N
     L = load_library()
     if out is None:
         out = torch.empty(geo.V, dtype=torch.float32, device=g.device)
-    _check(L.lm_dtv_div(C.byref(geo.g), _ptr(xi), _ptr(g), _ptr(out), _stream(stream)))
+    nv = geo.ndim * geo.V
+    _check(L.lm_dtv_div(C.byref(geo.g), _f32(xi, nv, "xi"), _f32(g, nv, "g"), _f32(out, geo.V, "out"),
+                        _stream(stream)))
     return out
 
 
@@ -428,7 +451,8 @@ def emtv_epoch(geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x: tor
     d = pe.events.desc()
     off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
     _check(L.lm_emtv_epoch(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d),
-                           off.ctypes.data_as(C.POINTER(C.c_int64)), int(off.shape[0] - 1), _ptr(sens_img), _ptr(x),
+                           off.ctypes.data_as(C.POINTER(C.c_int64)), int(off.shape[0] - 1),
+                           _f32(sens_img, geo.V, "sens_img"), _f32(x, geo.V, "x"),
                            float(beta), int(pdhg_iters), float(knorm), _ptr(ws), ws.numel(), _stream(stream)))
     return x
 
@@ -442,7 +466,8 @@ def emtv_em_step(geo: Geometry, ev: DeviceEvents, n_subsets: int, sens_img: torc
         out = torch.empty(geo.V, dtype=torch.float32, device=x.device)
     d = ev.desc()
     _check(L.lm_emtv_em_step(C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(d), int(n_subsets),
-                             _ptr(sens_img), _ptr(x), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+                             _f32(sens_img, geo.V, "sens_img"), _f32(x, geo.V, "x"), _f32(out, geo.V, "out"),
+                             _ptr(ws), ws.numel(), _stream(stream)))
     return out
 
 
@@ -454,7 +479,8 @@ def emtv_denoise(geo: Geometry, z: torch.Tensor, w: torch.Tensor, iters: int, kn
     ws = _emtv_ws(geo, ws, z.device)
     if out is None:
         out = torch.empty(geo.V, dtype=torch.float32, device=z.device)
-    _check(L.lm_emtv_denoise(C.byref(geo.g), _ptr(z), _ptr(w), _ptr(out), int(iters), float(knorm), _ptr(ws),
+    _check(L.lm_emtv_denoise(C.byref(geo.g), _f32(z, geo.V, "z"), _f32(w, geo.V, "w"), _f32(out, geo.V, "out"),
+                             int(iters), float(knorm), _ptr(ws),
                              ws.numel(), _stream(stream)))
     return out
 
@@ -543,9 +569,10 @@ class LMSPDHG:
                 self.tile = torch.empty(tb, dtype=torch.uint8, device=x0.device)
         self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan),
                                 int(group), int(image_kernel), None if self.tile is None else self.tile.data_ptr(),
-                                0 if self.tile is None else self.tile.numel(), _ptr(xi), float(res_fwhm),
+                                0 if self.tile is None else self.tile.numel(),
+                                _f32(xi, geo.ndim * geo.V, "xi"), float(res_fwhm),
                                 int(sinogram), _ptr(getattr(pe, "q", None)), _ptr(getattr(pe, "qoff", None)),
-                                _ptr(sino_lorf), float(sino_s))
+                                _f32(sino_lorf, geo.n_lor, "sino_lorf"), float(sino_s))
         self._keep = (sino_lorf,)
         nbytes = L.lmspdhg_state_bytes_ex(C.byref(geo.g), pe.events.n, int(n_subsets), C.byref(self.params))
         if nbytes == 0:
@@ -555,8 +582,9 @@ class LMSPDHG:
         self._off = np.ascontiguousarray(pe.sub_off, dtype=np.int64)
         h = C.c_void_p()
         _check(L.lmspdhg_create(C.byref(h), C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), C.byref(self._ev),
-                                _ptr(pe.mu), self._off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(sens_img),
-                                _ptr(x0), C.byref(self.params), _ptr(self.buf), self.buf.numel(), _stream(stream)))
+                                _ptr(pe.mu), self._off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                _f32(sens_img, geo.V, "sens_img"), _f32(x0, geo.V, "x0"), C.byref(self.params),
+                                _ptr(self.buf), self.buf.numel(), _stream(stream)))
         self.h = h
 
     def _seq(self, seq):
@@ -594,7 +622,7 @@ class LMSPDHG:
         return out
 
     def reinit(self, x0: torch.Tensor, stream=None):
-        _check(load_library().lmspdhg_reinit(self.h, _ptr(x0), _stream(stream)))
+        _check(load_library().lmspdhg_reinit(self.h, _f32(x0, self.geo.V, "x0"), _stream(stream)))
 
     def profile(self, seq, stream=None):
         """Per-kernel timing of `seq` (direct launches with CUDA events)."""

@@ -68,3 +68,44 @@ def test_invalid_arguments_rejected_on_host(L):
     assert rc == 1
     rc = L.lm_knorm_fp64(C.byref(g), 10, None, 0, None, None)
     assert rc == 1
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor (no GPU here): what the binding's
+    pointer marshalling looks at."""
+
+    is_cuda = True
+
+    def __init__(self, dtype, n, contiguous=True):
+        self.dtype, self._n, self._c = dtype, n, contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        return 4096
+
+
+def test_binding_checks_tensors_before_calling():
+    """Every device argument is checked (device, layout, dtype, size) in
+    Python before the library sees its pointer."""
+    torch = pytest.importorskip("torch")
+    from paper_2201_05497_gb300 import lm
+    f32 = torch.float32
+    assert lm._f32(_FakeCudaTensor(f32, 10), 10, "x").value == 4096
+    assert lm._f32(None, 10, "x") is None
+    with pytest.raises(TypeError, match="x: expected torch.float32"):
+        lm._f32(_FakeCudaTensor(torch.float64, 10), 10, "x")
+    with pytest.raises(ValueError, match="x: 9 elements, at least 10 needed"):
+        lm._f32(_FakeCudaTensor(f32, 9), 10, "x")
+    with pytest.raises(ValueError, match="contiguous"):
+        lm._f32(_FakeCudaTensor(f32, 10, contiguous=False), 10, "x")
+    with pytest.raises(ValueError, match="CUDA"):
+        lm._f32(torch.zeros(10), 10, "x")
+    ev = lm.DeviceEvents(_FakeCudaTensor(torch.int32, 5), _FakeCudaTensor(torch.int64, 5), None, None, None)
+    ev.det1.shape = (5,)
+    with pytest.raises(TypeError, match="det2"):
+        ev.desc()

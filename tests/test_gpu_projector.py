@@ -170,3 +170,18 @@ def test_empty_and_invalid_events_are_inert(lm):
                           torch.tensor([0, 0, 0, 0, 999], dtype=torch.int16, device="cuda"), None, None)
     p = lm.fwd(geo_g, x, bad).cpu().numpy()
     np.testing.assert_array_equal(p, 0.0)
+
+
+def test_binding_rejects_wrong_dtype_and_size(lm):
+    """Wrong dtypes and short buffers raise in the binding before any launch."""
+    wl = S.workload("2d_small")
+    geo = lm.Geometry.from_workload(wl)
+    x = torch.ones(geo.V, device="cuda")
+    with pytest.raises(TypeError):
+        lm.res_apply(geo, 4.5, x.double())
+    with pytest.raises(ValueError):
+        lm.tv_grad(geo, x[:-1])
+    ev = lm.DeviceEvents(torch.zeros(3, dtype=torch.int64, device="cuda"), torch.zeros(3, dtype=torch.int32,
+                                                                                       device="cuda"), None, None, None)
+    with pytest.raises(TypeError):
+        lm.fwd(geo, x, ev)
