@@ -501,7 +501,8 @@ def sino_setup(geo: Geometry, d: torch.Tensor, s: torch.Tensor, n_subsets: int,
     mu = torch.empty(nb, dtype=torch.uint16, device=dev)
     off = np.zeros(n_subsets + 1, dtype=np.int64)
     ws = _ws(L.lm_sino_workspace_bytes(C.byref(geo.sc), int(n_subsets)), dev)
-    _check(L.lm_sino_setup(C.byref(geo.sc), C.byref(geo.tof), int(n_subsets), _ptr(d), _ptr(s), _ptr(lor_factor),
+    _check(L.lm_sino_setup(C.byref(geo.sc), C.byref(geo.tof), int(n_subsets), _ptr(d, torch.uint16, nb, "d"),
+                           _f32(s, nb, "s"), _f32(lor_factor, geo.n_lor, "lor_factor"),
                            _ptr(ev.det1), _ptr(ev.det2), _ptr(ev.tof), _ptr(ev.corr), _ptr(ev.contam), _ptr(mu),
                            off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(ws), ws.numel(), _stream(stream)))
     return PermutedEvents(ev, mu, off)
@@ -730,7 +731,8 @@ class Server:
                                     int(max_slots), int(deterministic), int(kahan), int(group), int(max_events))
         self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=sens.device)
         h = C.c_void_p()
-        _check(L.lm_server_create(C.byref(h), C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof), _ptr(sens),
+        _check(L.lm_server_create(C.byref(h), C.byref(geo.sc), C.byref(geo.g), C.byref(geo.tof),
+                                  _f32(sens, geo.V, "sens"),
                                   C.byref(self.cfg), _ptr(self.pool), self.pool.numel()))
         self.h = h
 
