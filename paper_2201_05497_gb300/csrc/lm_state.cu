@@ -96,8 +96,6 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det,
     const size_t V = (size_t)nvox(g);
     const int nd = std::max(1, tv_ndim(g));
     const bool yf = g->n[1] > 1;
-    float* dummy = nullptr;
-    (void)dummy;
     auto F = [&](size_t cnt) { return c.take<float>(cnt * 4); };
     float* x0 = F(V);
     float* x1 = F(V);
