@@ -561,6 +561,16 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
              "subset offsets must span [0, n)");
     for (int k = 0; k < P.n_subsets; ++k)
         LM_CHECK(sub_off_host[k + 1] >= sub_off_host[k], LM_ERR_INVALID_ARG, "subset offsets must not decrease");
+    LM_CHECK(P.image_kernel >= 0 && P.image_kernel <= 3, LM_ERR_INVALID_ARG, "image_kernel must be 0, 1, 2 or 3");
+    LM_CHECK(!(P.image_kernel == 2 || P.image_kernel == 3) || tma_capable(grid), LM_ERR_INVALID_ARG,
+             "the TMA-staged image pass needs nx, ny multiples of 4 with nx >= 40, ny >= 36");
+    LM_CHECK(P.res_fwhm >= 0.0f, LM_ERR_INVALID_ARG, "res_fwhm must be >= 0");
+    if (P.res_fwhm > 0.0f) {
+        LM_CHECK(P.deterministic == 0, LM_ERR_INVALID_ARG, "the resolution model runs in float-atomic mode");
+        ResPlan rp;
+        rc = res_plan(grid, P.res_fwhm, rp);
+        if (rc) return rc;
+    }
     const size_t need = lmspdhg_state_bytes_ex(grid, ev->n, P.n_subsets, &P);
     LM_CHECK(state_bytes >= need, LM_ERR_NOMEM, "state buffer needs %zu bytes", need);
 
@@ -616,23 +626,8 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->tma = false;
     st->tma_data = false;
     st->zlen = 1;
-    if (P.image_kernel < 0 || P.image_kernel > 3) {
-        set_error("image_kernel must be 0, 1, 2 or 3");
-        return fail(LM_ERR_INVALID_ARG);
-    }
-    if ((P.image_kernel == 2 || P.image_kernel == 3) && !tma_capable(grid)) {
-        set_error("the TMA-staged image pass needs nx, ny multiples of 4 with nx >= 40, ny >= 36");
-        return fail(LM_ERR_INVALID_ARG);
-    }
     st->has_res = P.res_fwhm > 0.0f;
-    if (st->has_res) {
-        if (st->det) {
-            set_error("the resolution model runs in float-atomic mode");
-            return fail(LM_ERR_INVALID_ARG);
-        }
-        rc = res_plan(grid, P.res_fwhm, st->res);
-        if (rc) return fail(rc);
-    }
+    if (st->has_res) res_plan(grid, P.res_fwhm, st->res);  // validated above
     if (P.image_kernel != 1 && tma_capable(grid)) {
         TmaMaps h;
         rc = encode_tma_maps(grid, st->x, st->w, std::max(1, st->ndim), st->T, st->z, st->zc,

@@ -109,3 +109,35 @@ def test_binding_checks_tensors_before_calling():
     ev.det1.shape = (5,)
     with pytest.raises(TypeError, match="det2"):
         ev.desc()
+
+
+def test_state_options_rejected_on_host(L):
+    """lmspdhg_create refuses an unknown image kernel, a TMA kernel on a grid
+    it cannot tile, and an invalid resolution model before touching a
+    device (the pointers below are never dereferenced)."""
+    from paper_2201_05497_gb300 import lm
+    fake = C.c_void_p(4096)
+    sc = lm.lm_scanner(1, 16, fake)
+    tof = lm.lm_tof(25.0, 22.0, 3.0, 0)
+    ev = lm.lm_events(fake, fake, None, fake, fake, 8)
+    off = (C.c_int64 * 3)(0, 4, 8)
+
+    def create(n, **kw):
+        g = lm.lm_grid((C.c_int32 * 3)(*n), (C.c_float * 3)(2.5, 2.5, 2.5), (C.c_float * 3)(0, 0, 0))
+        p = lm.lm_params(beta=0.1, rho=0.999, n_subsets=2, kahan=1, **kw)
+        h = C.c_void_p()
+        rc = L.lmspdhg_create(C.byref(h), C.byref(sc), C.byref(g), C.byref(tof), C.byref(ev), fake, off, fake, fake,
+                              C.byref(p), fake, 1 << 40, None)
+        return rc, L.lm_last_error().decode()
+
+    rc, msg = create((48, 40, 8), image_kernel=4)
+    assert rc == 1 and "image_kernel" in msg
+    for kind in (2, 3):
+        rc, msg = create((16, 16, 8), image_kernel=kind)  # nx < 40
+        assert rc == 1 and "TMA" in msg
+    rc, msg = create((48, 40, 8), res_fwhm=4.5, deterministic=1)
+    assert rc == 1 and "float-atomic" in msg
+    rc, msg = create((48, 40, 8), res_fwhm=float("nan"))
+    assert rc == 1 and "res_fwhm" in msg
+    rc, msg = create((48, 40, 8), res_fwhm=200.0)  # more taps per side than the kernels take
+    assert rc == 1 and "too wide" in msg
