@@ -300,7 +300,8 @@ typedef struct {
     float res_fwhm;       /* image-space resolution model P = A G (lm_res_apply): */
                           /* FWHM in mm, 0 = none.  sens must then be G (lm_sens).*/
                           /* Float-atomic mode only (deterministic is rejected);  */
-                          /* direct projector; not for batches.                   */
+                          /* direct projector; not for batches.  Negative, NaN or */
+                          /* more than 31 taps per side: LM_ERR_INVALID_ARG.      */
     int32_t sinogram;     /* 1: Alg. 1 (sinogram SPDHG): the events are the bins */
                           /* of lm_sino_setup and mu their counts d_b (0 allowed);*/
                           /* the dual step uses prox with S_b d_b and back-       */
@@ -340,7 +341,10 @@ size_t lmspdhg_state_bytes_ex(const lm_grid* grid, int64_t n_events, int32_t n_s
  * sub_off_host: host int64[n+1].  state_buf: device buffer of
  * lmspdhg_state_bytes() bytes owned by the caller.  Synchronous (reads
  * max(x0), min(x0) and, if asked for, ||K||).  *out receives a host handle;
- * free it with lmspdhg_destroy. */
+ * free it with lmspdhg_destroy.  Invalid parameters (NULL pointers, subset
+ * offsets, beta, rho, image_kernel, res_fwhm, sinogram options, a buffer
+ * smaller than lmspdhg_state_bytes_ex) are rejected on the host before any
+ * device call. */
 int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof,
                    const lm_events* ev_perm, const uint16_t* mu, const int64_t* sub_off_host,
                    const float* sens, const float* x0, const lm_params* params, void* state_buf,
