@@ -293,10 +293,11 @@ typedef struct {
                           /* (6 per event), the direct kernel is used.            */
     const float* xi;      /* directional TV prior (lm_dtv_field): device field    */
                           /* [ndim][V], referenced, must outlive the state; NULL  */
-                          /* = TV.  Prior updates run the plain-load image pass  */
-                          /* (the TMA pass fuses the TV prior only); data updates */
-                          /* the TMA pass where the grid allows.  knorm may be    */
-                          /* the TV norm: ||K_DTV|| <= ||K_TV||.                  */
+                          /* = TV.  The prior's dual step (with the field) runs  */
+                          /* in the event kernel and stores D = P(w+ - w); the   */
+                          /* image pass (TMA-staged where the grid allows) forms */
+                          /* K^T(w+ - w) from D.  knorm may be the TV norm:      */
+                          /* ||K_DTV|| <= ||K_TV||.                               */
     float res_fwhm;       /* image-space resolution model P = A G (lm_res_apply): */
                           /* FWHM in mm, 0 = none.  sens must then be G (lm_sens).*/
                           /* Float-atomic mode only (deterministic is rejected);  */
