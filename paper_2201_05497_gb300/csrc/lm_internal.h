@@ -296,7 +296,7 @@ struct ImgArgs {
     int xcur;              // index of x_cur among the two x buffers
     int zlen;              // z slices per work item
     unsigned* err;         // set when a bounded wait gave up
-    const float* xi;       // directional TV field [ndim][V], or nullptr (TV; plain prior passes only)
+    const float* xi;       // directional TV field [ndim][V], or nullptr (TV)
     const float* dtv_d;    // directional TV: P (w+ - w) from the dual step, or nullptr (formed here)
     int skip_prior;        // 1: return at once when the update is a prior update
     int skip_data;         // 1: return at once when the update is a data update
