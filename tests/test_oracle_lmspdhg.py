@@ -225,3 +225,80 @@ def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free, prior):
     # exact in real arithmetic; (a + 1) - |a - 1| rounds to within a few ulps of 2
     assert np.max(np.abs(sino.y[empty] - 1.0)) <= 1e-14
     assert abs((sino.objective() - s.sum()) - lm.objective()) <= 1e-10 * abs(lm.objective())
+
+
+def _all_bins(O, geo, tof, lf):
+    """Every (LOR, TOF bin) of the scanner as one event, LOR factor in corr."""
+    d1, d2, m, c = [], [], [], []
+    for l in range(geo.n_lor):
+        a, b = geo.lor_dets(l)
+        for k in range(-tof.half, tof.half + 1):
+            d1.append(a)
+            d2.append(b)
+            m.append(k)
+            c.append(lf[l])
+    return O.EventArrays(np.array(d1), np.array(d2), np.array(m), np.array(c, np.float32))
+
+
+@pytest.mark.parametrize("binding,n_sub", [("data", 1), ("data", 3), ("prior", 1), ("prior", 3), ("mixed", 2)])
+def test_step_sizes_meet_the_spdhg_condition(oracle_mod, binding, n_sub):
+    """Eq. (lm_stepsizes) is SPDHG's diagonally preconditioned choice for
+    balanced subsets (column sums P_i^T 1 = P^T 1 / n).  Made exact here: the
+    n subsets are n copies of every bin, so the list's sensitivity is n P^T 1.
+    Then S_b = gamma rho / (P 1)_b and T = rho p_i n / (gamma n P^T 1) give
+    ||S^1/2 P_i T^1/2||^2 = rho^2 p_i, p_i = 1/(2n): a nonnegative P has the
+    positive singular pair (sqrt(P 1), sqrt(P^T 1)) with singular value 1 once
+    scaled (Perron-Frobenius).  The prior's S_{n+1} = gamma rho / ||K|| and
+    T = rho p_{n+1} / (gamma ||K||) give S_{n+1} T ||K||^2 = rho^2 p_{n+1},
+    p_{n+1} = 1/2.  T is the smaller of the two, so where one term sets T its
+    condition holds with equality and the other's as an inequality.  T comes
+    from the oracle's initialisation; S_{n+1} is read back from one prior
+    update whose projection is inactive (beta huge): w+ = S_{n+1} K x."""
+    O = oracle_mod
+    sc, g, tof, ev = tiny_problem(n=(6, 5, 1), n_bins=5, n_events=200, seed=8)
+    geo = _geometry(O, sc, g, tof)
+    V = geo.V
+    kn = _knorm(g.n)
+    gamma, rho = 0.7, 0.9
+    lf = np.random.default_rng(3).uniform(0.5, 1.0, geo.n_lor).astype(np.float32)
+    sens0 = O.sens(geo, lf)
+    # scale the LOR factors so that the chosen term sets T (T_data < T_prior <=> n P^T 1 > ||K||)
+    scale = {"data": 2.0, "prior": 0.5, "mixed": 1.0}[binding] * kn / n_sub
+    scale /= {"data": sens0.min(), "prior": sens0.max(), "mixed": np.median(sens0)}[binding]
+    lf = (lf * scale).astype(np.float32)
+    sens1 = O.sens(geo, lf)
+    assert sens1.min() > 0
+    E = O.EventArrays.from_events(ev)
+    mu = O.event_counts(ev.det1, ev.det2, ev.tof)
+    lm = O.LM(geo, E, mu, n_sub, beta=1e30, gamma=gamma, rho=rho, knorm=kn)
+    lm.init(np.full(V, 2.0, np.float32), n_sub * sens1)
+    T = lm.T.copy()
+    # data term of one subset (one copy of every bin): the dense operator; its column sums are P^T 1
+    A = _dense_lm_matrix(O, geo, _all_bins(O, geo, tof, lf))
+    np.testing.assert_allclose(A.sum(0), sens1, rtol=1e-12)
+    r = A.sum(1)
+    A, r = A[r > 0], r[r > 0]
+    c_data = np.linalg.norm(np.sqrt(gamma * rho / r)[:, None] * A * np.sqrt(T)[None, :], 2) ** 2
+    # prior term: S_{n+1} from one prior update, K dense from its columns
+    lm.update(n_sub)
+    Kx = O.tv_grad(geo, lm.x)
+    s_prior = float(lm.w @ Kx / (Kx @ Kx))
+    np.testing.assert_allclose(lm.w, s_prior * Kx, rtol=0, atol=1e-12 * np.abs(lm.w).max())
+    Km = np.zeros((geo.ndim * V, V))
+    for j in range(V):
+        e = np.zeros(V)
+        e[j] = 1.0
+        Km[:, j] = O.tv_grad(geo, e)
+    np.testing.assert_allclose(np.linalg.norm(Km, 2), kn, rtol=1e-12)
+    c_prior = np.linalg.norm(Km * np.sqrt(s_prior * T)[None, :], 2) ** 2
+    lim_data, lim_prior = rho ** 2 / (2 * n_sub), rho ** 2 / 2
+    if binding == "data":
+        assert abs(c_data - lim_data) <= 1e-10 * lim_data
+        assert c_prior <= lim_prior * (1 - 1e-3)
+    elif binding == "prior":
+        np.testing.assert_allclose(s_prior * T * kn ** 2, lim_prior, rtol=1e-12)
+        assert abs(c_prior - lim_prior) <= 1e-10 * lim_prior
+        assert c_data <= lim_data * (1 - 1e-3)
+    else:
+        assert (T < T.max()).any() and (T == T.max()).any()  # both terms set T somewhere
+        assert c_data <= lim_data * (1 + 1e-12) and c_prior <= lim_prior * (1 + 1e-12)
