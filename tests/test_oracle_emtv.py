@@ -274,8 +274,8 @@ def test_denoise_limits(oracle_mod):
 # --------------------------------------------------------------------------
 # the pass over the subsets
 # --------------------------------------------------------------------------
-def _problem(O, n_sub, seed=6):
-    sc, g, tof, ev = tiny(n=(6, 5, 1), n_events=300, seed=seed)
+def _problem(O, n_sub, seed=6, n=(6, 5, 1)):
+    sc, g, tof, ev = tiny(n=n, n_events=300, seed=seed)
     geo = geometry(O, sc, g, tof)
     E = O.EventArrays.from_events(ev)
     sens = O.sens(geo, np.ones(sc.n_lor, np.float32))
@@ -295,10 +295,11 @@ def test_epoch_small_beta_is_osem(oracle_mod):
     assert tv_of(tv) < 0.8 * tv_of(osem)
 
 
-def test_epoch_is_composition_of_steps(oracle_mod):
+@pytest.mark.parametrize("n", [(6, 5, 1), (4, 3, 2)])
+def test_epoch_is_composition_of_steps(oracle_mod, n):
     O = oracle_mod
     n_sub, beta, iters = 4, 0.2, 25
-    g, geo, E, sens, x0 = _problem(O, n_sub, seed=9)
+    g, geo, E, sens, x0 = _problem(O, n_sub, seed=9, n=n)
     sens[0] = 0.0  # a voxel outside the field of view is held at 0
     em = O.EMTV(geo, E, n_sub, beta=beta, knorm=knorm(g.n))
     x = x0.copy()

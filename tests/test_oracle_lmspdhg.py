@@ -84,7 +84,7 @@ def _dtv_field(O, geo, n, seed=21, eta=0.3):
     return O.dtv_xi(geo, v, eta)
 
 
-@pytest.mark.parametrize("prior", ["tv", "dtv", "tv+res"])
+@pytest.mark.parametrize("prior", ["tv", "dtv", "tv+res", "tv-3d"])
 def test_lmpdhg_reaches_independent_minimiser(oracle_mod, prior):
     """Brute force on a tiny grid: the dense P^LM is built column by column;
     L-BFGS-B on Eq. (1) with a smoothed TV (eps = 1e-9) gives the minimiser
@@ -92,9 +92,11 @@ def test_lmpdhg_reaches_independent_minimiser(oracle_mod, prior):
     gap and the KKT residual of x >= 0 become small.  For DTV the dense K is
     the dense TV matrix with P_j = I - xi_j xi_j^T applied to each voxel's
     rows, written here from the definition; with the resolution model the
-    dense forward model is A G (G from its columns) and P^T 1 = G A^T 1."""
+    dense forward model is A G (G from its columns) and P^T 1 = G A^T 1.
+    tv-3d and tv+res: two slices either side of the ring's plane (each
+    sample split half and half between them, TV and G across them)."""
     O = oracle_mod
-    sc, g, tof, ev = tiny_problem(n=(5, 4, 1), n_events=250, seed=5)
+    sc, g, tof, ev = tiny_problem(n=(4, 3, 2) if prior in ("tv-3d", "tv+res") else (5, 4, 1), n_events=250, seed=5)
     geo = _geometry(O, sc, g, tof)
     E = O.EventArrays.from_events(ev)
     mu = O.event_counts(ev.det1, ev.det2, ev.tof)
@@ -179,8 +181,10 @@ def _sino_setup(O, geo, sc, tof, ev, n_subsets, lm_subset_of_event):
     return d, s, sub, b
 
 
-@pytest.mark.parametrize("n_subsets,dup_free,prior", [(1, False, "tv"), (3, True, "tv"), (3, True, "dtv")])
-def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free, prior):
+@pytest.mark.parametrize("n_subsets,dup_free,prior,n", [(1, False, "tv", (6, 5, 1)), (3, True, "tv", (6, 5, 1)),
+                                                      (3, True, "dtv", (6, 5, 1)), (3, True, "tv", (4, 3, 2)),
+                                                      (2, True, "dtv", (4, 3, 2))])
+def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free, prior, n):
     """Appendix: LM-SPDHG is SPDHG on the listmode reformulation.  With the
     same selection sequence (n = 1 with duplicated events, or n = 3 on
     duplicate-free data with the sinogram subset of a bin = the listmode
@@ -189,7 +193,7 @@ def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free, prior):
     y of an event equals y of its bin.  Empty bins keep y = 1 (Sec.
     "Memory-efficient SPDHG").  The objectives differ by sum_b s_b only."""
     O = oracle_mod
-    sc, g, tof, ev = tiny_problem(n_events=350, seed=11, dup_free=dup_free)
+    sc, g, tof, ev = tiny_problem(n=n, n_events=350, seed=11, dup_free=dup_free)
     ev = S.Events(ev.det1, ev.det2, ev.tof, ev.corr, np.full(ev.n, np.float32(0.05)))
     geo = _geometry(O, sc, g, tof)
     lf = np.random.default_rng(2).uniform(0.4, 1.0, sc.n_lor).astype(np.float32)
