@@ -164,8 +164,8 @@ def test_lmpdhg_reaches_independent_minimiser(oracle_mod, prior):
 
 
 def _sino_setup(O, geo, sc, tof, ev, n_subsets, lm_subset_of_event):
-    nb = tof.n_bins
-    M = tof.half
+    nb = max(tof.n_bins, 1)  # non-TOF: one bin per LOR
+    M = (nb - 1) // 2
     l = S.lor_of_events(sc, ev.det1, ev.det2)
     # canonical orientation: the TOF bin is signed toward the canonical det2
     d1c = np.empty_like(ev.det1)
@@ -181,19 +181,20 @@ def _sino_setup(O, geo, sc, tof, ev, n_subsets, lm_subset_of_event):
     return d, s, sub, b
 
 
-@pytest.mark.parametrize("n_subsets,dup_free,prior,n", [(1, False, "tv", (6, 5, 1)), (3, True, "tv", (6, 5, 1)),
-                                                      (3, True, "dtv", (6, 5, 1)), (3, True, "tv", (4, 3, 2)),
-                                                      (2, True, "dtv", (4, 3, 2))])
-def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free, prior, n):
+@pytest.mark.parametrize("n_subsets,dup_free,prior,n,n_bins", [
+    (1, False, "tv", (6, 5, 1), 9), (3, True, "tv", (6, 5, 1), 9), (3, True, "dtv", (6, 5, 1), 9),
+    (3, True, "tv", (4, 3, 2), 9), (2, True, "dtv", (4, 3, 2), 9), (1, False, "tv", (6, 5, 1), 0)])
+def test_lm_spdhg_equals_sinogram_spdhg(oracle_mod, n_subsets, dup_free, prior, n, n_bins):
     """Appendix: LM-SPDHG is SPDHG on the listmode reformulation.  With the
     same selection sequence (n = 1 with duplicated events, or n = 3 on
     duplicate-free data with the sinogram subset of a bin = the listmode
     subset of its event), Alg. 1 on the full sinogram (empty bins included,
     y = 1 there, Eq. (yinit) elsewhere) and Alg. 2 give the same x, z, w, and
     y of an event equals y of its bin.  Empty bins keep y = 1 (Sec.
-    "Memory-efficient SPDHG").  The objectives differ by sum_b s_b only."""
+    "Memory-efficient SPDHG").  The objectives differ by sum_b s_b only.
+    Also on two-slice grids and without TOF (one bin per LOR)."""
     O = oracle_mod
-    sc, g, tof, ev = tiny_problem(n=n, n_events=350, seed=11, dup_free=dup_free)
+    sc, g, tof, ev = tiny_problem(n=n, n_bins=n_bins, n_events=350, seed=11, dup_free=dup_free)
     ev = S.Events(ev.det1, ev.det2, ev.tof, ev.corr, np.full(ev.n, np.float32(0.05)))
     geo = _geometry(O, sc, g, tof)
     lf = np.random.default_rng(2).uniform(0.4, 1.0, sc.n_lor).astype(np.float32)
@@ -277,6 +278,12 @@ def test_step_sizes_meet_the_spdhg_condition(oracle_mod, binding, n_sub):
     lm = O.LM(geo, E, mu, n_sub, beta=1e30, gamma=gamma, rho=rho, knorm=kn)
     lm.init(np.full(V, 2.0, np.float32), n_sub * sens1)
     T = lm.T.copy()
+    # Alg. 1's oracle takes the same primal step sizes
+    NB = geo.n_lor * tof.n_bins
+    sino = O.Sino(geo, lf, np.zeros(NB), np.ones(NB), np.zeros(NB, np.int32), n_sub, beta=1e30, gamma=gamma,
+                  rho=rho, knorm=kn)
+    sino.init(np.full(V, 2.0, np.float32), n_sub * sens1)
+    np.testing.assert_array_equal(sino.T, T)
     # data term of one subset (one copy of every bin): the dense operator; its column sums are P^T 1
     A = _dense_lm_matrix(O, geo, _all_bins(O, geo, tof, lf))
     np.testing.assert_allclose(A.sum(0), sens1, rtol=1e-12)
