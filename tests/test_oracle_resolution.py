@@ -22,8 +22,9 @@ def _sigma_vox(fwhm, h):
 
 
 @pytest.mark.parametrize("n,h,fwhm", [((24, 20, 1), (2.0, 2.0, 2.0), 4.5), ((16, 14, 12), (2.5, 2.5, 2.0), 6.0),
-                                      ((30, 9, 8), (1.0, 3.0, 2.5), 3.0)])
+                                      ((30, 9, 8), (1.0, 3.0, 2.5), 3.0), ((9, 7, 2), (2.0, 2.0, 6.0), 6.0)])
 def test_res_equals_scipy_gaussian_filter(oracle_mod, n, h, fwhm):
+    """Also on an axis of two voxels (one tap per side there)."""
     O = oracle_mod
     geo = _geo(O, n, h)
     rng = np.random.default_rng(1)
