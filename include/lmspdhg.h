@@ -409,6 +409,11 @@ int lmspdhg_image_kernel(lm_state* st, int32_t* kind);
  * the current events (0 for the direct kernel). */
 int lmspdhg_projector(lm_state* st, int32_t* kind, int64_t* n_segments);
 
+/* Frees the host handle, its captured epoch graph and its capture stream.
+ * The state buffer, the events and the images it referenced stay the
+ * caller's (no device memory is freed); work already queued on the caller's
+ * stream must be complete or ordered before the buffer is reused.  NULL is
+ * a no-op.  Returns LM_OK. */
 int lmspdhg_destroy(lm_state* st);
 
 /* ---- listmode EM-TV: the warm start x0 (Alg. 3) ------------------------- */
