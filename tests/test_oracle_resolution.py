@@ -95,3 +95,22 @@ def test_em_step_with_resolution_is_gradient_step(oracle_mod):
     want = x - x * n_sub / sens * grad
     z = O.EMTV(geo, E, n_sub, beta=0.0, knorm=1.0, res_fwhm=fwhm).em_step(x, sens, i)
     np.testing.assert_allclose(z, want, rtol=1e-6, atol=1e-7 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("sig_vox", [1.0, 1.6])
+def test_res_clipped_taps_equal_scipy_radius(oracle_mod, sig_vox):
+    """On axes shorter than the kernel the taps stop at r = n_d - 1 (each
+    image value reflected at most once): the same as scipy's mirrored
+    Gaussian filter with that radius.  sigma 1 voxel: r = 3 on axes of 5, 3
+    and 4 voxels (clipped on the axis of 3, where r = n); sigma 1.6: r = 5
+    (clipped on every axis)."""
+    pytest.importorskip("scipy", minversion="1.10")
+    O = oracle_mod
+    n, h = (5, 3, 4), (1.0, 1.0, 1.0)
+    fwhm = sig_vox * 2.0 * math.sqrt(2.0 * math.log(2.0))
+    geo = _geo(O, n, h)
+    x = np.random.default_rng(4).uniform(0.0, 2.0, geo.V)
+    got = O.res_apply(geo, fwhm, x).reshape(n[2], n[1], n[0])
+    r = [min(int(math.floor(3.0 * sig_vox + 0.5)), n[d] - 1) for d in (2, 1, 0)]
+    want = ndimage.gaussian_filter(x.reshape(n[2], n[1], n[0]), sigma=[sig_vox] * 3, mode="reflect", radius=r)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
