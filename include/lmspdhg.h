@@ -131,8 +131,11 @@ int lm_back(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const 
  * few words, 32 MiB + 256 B, held on every GPU that loads the library until
  * the process exits.  Grids above 2^22 voxels are rejected with
  * LM_ERR_NOMEM.  The result equals lm_back's deterministic result.  The first
- * call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Every call
+ * call in a CUDA context looks up the array's device address in that
+ * context (with its device current) and caches it under the context's id,
+ * so a context that is destroyed and created again (cudaDeviceReset) gets a
+ * fresh lookup; make the first call in each context before any stream
+ * capture.  Every call
  * clears and reuses the same array, so calls that overlap on the GPU (other
  * streams, other threads, concurrent graph replays) race and must be
  * serialised by the caller.  The paper has no counterpart to this call. */

@@ -12,7 +12,7 @@
 // GPU and stays allocated on every GPU that loads the library until the
 // process exits.  Host code must not use the array's name as an address
 // (in host code it is only a stand-in); the device address is looked up
-// once per device with cudaGetSymbolAddress and passed to the kernels.
+// once per CUDA context with cudaGetSymbolAddress and passed to the kernels.
 #include <cstring>
 #include <mutex>
 
@@ -28,26 +28,80 @@ constexpr int64_t kTail = 32;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kMaxVox + kTail];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the scratch on the current device (looked up on the
-// first call for that device, with that device current).
+// Identity of the calling thread's current CUDA context (0 when the thread
+// has none yet).  The scratch is a module global, so its address belongs to
+// the context that loaded the module: a context destroyed and created again
+// (cudaDeviceReset, or a re-created primary context) loads the module anew,
+// possibly at another address.  Context ids are unique within the process
+// and never reused, unlike context handles.
+int current_context_id(unsigned long long* id)
+{
+    static CtxGetCurrent get_cur = nullptr;
+    static CtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetId>(p);
+    });
+    LM_CHECK(get_cur != nullptr && get_id != nullptr, LM_ERR_CUDA,
+             "cuCtxGetCurrent / cuCtxGetId are not available from the driver");
+    *id = 0;
+    CUcontext ctx = nullptr;
+    CUresult r = get_cur(&ctx);
+    LM_CHECK(r == CUDA_SUCCESS, LM_ERR_CUDA, "cuCtxGetCurrent failed (%d)", (int)r);
+    if (ctx == nullptr) return LM_OK;
+    r = get_id(ctx, id);
+    LM_CHECK(r == CUDA_SUCCESS && *id != 0, LM_ERR_CUDA, "cuCtxGetId failed (%d)", (int)r);
+    return LM_OK;
+}
+
+constexpr int kMaxContexts = 64;
+std::mutex g_mu;
+unsigned long long g_ctx[kMaxContexts] = {};
+void* g_addr[kMaxContexts] = {};
+int g_n = 0;  // entries in use; when full, the oldest entry is replaced
+int g_next = 0;
+
+// Device address of the scratch in the current context, looked up with
+// cudaGetSymbolAddress on the first call made in that context (with its
+// device current) and cached under the context's id.
 int scratch_address(void** out)
 {
-    int dev = 0;
-    LM_CUDA(cudaGetDevice(&dev));
-    LM_CHECK(dev >= 0 && dev < kMaxDevices, LM_ERR_INVALID_ARG, "device ordinal %d not supported", dev);
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_addr[dev] == nullptr) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        LM_CHECK(e == cudaSuccess && p != nullptr, LM_ERR_CUDA, "cudaGetSymbolAddress of the scratch failed: %s",
-                 cudaGetErrorString(e));
-        g_addr[dev] = p;
+    for (int i = 0; id != 0 && i < g_n; ++i)
+        if (g_ctx[i] == id) {
+            *out = g_addr[i];
+            return LM_OK;
+        }
+    // first call in this context: cudaGetSymbolAddress also makes the runtime
+    // bind the device's primary context when the thread had none
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    LM_CHECK(e == cudaSuccess && p != nullptr, LM_ERR_CUDA, "cudaGetSymbolAddress of the scratch failed: %s",
+             cudaGetErrorString(e));
+    if (id == 0) {
+        rc = current_context_id(&id);
+        if (rc) return rc;
+        LM_CHECK(id != 0, LM_ERR_CUDA, "no current CUDA context after the symbol lookup");
     }
-    *out = g_addr[dev];
+    const int slot = g_n < kMaxContexts ? g_n++ : g_next;
+    if (g_n == kMaxContexts) g_next = (slot + 1) % kMaxContexts;
+    g_ctx[slot] = id;
+    g_addr[slot] = p;
+    *out = p;
     return LM_OK;
 }
 

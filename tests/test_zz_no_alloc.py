@@ -15,6 +15,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O
 from paper_2201_05497_gb300 import synth as S
 from tests import _helpers as H
 
@@ -45,11 +46,14 @@ def _noalloc(lm, geo, ev, v, img):
 def test_noalloc_matches_workspace_version_twice(lm, name, n):
     wl, lf, ev = H.workload_data(name, n)
     geo = lm.Geometry.from_workload(wl)
+    geo_o = O.Geometry.from_workload(wl)
     dev = lm.DeviceEvents.from_numpy(ev)
     rng = np.random.default_rng(4)
-    base = torch.from_numpy(rng.uniform(0, 1, geo.V).astype(np.float32)).cuda()
+    base_np = rng.uniform(0, 1, geo.V).astype(np.float32)
+    base = torch.from_numpy(base_np).cuda()
     for call in range(2):
-        v = torch.from_numpy(rng.normal(size=ev.n).astype(np.float32)).cuda()
+        v_np = rng.normal(size=ev.n).astype(np.float32)
+        v = torch.from_numpy(v_np).cuda()
         ref = lm.back(geo, v, dev, img=base.clone(), deterministic=True)
         out = base.clone()
         rc = _noalloc(lm, geo, dev, v, out)
@@ -59,6 +63,10 @@ def test_noalloc_matches_workspace_version_twice(lm, name, n):
         assert H.rel_l2(o, r) < H.REL_EVENT, f"call {call}"
         # the fixed-point sums are exact, so the two versions agree bit for bit
         np.testing.assert_array_equal(o, r)
+        # and both are the adjoint of the listmode projector: the FP64 oracle's
+        # (P^LM)^T v added to the starting image
+        img_or = base_np.astype(np.float64) + O.back(geo_o, ev, v_np.astype(np.float64))
+        assert H.rel_l2(o, img_or) < H.REL_EVENT, f"call {call} vs oracle"
 
 
 def test_noalloc_rejects_grids_above_its_capacity(lm):
