@@ -10,8 +10,9 @@ the paper's notation: ``fwd`` is P^LM (Eq. lmop), ``back`` its adjoint,
 ``sens`` is P^T 1, ``lm_init``/``lm_update`` are Alg. 2, ``sino_*`` are
 Alg. 1 on a full TOF sinogram, ``dtv_*`` the directional TV operator (the
 paper's second prior; ``xi`` of ``LM``/``Sino``), ``EMTV``/``emtv_denoise`` are Alg. 3 (the
-listmode EM-TV warm start).  The denoiser's iterate path at a fixed iteration
-count (its extrapolation step) is parity unpinned; its limit is pinned.
+listmode EM-TV warm start).  Every function is pinned by the CPU tests,
+including the denoiser's iterate path at a fixed iteration count and the two
+tolerance helpers ``tof_edge_distance`` and ``fwd_position_sensitivity``.
 """
 from __future__ import annotations
 

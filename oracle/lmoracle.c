@@ -43,10 +43,13 @@
  * grids, prox fixed points, TV adjoint and norm, LM == sinogram SPDHG; EM-TV:
  * the EM step as a scaled log-likelihood gradient step (finite differences),
  * the denoiser's closed form (two voxels), an independent dual solve,
- * optimality conditions, Chambolle-Pock's rate bound and limits (see the CPU
- * tests).  The denoiser's extrapolation ubar = u+ + theta (u+ - u) is pinned
- * only through these: leaving it out reaches the same limit, so the iterate
- * path at a fixed iteration count is parity unpinned.
+ * optimality conditions, Chambolle-Pock's asymptotic and non-asymptotic
+ * rate bounds (the latter fails without the extrapolation) and limits; the
+ * iterate path at a fixed iteration count against the first ten iterates of
+ * the two-voxel problem in 40-digit arithmetic (see the CPU tests).  The two
+ * tolerance helpers at the end are pinned through the forward projector:
+ * the TOF cut margin by moving the cut, the position sensitivity by finite
+ * differences under a detector shift.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1084,7 +1087,8 @@ void or_fwd_position_sensitivity(const or_scanner* sc, const or_grid* g, const o
                     }
                 double g1 = (1.0 - f2) * (v[1][0] - v[0][0]) + f2 * (v[1][1] - v[0][1]);
                 double g2 = (1.0 - f1) * (v[0][1] - v[0][0]) + f1 * (v[1][1] - v[1][0]);
-                acc += step * wt * (fabs(g1) + (g->n[s2] > 1 ? fabs(g2) : 0.0));
+                /* an axis of one voxel has no in-plane position to round */
+                acc += step * wt * ((g->n[s1] > 1 ? fabs(g1) : 0.0) + (g->n[s2] > 1 ? fabs(g2) : 0.0));
             }
         }
         out[e] = acc * (corr ? (double)corr[e] : 1.0);

@@ -350,3 +350,137 @@ def test_sensitivity_is_tof_summed_backprojection(oracle_mod):
         total += float(lf[l]) * O.lor_tofsum_fwd(geo, d1, d2, x)
     assert abs(np.dot(sens, x) - total) <= 1e-11 * abs(total)
     assert np.all(sens >= 0)
+
+
+# --------------------------------------------------------------------------
+# The two tolerance helpers (they state how loose a GPU parity check may be,
+# so they are pinned too): both are checked through the forward projector
+# alone, under a change of the TOF cut or of the detector positions.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["2d_small", "3d_small"])
+def test_tof_edge_distance_is_the_cut_margin(oracle_mod, name):
+    """d_e = distance of the event's nearest in-grid sample from the TOF
+    truncation edge.  The bin weight does not depend on the cut, only the
+    inclusion test |t - c_m| <= W does, so moving the cut W by less than d_e
+    leaves (P^LM 1)_e unchanged bit for bit, while moving it by a little more
+    than d_e (inwards or outwards, whichever side the nearest sample is on)
+    changes it.  The image is all ones so that every in-grid sample
+    contributes; the change is checked for d_e < sigma / 2, where the
+    crossing sample's bin weight is far from underflowing to 0 in FP64.
+    Events without an in-grid sample have d_e = inf and project to 0."""
+    O = oracle_mod
+    wl = S.workload(name)
+    t = S.Tof(8.0, 6.0, 3.0, 61)  # W = 24 mm: n_sigma's float32 resolution moves W by ~2e-6 mm
+    ev = S.uniform_events(wl.scanner, t, 600, seed=13)
+    E = O.EventArrays.from_events(ev)
+    geo = _geo(O, wl, t)
+    ones = np.ones(geo.V, np.float32)
+    d = O.tof_edge_distance(geo, E)
+    p0 = O.fwd(geo, E, ones)
+    assert np.all(p0[~np.isfinite(d)] == 0.0)
+    fin = np.isfinite(d) & (d > 1e-3)
+    assert fin.sum() > 200
+    W = t.n_sigma * t.sigma
+
+    def p_with_cut(Wn):
+        return O.fwd(_geo(O, wl, S.Tof(t.sigma, t.bin, Wn / t.sigma, t.n_bins)), E, ones)
+
+    # one geometry per distinct cut would be slow: group events by a cut that
+    # suits all of them (the margin scales with each event's own d_e)
+    for f_in, f_out, must_change in ((0.99, 0.99, False), (1.01, 1.01, True)):
+        idx = np.nonzero(fin)[0]
+        lo = np.empty(idx.size)
+        hi = np.empty(idx.size)
+        for k, e in enumerate(idx):
+            sub = O.EventArrays(E.det1[e:e + 1], E.det2[e:e + 1], E.tof[e:e + 1], E.corr[e:e + 1])
+            lo[k] = O.fwd(_geo(O, wl, S.Tof(t.sigma, t.bin, (W - f_in * d[e]) / t.sigma, t.n_bins)), sub, ones)[0]
+            hi[k] = O.fwd(_geo(O, wl, S.Tof(t.sigma, t.bin, (W + f_out * d[e]) / t.sigma, t.n_bins)), sub, ones)[0]
+        same = (lo == p0[idx]) & (hi == p0[idx])
+        if must_change:
+            near = d[idx] < 0.5 * t.sigma
+            assert near.sum() > 30
+            assert not np.any(same[near])
+        else:
+            assert np.all(same)
+
+
+@pytest.mark.parametrize("name", ["2d_small", "3d_small"])
+def test_position_sensitivity_is_the_gradient_norm(oracle_mod, name):
+    """G_e = corr_e sum_samples step w_tof (|d interp/d u_1| + |d interp/d u_2|),
+    u_1, u_2 the secondary voxel coordinates (axes k+1, k+2 mod 3 of the
+    principal axis k).  Translating every detector by delta along a
+    secondary axis a moves every sample of the event by delta/h_a voxels
+    along a and leaves the principal-axis planes and the TOF coordinates
+    alone, so (p(delta) - p(0))/delta h_a is the signed sum of d interp/d u_a.
+    For the ramp x = 1 + 3 i_x + 5 i_y + 7 i_z (bilinear interpolation of a
+    linear function is exact) and events whose samples keep all their
+    neighbours inside the grid, every sample's derivative along a is the
+    ramp's slope, so |D_1| + |D_2| = G_e; different slopes per axis catch a
+    wrong choice of axes.  For a random image, |D_1| + |D_2| <= G_e (triangle
+    inequality) away from cell crossings.  An axis of one voxel (z of a 2D
+    grid) has no position to round and no term."""
+    O = oracle_mod
+    wl = S.workload(name)
+    sc, g, t = wl.scanner, wl.grid, wl.tof
+    t = S.Tof(8.0, 6.0, 3.0, 61)  # a short TOF window: more events keep all samples inside the grid
+    ev = S.uniform_events(sc, t, 3000, seed=17)
+    E = O.EventArrays.from_events(ev)
+    tab = sc.crystal_table().astype(np.float32)
+    geo = _geo(O, wl, t)
+    nx, ny, nz = g.n
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ramp = (1.0 + 3.0 * ix + 5.0 * iy + 7.0 * iz).astype(np.float32).reshape(-1)
+    slope = (3.0, 5.0, 7.0)
+    # interior events: enlarging the grid by two voxels on every side (same
+    # voxel centres) does not change their projection of ones
+    big_n = tuple(m + 4 if m > 1 else m for m in g.n)
+    big_o = tuple(o - 2 * hh if m > 1 else o for o, hh, m in zip(g.origin, g.h, g.n))
+    geo_big = O.Geometry(tab, sc.n_rings, sc.n_xtal, big_n, g.h, big_o, (t.sigma, t.bin, t.n_sigma, t.n_bins))
+    p1 = O.fwd(geo, E, np.ones(geo.V, np.float32))
+    p1b = O.fwd(geo_big, E, np.ones(int(np.prod(big_n)), np.float32))
+    inner = (p1 > 0) & (np.abs(p1b - p1) <= 1e-13 * p1)
+    assert inner.sum() > 40
+    # principal axis of each event as the projector defines it (float32 differences)
+    dd = (tab[ev.det2] - tab[ev.det1]).astype(np.float32)
+    k = np.argmax(np.abs(dd), axis=1)
+    delta = 2.0 ** -6  # mm; the shifted float32 coordinates stay exact to ~1e-6 mm
+
+    def deriv(x, axis, sign):
+        sh = tab.copy()
+        sh[:, axis] += np.float32(sign * delta)
+        step = (sh[:, axis].astype(np.float64) - tab[:, axis])  # the shift actually applied per crystal
+        geo_s = O.Geometry(sh, sc.n_rings, sc.n_xtal, g.n, g.h, g.origin, (t.sigma, t.bin, t.n_sigma, t.n_bins))
+        assert np.all(np.abs(step - sign * delta) <= 1e-6)
+        return (O.fwd(geo_s, E, x) - O.fwd(geo, E, x)) / (sign * delta) * g.h[axis]
+
+    ev_i = np.arange(E.n)
+    s1, s2 = (k + 1) % 3, (k + 2) % 3
+    for x, exact in ((ramp, True), (np.random.default_rng(5).uniform(0, 1, geo.V).astype(np.float32), False)):
+        G = O.fwd_position_sensitivity(geo, E, x)
+        Dp = np.array([deriv(x, a, +1.0) for a in range(3)])
+        Dm = np.array([deriv(x, a, -1.0) for a in range(3)])
+        # no sample crosses a cell face within +-delta (else the one-sided
+        # derivatives differ, e.g. a sample exactly on the last slice)
+        # (an axis of one voxel always has its face at the sample: there the
+        # helper, like the forward difference, takes the derivative upwards)
+        smooth = np.ones(E.n, bool)
+        for s in (s1, s2):
+            a, b = Dp[s, ev_i], Dm[s, ev_i]
+            flat = np.array([g.n[v] == 1 for v in s])
+            smooth &= flat | (np.abs(a - b) <= 1e-5 * (np.abs(a) + np.abs(b) + 1e-12 * G.max()))
+        use1 = np.array([g.n[v] > 1 for v in s1])
+        use2 = np.array([g.n[v] > 1 for v in s2])
+        both = np.where(use1, np.abs(Dp[s1, ev_i]), 0.0) + np.where(use2, np.abs(Dp[s2, ev_i]), 0.0)
+        if exact:
+            sel = inner & smooth
+            assert sel.sum() > 40
+            np.testing.assert_allclose(both[sel], G[sel], rtol=1e-4)
+            # per axis, the derivative is the ramp's slope times the event's summed weight
+            for e in np.nonzero(sel)[0]:
+                a1, a2 = s1[e], s2[e]
+                if g.n[a1] > 1 and g.n[a2] > 1:
+                    assert abs(Dp[a1, e] / Dp[a2, e] - slope[a1] / slope[a2]) <= 1e-3 * slope[a1] / slope[a2]
+        else:
+            assert smooth.mean() > 0.8
+            sel = smooth & (G > 0)
+            assert np.all(both[sel] <= G[sel] * (1 + 1e-4))
