@@ -1,21 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of LM-SPDHG (Alg. 2) on one GB300 per rank.
 
-Workload (default): the 3D short dynamic frame - 36 rings x 672 crystals on
-a 410 mm radius, 200 x 200 x 96 float32 image of 2.5 mm voxels, ellipsoid
+Workload (default): the 3D long static acquisition - 36 rings x 672 crystals
+on a 410 mm radius, 200 x 200 x 96 float32 image of 2.5 mm voxels, ellipsoid
 phantom in an attenuating elliptic cylinder, 400 ps TOF (41 bins of 22.2 mm,
-3-sigma cut), 1e7 Monte Carlo events (int32 crystal pairs, int16 TOF bin,
-float32 correction and contamination, 20 % flat contamination), 28 subsets,
-TV beta = 0.03.
+3-sigma cut), 5e8 Monte Carlo events with every per-event array resident in
+HBM (int32 crystal pairs, int16 TOF bin, float32 correction and
+contamination, 20 % flat contamination), 56 subsets, 10 epochs, TV
+beta = 0.01.  The largest configuration that one GPU holds.
 
 One step = one frame reconstruction through the C ABI: event set-up
 (validation, event counts, subset split), initialisation (y, z, T, first
-primal step), 10 epochs of 2n = 56 updates (each epoch a replayed CUDA
-graph) and the FP64 objective.  The sensitivity image P^T 1 and ||K|| are
-per scanner / grid and computed once before the timed steps (reported as
-sens_ms, knorm_ms).  The metric counts the events forward- and
-back-projected per second: the initialisation's N plus the events of every
-data update.
+primal step), 10 epochs of 2n updates (each epoch a replayed CUDA graph) and
+the FP64 objective.  The sensitivity image P^T 1 and ||K|| are per scanner /
+grid and computed once before the timed steps (reported as sens_ms,
+knorm_ms).  The metric counts the events forward- and back-projected per
+second: the initialisation's N plus the events of every data update.
+
+Beside the headline the same JSON line carries, measured after it: the 3D
+short dynamic frame (1e7 events, 28 subsets, TV beta = 0.03, 10 epochs) as
+"short_frame", and the serving stream (64 frames, N log-uniform in
+[1e5, 2e7], continuous batching against one frame at a time) as "serving".
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch with torchrun; every rank reconstructs its own frame
@@ -49,13 +54,16 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="3d_short")
+    ap.add_argument("--workload", default="3d_long")
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--events", type=int, default=0, help="override the event count")
     ap.add_argument("--deterministic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="events in the oracle's timed sample")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the short-frame and serving measurements that follow the headline")
+    ap.add_argument("--cpu-sample", type=int, default=500_000, help="events in the oracle's timed sample")
     ap.add_argument("--knorm-iters", type=int, default=1000)
     ap.add_argument("--prior", default="tv", choices=["tv", "dtv"],
                     help="tv: the TV prior; dtv: the directional TV prior with the flipped-contrast phantom "
@@ -68,8 +76,9 @@ def parse_args():
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the (untimed-region) measurement of the listmode EM-TV warm start")
     ap.add_argument("--pdhg-iters", type=int, default=20, help="inner iterations of the EM-TV denoising")
-    ap.add_argument("--projector", default="direct", choices=["direct", "tiled"],
-                    help="projector of the data updates: the direct event kernel or the tile-binned one")
+    ap.add_argument("--projector", default="auto", choices=["auto", "table", "direct", "tiled"],
+                    help="projector of the data updates: the traversal table (auto: where it applies), the "
+                         "direct event kernel or the tile-binned one")
     ap.add_argument("--serve", action="store_true",
                     help="serving run: a stream of dynamic frames through the continuous-batching server")
     ap.add_argument("--frames", type=int, default=64, help="frames in the serving run")
@@ -197,8 +206,9 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 def oracle_sample_step(wl, ev_np, n_sample, seq_epoch, beta=None, xi=None):
     """One oracle run on a bounded sample of the frame: the first n_sample
-    events, full image grid, initialisation + one epoch (2n updates), with
-    the TV prior or (xi given) the directional TV.
+    events, full image grid, initialisation + the updates of seq_epoch (one
+    epoch, 2n updates, or its first few), with the TV prior or (xi given) the
+    directional TV.
     Returns (events fwd+back projected, seconds)."""
     import oracle as O
     n = min(n_sample, ev_np.n)
@@ -230,10 +240,13 @@ def run_reference(args):
         return 0
     from paper_2201_05497_gb300 import synth as S
     wl = S.workload(args.workload)
-    n_sample = max(1000, args.cpu_sample // 4)
+    n_sample = max(1000, args.cpu_sample // 2)
     lf = S.lor_attenuation(wl.scanner, wl.phantom)
     ev = S.monte_carlo_events(wl.scanner, wl.phantom, wl.tof, n_sample, seed=2, lor_att=lf)
-    seq = S.selection_sequence(wl.n_subsets, 2 * wl.n_subsets, seed=3)
+    # a bounded step: the initialisation and the epoch's first updates (each full-grid
+    # update costs the oracle ~0.15 s whatever the event count)
+    n_upd = min(2 * wl.n_subsets, 8)
+    seq = S.selection_sequence(wl.n_subsets, 2 * wl.n_subsets, seed=3)[:n_upd]
     for _ in range(args.warmup):
         oracle_sample_step(wl, ev, n_sample, seq)
     tot_ev, tot_s = 0, 0.0
@@ -247,10 +260,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: FP64 CPU oracle, bounded sample of {n_sample} events on the full "
-                               f"grid, initialisation + one epoch per step", "events_per_step": tot_ev / args.steps},
+                               f"grid, initialisation + the first {n_upd} updates of an epoch per step",
+                   "events_per_step": tot_ev / args.steps},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"first {n_sample} Monte Carlo events of the frame, full "
-                                   f"{'x'.join(str(v) for v in wl.grid.n)} grid, init + {2 * wl.n_subsets} updates"},
+                                   f"{'x'.join(str(v) for v in wl.grid.n)} grid, init + {n_upd} updates"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -372,8 +386,9 @@ def run_gpu(args):
         h2d = sum(t.numel() * t.element_size() for t in host.values())
         d2h = geo.V * 4 + 8
         e2e_ms = []
+        n_e2e = max(1, min(args.steps, args.e2e_steps))
         barrier(world)
-        for k in range(args.steps):
+        for k in range(n_e2e):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for name, t in host.items():
@@ -386,13 +401,14 @@ def run_gpu(args):
             flush.zero_()
         barrier(world)
         te = reduce_max(world, sum(e2e_ms) / 1e3)
-        e2e = {"value": total_events / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * te / args.steps}
+        e2e = {"value": world * events_per_step * n_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * te / n_e2e, "steps": n_e2e}
 
     # ---- per-kernel timing of one epoch (direct launches, CUDA events on this stream) ----
     L.event_setup(geo, raw_dev, n_sub, into=pe, ws=setup_ws)
     st.reinit(x0)
     prof = st.profile(seqs[0])
+    tune = st.tuning()
     # exact traversal statistics per subset
     touches, samples = [], []
     for i in range(n_sub):
@@ -428,7 +444,7 @@ def run_gpu(args):
             "frac": ((b_gather + b_atomic) / t / 1e9) / eff_peak,
             "hbm_event_stream_gbs": b_events / t / 1e9, "hbm_frac": b_events / t / 1e9 / hbm_peak}
     # the TMA pass fuses the TV's dual step; the directional TV's stays in the event kernel
-    fused = st.tuning()["image_kernel"] == "tma" and xi is None
+    fused = tune["image_kernel"] == "tma" and xi is None
     if fused:
         # TMA-staged passes: the prior's dual step runs inside the image pass; the event
         # kernel launched for a prior update only reads the selection and returns
@@ -438,7 +454,7 @@ def run_gpu(args):
     elif xi is not None:
         # directional TV: the dual step reads x, w and the field and writes w+ and D = P(w+ - w);
         # the prior pass reads D (nd floats per voxel) in place of w and w+
-        tma = st.tuning()["image_kernel"] == "tma"
+        tma = tune["image_kernel"] == "tma"
         rows = [("prior_dual", 1, 4 + 16 * nd), ("image_pass_data", 2, 48 if args.deterministic else 64),
                 ("image_pass_prior_tma" if tma else "image_pass_prior", 3, 32 + 4 * nd)]
     else:
@@ -458,14 +474,27 @@ def run_gpu(args):
     dom = max(shares, key=shares.get)
     d = kern[dom]
     if d["bound"] == "l2":
+        table = tune["projector"] == "table"
         traffic = None
-        if args.workload == "3d_short" and args.events in (0, N) and not args.deterministic:
-            traffic = profiled_traffic("ev_kernel_data_update_3d_short.txt",
-                                       ["paper_2201_05497_gb300/csrc/lm_project.cu",
-                                        "paper_2201_05497_gb300/csrc/lm_device.cuh"])
+        if not args.deterministic and args.prior == "tv" and args.res_fwhm == 0:
+            # DRAM bytes per data update from the committed ncu summary of the 3D short frame
+            # (357 143 events per update), scaled by the events this workload's updates process
+            if table:
+                t_short = profiled_traffic("ev_table_kernel_data_update_3d_short.txt",
+                                           ["paper_2201_05497_gb300/csrc/lm_table.cu",
+                                            "paper_2201_05497_gb300/csrc/lm_device.cuh",
+                                            "paper_2201_05497_gb300/csrc/lm_internal.h"])
+            else:
+                t_short = profiled_traffic("ev_kernel_data_update_3d_short.txt",
+                                           ["paper_2201_05497_gb300/csrc/lm_project.cu",
+                                            "paper_2201_05497_gb300/csrc/lm_device.cuh"])
+            if t_short is not None:
+                traffic = t_short * (d["events_per_launch"] / 357143.0)
         roofline = {"bound": "l2", "achieved": d["achieved_gbs"], "peak": d["peak_gbs"], "unit": "GB/s",
-                    "frac": d["frac"], "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)",
-                    "kernel": "ev_kernel<EV_DATA> (fused data update)",
+                    "frac": d["frac"], "traffic": traffic,
+                    "traffic_unit": "DRAM bytes per data update (ncu, 3D short frame, scaled by events)",
+                    "kernel": ("ev_table_kernel (traversal-table data update: one launch per principal-axis "
+                               "family)" if table else "ev_kernel<EV_DATA> (fused data update)"),
                     "peak_source": "in-run L2 probe: harmonic mix of coalesced read %.0f GB/s and float atomic "
                                    "%.0f GB/s weighted by the kernel's gather/atomic bytes" % (peak_read, peak_atom),
                     "hbm_event_stream": {"achieved": d["hbm_event_stream_gbs"], "peak": hbm_peak,
@@ -498,6 +527,19 @@ def run_gpu(args):
                "sample": f"first {min(args.cpu_sample, N)} events of the frame on the full grid: FP64 init + "
                          f"one epoch ({2 * n_sub} updates), {s_cpu:.1f} s"}
 
+    # ---- the short frame and the serving stream, after the headline (one GPU only) ----
+    short, serving = None, None
+    if rank == 0 and world == 1 and not args.no_extra:
+        st.close()
+        del st, pe, raw, raw_dev, setup_ws, flush
+        torch.cuda.empty_cache()
+        if args.workload != "3d_short":
+            short = frame_measure("3d_short", 5, 3, args.knorm_iters)
+        cfg, serving, gen_serve = serve_measure("3d_short", args.frames, 10, args.max_slots, False,
+                                                args.knorm_iters)
+        serving["config"] = cfg
+        serving["generate_s"] = gen_serve
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -510,21 +552,95 @@ def run_gpu(args):
                                    + f"{'deterministic' if args.deterministic else 'atomic'} back-projection",
                        "n_events": N, "n_subsets": n_sub, "epochs_per_step": E,
                        "events_per_step": events_per_step, "parallelism": f"replicas x{world}",
-                       "l2": "256 MiB write between steps; per-step inputs (0.42 GB of events, 0.2 GB of images) "
-                             "exceed the 129 MB L2"},
+                       "l2": f"256 MiB write between steps; per-step inputs ({N * 42 / 1e9:.2f} GB of raw and "
+                             f"subset-ordered events, {17 * geo.V * 4 / 1e9:.2f} GB of images) exceed the 129 MB L2"},
             "epoch_ms": statistics.median(epoch_ms) if epoch_ms else None,
             "frames_per_s": world * args.steps / t_max,
             "sens_ms": sens_ms, "knorm_ms": knorm_ms, "generate_s": gen_s, "wall_s": wall,
             "roofline": roofline, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(launches), "clocks": clocks, "tuning": st.tuning(), "warm_start": warm,
+            "gpu_launches": int(launches), "clocks": clocks, "tuning": tune, "warm_start": warm,
             "sinogram_spdhg": sino,
             "objective_last": f_last,
+            "short_frame": short, "serving": serving,
         }
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def frame_measure(workload, steps, warmup, knorm_iters):
+    """One more workload on the same GPU, measured like the headline (frames
+    through the C ABI, CUDA events on the launching stream, L2 flush between
+    steps) with fewer steps: value, step and epoch times and the data
+    update's per-launch time from one profiled epoch."""
+    import torch
+    from paper_2201_05497_gb300 import lm as L, synth as S
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = S.workload(workload)
+    N, n_sub = wl.n_events, wl.n_subsets
+    geo = L.Geometry.from_workload(wl, device=dev)
+    lor_att = S.lor_attenuation_torch(wl.scanner, wl.phantom, device=dev)
+    raw = S.monte_carlo_events_torch(wl.scanner, wl.phantom, wl.tof, N, seed=2, lor_att=lor_att, device=dev)
+    raw_dev = L.DeviceEvents(raw.det1, raw.det2, raw.tof, raw.corr, raw.contam)
+    sens = L.sens(geo, lor_att)
+    del lor_att
+    kn = L.knorm_fp64(geo, knorm_iters)
+    x0 = torch.full((geo.V,), 0.8 * N / float(sens.double().sum().item()), dtype=torch.float32, device=dev)
+    ws = torch.empty(L.load_library().lm_setup_workspace_bytes(N), dtype=torch.uint8, device=dev)
+    pe = L.event_setup(geo, raw_dev, n_sub, ws=ws)
+    st = L.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=n_sub, rho=0.999, knorm=kn, kahan=True)
+    E = 10
+    seq = S.selection_sequence(n_sub, 2 * n_sub * E, seed=3)
+    seqs = [seq[2 * n_sub * e:2 * n_sub * (e + 1)] for e in range(E)]
+    sizes = np.diff(pe.sub_off)
+    per_step = N + int(sum(sizes[i] for i in seq if i < n_sub))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def frame(evs=None):
+        L.event_setup(geo, raw_dev, n_sub, into=pe, ws=ws)
+        st.reinit(x0)
+        for s_ in seqs:
+            if evs is not None:
+                a = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                evs.append(a)
+            st.epoch(s_)
+        if evs is not None:
+            a = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            evs.append(a)
+        return st.objective()
+
+    for _ in range(warmup):
+        frame()
+    torch.cuda.synchronize()
+    step_ms, epoch_ms = [], []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        evs = []
+        a.record(stream)
+        frame(evs)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        epoch_ms.extend(evs[i].elapsed_time(evs[i + 1]) for i in range(len(evs) - 1))
+        flush.zero_()
+    L.event_setup(geo, raw_dev, n_sub, into=pe, ws=ws)
+    st.reinit(x0)
+    prof = st.profile(seqs[0])
+    ms_data, n_data = prof["data_events"]
+    out = {"workload": f"{workload}: {wl.scanner.n_rings} rings x {wl.scanner.n_xtal} crystals, "
+                       f"{wl.grid.n[0]}x{wl.grid.n[1]}x{wl.grid.n[2]} image, {N} events, {n_sub} subsets, "
+                       f"TV beta={wl.beta}, {E} epochs per frame",
+           "value": per_step * steps / (sum(step_ms) / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": sum(step_ms) / steps, "epoch_ms": statistics.median(epoch_ms),
+           "frames_per_s": steps / (sum(step_ms) / 1e3), "events_per_step": per_step,
+           "data_update_us": 1e3 * ms_data / max(1, n_data), "tuning": st.tuning()}
+    st.close()
+    return out
 
 
 def sino_compare(L, S, wl, geo, raw, lor_att, sens, x0, beta, kn, seqs, n_sub, stream, dev, lm_epoch_ms):
@@ -664,38 +780,40 @@ def serving_frames(wl, n_frames, device):
     return frames, lor_att
 
 
-def run_serve(args):
+def serve_measure(workload, n_frames, E, max_slots, det, knorm_iters):
     """Serving: every frame of the stream reconstructed (E epochs) by the
-    continuous-batching server, against plain LM-SPDHG one frame at a time.
-    Throughput with all frames queued at t=0; latency (arrival to x on the
-    host) under Poisson arrivals at 0.8 x the one-at-a-time capacity."""
+    continuous-batching server, against plain LM-SPDHG one frame at a time
+    (the projector a lone frame gets by default).  Throughput with all
+    frames queued at t=0; latency (arrival to x on the host) under Poisson
+    arrivals at 0.8 x the one-at-a-time capacity.  Returns (config, serving
+    summary, generation seconds)."""
     import torch
     from paper_2201_05497_gb300 import build, lm as L, synth as S
     build.build()
     L.load_library()
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = S.workload(args.workload)
-    n_sub, E = wl.n_subsets, args.epochs
+    wl = S.workload(workload)
+    n_sub = wl.n_subsets
     geo = L.Geometry.from_workload(wl, device=dev)
     t0 = time.perf_counter()
-    frames, lor_att = serving_frames(wl, args.frames, dev)
+    frames, lor_att = serving_frames(wl, n_frames, dev)
     gen_s = time.perf_counter() - t0
     sens = L.sens(geo, lor_att)
     del lor_att
-    kn = L.knorm_fp64(geo, args.knorm_iters)
+    kn = L.knorm_fp64(geo, knorm_iters)
     ssum = float(sens.double().sum().item())
     seqs = [np.asarray(S.selection_sequence(n_sub, 2 * n_sub * E, seed=3 + k), dtype=np.uint16).reshape(E, -1)
             for k in range(len(frames))]
     x0v = [np.float32(0.8 * f[0].size / ssum) for f in frames]
     n_ev = [int(f[0].size) for f in frames]
-    det = bool(args.deterministic)
+    det = bool(det)
 
     # one frame at a time: host arrays -> device, set-up, create, E epochs, objective, x -> host
     def one(k):
         d1, d2, tb, cr, ct = (torch.from_numpy(a).to(dev, non_blocking=False) for a in frames[k])
         pe = L.event_setup(geo, L.DeviceEvents(d1, d2, tb, cr, ct), n_sub)
         st = L.LMSPDHG(geo, pe, sens, torch.full((geo.V,), float(x0v[k]), device=dev), beta=wl.beta,
-                       n_subsets=n_sub, knorm=kn, deterministic=det, kahan=True, group=32, projector="direct")
+                       n_subsets=n_sub, knorm=kn, deterministic=det, kahan=True)
         for e in range(E):
             st.epoch(seqs[k][e])
         obj = st.objective()
@@ -719,7 +837,7 @@ def run_serve(args):
     pool = int(min(0.6 * free, max(4 * fb_max, 48 << 30)))
 
     def server():
-        return L.Server(geo, sens, beta=wl.beta, knorm=kn, n_subsets=n_sub, epochs=E, max_slots=args.max_slots,
+        return L.Server(geo, sens, beta=wl.beta, knorm=kn, n_subsets=n_sub, epochs=E, max_slots=max_slots,
                         max_events=max(n_ev), pool_bytes=pool, deterministic=det, kahan=True, group=32)
 
     def drain(srv, tickets):
@@ -773,26 +891,31 @@ def run_serve(args):
         done = start + service[k]
         lat_one.append(1e3 * (done - arr[k]))
     lat_one = np.array(lat_one)
-    out = {
-        "metric": "serving frames/sec and p99 latency", "value": cap_srv, "unit": "frames/s", "n_gpus": 1,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"serving: {len(frames)} frames of the {args.workload} scanner and grid, "
-                               f"N log-uniform[1e5, 2e7] (total {sum(n_ev)} events), {E} epochs each, "
-                               f"{n_sub} subsets, FP32 with Kahan z, "
-                               f"{'deterministic' if det else 'atomic'} back-projection",
-                   "max_slots": args.max_slots, "pool_bytes": pool},
-        "serving": {
-            "frames_per_s": cap_srv, "frames_per_s_one_at_a_time": cap_one, "speedup": cap_srv / cap_one,
-            "events_per_s": sum(n_ev) * (1 + E) / sat_s,
-            "max_in_flight_saturated": inflight_sat, "max_in_flight_poisson": inflight_poi,
-            "lambda_per_s": lam, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "p50_ms_one_at_a_time": float(np.percentile(lat_one, 50)),
-            "p99_ms_one_at_a_time": float(np.percentile(lat_one, 99)),
-            "latency": "submit of the host arrays to x copied back to the host; one-at-a-time latencies "
-                       "from a FIFO of its measured per-frame service times under the same arrivals",
-        },
-        "generate_s": gen_s,
+    config = {"workload": f"serving: {len(frames)} frames of the {workload} scanner and grid, "
+                          f"N log-uniform[1e5, 2e7] (total {sum(n_ev)} events), {E} epochs each, "
+                          f"{n_sub} subsets, FP32 with Kahan z, "
+                          f"{'deterministic' if det else 'atomic'} back-projection",
+              "max_slots": max_slots, "pool_bytes": pool}
+    serving = {
+        "frames_per_s": cap_srv, "frames_per_s_one_at_a_time": cap_one, "speedup": cap_srv / cap_one,
+        "events_per_s": sum(n_ev) * (1 + E) / sat_s,
+        "max_in_flight_saturated": inflight_sat, "max_in_flight_poisson": inflight_poi,
+        "lambda_per_s": lam, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "p50_ms_one_at_a_time": float(np.percentile(lat_one, 50)),
+        "p99_ms_one_at_a_time": float(np.percentile(lat_one, 99)),
+        "latency": "submit of the host arrays to x copied back to the host; one-at-a-time latencies "
+                   "from a FIFO of its measured per-frame service times under the same arrivals",
+        "frames": len(frames), "epochs": E, "n_subsets": n_sub,
     }
+    return config, serving, gen_s
+
+
+def run_serve(args):
+    config, serving, gen_s = serve_measure(args.workload, args.frames, args.epochs, args.max_slots,
+                                           args.deterministic, args.knorm_iters)
+    out = {"metric": "serving frames/sec and p99 latency", "value": serving["frames_per_s"], "unit": "frames/s",
+           "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic", "config": config,
+           "serving": serving, "generate_s": gen_s}
     print(json.dumps(out))
     return 0
 

@@ -317,7 +317,25 @@ typedef struct {
     const int64_t* sino_qoff;/* sinogram = 2: qoff_out of lm_sino_count            */
     const float* sino_lorf;  /* sinogram = 2: LOR factor [lm_n_lor] (NULL = 1)     */
     float sino_s;            /* sinogram = 2: flat contamination s_b > 0           */
+    void* trav_buf;       /* device buffer of lmspdhg_trav_bytes() bytes for the  */
+    size_t trav_bytes;    /* traversal-table data update, or NULL.  Used for TOF  */
+                          /* data on 3D grids (n_y, n_z > 1, every axis < 2^15)  */
+                          /* in float-atomic mode without the resolution model,  */
+                          /* the tile-binned projector or sinogram bins; else    */
+                          /* ignored.  At create/reinit every event's traversal  */
+                          /* (the reading of Joseph's method: principal axis,    */
+                          /* plane range, secondary and TOF coordinates, sample  */
+                          /* length), 1/(P^LM 1)_e and 1/mu_e are stored (40 B   */
+                          /* per event); each data update then reads them        */
+                          /* instead of setting the traversals up again.  Same   */
+                          /* per-sample arithmetic as the direct kernel; S_e and */
+                          /* (y+ - y)/mu from the stored reciprocals.  Not used  */
+                          /* by batches.                                         */
 } lm_params;
+
+/* Bytes of the optional traversal-table buffer (lm_params.trav_buf): 40 per
+ * event (plus alignment); 0 for a grid the table does not serve. */
+size_t lmspdhg_trav_bytes(const lm_grid* grid, int64_t n_events);
 
 /* Bytes of the optional tile-binned projector buffer (lm_params.tile_buf):
  * about 136 per event plus per-tile tables. */
@@ -408,8 +426,9 @@ int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, doubl
 int lmspdhg_image_kernel(lm_state* st, int32_t* kind);
 
 /* Which projector the data updates use: 1 direct event kernel, 2 tile-binned
- * (lm_params.tile_buf); *n_segments receives the number of tile segments of
- * the current events (0 for the direct kernel). */
+ * (lm_params.tile_buf), 3 traversal table (lm_params.trav_buf); *n_segments
+ * receives the number of tile segments of the current events (0 for the
+ * others). */
 int lmspdhg_projector(lm_state* st, int32_t* kind, int64_t* n_segments);
 
 /* Frees the host handle, its captured epoch graph and its capture stream.

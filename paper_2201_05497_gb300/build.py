@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblmspdhg.so")
 SOURCES = ["lm_project.cu", "lm_image.cu", "lm_setup.cu", "lm_state.cu", "lm_noalloc.cu", "lm_server.cu", "lm_tile.cu",
-           "lm_emtv.cu", "lm_res.cu", "lm_sino.cu"]
+           "lm_emtv.cu", "lm_res.cu", "lm_sino.cu", "lm_table.cu"]
 HEADERS = ["lm_device.cuh", "lm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -64,6 +64,61 @@ __device__ __forceinline__ float tof_weight_tab(const lmk::Geo& G, const float* 
     return fmaf(f, tab[k + 1] - a, a);
 }
 
+// One sample of a traversal with the TOF weight from the table: base voxel
+// index and the four bilinear weights times TOF weight times sample length.
+template <bool TWO_D>
+__device__ __forceinline__ bool sample_tab(const lmk::Geo& G, const lmk::Lor& L, const float* tab, float inv_dt, int i, lmk::Smp& s)
+{
+    const float fi = (float)i;
+    const float tau = fmaf(fi, L.dtau, L.tau0);
+    const float wt = L.step * tof_weight_tab(G, tab, inv_dt, tau);
+    if (wt == 0.0f) return false;
+    const float ua = fmaf(fi, L.sa, L.ua0);
+    const float fla = floorf(ua);
+    const int ia = (int)fla;
+    const float fa = ua - fla;
+    const float wa0 = (ia >= 0 && ia < L.nA) ? (1.0f - fa) : 0.0f;
+    const float wa1 = (ia + 1 >= 0 && ia + 1 < L.nA) ? fa : 0.0f;
+    if (TWO_D) {
+        s.base = i * L.sk + ia * L.sA;
+        s.w0 = wt * wa0;
+        s.w1 = wt * wa1;
+        s.w2 = 0.0f;
+        s.w3 = 0.0f;
+        return (wa0 != 0.0f) || (wa1 != 0.0f);
+    } else {
+        const float ub = fmaf(fi, L.sb, L.ub0);
+        const float flb = floorf(ub);
+        const int ib = (int)flb;
+        const float fb = ub - flb;
+        const float wb0 = (ib >= 0 && ib < L.nB) ? (1.0f - fb) : 0.0f;
+        const float wb1 = (ib + 1 >= 0 && ib + 1 < L.nB) ? fb : 0.0f;
+        s.base = i * L.sk + ia * L.sA + ib * L.sB;
+        const float wtA0 = wt * wa0, wtA1 = wt * wa1;
+        s.w0 = wtA0 * wb0;
+        s.w1 = wtA1 * wb0;
+        s.w2 = wtA0 * wb1;
+        s.w3 = wtA1 * wb1;
+        return (s.w0 != 0.0f) || (s.w1 != 0.0f) || (s.w2 != 0.0f) || (s.w3 != 0.0f);
+    }
+}
+
+// Strides and extents of the traversal for principal axis k (set-up results
+// travel between lanes as k plus the affine coefficients).
+__device__ __forceinline__ void lor_strides(const lmk::Geo& G, int k, bool has_yf, lmk::Lor& L)
+{
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    if (k == 0) {
+        L.sk = 1; L.sA = nx; L.sB = nx * ny; L.nA = ny; L.nB = nz; L.yf = 0;
+    } else if (k == 1) {
+        L.nA = nx; L.nB = nz;
+        if (has_yf) { L.sk = 1; L.sA = ny; L.sB = nx * ny; L.yf = 1; }
+        else { L.sk = nx; L.sA = 1; L.sB = nx * ny; L.yf = 0; }
+    } else {
+        L.sk = nx * ny; L.sA = 1; L.sB = nx; L.nA = nx; L.nB = ny; L.yf = 0;
+    }
+}
+
 // Kernel launches issued by the library (graph replays count their nodes).
 void count_launch(int64_t n = 1);
 int64_t launch_total();
@@ -225,6 +280,50 @@ int tile_build(TileArgs& A, const TileLayout& L, char* base, int64_t N, const st
                bool two_d, cudaStream_t st, int64_t* n_segments);
 void tile_attributes();
 int launch_tile_update(const TileArgs& A, bool two_d, cudaStream_t st);
+
+// ---- traversal-table data update (lm_table.cu) ----
+// Per event (subset-contiguous order): the traversal of reading 1,
+// 1/(P^LM 1)_e and 1/mu_e, computed once per state.
+struct TravLayout {
+    size_t r0, r1, meta, total;
+};
+TravLayout trav_layout(const lm_grid* g, int64_t N);
+bool trav_capable(const lm_grid* g);  // 3D grids with n_y > 1, every axis < 2^15
+
+struct TabArgs {
+    lmk::Geo G;
+    // table
+    const float4* r0;      // (ua0, sa, ub0, sb)
+    const float4* r1;      // (tau0, dtau, step, 1/(P^LM 1)_e)
+    const int2* meta;      // (i0 | cnt << 15 | k << 30, bits of 1/mu_e); cnt = 0: inert event
+    // events
+    const float* corr;
+    const float* contam;
+    const uint16_t* mu;
+    float* y;
+    // images: the x the update gathers from, both layouts; z-paired accumulators (see EvArgs)
+    const float* x_std;
+    const float* x_yf;
+    float* acc_std;
+    float* acc_yf;
+    const float* tof_tab;  // TOF_TAB_N + 1 floats
+    // selection
+    const uint16_t* seq;
+    int u;
+    const int64_t* sub_off;
+    int n_subsets;
+    int64_t e_begin, e_end;  // used when seq == nullptr
+    float gamma_rho;
+    unsigned long long* queue;
+    unsigned* done;
+    int phase;             // 0: x-principal events only, 1: the others, -1: all
+};
+int trav_build(const lmk::Geo& G, const lm_events& ev, const uint16_t* mu, const float* tof_tab,
+               const TravLayout& L, char* base, cudaStream_t st);
+// variant: the lane-group width 8, 16 or 32 (32 compiled for 3 resident
+// blocks per SM), or 33 (width 32 compiled for 4 blocks per SM)
+int launch_table_update(const TabArgs& a, int variant, int grid, cudaStream_t st);
+int table_grid(int variant);
 
 // ---- image kernels (lm_image.cu) ----
 void launch_transpose_to_yf(const lm_grid* g, const float* src, float* dst, cudaStream_t st);

@@ -311,44 +311,8 @@ struct Cache {
     static constexpr int passes = ((TWO_D ? 80 : 64) + G - 1) / G;
 };
 
+using lmh::sample_tab;
 using lmh::tof_weight_tab;
-
-template <bool TWO_D>
-__device__ __forceinline__ bool sample_tab(const Geo& G, const Lor& L, const float* tab, float inv_dt, int i, Smp& s)
-{
-    const float fi = (float)i;
-    const float tau = fmaf(fi, L.dtau, L.tau0);
-    const float wt = L.step * tof_weight_tab(G, tab, inv_dt, tau);
-    if (wt == 0.0f) return false;
-    const float ua = fmaf(fi, L.sa, L.ua0);
-    const float fla = floorf(ua);
-    const int ia = (int)fla;
-    const float fa = ua - fla;
-    const float wa0 = (ia >= 0 && ia < L.nA) ? (1.0f - fa) : 0.0f;
-    const float wa1 = (ia + 1 >= 0 && ia + 1 < L.nA) ? fa : 0.0f;
-    if (TWO_D) {
-        s.base = i * L.sk + ia * L.sA;
-        s.w0 = wt * wa0;
-        s.w1 = wt * wa1;
-        s.w2 = 0.0f;
-        s.w3 = 0.0f;
-        return (wa0 != 0.0f) || (wa1 != 0.0f);
-    } else {
-        const float ub = fmaf(fi, L.sb, L.ub0);
-        const float flb = floorf(ub);
-        const int ib = (int)flb;
-        const float fb = ub - flb;
-        const float wb0 = (ib >= 0 && ib < L.nB) ? (1.0f - fb) : 0.0f;
-        const float wb1 = (ib + 1 >= 0 && ib + 1 < L.nB) ? fb : 0.0f;
-        s.base = i * L.sk + ia * L.sA + ib * L.sB;
-        const float wtA0 = wt * wa0, wtA1 = wt * wa1;
-        s.w0 = wtA0 * wb0;
-        s.w1 = wtA1 * wb0;
-        s.w2 = wtA0 * wb1;
-        s.w3 = wtA1 * wb1;
-        return (s.w0 != 0.0f) || (s.w1 != 0.0f) || (s.w2 != 0.0f) || (s.w3 != 0.0f);
-    }
-}
 
 // One sample, TOF weight from the table when the caller gave one.
 template <bool TWO_D>
@@ -359,21 +323,7 @@ __device__ __forceinline__ bool sample_any(const Geo& G, const Lor& L, int tofmo
     return sample_at<TWO_D>(G, L, tofmode, i, s);
 }
 
-// Strides and extents of the traversal for principal axis k (set-up results
-// travel between lanes as k plus the affine coefficients).
-__device__ __forceinline__ void lor_strides(const Geo& G, int k, bool has_yf, Lor& L)
-{
-    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
-    if (k == 0) {
-        L.sk = 1; L.sA = nx; L.sB = nx * ny; L.nA = ny; L.nB = nz; L.yf = 0;
-    } else if (k == 1) {
-        L.nA = nx; L.nB = nz;
-        if (has_yf) { L.sk = 1; L.sA = ny; L.sB = nx * ny; L.yf = 1; }
-        else { L.sk = nx; L.sA = 1; L.sB = nx * ny; L.yf = 0; }
-    } else {
-        L.sk = nx * ny; L.sA = 1; L.sB = nx; L.nA = nx; L.nB = ny; L.yf = 0;
-    }
-}
+using lmh::lor_strides;
 
 // One chunk of events [e0, e0 + nev) processed by the calling warp (see
 // ev_kernel).  x_std_in / x_yf_in: the image being projected, both layouts.

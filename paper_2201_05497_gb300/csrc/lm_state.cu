@@ -60,6 +60,9 @@ struct lm_state_s {
     float* dtvd;      // directional TV: P (w+ - w) of the last prior dual step [ndim][V]
     ResPlan res;
     int zlen;         // z slices per TMA work item
+    bool table;       // data updates from the traversal table (lm_table.cu)
+    TravLayout tv;    // its layout in the caller's buffer
+    char* tv_base;
     bool tiled;       // data updates by the tile-binned projector
     TileArgs ta;      // its per-frame tables (pointers into the caller's tile buffer)
     TileLayout tl;
@@ -67,6 +70,9 @@ struct lm_state_s {
     int64_t n_segments;
     size_t scr_bytes;
     int grid_ev, grid_fx, chunk;
+    int grid_tab;       // blocks of the traversal-table kernel
+    int tab_variant;    // its compiled variant (launch_table_update)
+    bool tab_split;     // one launch per principal-axis family (else one for all)
     int group;          // lanes per event of the event kernels
     double tune_ms[3];  // autotuner: forward projection of subset 0 with 8, 16, 32 lanes
     cudaStream_t cap_stream;
@@ -236,6 +242,47 @@ ImgArgs base_img_args(const lm_state* st)
     return a;
 }
 
+// Arguments of the traversal-table data update of update u (x in buffer cur).
+TabArgs base_tab_args(const lm_state* st, int cur)
+{
+    TabArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.G = st->G;
+    t.r0 = (const float4*)(st->tv_base + st->tv.r0);
+    t.r1 = (const float4*)(st->tv_base + st->tv.r1);
+    t.meta = (const int2*)(st->tv_base + st->tv.meta);
+    t.corr = st->corr;
+    t.contam = st->contam;
+    t.mu = st->mu;
+    t.y = st->y;
+    t.x_std = st->x[cur];
+    t.x_yf = st->xyf[cur];
+    t.acc_std = st->acc_std;
+    t.acc_yf = st->acc_yf;
+    t.tof_tab = st->tof_tab;
+    t.sub_off = st->sub_off;
+    t.n_subsets = st->n;
+    t.gamma_rho = (float)(st->gamma * (double)st->P.rho);
+    t.queue = st->queue;
+    t.done = st->done;
+    t.phase = -1;
+    return t;
+}
+
+// Stores every event's traversal and (P^LM 1)_e in the caller's table buffer.
+int build_table(lm_state* st, cudaStream_t s)
+{
+    lm_events ev;
+    std::memset(&ev, 0, sizeof(ev));
+    ev.det1 = st->det1;
+    ev.det2 = st->det2;
+    ev.tof = st->tofb;
+    ev.corr = st->corr;
+    ev.contam = st->contam;
+    ev.n = st->N;
+    return trav_build(st->G, ev, st->mu, st->tof_tab, st->tv, st->tv_base, s);
+}
+
 // Resolution model: G x into gx (x-fastest) and gxyf (y-fastest).  The pair
 // accumulators, zero between updates, hold the passes' temporaries and are
 // cleared again.
@@ -289,6 +336,25 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
             t.gamma_rho = (float)(st->gamma * (double)st->P.rho);
             int rc = launch_tile_update(t, st->two_d, s);
             LM_CHECK(rc == LM_OK, rc, "tile data update launch failed");
+            if (!tma_fuses_prior(st)) {
+                // the image pass needs w+ (and D) from the event kernel's prior branch
+                a.prior_only = 1;
+                rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
+                LM_CHECK(rc == LM_OK, rc, "prior update launch failed");
+            }
+        } else if (st->table) {
+            // the table kernel, one launch per principal-axis family so that one
+            // image layout and one accumulator layout share L2 (both return at
+            // once on a prior update)
+            TabArgs t = base_tab_args(st, cur);
+            t.seq = st->seq;
+            t.u = u;
+            int rc = LM_OK;
+            for (int ph = st->tab_split ? 0 : -1; ph < (st->tab_split ? 2 : 0) && rc == LM_OK; ++ph) {
+                t.phase = ph;
+                rc = launch_table_update(t, st->tab_variant, st->grid_tab, s);
+            }
+            LM_CHECK(rc == LM_OK, rc, "data update launch failed");
             if (!tma_fuses_prior(st)) {
                 // the image pass needs w+ (and D) from the event kernel's prior branch
                 a.prior_only = 1;
@@ -488,6 +554,91 @@ int autotune_group(lm_state* st, cudaStream_t s)
     return LM_OK;
 }
 
+// Autotuner of the traversal-table path: times the data update of subset 0
+// (from the x of the first update) with 8, 16 and 32 lanes per event, three
+// runs each (the first warms the caches), restoring the subset's duals
+// before every run; the accumulators are cleared afterwards, so the state is
+// as it was.
+int autotune_table(lm_state* st, cudaStream_t s)
+{
+    st->tune_ms[0] = st->tune_ms[1] = st->tune_ms[2] = 0.0;
+    const int64_t b0 = st->sub_off_h[0], n0 = st->sub_off_h[1] - st->sub_off_h[0];
+    if (n0 <= 0) return LM_OK;
+    float* ysave = st->scr;  // the per-event scratch holds N floats
+    LM_CUDA(cudaMemcpyAsync(ysave, st->y + b0, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s));
+    TabArgs t = base_tab_args(st, st->xpar);
+    t.e_begin = b0;
+    t.e_end = b0 + n0;
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0));
+    LM_CUDA(cudaEventCreate(&e1));
+    // variants: widths 8, 16, 32 (3 blocks per SM) and 32 (4 blocks per SM)
+    const int variants[4] = {8, 16, 32, 33};
+    double ms[4] = {0.0, 0.0, 0.0, 0.0};
+    double best = 1e30;
+    int best_v = 32, rc = LM_OK;
+    for (int w = 0; w < 4 && rc == LM_OK; ++w) {
+        float tot = 0.0f;
+        for (int rep = 0; rep < 3 && rc == LM_OK; ++rep) {
+            cudaMemcpyAsync(st->y + b0, ysave, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s);
+            cudaEventRecord(e0, s);
+            rc = launch_table_update(t, variants[w], table_grid(variants[w]), s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float m = 0.0f;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (rep > 0) tot += m;
+        }
+        ms[w] = tot / 2.0;
+        if (ms[w] < best) {
+            best = ms[w];
+            best_v = variants[w];
+        }
+    }
+    // the chosen variant with the principal-axis families in one launch
+    // instead of two
+    double one = 0.0;
+    t.phase = -1;
+    for (int rep = 0; rep < 3 && rc == LM_OK; ++rep) {
+        cudaMemcpyAsync(st->y + b0, ysave, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s);
+        cudaEventRecord(e0, s);
+        rc = launch_table_update(t, best_v, table_grid(best_v), s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float m = 0.0f;
+        cudaEventElapsedTime(&m, e0, e1);
+        if (rep > 0) one += m / 2.0;
+    }
+    double two = 0.0;
+    for (int rep = 0; rep < 3 && rc == LM_OK; ++rep) {
+        cudaMemcpyAsync(st->y + b0, ysave, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s);
+        cudaEventRecord(e0, s);
+        for (int ph = 0; ph < 2 && rc == LM_OK; ++ph) {
+            t.phase = ph;
+            rc = launch_table_update(t, best_v, table_grid(best_v), s);
+        }
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float m = 0.0f;
+        cudaEventElapsedTime(&m, e0, e1);
+        if (rep > 0) two += m / 2.0;
+    }
+    st->tab_split = two <= one;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    st->tune_ms[0] = ms[0];
+    st->tune_ms[1] = ms[1];
+    st->tune_ms[2] = std::min(ms[2], ms[3]);
+    LM_CUDA(cudaMemcpyAsync(st->y + b0, ysave, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s));
+    LM_CUDA(cudaMemsetAsync(st->acc_std, 0, 2 * (size_t)st->V * 4, s));
+    LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, 2 * (size_t)st->V * 4, s));
+    st->tab_variant = best_v;
+    const int best_g = best_v == 33 ? 32 : best_v;
+    st->group = best_g;
+    return LM_OK;
+}
+
 // Events per work item for a launch over `count` events on `grid` blocks of
 // 8 warps: about four items per warp, between 1 and 32 (a whole warp's
 // per-lane set-up).
@@ -514,6 +665,12 @@ size_t lmspdhg_tile_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subse
 {
     if (check_grid(grid) || n_events < 0 || n_subsets < 1) return 0;
     return tile_layout(grid, n_events, n_subsets).total;
+}
+
+size_t lmspdhg_trav_bytes(const lm_grid* grid, int64_t n_events)
+{
+    if (check_grid(grid) || n_events < 0 || !trav_capable(grid)) return 0;
+    return trav_layout(grid, n_events).total;
 }
 
 size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subsets, int32_t deterministic)
@@ -695,6 +852,21 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
             st->tiled = true;
         }
     }
+    st->table = false;
+    st->tv_base = nullptr;
+    if (P.trav_buf != nullptr && tof->n_bins > 0 && !st->det && !st->has_res && !P.sinogram && !st->tiled &&
+        trav_capable(grid)) {
+        st->tv = trav_layout(grid, ev->n);
+        char* tb = (char*)(((uintptr_t)P.trav_buf + 255) / 256 * 256);
+        if (P.trav_bytes < st->tv.total || P.trav_bytes - (size_t)(tb - (char*)P.trav_buf) < st->tv.total - 256) {
+            set_error("traversal-table buffer of %zu bytes, %zu needed", P.trav_bytes, st->tv.total);
+            return fail(LM_ERR_NOMEM);
+        }
+        st->tv_base = tb;
+        rc = build_table(st, s);
+        if (rc) return fail(rc);
+        st->table = true;
+    }
     if (P.knorm > 0.0) {
         st->knorm = P.knorm;
     } else if (st->ndim == 0) {
@@ -712,9 +884,14 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     rc = init_iteration(st, x0, s);
     if (rc) return fail(rc);
     if (P.group == 0) {
-        rc = autotune_group(st, s);
+        rc = st->table ? autotune_table(st, s) : autotune_group(st, s);
         if (rc) return fail(rc);
     }
+    if (P.group != 0) {
+        st->tab_variant = st->group;
+        st->tab_split = true;
+    }
+    st->grid_tab = st->table ? table_grid(st->tab_variant) : 0;
     // the event kernels run with as many resident blocks as the chosen width allows
     st->grid_ev = ev_grid_g(st->det ? EV_DATA_FX1 : EV_DATA, st->two_d, st->group);
     st->grid_fx = ev_grid_g(EV_BACK_FX, st->two_d, st->group);
@@ -797,6 +974,11 @@ int lmspdhg_reinit(lm_state* st, const float* x0, void* stream)
             return rc;
         }
     }
+    if (st->table) {
+        // the events may be another frame's: store their traversals again
+        int rc = build_table(st, S(stream));
+        if (rc) return rc;
+    }
     return init_iteration(st, x0, S(stream));
 }
 
@@ -804,7 +986,7 @@ int lmspdhg_projector(lm_state* st, int32_t* kind, int64_t* n_segments)
 {
     clear_error();
     LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
-    if (kind) *kind = st->tiled ? 2 : 1;
+    if (kind) *kind = st->table ? 3 : (st->tiled ? 2 : 1);
     if (n_segments) *n_segments = st->tiled ? st->n_segments : 0;
     return LM_OK;
 }

@@ -53,7 +53,8 @@ class lm_params(C.Structure):
                 ("kahan", C.c_int32), ("group", C.c_int32), ("image_kernel", C.c_int32),
                 ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t), ("xi", C.c_void_p),
                 ("res_fwhm", C.c_float), ("sinogram", C.c_int32), ("sino_q", C.c_void_p),
-                ("sino_qoff", C.c_void_p), ("sino_lorf", C.c_void_p), ("sino_s", C.c_float)]
+                ("sino_qoff", C.c_void_p), ("sino_lorf", C.c_void_p), ("sino_s", C.c_float),
+                ("trav_buf", C.c_void_p), ("trav_bytes", C.c_size_t)]
 
 
 _lib = None
@@ -120,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lmspdhg_image_kernel": ([V, P(I32)], C.c_int),
         "lmspdhg_projector": ([V, P(I32), P(I64)], C.c_int),
         "lmspdhg_tile_bytes": ([P(lm_grid), I64, I32], SZ),
+        "lmspdhg_trav_bytes": ([P(lm_grid), I64], SZ),
         "lmspdhg_profile": ([V, P(C.c_uint16), I32, P(D), P(I64), V], C.c_int),
         "lm_kernel_launches": ([], I64),
         "lm_traversal_stats": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, SZ, P(I64), P(I64), V],
@@ -551,29 +553,43 @@ class LMSPDHG:
     def __init__(self, geo: Geometry, pe: PermutedEvents, sens_img: torch.Tensor, x0: torch.Tensor, *,
                  beta: float, n_subsets: int, gamma: float = 0.0, rho: float = 0.999, knorm: float = 0.0,
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
-                 image_kernel: int = 0, projector: str = "direct", xi: Optional[torch.Tensor] = None,
+                 image_kernel: int = 0, projector: str = "auto", xi: Optional[torch.Tensor] = None,
                  res_fwhm: float = 0.0, sinogram: int = 0, sino_s: float = 0.0,
                  sino_lorf: Optional[torch.Tensor] = None, stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.xi = xi  # directional TV field (referenced by the state), None = TV
         self.n_subsets = n_subsets
-        # projector of the data updates: "direct" (the event kernel) or "tiled" (the
-        # tile-binned projector, TOF data in float-atomic mode); "auto" takes the tiled
-        # one when its buffer needs at most a quarter of the free device memory
+        # projector of the data updates: "table" (stored traversals, 40 B per
+        # event; 3D TOF data in float-atomic mode without the resolution model
+        # or sinogram bins), "direct" (the event kernel), "tiled" (the
+        # tile-binned projector, TOF data in float-atomic mode); "auto" takes the
+        # table where it applies and the direct kernel elsewhere
         self.tile = None
-        if projector not in ("auto", "direct", "tiled"):
-            raise ValueError("projector must be 'auto', 'direct' or 'tiled'")
-        if projector != "direct" and geo.tof_nbins > 0 and not deterministic:
+        self.trav = None
+        if projector not in ("auto", "table", "direct", "tiled"):
+            raise ValueError("projector must be 'auto', 'table', 'direct' or 'tiled'")
+        if projector == "tiled" and geo.tof_nbins > 0 and not deterministic:
             tb = int(L.lmspdhg_tile_bytes(C.byref(geo.g), pe.events.n, int(n_subsets)))
-            if projector == "tiled" or tb <= torch.cuda.mem_get_info(x0.device)[0] // 4:
-                self.tile = torch.empty(tb, dtype=torch.uint8, device=x0.device)
+            self.tile = torch.empty(tb, dtype=torch.uint8, device=x0.device)
+        table_ok = (geo.tof_nbins > 0 and not deterministic and res_fwhm == 0.0 and sinogram == 0)
+        if projector == "table" and not table_ok:
+            raise ValueError("the traversal table needs TOF data in float-atomic mode, without the "
+                             "resolution model or sinogram bins")
+        if projector in ("auto", "table") and table_ok:
+            nb = int(L.lmspdhg_trav_bytes(C.byref(geo.g), pe.events.n))
+            if nb == 0 and projector == "table":
+                raise ValueError("the traversal table needs a 3D grid (n_y, n_z > 1)")
+            if nb > 0:
+                self.trav = torch.empty(nb, dtype=torch.uint8, device=x0.device)
         self.params = lm_params(beta, gamma, rho, knorm, knorm_iters, n_subsets, int(deterministic), int(kahan),
                                 int(group), int(image_kernel), None if self.tile is None else self.tile.data_ptr(),
                                 0 if self.tile is None else self.tile.numel(),
                                 _f32(xi, geo.ndim * geo.V, "xi"), float(res_fwhm),
                                 int(sinogram), _ptr(getattr(pe, "q", None)), _ptr(getattr(pe, "qoff", None)),
-                                _f32(sino_lorf, geo.n_lor, "sino_lorf"), float(sino_s))
+                                _f32(sino_lorf, geo.n_lor, "sino_lorf"), float(sino_s),
+                                None if self.trav is None else self.trav.data_ptr(),
+                                0 if self.trav is None else self.trav.numel())
         self._keep = (sino_lorf,)
         nbytes = L.lmspdhg_state_bytes_ex(C.byref(geo.g), pe.events.n, int(n_subsets), C.byref(self.params))
         if nbytes == 0:
@@ -656,7 +672,7 @@ class LMSPDHG:
         _check(load_library().lmspdhg_projector(self.h, C.byref(pk), C.byref(nseg)))
         return dict(group=g.value, ms_g8=ms[0], ms_g16=ms[1], ms_g32=ms[2],
                     image_kernel={1: "plain", 2: "tma", 3: "tma_data"}[kind.value],
-                    projector={1: "direct", 2: "tiled"}[pk.value], tile_segments=nseg.value)
+                    projector={1: "direct", 2: "tiled", 3: "table"}[pk.value], tile_segments=nseg.value)
 
     def close(self):
         if getattr(self, "h", None):

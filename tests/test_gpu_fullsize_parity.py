@@ -6,8 +6,8 @@ Monte Carlo events of the frame's generator (the FP64 oracle runs two epochs
 of these in about a minute).  The GPU runs the benchmark's own settings:
 float mode with the compensated z, the paired accumulators, the TMA-staged
 image passes chosen automatically, graph-replayed epochs, and the event
-kernel's lane-group width forced to 8, 16 and 32 in turn (the autotuner picks
-32 on this frame).  After two epochs x and z must be within 1e-3 relative L2
+kernel's lane-group width forced to 8, 16 and 32 in turn, with both the
+traversal-table data update (the benchmark's) and the direct event kernel.  After two epochs x and z must be within 1e-3 relative L2
 of the oracle and the FP64 objectives within 1e-5.
 
 The sensitivity image of the full scanner (P^T 1 over 2.9e8 LORs x 41 TOF
@@ -97,14 +97,15 @@ def frame(lm):
     return Frame(lm)
 
 
-@pytest.mark.parametrize("group", [8, 16, 32])
-def test_3d_short_grid_two_epochs_match_oracle(frame, group):
-    g = frame.gpu(group=group, kahan=True)
+@pytest.mark.parametrize("projector,group", [("table", 8), ("table", 16), ("table", 32), ("direct", 8),
+                                             ("direct", 16), ("direct", 32)])
+def test_3d_short_grid_two_epochs_match_oracle(frame, projector, group):
+    g = frame.gpu(group=group, kahan=True, projector=projector)
     t = g.tuning()
-    assert t["group"] == group and t["image_kernel"] == "tma" and t["projector"] == "direct", t
+    assert t["group"] == group and t["image_kernel"] == "tma" and t["projector"] == projector, t
     r = frame.compare(g)
     g.close()
-    print(f"FULLGRID_PARITY group={group} " + json.dumps(r))
+    print(f"FULLGRID_PARITY projector={projector} group={group} " + json.dumps(r))
     assert r["x_rel_l2"] < H.REL_L2_IMAGE, r
     assert r["z_rel_l2"] < H.REL_L2_IMAGE, r
     assert abs(r["objective_rel_gap"]) < 1e-5, r

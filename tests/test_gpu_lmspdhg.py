@@ -49,7 +49,7 @@ class Case:
         o.init(self.x0, self.sens_or)
         return o
 
-    def gpu(self, deterministic=False, kahan=True, sens=None, image_kernel=0, group=0, projector="direct"):
+    def gpu(self, deterministic=False, kahan=True, sens=None, image_kernel=0, group=0, projector="auto"):
         lm = self.lm
         pe = lm.event_setup(self.geo_g, lm.DeviceEvents.from_numpy(self.ev), self.n_sub)
         if sens is None:
@@ -276,3 +276,73 @@ def test_tiled_projector_reinit_rebins(lm):
                    knorm=c.knorm, projector="direct", group=16)
     h.epoch(seq)
     assert H.rel_l2(x_t, h.x().cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["3d_small", "3d_quad", "3d_mid"])
+@pytest.mark.parametrize("group", [8, 16, 32])
+def test_table_projector_matches_direct_and_oracle(lm, name, group):
+    """The traversal-table data update (stored traversals and (P^LM 1)_e,
+    quad gathers, x-principal events before the others) evaluates the direct
+    kernel's per-sample terms in the same order: after two epochs its
+    iterates agree with the direct kernel's to float32 rounding ((P^LM 1)_e
+    is summed in another order and the atomics' order differs) and with the
+    oracle to the image tolerance."""
+    c = Case(lm, name)
+    seq = S.selection_sequence(c.n_sub, 4 * c.n_sub, seed=9)
+    out = {}
+    for proj in ("direct", "table"):
+        g = c.gpu(projector=proj, group=group)
+        assert g.tuning()["projector"] == proj and g.tuning()["group"] == group
+        g.epoch(seq[:2 * c.n_sub])
+        g.epoch(seq[2 * c.n_sub:])
+        out[proj] = (g.x().cpu().numpy(), g.y().cpu().numpy(), g.z().cpu().numpy(), g.objective())
+        g.close()
+    for k in range(3):
+        assert H.rel_l2(out["table"][k], out["direct"][k]) < 1e-5, k
+    o = c.oracle()
+    o.run(seq[:2 * c.n_sub])
+    o.run(seq[2 * c.n_sub:])
+    assert H.rel_l2(out["table"][0], o.x) < H.REL_L2_IMAGE
+    assert H.rel_l2(out["table"][2], o.z) < H.REL_L2_IMAGE
+    np.testing.assert_allclose(out["table"][1][c.perm], o.y, rtol=1e-3, atol=1e-3 * np.abs(o.y).max())
+    assert abs(out["table"][3] - o.objective()) <= 1e-5 * abs(o.objective())
+
+
+def test_table_single_data_update_matches_direct(lm):
+    """One data update: the duals of every event agree with the direct
+    kernel's to a few float32 ulps (same forward projections, S_e from a
+    differently ordered (P^LM 1)_e)."""
+    c = Case(lm, "3d_mid")
+    ys = []
+    for proj in ("direct", "table"):
+        g = c.gpu(projector=proj, group=32)
+        g.updates([1])
+        ys.append(g.y().cpu().numpy())
+        g.close()
+    np.testing.assert_allclose(ys[1], ys[0], rtol=4e-6, atol=4e-6 * np.abs(ys[0]).max())
+
+
+def test_table_reinit_rebuilds(lm):
+    """reinit with another frame's events in the same buffers stores their
+    traversals anew."""
+    c = Case(lm, "3d_quad")
+    g = c.gpu(projector="table", group=32)
+    pe2 = lm.event_setup(c.geo_g, lm.DeviceEvents.from_numpy(H.workload_data("3d_quad", seed=5)[2]), c.n_sub,
+                         into=g.pe)
+    g.reinit(torch.from_numpy(c.x0).cuda())
+    seq = S.selection_sequence(c.n_sub, 2 * c.n_sub, seed=2)
+    g.epoch(seq)
+    x_t = g.x().cpu().numpy()
+    g.close()
+    h = lm.LMSPDHG(c.geo_g, pe2, torch.from_numpy(c.sens_or.astype(np.float32)).cuda(),
+                   torch.from_numpy(c.x0).cuda(), beta=c.beta, n_subsets=c.n_sub, gamma=c.gamma, rho=0.999,
+                   knorm=c.knorm, projector="direct", group=32)
+    h.epoch(seq)
+    assert H.rel_l2(x_t, h.x().cpu().numpy()) < 1e-5
+
+
+def test_table_autotuner_picks_a_width(lm):
+    g = Case(lm, "3d_mid").gpu(projector="table")
+    t = g.tuning()
+    assert t["projector"] == "table" and t["group"] in (8, 16, 32)
+    assert min(t["ms_g8"], t["ms_g16"], t["ms_g32"]) > 0.0
