@@ -204,14 +204,36 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # the oracle's timed sample (CPU baseline and reference arm)
 # --------------------------------------------------------------------------
-def oracle_sample_step(wl, ev_np, n_sample, seq_epoch, beta=None, xi=None):
+def host_cpu() -> str:
+    """The host's CPU model (as the kernel reports it), for the CPU baseline."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip().lower() in ("model name", "cpu model", "hardware"):
+                    return v.strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_sample_step(wl, ev_np, n_sample, seq_epoch, beta=None, xi=None, threads=1):
     """One oracle run on a bounded sample of the frame: the first n_sample
     events, full image grid, initialisation + the updates of seq_epoch (one
     epoch, 2n updates, or its first few), with the TV prior or (xi given) the
     directional TV.
-    Returns (events fwd+back projected, seconds)."""
+    threads > 1 runs the oracle's OpenMP build on that many host threads.
+    Returns (events fwd+back projected, seconds, threads used)."""
     import oracle as O
     n = min(n_sample, ev_np.n)
+    threads = O.use_threads(threads)
     sub = ev_np.subset(slice(0, n))
     geo = O.Geometry.from_workload(wl)
     E = O.EventArrays.from_events(sub)
@@ -230,7 +252,7 @@ def oracle_sample_step(wl, ev_np, n_sample, seq_epoch, beta=None, xi=None):
     dt = time.perf_counter() - t0
     off = O.subset_offsets(n, wl.n_subsets)
     projected = n + sum(int(off[i + 1] - off[i]) for i in seq_epoch if i < wl.n_subsets)
-    return projected, dt
+    return projected, dt, threads
 
 
 def run_reference(args):
@@ -247,11 +269,12 @@ def run_reference(args):
     # update costs the oracle ~0.15 s whatever the event count)
     n_upd = min(2 * wl.n_subsets, 8)
     seq = S.selection_sequence(wl.n_subsets, 2 * wl.n_subsets, seed=3)[:n_upd]
+    ncpu = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_sample_step(wl, ev, n_sample, seq)
-    tot_ev, tot_s = 0, 0.0
+        oracle_sample_step(wl, ev, n_sample, seq, threads=ncpu)
+    tot_ev, tot_s, cores = 0, 0.0, 1
     for _ in range(args.steps):
-        e, s = oracle_sample_step(wl, ev, n_sample, seq)
+        e, s, cores = oracle_sample_step(wl, ev, n_sample, seq, threads=ncpu)
         tot_ev += e
         tot_s += s
     value = tot_ev / tot_s
@@ -262,9 +285,10 @@ def run_reference(args):
         "config": {"workload": f"{args.workload}: FP64 CPU oracle, bounded sample of {n_sample} events on the full "
                                f"grid, initialisation + the first {n_upd} updates of an epoch per step",
                    "events_per_step": tot_ev / args.steps},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                          "sample": f"first {n_sample} Monte Carlo events of the frame, full "
-                                   f"{'x'.join(str(v) for v in wl.grid.n)} grid, init + {n_upd} updates"},
+                                   f"{'x'.join(str(v) for v in wl.grid.n)} grid, init + {n_upd} updates, FP64 "
+                                   f"oracle on {cores} host threads (OpenMP build)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -522,10 +546,13 @@ def run_gpu(args):
         ev_np = S.Events(*(getattr(raw, k)[:args.cpu_sample].cpu().numpy() for k in
                            ("det1", "det2", "tof", "corr", "contam")))
         xi_np = None if xi is None else xi.cpu().numpy().astype(np.float64)
-        e_cpu, s_cpu = oracle_sample_step(wl, ev_np, args.cpu_sample, seqs[0], beta=beta, xi=xi_np)
-        cpu = {"value": e_cpu / s_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+        ncpu = os.cpu_count() or 1
+        e_cpu, s_cpu, cores = oracle_sample_step(wl, ev_np, args.cpu_sample, seqs[0], beta=beta, xi=xi_np,
+                                                 threads=ncpu)
+        cpu = {"value": e_cpu / s_cpu, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                "sample": f"first {min(args.cpu_sample, N)} events of the frame on the full grid: FP64 init + "
-                         f"one epoch ({2 * n_sub} updates), {s_cpu:.1f} s"}
+                         f"one epoch ({2 * n_sub} updates), {s_cpu:.1f} s on {cores} host threads "
+                         f"(the oracle's OpenMP build)"}
 
     # ---- the short frame and the serving stream, after the headline (one GPU only) ----
     short, serving = None, None

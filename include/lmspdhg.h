@@ -331,6 +331,20 @@ typedef struct {
                           /* per-sample arithmetic as the direct kernel; S_e and */
                           /* (y+ - y)/mu from the stored reciprocals.  Not used  */
                           /* by batches.                                         */
+    int32_t shard;        /* 1: event sharding of one frame over several states  */
+                          /* (one per GPU), each holding a slice of every        */
+                          /* subset's events (mu counted over the whole list:   */
+                          /* lm_event_setup on the whole list, then a slice of   */
+                          /* each subset).  The data term is a sum over events,  */
+                          /* so each update's dz is the sum of the states'       */
+                          /* partial back-projections: updates then run through  */
+                          /* lmspdhg_shard_begin / _finish with the caller's sum */
+                          /* of lmspdhg_shard_buffer over the states in between; */
+                          /* prior updates and primal steps are replicated.      */
+                          /* Float-atomic mode; not with the resolution model,   */
+                          /* the tile-binned projector or sinogram bins          */
+                          /* (LM_ERR_INVALID_ARG).  0: the frame's events all    */
+                          /* belong to this state.                               */
 } lm_params;
 
 /* Bytes of the optional traversal-table buffer (lm_params.trav_buf): 40 per
@@ -418,6 +432,39 @@ int lmspdhg_reinit(lm_state* st, const float* x0, void* stream);
  * after prior updates.  Synchronous. */
 int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, double* ms4, int64_t* n4,
                     void* stream);
+
+/* ---- event sharding of one frame (lm_params.shard = 1) -------------------
+ * Alg. 2's data update of subset i adds dz = (P^LM_{N_i})^T ((y+ - y)/mu)
+ * over the subset's events, a sum that splits over any partition of the
+ * events; the dual step of each event needs only its own projection.  A
+ * frame's events can therefore be spread over states (ranks) that each hold
+ * a slice of every subset and a full copy of the image variables: after
+ * each rank's event kernels the ranks sum their partial dz (all-reduce),
+ * and every rank applies the same image pass.  The initialisation's
+ * back-projection z0 = P^T 1 + (P^LM)^T((y - 1)/mu) splits the same way.
+ * Protocol per state:
+ *   lmspdhg_create (shard = 1): y of the state's events; its partial
+ *     back-projection of the initialisation is left in the exchange buffer;
+ *   the caller sums the buffers of all states into each (an all-reduce);
+ *   lmspdhg_shard_init_finish: z, T and the first primal step;
+ *   per update: lmspdhg_shard_begin(sel) (for a data selection the state's
+ *     partial dz lands in the buffer), the caller's sum over states (data
+ *     selections only), lmspdhg_shard_finish.
+ * lmspdhg_epoch / lmspdhg_updates / lmspdhg_profile are rejected on a shard
+ * state (LM_ERR_INVALID_ARG), as are calls out of this order.  The buffer is
+ * V floats of device memory inside the state buffer (valid while the state
+ * lives); its content between begin and finish is the state's partial dz. */
+int lmspdhg_shard_buffer(lm_state* st, float** dz_out);
+int lmspdhg_shard_init_finish(lm_state* st, void* stream);
+int lmspdhg_shard_begin(lm_state* st, uint16_t sel, void* stream);
+int lmspdhg_shard_finish(lm_state* st, void* stream);
+
+/* The FP64 objective's parts: out4[0] = <P^T 1, x>, out4[1] = ||K x||_{2,1},
+ * out4[2] = sum_e w_e log((P^LM x)_e + s_e) over this state's events,
+ * out4[3] = sum of s over sinogram bins (0 for listmode).  The objective is
+ * out4[0] - out4[2] + beta out4[1] + out4[3]; with event sharding out4[2]
+ * is summed over the states.  Synchronous. */
+int lmspdhg_objective_parts_fp64(lm_state* st, double* out4, void* stream);
 
 /* Which image-pass kernel the state uses (lm_params.image_kernel): 1 plain
  * loads, 2 TMA-staged (the TV's dual step fused in; the directional TV's
@@ -577,21 +624,8 @@ int lm_server_destroy(lm_server* s);
  * epoch graph counts each of its kernel nodes). */
 int64_t lm_kernel_launches(void);
 
-/* Exact traversal counts of an event list: samples with a non-zero TOF
- * weight and an in-grid neighbour, and in-grid neighbour touches (each touch
- * is one 4-byte image read in a forward projection and one 4-byte atomic add
- * in a back-projection).  ws: device, >= 16 bytes.  Synchronous. */
-int lm_traversal_stats(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev,
-                       void* ws, size_t ws_bytes, int64_t* n_samples, int64_t* n_touches, void* stream);
-
-/* L2 throughput probe on the caller's device buffer (use one that fits in
- * L2): mode 0 coalesced 16-byte reads, 1 coalesced float atomic adds, 2
- * random 4-byte reads, 3 random float atomic adds; *gbs_out = payload GB/s
- * over `iters` passes.  The buffer is overwritten.  Modes 4 and 5 probe
- * shared memory instead (random 4-byte reads / float atomic adds on a 32 KB
- * array per block, 64 x iters accesses per thread; buf only receives a
- * guard value).  Synchronous. */
-int lm_probe_l2(void* buf, size_t bytes, int32_t mode, int32_t iters, double* gbs_out, void* stream);
+/* The benchmark's own measurement utilities (throughput probes, traversal
+ * statistics) are declared in lm_measure.h. */
 
 #ifdef __cplusplus
 }

@@ -26,17 +26,50 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lmoracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_threads = 1
+
+
+def _compile(out: str, extra) -> None:
+    if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable C, no target-specific flags)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+    """Compile the oracle with gcc (portable C, no target-specific flags):
+    liboracle.so, single-threaded (every parity test uses it), and
+    liboracle_omp.so, the same source with OpenMP (event loops over
+    thread-private FP64 images added in thread order, voxel loops split):
+    used only to time the oracle on all host cores."""
+    if force:
+        for f in (_LIB_PATH, _LIB_OMP_PATH):
+            if os.path.exists(f):
+                os.remove(f)
+    _compile(_LIB_PATH, [])
+    try:
+        _compile(_LIB_OMP_PATH, ["-fopenmp"])
+    except (subprocess.CalledProcessError, OSError):
+        pass  # no OpenMP in this compiler: the timing baseline stays single-threaded
     return _LIB_PATH
+
+
+def use_threads(n: int) -> int:
+    """Select the OpenMP build with n threads (n > 1) or the single-threaded
+    build (n <= 1) for every later call; returns the threads in use.  Only
+    the CPU timing baseline calls this."""
+    global _threads
+    build()
+    if n > 1 and os.path.exists(_LIB_OMP_PATH):
+        L = _load(_LIB_OMP_PATH)
+        L.or_set_threads(int(n))
+        _threads = int(L.or_threads())
+    else:
+        _threads = 1
+    return _threads
 
 
 class Scanner(C.Structure):
@@ -81,10 +114,16 @@ def _p(a, ct):
 
 
 def lib():
-    global _lib
+    """The oracle library in use (single-threaded unless use_threads chose
+    the OpenMP build)."""
+    build()
+    return _load(_LIB_OMP_PATH if _threads > 1 else _LIB_PATH)
+
+
+def _load(path):
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if path not in _libs:
+            L = C.CDLL(path)
             P = C.POINTER
             L.or_fwd.argtypes = [P(Scanner), P(Grid), P(Tof), P(C.c_int32), P(C.c_int32), P(C.c_int16),
                                  P(C.c_float), C.c_int64, P(C.c_float), P(C.c_double)]
@@ -130,8 +169,10 @@ def lib():
             L.or_emtv_denoise.argtypes = [P(Grid), P(C.c_double), P(C.c_double), P(C.c_uint8), C.c_int,
                                           C.c_double, P(C.c_double), P(C.c_double)]
             L.or_emtv_epoch.argtypes = [P(LmProblem), P(C.c_double), P(C.c_double), C.c_int]
-            _lib = L
-    return _lib
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_threads.restype = C.c_int
+            _libs[path] = L
+    return _libs[path]
 
 
 # --------------------------------------------------------------------------

@@ -52,6 +52,9 @@
  * differences under a detector shift.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -349,6 +352,7 @@ void or_tv_grad(const or_grid* g, const double* x, double* out)
     for (int c = 0; c < nd; ++c) {
         int d = ax[c];
         int64_t st = stride_of(g, d);
+#pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < V; ++j)
             out[c * V + j] = coord_of(g, j, d) < g->n[d] - 1 ? x[j + st] - x[j] : 0.0;
     }
@@ -364,6 +368,7 @@ void or_tv_adj(const or_grid* g, const double* q, double* out)
     for (int c = 0; c < nd; ++c) {
         int d = ax[c];
         int64_t st = stride_of(g, d);
+#pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < V; ++j) {
             int cj = coord_of(g, j, d);
             if (cj < g->n[d] - 1) out[j] -= q[c * V + j];
@@ -378,6 +383,7 @@ void or_tv_prox(const or_grid* g, double* w, double beta)
 {
     int nd = or_tv_ndim(g);
     int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < V; ++j) {
         double s = 0.0;
         for (int c = 0; c < nd; ++c) s += w[c * V + j] * w[c * V + j];
@@ -405,6 +411,7 @@ static void dtv_project(const or_grid* g, const double* xi, double* q)
 {
     int nd = or_tv_ndim(g);
     int64_t V = (int64_t)g->n[0] * g->n[1] * g->n[2];
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < V; ++j) {
         double s = 0.0;
         for (int c = 0; c < nd; ++c) s += xi[c * V + j] * q[c * V + j];
@@ -610,6 +617,55 @@ static double ev_fwd_one_img(const or_lm_problem* P, int64_t e, const double* g1
     return g1 ? ev_fwd(P, e, g1) : ev_fwd_ones(P, e);
 }
 
+/* The event loops of Alg. 2 (the initialisation over every event, a data
+ * update over the events e = e0, e0 + de, ...): each event's dual step is
+ * its own, and its back-projection is added into img.  In the plain build
+ * the events run in list order.  Built with OpenMP (the timing baseline on
+ * all host cores), every thread adds into its own FP64 image, and those are
+ * added into img in thread order after the loop. */
+enum { STEP_INIT = 0, STEP_DATA = 1 };
+
+static double event_step(const or_lm_problem* P, or_lm_state* S, int64_t e, int kind, const double* gx,
+                         const double* g1)
+{
+    double mu = (double)P->mu[e];
+    if (kind == STEP_INIT) {
+        double u = ev_fwd(P, e, gx) + (double)P->contam[e];
+        S->y[e] = 1.0 - mu / u;                                 /* Eq. (yinit) */
+        return (S->y[e] - 1.0) / mu;
+    }
+    double p1 = ev_fwd_one_img(P, e, g1);
+    double Se = p1 > 0.0 ? P->gamma * P->rho / p1 : 0.0;       /* S_k = gamma rho / P^LM_{N_k} 1 */
+    double a = S->y[e] + Se * (ev_fwd(P, e, gx) + (double)P->contam[e]);
+    double yp = or_prox_dstar(a, mu * Se, 1.0);
+    double v = (yp - S->y[e]) / mu;
+    S->y[e] = yp;
+    return v;
+}
+
+static void event_pass(const or_lm_problem* P, or_lm_state* S, int64_t e0, int64_t de, int kind, const double* gx,
+                       const double* g1, double* img)
+{
+#ifdef _OPENMP
+    int64_t V = (int64_t)P->g->n[0] * P->g->n[1] * P->g->n[2];
+    int nt = omp_get_max_threads();
+    double* part = (double*)calloc((size_t)nt * V, sizeof(double));
+#pragma omp parallel
+    {
+        double* mine = part + (size_t)omp_get_thread_num() * V;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t e = e0; e < P->n_ev; e += de) ev_back(P, e, event_step(P, S, e, kind, gx, g1), mine);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < V; ++j)
+        for (int t = 0; t < nt; ++t) img[j] += part[(size_t)t * V + j];
+    free(part);
+#else
+    for (int64_t e = e0; e < P->n_ev; e += de) ev_back(P, e, event_step(P, S, e, kind, gx, g1), img);
+#endif
+}
+
+
 /* Initialisation of Alg. 2 (duals, z, step sizes) plus the first primal step's inputs:
  *   y_e = 1 - mu_e / ((P^LM x0)_e + s_e)                    (Eq. yinit)
  *   z = zbar = P^T 1 + (P^LM)^T ((y - 1)/mu) + K^T w, w = 0
@@ -627,11 +683,7 @@ void or_lm_init(const or_lm_problem* P, const float* x0, const double* sens, or_
     double* gbuf;
     const double* gx = res_in(P, x0d, &gbuf);
     double* bz = gbuf ? (double*)calloc(V, sizeof(double)) : S->z;
-    for (int64_t e = 0; e < P->n_ev; ++e) {
-        double u = ev_fwd(P, e, gx) + (double)P->contam[e];
-        S->y[e] = 1.0 - (double)P->mu[e] / u;
-        ev_back(P, e, (S->y[e] - 1.0) / (double)P->mu[e], bz);
-    }
+    event_pass(P, S, 0, 1, STEP_INIT, gx, NULL, bz);  /* y, and (P^LM)^T((y - 1)/mu) into bz */
     if (gbuf) {
         res_add(P, bz, S->z);
         free(bz);
@@ -656,6 +708,7 @@ void or_lm_update(const or_lm_problem* P, or_lm_state* S, int32_t i, double* dz,
     int nd = or_tv_ndim(P->g);
     double n = (double)P->n_subsets;
     /* x <- proj_{>=0}(x - T zbar) */
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < V; ++j) {
         double v = S->x[j] - S->T[j] * S->zbar[j];
         S->x[j] = v > 0.0 ? v : 0.0;
@@ -674,15 +727,8 @@ void or_lm_update(const or_lm_problem* P, or_lm_state* S, int32_t i, double* dz,
             free(ones);
         }
         double* bz = gbuf ? (double*)calloc(V, sizeof(double)) : dz;
-        for (int64_t e = i; e < P->n_ev; e += P->n_subsets) {
-            double p1 = ev_fwd_one_img(P, e, g1);
-            double Se = p1 > 0.0 ? P->gamma * P->rho / p1 : 0.0; /* S_k = gamma rho / P^LM_{N_k} 1 */
-            double a = S->y[e] + Se * (ev_fwd(P, e, gx) + (double)P->contam[e]);
-            double mu = (double)P->mu[e];
-            double yp = or_prox_dstar(a, mu * Se, 1.0);
-            ev_back(P, e, (yp - S->y[e]) / mu, bz);
-            S->y[e] = yp;
-        }
+        /* subset i: every n-th event from i; y+ = prox (Eq. proxD), dz += P^T (y+ - y)/mu */
+        event_pass(P, S, i, P->n_subsets, STEP_DATA, gx, g1, bz);
         if (gbuf) {
             res_add(P, bz, dz);
             free(bz);
@@ -702,6 +748,7 @@ void or_lm_update(const or_lm_problem* P, or_lm_state* S, int32_t i, double* dz,
         }
         or_dtv_adj(P->g, P->xi, gw, dz);               /* dz = K^T (w^+ - w) */
     }
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < V; ++j) {
         S->z[j] += dz[j];
         S->zbar[j] = S->z[j] + dz[j] / p_i;
@@ -962,6 +1009,7 @@ void or_sino_update(const or_sino_problem* P, or_lm_state* S, int32_t i, double*
         }
         or_dtv_adj(P->g, P->xi, gw, dz);
     }
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < V; ++j) {
         S->z[j] += dz[j];
         S->zbar[j] = S->z[j] + dz[j] / p_i;
@@ -1093,4 +1141,23 @@ void or_fwd_position_sensitivity(const or_scanner* sc, const or_grid* g, const o
         }
         out[e] = acc * (corr ? (double)corr[e] : 1.0);
     }
+}
+
+/* Threads of the OpenMP build (the timing baseline); the plain build has one. */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

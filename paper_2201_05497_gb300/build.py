@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblmspdhg.so")
 SOURCES = ["lm_project.cu", "lm_image.cu", "lm_setup.cu", "lm_state.cu", "lm_noalloc.cu", "lm_server.cu", "lm_tile.cu",
-           "lm_emtv.cu", "lm_res.cu", "lm_sino.cu", "lm_table.cu"]
+           "lm_emtv.cu", "lm_res.cu", "lm_sino.cu", "lm_table.cu", "lm_measure.cu"]
 HEADERS = ["lm_device.cuh", "lm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -38,6 +38,7 @@ def _flags(extra=()):
 def _newest_input() -> float:
     paths = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     paths.append(os.path.join(os.path.dirname(HERE), "include", "lmspdhg.h"))
+    paths.append(os.path.join(os.path.dirname(HERE), "include", "lm_measure.h"))
     paths.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in paths)
 

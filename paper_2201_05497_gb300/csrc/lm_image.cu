@@ -621,8 +621,8 @@ __device__ __forceinline__ Item item_of(const lmh::ImgArgs& A, int64_t it)
 }
 
 // Copies of one slice (thread 0).  Prior: x slices z (first only) and z+1
-// with halo, w(z) (the directional TV: D(z)) with halo and, for slices the
-// block owns, T, z, zc.
+// with halo, w(z) with halo and, for slices the block owns, T, z, zc (the
+// directional TV's field is read with plain loads where it is needed).
 // Data: both accumulators, x, T, z, zc of the tile.
 __device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, int xcur, int wp, uint8_t* sm, int s,
                                             int z, int zs, const Item& I, bool first, uint64_t* bar)
@@ -633,7 +633,7 @@ __device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, i
     if (first) {
         if (prior) {
             tmap_acquire(&M->xh[xcur]);
-            tmap_acquire(A.dtv_d != nullptr ? &M->dtvd : &M->w[wp]);
+            tmap_acquire(&M->w[wp]);
         } else {
             tmap_acquire(&M->acc_std);
             tmap_acquire(&M->acc_yf);
@@ -653,9 +653,7 @@ __device__ __forceinline__ void issue_slice(const lmh::ImgArgs& A, bool prior, i
         if (first) tma_load_3d(sm + TmaLayout::xh + ((z - zs) % 3) * TmaLayout::xh_sz, xm, I.x0 - 4, I.y0 - 1, z, bar + s);
         tma_load_3d(sm + TmaLayout::xh + ((z + 1 - zs) % 3) * TmaLayout::xh_sz, xm, I.x0 - 4, I.y0 - 1, z + 1,
                     bar + s);
-        // the directional TV stages D = P (w+ - w) from its dual step in w's place
-        tma_load_4d(st + TmaLayout::p_wc, A.dtv_d != nullptr ? &M->dtvd : &M->w[wp], I.x0 - 4, I.y0 - 1, z, 0,
-                    bar + s);
+        tma_load_4d(st + TmaLayout::p_wc, &M->w[wp], I.x0 - 4, I.y0 - 1, z, 0, bar + s);
         if (own) {
             tma_load_3d(st + TmaLayout::p_T, &M->T, I.x0, I.y0, z, bar + s);
             tma_load_3d(st + TmaLayout::p_z, &M->z, I.x0, I.y0, z, bar + s);
@@ -730,36 +728,45 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
     float* XO = (float*)(sm + TmaLayout::xo);
     float* wn = A.w_nxt[wp];
     const float sp = A.s_prior, beta = A.beta;
-    const bool dtv = A.dtv_d != nullptr;
+    const float* xi = A.xi;  // directional TV: the structural field [3][V] (3D grids), else nullptr
     // w+ = v / max(1, |v|/beta), v = w + S K x, over the tile (4 points per
-    // thread) and its -1 halo (row y0-1 and column x0-1: 65 points); the
-    // directional TV's dual step has run already and left D = P (w+ - w)
+    // thread) and its -1 halo (row y0-1 and column x0-1: 65 points), and
+    // D = K^T's operand w+ - w; the directional TV takes the part of the
+    // difference vector perpendicular to the field before v and again of
+    // w+ - w (D = P (w+ - w)), in the order of the event kernel's dual step
     auto wplus = [&](int ex, int ey, bool tile_pt) {
         const int ix = I.x0 - 1 + ex, iy = I.y0 - 1 + ey;
         float dx = 0.0f, dy = 0.0f, dzc = 0.0f;
-        if (dtv && ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
-            const int wb = ey * WBW + ex + 3;
-            dx = WC[wb];
-            dy = WC[WBW * WBH + wb];
-            if (hz) dzc = WC[2 * WBW * WBH + wb];
-        } else if (ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
+        if (ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
             const int xb = ey * XHW + ex + 3;
             const int wb = ey * WBW + ex + 3;
             const float xc = X0[xb];
             const float wx = WC[wb], wy = WC[WBW * WBH + wb];
-            const float vx = fmaf(sp, ix < nx - 1 ? X0[xb + 1] - xc : 0.0f, wx);
-            const float vy = fmaf(sp, iy < ny - 1 ? X0[xb + XHW] - xc : 0.0f, wy);
+            float gx = ix < nx - 1 ? X0[xb + 1] - xc : 0.0f;
+            float gy = iy < ny - 1 ? X0[xb + XHW] - xc : 0.0f;
+            float gz = hz ? (z < nz - 1 ? X1[xb] - xc : 0.0f) : 0.0f;
+            float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+            if (xi != nullptr) {
+                const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
+                fx = __ldg(xi + j);
+                fy = __ldg(xi + V + j);
+                if (hz) fz = __ldg(xi + 2 * V + j);
+                dtv_perp(fx, fy, fz, gx, gy, gz);
+            }
+            const float vx = fmaf(sp, gx, wx);
+            const float vy = fmaf(sp, gy, wy);
             float vz = 0.0f, wz = 0.0f;
             if (hz) {
                 wz = WC[2 * WBW * WBH + wb];
-                vz = fmaf(sp, z < nz - 1 ? X1[xb] - xc : 0.0f, wz);
+                vz = fmaf(sp, gz, wz);
             }
             const float sc = tv_ball_scale(fmaf(vx, vx, fmaf(vy, vy, vz * vz)), beta);
             // rounded products (never fused into the differences below), as stored by the plain path
             const float ox = __fmul_rn(vx, sc), oy = __fmul_rn(vy, sc), oz = __fmul_rn(vz, sc);
             dx = ox - wx;
             dy = oy - wy;
-            dzc = oz - wz;
+            dzc = hz ? oz - wz : 0.0f;
+            if (xi != nullptr) dtv_perp(fx, fy, fz, dx, dy, dzc);
             if (own && tile_pt) {
                 const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
                 wn[j] = ox;
@@ -1419,74 +1426,6 @@ __global__ void zadd_kernel(const float* z, const float* zc, float* out, int64_t
         out[j] = zc ? z[j] + zc[j] : z[j];
 }
 
-// ---- L2 throughput probes (measurement utility) ----
-__device__ __forceinline__ unsigned hash32(unsigned x)
-{
-    x ^= x >> 16;
-    x *= 0x7feb352dU;
-    x ^= x >> 15;
-    x *= 0x846ca68bU;
-    x ^= x >> 16;
-    return x;
-}
-
-// Shared-memory probe: random 4-byte reads (mode 4) or float atomic adds
-// (mode 5) on a 32 KB array per block, indices from a linear congruential
-// sequence per thread (two instructions per index).
-constexpr int SPROBE_N = 8192;
-__global__ void __launch_bounds__(256) smem_probe_kernel(int mode, int iters, float* sink)
-{
-    __shared__ float sm[SPROBE_N];
-    for (int k = threadIdx.x; k < SPROBE_N; k += blockDim.x) sm[k] = 0.0f;
-    __syncthreads();
-    unsigned idx = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u;
-    float acc = 0.0f;
-    if (mode == 4) {
-        for (int it = 0; it < iters; ++it) {
-#pragma unroll 8
-            for (int r = 0; r < 64; ++r) {
-                idx = idx * 1664525u + 1013904223u;
-                acc += sm[idx >> 19];
-            }
-        }
-    } else {
-        for (int it = 0; it < iters; ++it) {
-#pragma unroll 8
-            for (int r = 0; r < 64; ++r) {
-                idx = idx * 1664525u + 1013904223u;
-                atomicAdd(sm + (idx >> 19), 1.0f);
-            }
-        }
-        __syncthreads();
-        acc = sm[threadIdx.x];
-    }
-    if (acc == 12345.678f) *sink = acc;
-}
-
-__global__ void __launch_bounds__(256) probe_kernel(float* buf, size_t n, int mode, int iters, float* sink)
-{
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t nth = (size_t)gridDim.x * blockDim.x;
-    float acc = 0.0f;
-    const size_t mask = n - 1;  // n is a power of two
-    for (int it = 0; it < iters; ++it) {
-        if (mode == 0) {
-            const float4* b4 = reinterpret_cast<const float4*>(buf);
-            for (size_t i = tid; i < n / 4; i += nth) {
-                const float4 v = __ldcg(b4 + i);
-                acc += v.x + v.y + v.z + v.w;
-            }
-        } else if (mode == 1) {
-            for (size_t i = tid; i < n; i += nth) atomicAdd(buf + i, 1.0f);
-        } else if (mode == 2) {
-            for (size_t i = tid; i < n; i += nth) acc += __ldcg(buf + (hash32((unsigned)(i + it * 7919u)) & mask));
-        } else {
-            for (size_t i = tid; i < n; i += nth) atomicAdd(buf + (hash32((unsigned)(i + it * 7919u)) & mask), 1.0f);
-        }
-    }
-    if (acc == 12345.678f) *sink = acc;
-}
-
 int flat_grid(int64_t n)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)lmh::num_sms() * 16));
@@ -1821,58 +1760,6 @@ int lm_tv_prox(const lm_grid* grid, float* w, float beta, void* stream)
     return LM_OK;
 }
 
-int lm_probe_l2(void* buf, size_t bytes, int32_t mode, int32_t iters, double* gbs_out, void* stream)
-{
-    clear_error();
-    LM_CHECK(buf && gbs_out && bytes >= 4096 && mode >= 0 && mode <= 5 && iters >= 1, LM_ERR_INVALID_ARG,
-             "bad probe arguments");
-    if (mode >= 4) {
-        cudaStream_t st = S(stream);
-        int bps = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, smem_probe_kernel, 256, 0);
-        const int grid = std::max(1, bps) * num_sms();
-        smem_probe_kernel<<<grid, 256, 0, st>>>(mode, 1, (float*)buf);  // warm-up
-        cudaEvent_t e0, e1;
-        LM_CUDA(cudaEventCreate(&e0));
-        LM_CUDA(cudaEventCreate(&e1));
-        cudaEventRecord(e0, st);
-        smem_probe_kernel<<<grid, 256, 0, st>>>(mode, iters, (float*)buf);
-        cudaEventRecord(e1, st);
-        count_launch(2);
-        cudaError_t ce = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "probe failed: %s", cudaGetErrorString(ce));
-        *gbs_out = (double)grid * 256.0 * 64.0 * iters * 4.0 / (ms * 1e-3) / 1e9;
-        return LM_OK;
-    }
-    size_t n = 1024;
-    while (n * 2 * 4 <= bytes) n *= 2;  // power-of-two float count
-    cudaStream_t st = S(stream);
-    int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, probe_kernel, 256, 0);
-    const int grid = std::max(1, bps) * num_sms();
-    float* f = (float*)buf;
-    LM_CUDA(cudaMemsetAsync(buf, 0, n * 4, st));
-    probe_kernel<<<grid, 256, 0, st>>>(f, n, mode, 1, f);  // warm L2
-    cudaEvent_t e0, e1;
-    LM_CUDA(cudaEventCreate(&e0));
-    LM_CUDA(cudaEventCreate(&e1));
-    cudaEventRecord(e0, st);
-    probe_kernel<<<grid, 256, 0, st>>>(f, n, mode, iters, f);
-    cudaEventRecord(e1, st);
-    count_launch(2);
-    cudaError_t ce = cudaEventSynchronize(e1);
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    LM_CHECK(ce == cudaSuccess, LM_ERR_CUDA, "probe failed: %s", cudaGetErrorString(ce));
-    *gbs_out = (double)n * 4.0 * iters / (ms * 1e-3) / 1e9;
-    return LM_OK;
-}
 
 size_t lm_knorm_workspace_bytes(const lm_grid* grid)
 {

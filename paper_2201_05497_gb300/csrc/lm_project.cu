@@ -1149,42 +1149,5 @@ int lm_sens(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const 
 
 int64_t lm_kernel_launches(void) { return launch_total(); }
 
-int lm_traversal_stats(const lm_scanner* sc, const lm_grid* grid, const lm_tof* tof, const lm_events* ev,
-                       void* ws, size_t ws_bytes, int64_t* n_samples, int64_t* n_touches, void* stream)
-{
-    clear_error();
-    Geo G;
-    int rc = make_geo(sc, grid, tof, G, true);
-    if (rc) return rc;
-    rc = check_events(ev, false);
-    if (rc) return rc;
-    LM_CHECK(n_samples && n_touches, LM_ERR_INVALID_ARG, "NULL output");
-    LM_CHECK(ws != nullptr && ws_bytes >= 16, LM_ERR_NOMEM, "statistics need 16 workspace bytes");
-    *n_samples = 0;
-    *n_touches = 0;
-    if (ev->n == 0) return LM_OK;
-    cudaStream_t st = S(stream);
-    unsigned long long* cnt = (unsigned long long*)ws;
-    LM_CUDA(cudaMemsetAsync(cnt, 0, 16, st));
-    EvArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.G = G;
-    a.det1 = ev->det1;
-    a.det2 = ev->det2;
-    a.tof = ev->tof;
-    a.e_begin = 0;
-    a.e_end = ev->n;
-    a.chunk = 32;
-    a.acci_std = cnt;
-    const bool two_d = grid->n[2] == 1 && sc->n_rings == 1;
-    rc = launch_events(EV_COUNT, two_d, a, ev_grid(EV_COUNT, two_d), st);
-    unsigned long long h[2] = {0, 0};
-    cudaMemcpyAsync(h, cnt, 16, cudaMemcpyDeviceToHost, st);
-    LM_CUDA(cudaStreamSynchronize(st));
-    LM_CHECK(rc == LM_OK, rc, "statistics launch failed");
-    *n_samples = (int64_t)h[0];
-    *n_touches = (int64_t)h[1];
-    return LM_OK;
-}
 
 }  // extern "C"

@@ -79,6 +79,10 @@ struct lm_state_s {
     cudaGraphExec_t exec;
     bool have_graph;
     int64_t graph_nodes;
+    bool shard;         // event sharding: updates through lmspdhg_shard_begin / _finish
+    float* dz;          // the exchange buffer: this state's partial back-projection [V]
+    int shard_stage;    // 0 ready, 1 initialisation awaiting the exchange, 2 update awaiting it
+    int shard_sel;      // selection of the update in progress
     int xpar;           // buffer holding the x the next update starts from
     int64_t n_updates;
 };
@@ -97,7 +101,7 @@ struct Carve {
     }
 };
 
-void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det, bool dtv)
+void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det, bool dtv, bool shard)
 {
     const size_t V = (size_t)nvox(g);
     const int nd = std::max(1, tv_ndim(g));
@@ -121,6 +125,7 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det,
     float* gx = det ? nullptr : F(V);
     float* gxyf = det ? nullptr : F(V);
     float* dtvd = dtv ? F(nd * V) : nullptr;
+    float* dz = shard ? F(V) : nullptr;
     float* y = F((size_t)std::max<int64_t>(N, 1));
     const size_t scr_bytes = std::max<size_t>((size_t)std::max<int64_t>(N, 1) * 4,
                                               std::max(lm_knorm_workspace_bytes(g), objective_scratch_bytes()));
@@ -147,14 +152,15 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det,
         st->y = y; st->scr = scr; st->scr_bytes = scr_bytes; st->sub_off = sub_off; st->seq = seq;
         st->wpar = wpar; st->wbase = wbase; st->maxbits = maxbits; st->queue = queue; st->done = done;
         st->redf = redf; st->redd = redd;
-        st->gx = gx; st->gxyf = gxyf; st->dtvd = dtvd;
+        st->gx = gx; st->gxyf = gxyf; st->dtvd = dtvd; st->dz = dz;
     }
 }
 
-// The TMA-staged prior pass computes the TV's dual step itself; the
-// directional TV's dual step (with its field) stays in the event kernel,
-// which stores D = P (w+ - w) for the pass.
-bool tma_fuses_prior(const lm_state* st) { return st->tma && st->dtvd == nullptr; }
+// The TMA-staged prior pass computes the prior's dual step itself (with the
+// directional TV's field read where it needs it); the plain prior pass
+// takes it from the event kernel's prior branch (which stores D = P (w+ - w)
+// for the directional TV).
+bool tma_fuses_prior(const lm_state* st) { return st->tma; }
 
 EvArgs base_ev_args(const lm_state* st)
 {
@@ -308,6 +314,113 @@ int res_back(lm_state* st, const uint16_t* seq, int u, cudaStream_t s)
     return launch_res(&st->g, st->res, st->gx, st->acc_std, st->gxyf, st->gx, seq, u, st->n, s, true);
 }
 
+// The event part of update u (selection st->seq[u], x in buffer cur, scale
+// slot `slot`): the data update's event kernels, which leave the
+// back-projection of the dual change in the accumulators (or, with the
+// directional TV or the plain image passes, the prior's dual step).
+int launch_event_part(lm_state* st, int u, int cur, int slot, cudaStream_t s)
+{
+    EvArgs a = base_ev_args(st);
+    a.seq = st->seq;
+    a.u = u;
+    a.x_std = st->has_res ? st->gx : st->x[cur];  // G x with the resolution model
+    a.x_yf = st->has_res ? st->gxyf : st->xyf[cur];
+    a.px = st->x[cur];
+    a.maxbits = st->maxbits + slot;
+    if (st->tiled) {
+        TileArgs t = st->ta;
+        t.seq = st->seq;
+        t.u = u;
+        t.x = st->x[cur];
+        t.acc = st->acc_std;
+        t.v = st->scr;
+        t.gamma_rho = (float)(st->gamma * (double)st->P.rho);
+        int rc = launch_tile_update(t, st->two_d, s);
+        LM_CHECK(rc == LM_OK, rc, "tile data update launch failed");
+        if (!tma_fuses_prior(st)) {
+            // the image pass needs w+ (and D) from the event kernel's prior branch
+            a.prior_only = 1;
+            rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
+            LM_CHECK(rc == LM_OK, rc, "prior update launch failed");
+        }
+    } else if (st->table) {
+        // the table kernel, one launch per principal-axis family so that one
+        // image layout and one accumulator layout share L2 (both return at
+        // once on a prior update)
+        TabArgs t = base_tab_args(st, cur);
+        t.seq = st->seq;
+        t.u = u;
+        int rc = LM_OK;
+        for (int ph = st->tab_split ? 0 : -1; ph < (st->tab_split ? 2 : 0) && rc == LM_OK; ++ph) {
+            t.phase = ph;
+            rc = launch_table_update(t, st->tab_variant, st->grid_tab, s);
+        }
+        LM_CHECK(rc == LM_OK, rc, "data update launch failed");
+        if (!tma_fuses_prior(st)) {
+            // the image pass needs w+ (and D) from the event kernel's prior branch
+            a.prior_only = 1;
+            rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
+            LM_CHECK(rc == LM_OK, rc, "prior update launch failed");
+        }
+    } else if (!st->det) {
+        a.acc_std = st->acc_std;
+        a.acc_yf = st->acc_yf;
+        int rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
+        LM_CHECK(rc == LM_OK, rc, "data update launch failed");
+        if (st->has_res) {
+            rc = res_back(st, st->seq, u, s);
+            if (rc) return rc;
+        }
+    } else {
+        a.out = st->scr;
+        int rc = launch_events(EV_DATA_FX1, st->two_d, a, st->grid_ev, s);
+        LM_CHECK(rc == LM_OK, rc, "data update launch failed");
+        EvArgs b = base_ev_args(st);
+        b.seq = st->seq;
+        b.u = u;
+        b.vin = st->scr;
+        b.acci_std = st->acci_std;
+        b.acci_yf = st->acci_yf;
+        b.maxbits = st->maxbits + slot;
+        rc = launch_events(EV_BACK_FX, st->two_d, b, st->grid_fx, s);
+        LM_CHECK(rc == LM_OK, rc, "fixed-point back-projection launch failed");
+    }
+    return LM_OK;
+}
+
+// The image part of update u: merges the accumulators into z and z-bar (or
+// runs the prior's steps) and takes the next primal step into buffer nxt.
+int launch_image_part(lm_state* st, int u, int cur, int nxt, int slot0, cudaStream_t s)
+{
+    ImgArgs im = base_img_args(st);
+    im.mode = IP_UPDATE;
+    im.seq = st->seq;
+    im.u = u;
+    im.x_cur = st->x[cur];
+    im.x_nxt_std = st->x[nxt];
+    im.x_nxt_yf = st->xyf[nxt];
+    // scale slots: update u reads slot (slot0 + u) & 1, its pass clears the other one
+    im.slot0 = slot0;
+    im.xcur = cur;
+    if (st->tma) {
+        launch_image_tma(im, s);
+    } else if (st->tma_data) {
+        // TMA-staged data passes, plain prior passes
+        ImgArgs d = im, q = im;
+        d.skip_prior = 1;
+        q.skip_data = 1;
+        launch_image_tma(d, s);
+        launch_image_pass(q, s);
+    } else {
+        launch_image_pass(im, s);
+    }
+    if (st->has_res) {
+        int rc = res_fwd(st, st->x[nxt], s);  // the next update's projections read G x
+        if (rc) return rc;
+    }
+    return LM_OK;
+}
+
 // Launches updates 0..count-1 of the selection already in st->seq; x starts
 // in buffer xpar0; the fixed-point scale slot of update u is (slot0 + u) & 1.
 // If `ev` is given (profiling), events ev[3u], ev[3u+1], ev[3u+2] are
@@ -319,98 +432,11 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
         const int cur = (xpar0 + u) & 1, nxt = cur ^ 1;
         const int slot = (slot0 + u) & 1;
         if (ev) LM_CUDA(cudaEventRecord(ev[3 * u], s));
-        EvArgs a = base_ev_args(st);
-        a.seq = st->seq;
-        a.u = u;
-        a.x_std = st->has_res ? st->gx : st->x[cur];  // G x with the resolution model
-        a.x_yf = st->has_res ? st->gxyf : st->xyf[cur];
-        a.px = st->x[cur];
-        a.maxbits = st->maxbits + slot;
-        if (st->tiled) {
-            TileArgs t = st->ta;
-            t.seq = st->seq;
-            t.u = u;
-            t.x = st->x[cur];
-            t.acc = st->acc_std;
-            t.v = st->scr;
-            t.gamma_rho = (float)(st->gamma * (double)st->P.rho);
-            int rc = launch_tile_update(t, st->two_d, s);
-            LM_CHECK(rc == LM_OK, rc, "tile data update launch failed");
-            if (!tma_fuses_prior(st)) {
-                // the image pass needs w+ (and D) from the event kernel's prior branch
-                a.prior_only = 1;
-                rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
-                LM_CHECK(rc == LM_OK, rc, "prior update launch failed");
-            }
-        } else if (st->table) {
-            // the table kernel, one launch per principal-axis family so that one
-            // image layout and one accumulator layout share L2 (both return at
-            // once on a prior update)
-            TabArgs t = base_tab_args(st, cur);
-            t.seq = st->seq;
-            t.u = u;
-            int rc = LM_OK;
-            for (int ph = st->tab_split ? 0 : -1; ph < (st->tab_split ? 2 : 0) && rc == LM_OK; ++ph) {
-                t.phase = ph;
-                rc = launch_table_update(t, st->tab_variant, st->grid_tab, s);
-            }
-            LM_CHECK(rc == LM_OK, rc, "data update launch failed");
-            if (!tma_fuses_prior(st)) {
-                // the image pass needs w+ (and D) from the event kernel's prior branch
-                a.prior_only = 1;
-                rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
-                LM_CHECK(rc == LM_OK, rc, "prior update launch failed");
-            }
-        } else if (!st->det) {
-            a.acc_std = st->acc_std;
-            a.acc_yf = st->acc_yf;
-            int rc = launch_events(EV_DATA, st->two_d, a, st->grid_ev, s);
-            LM_CHECK(rc == LM_OK, rc, "data update launch failed");
-            if (st->has_res) {
-                rc = res_back(st, st->seq, u, s);
-                if (rc) return rc;
-            }
-        } else {
-            a.out = st->scr;
-            int rc = launch_events(EV_DATA_FX1, st->two_d, a, st->grid_ev, s);
-            LM_CHECK(rc == LM_OK, rc, "data update launch failed");
-            EvArgs b = base_ev_args(st);
-            b.seq = st->seq;
-            b.u = u;
-            b.vin = st->scr;
-            b.acci_std = st->acci_std;
-            b.acci_yf = st->acci_yf;
-            b.maxbits = st->maxbits + slot;
-            rc = launch_events(EV_BACK_FX, st->two_d, b, st->grid_fx, s);
-            LM_CHECK(rc == LM_OK, rc, "fixed-point back-projection launch failed");
-        }
+        int rc = launch_event_part(st, u, cur, slot, s);
+        if (rc) return rc;
         if (ev) LM_CUDA(cudaEventRecord(ev[3 * u + 1], s));
-        ImgArgs im = base_img_args(st);
-        im.mode = IP_UPDATE;
-        im.seq = st->seq;
-        im.u = u;
-        im.x_cur = st->x[cur];
-        im.x_nxt_std = st->x[nxt];
-        im.x_nxt_yf = st->xyf[nxt];
-        // scale slots: update u reads slot (slot0 + u) & 1, its pass clears the other one
-        im.slot0 = slot0;
-        im.xcur = cur;
-        if (st->tma) {
-            launch_image_tma(im, s);
-        } else if (st->tma_data) {
-            // TMA-staged data passes, plain prior passes
-            ImgArgs d = im, q = im;
-            d.skip_prior = 1;
-            q.skip_data = 1;
-            launch_image_tma(d, s);
-            launch_image_pass(q, s);
-        } else {
-            launch_image_pass(im, s);
-        }
-        if (st->has_res) {
-            int rc = res_fwd(st, st->x[nxt], s);  // the next update's projections read G x
-            if (rc) return rc;
-        }
+        rc = launch_image_part(st, u, cur, nxt, slot0, s);
+        if (rc) return rc;
         if (ev) LM_CUDA(cudaEventRecord(ev[3 * u + 2], s));
     }
     LM_CUDA(cudaGetLastError());
@@ -420,6 +446,42 @@ int launch_updates(lm_state* st, int count, int xpar0, int slot0, cudaStream_t s
 // Initialisation of Alg. 2 and the first primal step for the state's current events:
 // gamma, T, y = Eq. (yinit), z = P^T 1 + (P^LM)^T((y-1)/mu), w = 0, x from x0.
 int chunk_for(int64_t count, int grid);
+
+// The initialisation's image pass: z = P^T 1 + the accumulated
+// back-projection, z-bar = z, T and the first primal step from x0; x0 is
+// also kept in x[1] (the x the most recent update used).
+int init_image_pass(lm_state* st, const float* x0, cudaStream_t s)
+{
+    ImgArgs im = base_img_args(st);
+    im.mode = IP_INIT;
+    im.x_cur = x0;
+    im.x_keep = st->x[1];
+    im.x_nxt_std = st->x[0];
+    im.x_nxt_yf = st->xyf[0];
+    launch_image_pass(im, s);
+    if (st->has_res) {
+        int rc = res_fwd(st, st->x[0], s);
+        if (rc) return rc;
+    }
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+// Event sharding: dz (summed over the states) back into the first halves of
+// the z-paired accumulators, where the image passes read a data update's
+// back-projection (the fold left both accumulators zero).
+__global__ void unfold_pairs_kernel(const float* __restrict__ dz, float2* __restrict__ acc_std, int64_t V)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < V; j += (int64_t)gridDim.x * blockDim.x)
+        acc_std[j] = make_float2(dz[j], 0.0f);
+}
+
+void launch_unfold(lm_state* st, cudaStream_t s)
+{
+    const int grid = (int)std::min<int64_t>((st->V + 255) / 256, (int64_t)num_sms() * 8);
+    unfold_pairs_kernel<<<std::max(grid, 1), 256, 0, s>>>(st->dz, (float2*)st->acc_std, st->V);
+    count_launch();
+}
 
 int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
 {
@@ -486,21 +548,19 @@ int init_iteration(lm_state* st, const float* x0, cudaStream_t s)
         }
         LM_CHECK(rc == LM_OK, rc, "initialisation launch failed");
     }
-    ImgArgs im = base_img_args(st);
-    im.mode = IP_INIT;
-    im.x_cur = x0;
-    im.x_keep = st->x[1];
-    im.x_nxt_std = st->x[0];
-    im.x_nxt_yf = st->xyf[0];
-    launch_image_pass(im, s);
-    if (st->has_res) {
-        rc = res_fwd(st, st->x[0], s);
-        if (rc) return rc;
-    }
-    LM_CUDA(cudaGetLastError());
     st->xpar = 0;
     st->n_updates = 0;
-    return LM_OK;
+    if (st->shard) {
+        // this state's part of the initialisation's back-projection goes to the exchange
+        // buffer; z, T and the first primal step follow the caller's sum over the states
+        // (lmspdhg_shard_init_finish), from the copy of x0 kept in x[1]
+        launch_res_fold(&st->g, st->acc_std, st->acc_yf, st->dz, nullptr, 0, st->n, s);
+        LM_CUDA(cudaMemcpyAsync(st->x[1], x0, V * 4, cudaMemcpyDeviceToDevice, s));
+        LM_CUDA(cudaGetLastError());
+        st->shard_stage = 1;
+        return LM_OK;
+    }
+    return init_image_pass(st, x0, s);
 }
 
 // Autotuner: times the forward projection of subset 0 (x of the first
@@ -677,7 +737,7 @@ size_t lmspdhg_state_bytes(const lm_grid* grid, int64_t n_events, int32_t n_subs
 {
     if (check_grid(grid) || n_events < 0 || n_subsets < 1) return 0;
     Carve c;
-    carve(nullptr, c, grid, n_events, n_subsets, deterministic != 0, false);
+    carve(nullptr, c, grid, n_events, n_subsets, deterministic != 0, false, false);
     return c.off + 256;
 }
 
@@ -685,7 +745,8 @@ size_t lmspdhg_state_bytes_ex(const lm_grid* grid, int64_t n_events, int32_t n_s
 {
     if (check_grid(grid) || n_events < 0 || n_subsets < 1 || params == nullptr) return 0;
     Carve c;
-    carve(nullptr, c, grid, n_events, n_subsets, params->deterministic != 0, params->xi != nullptr);
+    carve(nullptr, c, grid, n_events, n_subsets, params->deterministic != 0, params->xi != nullptr,
+          params->shard != 0);
     return c.off + 256;
 }
 
@@ -728,6 +789,10 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         rc = res_plan(grid, P.res_fwhm, rp);
         if (rc) return rc;
     }
+    LM_CHECK(P.shard == 0 || P.shard == 1, LM_ERR_INVALID_ARG, "shard must be 0 or 1");
+    LM_CHECK(!P.shard || (!P.deterministic && P.res_fwhm == 0.0f && !P.sinogram && P.tile_buf == nullptr),
+             LM_ERR_INVALID_ARG,
+             "event sharding runs in float-atomic mode without the resolution model, sinogram bins or tiles");
     const size_t need = lmspdhg_state_bytes_ex(grid, ev->n, P.n_subsets, &P);
     LM_CHECK(state_bytes >= need, LM_ERR_NOMEM, "state buffer needs %zu bytes", need);
 
@@ -744,6 +809,9 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->two_d = grid->n[2] == 1 && sc->n_rings == 1;
     st->det = P.deterministic != 0;
     st->kahan = P.kahan != 0;
+    st->shard = P.shard != 0;
+    st->shard_stage = 0;
+    st->shard_sel = 0;
     st->det1 = ev->det1;
     st->det2 = ev->det2;
     st->tofb = ev->tof;
@@ -754,7 +822,7 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->sub_off_h.assign(sub_off_host, sub_off_host + P.n_subsets + 1);
     Carve c;
     c.base = (char*)(((uintptr_t)state_buf + 255) / 256 * 256);
-    carve(st, c, grid, ev->n, st->n, st->det, P.xi != nullptr);
+    carve(st, c, grid, ev->n, st->n, st->det, P.xi != nullptr, P.shard != 0);
     st->exec = nullptr;
     st->have_graph = false;
     st->xpar = 0;
@@ -906,6 +974,7 @@ int lmspdhg_updates(lm_state* st, const uint16_t* seq_host, int32_t count, void*
 {
     clear_error();
     LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    LM_CHECK(!st->shard, LM_ERR_INVALID_ARG, "a shard state updates through lmspdhg_shard_begin / _finish");
     LM_CHECK(count >= 0, LM_ERR_INVALID_ARG, "count < 0");
     if (count == 0) return LM_OK;
     LM_CHECK(seq_host != nullptr, LM_ERR_INVALID_ARG, "seq is NULL");
@@ -928,6 +997,7 @@ int lmspdhg_epoch(lm_state* st, const uint16_t* seq_host, void* stream)
 {
     clear_error();
     LM_CHECK(st != nullptr && seq_host != nullptr, LM_ERR_INVALID_ARG, "NULL argument");
+    LM_CHECK(!st->shard, LM_ERR_INVALID_ARG, "a shard state updates through lmspdhg_shard_begin / _finish");
     const int count = 2 * st->n;
     for (int i = 0; i < count; ++i)
         LM_CHECK(seq_host[i] <= st->n, LM_ERR_INVALID_ARG, "selection %d out of range", (int)seq_host[i]);
@@ -996,6 +1066,7 @@ int lmspdhg_profile(lm_state* st, const uint16_t* seq_host, int32_t count, doubl
 {
     clear_error();
     LM_CHECK(st && seq_host && ms4 && n4, LM_ERR_INVALID_ARG, "NULL argument");
+    LM_CHECK(!st->shard, LM_ERR_INVALID_ARG, "a shard state updates through lmspdhg_shard_begin / _finish");
     LM_CHECK(count >= 1 && count <= 2 * st->n, LM_ERR_INVALID_ARG, "count must be in [1, 2n]");
     for (int i = 0; i < count; ++i)
         LM_CHECK(seq_host[i] <= st->n, LM_ERR_INVALID_ARG, "selection %d out of range", (int)seq_host[i]);
@@ -1074,6 +1145,20 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
 {
     clear_error();
     LM_CHECK(st && out_host, LM_ERR_INVALID_ARG, "NULL argument");
+    double parts[4];
+    int rc = lmspdhg_objective_parts_fp64(st, parts, stream);
+    if (rc) return rc;
+    // listmode: <P^T 1, x> - sum_e log(...) + beta R (Eq. (1) without the constant sum of s);
+    // sinogram bins: Eq. (1) itself, sum_b (Px + s)_b - d_b log(Px + s)_b + beta R
+    *out_host = parts[0] - parts[2] + (double)st->P.beta * parts[1] + parts[3];
+    return LM_OK;
+}
+
+int lmspdhg_objective_parts_fp64(lm_state* st, double* out4, void* stream)
+{
+    clear_error();
+    LM_CHECK(st && out4, LM_ERR_INVALID_ARG, "NULL argument");
+    LM_CHECK(st->shard_stage == 0, LM_ERR_INVALID_ARG, "an exchange of the shard protocol is pending");
     cudaStream_t s = S(stream);
     const int xb = st->xpar ^ 1;
     float* p = st->scr;
@@ -1104,17 +1189,74 @@ int lmspdhg_objective_fp64(lm_state* st, double* out_host, void* stream)
             if (st->acc_yf) LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, 2 * (size_t)st->V * 4, s));
         }
     }
-    double parts[4];
     int rc = objective_parts(&st->g, st->sens, st->x[xb], st->P.xi, p, st->contam, st->P.sino_s,
-                             st->P.sinogram ? st->mu : nullptr, st->N, st->redd, parts, s);
+                             st->P.sinogram ? st->mu : nullptr, st->N, st->redd, out4, s);
     if (rc) return rc;
     unsigned err = 0;
     LM_CUDA(cudaMemcpyAsync(&err, st->err, sizeof(err), cudaMemcpyDeviceToHost, s));
     LM_CUDA(cudaStreamSynchronize(s));
     LM_CHECK(err == 0, LM_ERR_TIMEOUT, "a bounded wait of the image pass gave up; the iterate is not valid");
-    // listmode: <P^T 1, x> - sum_e log(...) + beta R (Eq. (1) without the constant sum of s);
-    // sinogram bins: Eq. (1) itself, sum_b (Px + s)_b - d_b log(Px + s)_b + beta R
-    *out_host = parts[0] - parts[2] + (double)st->P.beta * parts[1] + parts[3];
+    return LM_OK;
+}
+
+int lmspdhg_shard_buffer(lm_state* st, float** dz_out)
+{
+    clear_error();
+    LM_CHECK(st && dz_out, LM_ERR_INVALID_ARG, "NULL argument");
+    LM_CHECK(st->shard, LM_ERR_INVALID_ARG, "not a shard state (lm_params.shard)");
+    *dz_out = st->dz;
+    return LM_OK;
+}
+
+int lmspdhg_shard_init_finish(lm_state* st, void* stream)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    LM_CHECK(st->shard && st->shard_stage == 1, LM_ERR_INVALID_ARG,
+             "no initialisation awaits its exchange (shard state after create / reinit)");
+    cudaStream_t s = S(stream);
+    launch_unfold(st, s);
+    int rc = init_image_pass(st, st->x[1], s);
+    if (rc) return rc;
+    st->shard_stage = 0;
+    return LM_OK;
+}
+
+int lmspdhg_shard_begin(lm_state* st, uint16_t sel, void* stream)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    LM_CHECK(st->shard && st->shard_stage == 0, LM_ERR_INVALID_ARG,
+             "a shard update starts after the initialisation's or the previous update's finish");
+    LM_CHECK(sel <= st->n, LM_ERR_INVALID_ARG, "selection %d out of range", (int)sel);
+    cudaStream_t s = S(stream);
+    const uint16_t h = sel;
+    LM_CUDA(cudaMemcpyAsync(st->seq, &h, 2, cudaMemcpyHostToDevice, s));
+    LM_CUDA(cudaStreamSynchronize(s));  // h lives on this stack frame
+    launch_wpar(st->seq, 1, st->n, st->wpar, st->wbase, s);
+    int rc = launch_event_part(st, 0, st->xpar, (int)(st->n_updates & 1), s);
+    if (rc) return rc;
+    if (sel < st->n) launch_res_fold(&st->g, st->acc_std, st->acc_yf, st->dz, nullptr, 0, st->n, s);
+    LM_CUDA(cudaGetLastError());
+    st->shard_sel = sel;
+    st->shard_stage = 2;
+    return LM_OK;
+}
+
+int lmspdhg_shard_finish(lm_state* st, void* stream)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    LM_CHECK(st->shard && st->shard_stage == 2, LM_ERR_INVALID_ARG, "no shard update awaits its finish");
+    cudaStream_t s = S(stream);
+    if (st->shard_sel < st->n) launch_unfold(st, s);
+    const int cur = st->xpar;
+    int rc = launch_image_part(st, 0, cur, cur ^ 1, (int)(st->n_updates & 1), s);
+    if (rc) return rc;
+    LM_CUDA(cudaGetLastError());
+    st->xpar ^= 1;
+    st->n_updates += 1;
+    st->shard_stage = 0;
     return LM_OK;
 }
 
@@ -1386,6 +1528,7 @@ int lmspdhg_batch_set(lm_batch* b, int32_t slot, lm_state* st, void* stream)
     if (st != nullptr) {
         LM_CHECK(st->n == b->n, LM_ERR_INVALID_ARG, "state has %d subsets, batch %d", st->n, b->n);
         LM_CHECK(!st->has_res, LM_ERR_INVALID_ARG, "states with the resolution model do not run in batches");
+        LM_CHECK(!st->shard, LM_ERR_INVALID_ARG, "shard states do not run in batches");
         LM_CHECK(!b->have_cfg || same_config(b->cfg, st), LM_ERR_INVALID_ARG,
                  "state differs from the batch's grid, TOF kernel or mode");
         LM_CHECK(st->xpar == 0 && (st->n_updates & 1) == 0, LM_ERR_INVALID_ARG,

@@ -54,7 +54,7 @@ class lm_params(C.Structure):
                 ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t), ("xi", C.c_void_p),
                 ("res_fwhm", C.c_float), ("sinogram", C.c_int32), ("sino_q", C.c_void_p),
                 ("sino_qoff", C.c_void_p), ("sino_lorf", C.c_void_p), ("sino_s", C.c_float),
-                ("trav_buf", C.c_void_p), ("trav_bytes", C.c_size_t)]
+                ("trav_buf", C.c_void_p), ("trav_bytes", C.c_size_t), ("shard", C.c_int32)]
 
 
 _lib = None
@@ -122,6 +122,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lmspdhg_projector": ([V, P(I32), P(I64)], C.c_int),
         "lmspdhg_tile_bytes": ([P(lm_grid), I64, I32], SZ),
         "lmspdhg_trav_bytes": ([P(lm_grid), I64], SZ),
+        "lmspdhg_shard_buffer": ([V, P(V)], C.c_int),
+        "lmspdhg_shard_init_finish": ([V, V], C.c_int),
+        "lmspdhg_shard_begin": ([V, C.c_uint16, V], C.c_int),
+        "lmspdhg_shard_finish": ([V, V], C.c_int),
+        "lmspdhg_objective_parts_fp64": ([V, P(D), V], C.c_int),
         "lmspdhg_profile": ([V, P(C.c_uint16), I32, P(D), P(I64), V], C.c_int),
         "lm_kernel_launches": ([], I64),
         "lm_traversal_stats": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, SZ, P(I64), P(I64), V],
@@ -381,7 +386,8 @@ def kernel_launches() -> int:
 
 
 def traversal_stats(geo: Geometry, ev: DeviceEvents, stream=None):
-    """(samples, neighbour touches) of the events' traversals."""
+    """(samples, neighbour touches) of the events' traversals.  A measurement
+    utility of the benchmark (include/lm_measure.h), not part of Alg. 2."""
     L = load_library()
     ws = torch.empty(16, dtype=torch.uint8, device=ev.det1.device)
     ns, nt = C.c_int64(), C.c_int64()
@@ -392,7 +398,8 @@ def traversal_stats(geo: Geometry, ev: DeviceEvents, stream=None):
 
 
 def probe_l2(nbytes: int, mode: int, iters: int = 20, device="cuda", stream=None) -> float:
-    """L2 throughput (GB/s) of the library's probe kernel on a buffer of nbytes."""
+    """L2 throughput (GB/s) of the library's probe kernel on a buffer of nbytes.
+    A measurement utility of the benchmark (include/lm_measure.h)."""
     buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
     out = C.c_double()
     _check(load_library().lm_probe_l2(_ptr(buf), buf.numel(), int(mode), int(iters), C.byref(out), _stream(stream)))
@@ -555,9 +562,10 @@ class LMSPDHG:
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
                  image_kernel: int = 0, projector: str = "auto", xi: Optional[torch.Tensor] = None,
                  res_fwhm: float = 0.0, sinogram: int = 0, sino_s: float = 0.0,
-                 sino_lorf: Optional[torch.Tensor] = None, stream=None):
+                 sino_lorf: Optional[torch.Tensor] = None, shard: bool = False, stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
+        self.shard = bool(shard)
         self.xi = xi  # directional TV field (referenced by the state), None = TV
         self.n_subsets = n_subsets
         # projector of the data updates: "table" (stored traversals, 40 B per
@@ -589,7 +597,7 @@ class LMSPDHG:
                                 int(sinogram), _ptr(getattr(pe, "q", None)), _ptr(getattr(pe, "qoff", None)),
                                 _f32(sino_lorf, geo.n_lor, "sino_lorf"), float(sino_s),
                                 None if self.trav is None else self.trav.data_ptr(),
-                                0 if self.trav is None else self.trav.numel())
+                                0 if self.trav is None else self.trav.numel(), int(self.shard))
         self._keep = (sino_lorf,)
         nbytes = L.lmspdhg_state_bytes_ex(C.byref(geo.g), pe.events.n, int(n_subsets), C.byref(self.params))
         if nbytes == 0:
@@ -654,6 +662,47 @@ class LMSPDHG:
         v = C.c_double()
         _check(load_library().lmspdhg_objective_fp64(self.h, C.byref(v), _stream(stream)))
         return float(v.value)
+
+    # ---- event sharding of one frame (shard=True): see lmspdhg_shard_* ----
+    def shard_buffer(self) -> torch.Tensor:
+        """The state's exchange buffer (V floats inside the state buffer): the
+        partial back-projection of this state's events between shard_begin and
+        shard_finish, which the caller sums over the states in place."""
+        p = C.c_void_p()
+        _check(load_library().lmspdhg_shard_buffer(self.h, C.byref(p)))
+        off = p.value - self.buf.data_ptr()
+        return self.buf[off:off + 4 * self.geo.V].view(torch.float32)
+
+    def shard_init_finish(self, stream=None):
+        _check(load_library().lmspdhg_shard_init_finish(self.h, _stream(stream)))
+
+    def shard_begin(self, sel: int, stream=None):
+        _check(load_library().lmspdhg_shard_begin(self.h, int(sel), _stream(stream)))
+
+    def shard_finish(self, stream=None):
+        _check(load_library().lmspdhg_shard_finish(self.h, _stream(stream)))
+
+    def shard_init(self, exchange, stream=None):
+        """Completes a shard state's initialisation: exchange(buf) must sum the
+        states' buffers in place on every rank (e.g. torch.distributed.all_reduce
+        over the ranks that share the frame)."""
+        exchange(self.shard_buffer())
+        self.shard_init_finish(stream)
+
+    def shard_updates(self, seq, exchange, stream=None):
+        """The updates of `seq` on a shard state, with exchange(buf) between the
+        event kernels and the image pass of every data update (a prior update
+        needs none: every rank holds the same x and w)."""
+        for sel in np.asarray(seq, dtype=np.int64):
+            self.shard_begin(int(sel), stream)
+            if sel < self.n_subsets:
+                exchange(self.shard_buffer())
+            self.shard_finish(stream)
+
+    def objective_parts(self, stream=None):
+        out = (C.c_double * 4)()
+        _check(load_library().lmspdhg_objective_parts_fp64(self.h, out, _stream(stream)))
+        return list(out)
 
     def info(self):
         n = C.c_int64()

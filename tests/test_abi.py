@@ -1,5 +1,6 @@
 """CPU checks of the C ABI: the library builds and loads, exports every
-function include/lmspdhg.h declares, and rejects invalid host arguments
+function include/lmspdhg.h and the benchmark's include/lm_measure.h
+declare, and rejects invalid host arguments
 before touching a device.  No compute call is made (no GPU here)."""
 import ctypes as C
 import os
@@ -9,10 +10,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "lmspdhg.h")
+MEASURE_HEADER = os.path.join(ROOT, "include", "lm_measure.h")
 
 
 def _declared():
-    src = open(HEADER).read()
+    src = open(HEADER).read() + open(MEASURE_HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"\b((?:lm|lmspdhg)_[a-z0-9_]+)\s*\(", src)
     return sorted(set(names))

@@ -1,7 +1,8 @@
 """World-size-2 gloo tests (CPU) of the multi-rank logic: the benchmark's
 independent replicas (whole-job value = all ranks' events / slowest rank's
 time; only rank 0 prints), and the decomposition behind event sharding of
-one frame (partial back-projections summed by an all-reduce)."""
+one frame (partial back-projections summed by an all-reduce) and the
+binding's exchange protocol for shard states."""
 import os
 import socket
 
@@ -119,3 +120,72 @@ def test_event_sharded_data_update_two_ranks():
         np.testing.assert_allclose(dz, full, rtol=0, atol=1e-12 * scale)
         # the oracle projects the FP64 x, the primitives above its float32 copy
         np.testing.assert_allclose(dz, dz_oracle, rtol=0, atol=1e-6 * scale)
+
+
+class _FakeShardState:
+    """Stands in for a shard state of the library on CPU ranks (the library
+    needs a GPU): shard_begin puts this rank's partial dz of a data update in
+    the buffer, shard_finish records what the exchange left there."""
+
+    def __init__(self, rank, n_subsets, V=8):
+        self.rank, self.n_subsets = rank, n_subsets
+        self.buf = torch.zeros(V)
+        self.log = []
+        self.pending = None
+
+    def shard_buffer(self):
+        return self.buf
+
+    def shard_begin(self, sel, stream=None):
+        assert self.pending is None
+        self.pending = sel
+        if sel < self.n_subsets:
+            self.buf.copy_(torch.arange(self.buf.numel(), dtype=torch.float32) * (self.rank + 1) + sel)
+
+    def shard_finish(self, stream=None):
+        sel = self.pending
+        self.pending = None
+        self.log.append((sel, self.buf.clone() if sel < self.n_subsets else None))
+
+    def shard_init_finish(self, stream=None):
+        self.log.append(("init", self.buf.clone()))
+
+
+def _protocol_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2201_05497_gb300.lm import LMSPDHG
+    st = _FakeShardState(rank, n_subsets=3)
+    st.buf.fill_(float(rank + 1))
+    LMSPDHG.shard_init(st, dist.all_reduce)
+    LMSPDHG.shard_updates(st, [0, 3, 2, 3, 1], dist.all_reduce)
+    q.put((rank, [(s, None if b is None else b.numpy()) for s, b in st.log]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shard_protocol_two_ranks():
+    """The binding's shard protocol over a real process group: every data
+    update's buffer holds the sum of both ranks' partials when the update
+    finishes, prior updates exchange nothing, and both ranks see the same
+    values (they then apply identical image passes)."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_protocol_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ar = np.arange(8, dtype=np.float32)
+    for rank in (0, 1):
+        log = res[rank]
+        assert log[0][0] == "init" and np.all(log[0][1] == 3.0)
+        assert [s for s, _ in log[1:]] == [0, 3, 2, 3, 1]
+        for sel, b in log[1:]:
+            if sel == 3:
+                assert b is None
+            else:
+                np.testing.assert_array_equal(b, ar * 3 + 2 * sel)
