@@ -468,19 +468,19 @@ def run_gpu(args):
             "frac": ((b_gather + b_atomic) / t / 1e9) / eff_peak,
             "hbm_event_stream_gbs": b_events / t / 1e9, "hbm_frac": b_events / t / 1e9 / hbm_peak}
     # the TMA pass fuses the TV's dual step; the directional TV's stays in the event kernel
-    fused = tune["image_kernel"] == "tma" and xi is None
+    fused = tune["image_kernel"] == "tma"
     if fused:
-        # TMA-staged passes: the prior's dual step runs inside the image pass; the event
-        # kernel launched for a prior update only reads the selection and returns
+        # TMA-staged passes: the prior's dual step runs inside the image pass (with the
+        # directional TV's field read there: nd more floats per voxel); the event kernel
+        # launched for a prior update only reads the selection and returns.
         # data pass: float accumulators are z pairs (8 B read + 8 B cleared per layout) unless deterministic
         rows = [("event_kernel_prior_update_idle", 1, 0), ("image_pass_data_tma", 2, 48 if args.deterministic else 64),
-                ("prior_update_fused_tma", 3, 32 + 8 * nd)]
+                ("prior_update_fused_tma", 3, 32 + 8 * nd + (4 * nd if xi is not None else 0))]
     elif xi is not None:
-        # directional TV: the dual step reads x, w and the field and writes w+ and D = P(w+ - w);
-        # the prior pass reads D (nd floats per voxel) in place of w and w+
-        tma = tune["image_kernel"] == "tma"
+        # directional TV, plain passes: the dual step reads x, w and the field and writes w+ and
+        # D = P(w+ - w); the prior pass reads D (nd floats per voxel) in place of w and w+
         rows = [("prior_dual", 1, 4 + 16 * nd), ("image_pass_data", 2, 48 if args.deterministic else 64),
-                ("image_pass_prior_tma" if tma else "image_pass_prior", 3, 32 + 4 * nd)]
+                ("image_pass_prior", 3, 32 + 4 * nd)]
     else:
         rows = [("prior_dual", 1, 4 + 8 * nd), ("image_pass_data", 2, 48 if args.deterministic else 64),
                 ("image_pass_prior", 3, 32 + 8 * nd)]

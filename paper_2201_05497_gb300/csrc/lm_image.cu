@@ -734,7 +734,32 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
     // D = K^T's operand w+ - w; the directional TV takes the part of the
     // difference vector perpendicular to the field before v and again of
     // w+ - w (D = P (w+ - w)), in the order of the event kernel's dual step
-    auto wplus = [&](int ex, int ey, bool tile_pt) {
+    // the field at the thread's points (4 of the tile, at most one of the
+    // halo), all loads issued before any arithmetic
+    const int lane0 = threadIdx.x & 31, wrow0 = threadIdx.x >> 5, t0 = threadIdx.x;
+    float fxr[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, fyr[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
+          fzr[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (xi != nullptr) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            int ex, ey;
+            if (k < 4) {
+                ex = lane0 + 1;
+                ey = wrow0 + 8 * k + 1;
+            } else {
+                ex = t0 < EW ? t0 : 0;
+                ey = t0 < EW ? 0 : t0 - EW + 1;
+            }
+            const int ix = I.x0 - 1 + ex, iy = I.y0 - 1 + ey;
+            if ((k < 4 || t0 < 2 * EW - 1) && ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
+                const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
+                fxr[k] = __ldg(xi + j);
+                fyr[k] = __ldg(xi + V + j);
+                if (hz) fzr[k] = __ldg(xi + 2 * V + j);
+            }
+        }
+    }
+    auto wplus = [&](int ex, int ey, bool tile_pt, int k) {
         const int ix = I.x0 - 1 + ex, iy = I.y0 - 1 + ey;
         float dx = 0.0f, dy = 0.0f, dzc = 0.0f;
         if (ix >= 0 && iy >= 0 && ix < nx && iy < ny) {
@@ -745,14 +770,8 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
             float gx = ix < nx - 1 ? X0[xb + 1] - xc : 0.0f;
             float gy = iy < ny - 1 ? X0[xb + XHW] - xc : 0.0f;
             float gz = hz ? (z < nz - 1 ? X1[xb] - xc : 0.0f) : 0.0f;
-            float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-            if (xi != nullptr) {
-                const int64_t j = ((int64_t)z * ny + iy) * nx + ix;
-                fx = __ldg(xi + j);
-                fy = __ldg(xi + V + j);
-                if (hz) fz = __ldg(xi + 2 * V + j);
-                dtv_perp(fx, fy, fz, gx, gy, gz);
-            }
+            const float fx = fxr[k], fy = fyr[k], fz = fzr[k];
+            if (xi != nullptr) dtv_perp(fx, fy, fz, gx, gy, gz);
             const float vx = fmaf(sp, gx, wx);
             const float vy = fmaf(sp, gy, wy);
             float vz = 0.0f, wz = 0.0f;
@@ -782,10 +801,10 @@ __device__ __forceinline__ void prior_slice(const lmh::ImgArgs& A, int wp, uint8
     {
         const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) wplus(lane + 1, wrow + 8 * k + 1, true);
+        for (int k = 0; k < 4; ++k) wplus(lane + 1, wrow + 8 * k + 1, true, k);
         const int t = threadIdx.x;
-        if (t < EW) wplus(t, 0, false);
-        else if (t < 2 * EW - 1) wplus(0, t - EW + 1, false);
+        if (t < EW) wplus(t, 0, false, 4);
+        else if (t < 2 * EW - 1) wplus(0, t - EW + 1, false, 4);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
