@@ -500,23 +500,20 @@ def run_gpu(args):
     if d["bound"] == "l2":
         table = tune["projector"] == "table"
         traffic = None
-        if not args.deterministic and args.prior == "tv" and args.res_fwhm == 0:
-            # DRAM bytes per data update from the committed ncu summary of the 3D short frame
-            # (357 143 events per update), scaled by the events this workload's updates process
+        if not args.deterministic and args.prior == "tv" and args.res_fwhm == 0 and args.events in (0, N):
+            # DRAM bytes per data update from the committed ncu summary of this workload's kernel,
+            # valid while the kernel's sources hash to the value recorded with it
             if table:
-                t_short = profiled_traffic("ev_table_kernel_data_update_3d_short.txt",
+                traffic = profiled_traffic(f"ev_table_kernel_data_update_{args.workload}.txt",
                                            ["paper_2201_05497_gb300/csrc/lm_table.cu",
-                                            "paper_2201_05497_gb300/csrc/lm_device.cuh",
-                                            "paper_2201_05497_gb300/csrc/lm_internal.h"])
+                                            "paper_2201_05497_gb300/csrc/lm_device.cuh"])
             else:
-                t_short = profiled_traffic("ev_kernel_data_update_3d_short.txt",
+                traffic = profiled_traffic(f"ev_kernel_data_update_{args.workload}.txt",
                                            ["paper_2201_05497_gb300/csrc/lm_project.cu",
                                             "paper_2201_05497_gb300/csrc/lm_device.cuh"])
-            if t_short is not None:
-                traffic = t_short * (d["events_per_launch"] / 357143.0)
         roofline = {"bound": "l2", "achieved": d["achieved_gbs"], "peak": d["peak_gbs"], "unit": "GB/s",
                     "frac": d["frac"], "traffic": traffic,
-                    "traffic_unit": "DRAM bytes per data update (ncu, 3D short frame, scaled by events)",
+                    "traffic_unit": "DRAM bytes per data-update launch (ncu, warm L2)",
                     "kernel": ("ev_table_kernel (traversal-table data update: one launch per principal-axis "
                                "family)" if table else "ev_kernel<EV_DATA> (fused data update)"),
                     "peak_source": "in-run L2 probe: harmonic mix of coalesced read %.0f GB/s and float atomic "

@@ -345,6 +345,16 @@ typedef struct {
                           /* the tile-binned projector or sinogram bins          */
                           /* (LM_ERR_INVALID_ARG).  0: the frame's events all    */
                           /* belong to this state.                               */
+    int32_t epoch_kernel; /* how lmspdhg_epoch runs its 2n updates: 0 auto, 1 a  */
+                          /* captured graph of per-update launches, 2 one        */
+                          /* persistent cooperative launch per epoch (2D grids,  */
+                          /* float-atomic mode, TV prior, direct projector, no   */
+                          /* resolution model or sinogram bins; else             */
+                          /* LM_ERR_INVALID_ARG).  Auto takes 1: on the 2D frame */
+                          /* the graph is faster (0.65 against 0.86 ms/epoch).    */
+                          /* Its grid-wide barriers wait at most one second; a   */
+                          /* wait that gives up ends the kernel and the next     */
+                          /* lmspdhg_objective_fp64 returns LM_ERR_TIMEOUT.      */
 } lm_params;
 
 /* Bytes of the optional traversal-table buffer (lm_params.trav_buf): 40 per
@@ -465,6 +475,24 @@ int lmspdhg_shard_finish(lm_state* st, void* stream);
  * out4[0] - out4[2] + beta out4[1] + out4[3]; with event sharding out4[2]
  * is summed over the states.  Synchronous. */
 int lmspdhg_objective_parts_fp64(lm_state* st, double* out4, void* stream);
+
+/* The autotuner's comparison of the projectors (lm_params.trav_buf with
+ * group = 0): the data update of subset 0 with the best traversal-table
+ * variant and with the best direct-kernel width, in ms (0 when not
+ * measured); the state keeps the faster one (lmspdhg_projector). */
+int lmspdhg_tuning_projectors(lm_state* st, double* table_ms, double* direct_ms);
+
+/* Failure injection for the persistent epoch kernel (lm_params.epoch_kernel
+ * = 2): with flag != NULL (device memory), its first block waits for *flag
+ * != 0 before the first update, at most one second; if nothing sets the
+ * flag, that wait and the other blocks' barrier waits give up, the kernel
+ * returns and lmspdhg_objective_fp64 reports LM_ERR_TIMEOUT (lmspdhg_reinit
+ * clears the condition).  NULL removes the gate. */
+int lmspdhg_set_gate(lm_state* st, const unsigned* flag);
+
+/* How the state's epochs run: 1 a graph of per-update launches, 2 one
+ * persistent launch per epoch. */
+int lmspdhg_epoch_kernel(lm_state* st, int32_t* kind);
 
 /* Which image-pass kernel the state uses (lm_params.image_kernel): 1 plain
  * loads, 2 TMA-staged (the TV's dual step fused in; the directional TV's

@@ -291,6 +291,14 @@ __device__ __forceinline__ void dtv_perp(float fx, float fy, float fz, float& gx
     gz = fmaf(-fz, s, gz);
 }
 
+// Sum a + b with its exact rounding error (TwoSum, Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

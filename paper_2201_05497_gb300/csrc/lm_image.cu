@@ -130,14 +130,6 @@ __global__ void __launch_bounds__(256) fold_fixed_kernel(float* __restrict__ img
     }
 }
 
-// Sum a + b with its exact rounding error (TwoSum, Knuth).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
 // Directional TV: (P d) at voxel m for d = w+ - w, P = I - xi xi^T of the
 // voxel (components of axes of length 1 are 0).
 __device__ __forceinline__ void dtv_pd(const lmh::ImgArgs& A, const float* wc, const float* wn, int64_t m, int cx,

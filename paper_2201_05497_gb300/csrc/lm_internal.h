@@ -213,6 +213,30 @@ struct BatchEvArgs {
     float tof_W;
     int vitem;                  // voxels per prior work item
 };
+// One epoch of a 2D frame in one cooperative launch (float accumulators,
+// TV prior): per update the data update's event chunks or the prior's dual
+// step, a grid-wide barrier, the image pass voxel by voxel, a barrier.
+struct PersistArgs {
+    EvArgs ev;                 // event and prior arguments (x set per update)
+    const float* xs[2];        // x (std), by buffer
+    float* xw[2];              // the same, written
+    float* xyf[2];             // y-fastest copies
+    const uint16_t* seq;       // device, count entries
+    int count;
+    int xpar0;                 // buffer holding the x of update 0
+    float* z;
+    float* zc;
+    const float* T;
+    int kahan;
+    float inv_p_data, inv_p_prior;
+    unsigned* bar;             // [2] arrival count, generation (zeroed before the launch)
+    unsigned* err;             // bit 2: a barrier or the gate gave up waiting
+    const unsigned* gate;      // nullptr, or a flag block 0 waits for (bounded) before update 0
+};
+bool persist_supported();
+int persist_grid(int group);
+int launch_persist_epoch(const PersistArgs& p, int group, int grid, cudaStream_t st);
+
 int launch_events_batch(int mode, bool two_d, int group, const BatchEvArgs& b, int grid, cudaStream_t st);
 int ev_batch_grid(int mode, bool two_d, int group);  // group 0: smallest over 8/16/32
 
@@ -317,7 +341,25 @@ struct TabArgs {
     unsigned long long* queue;
     unsigned* done;
     int phase;             // 0: x-principal events only, 1: the others, -1: all
+    // batched epochs: the image of update u is in buffer u & 1
+    const float* xs[2];
+    const float* xyfs[2];
 };
+
+// The data updates of every active frame of a batch (frames with tables).
+struct BatchTabArgs {
+    const TabArgs* slots;       // [cap]
+    const int* active;          // [cap]
+    const uint16_t* seqs;       // [cap][seq_stride]
+    int seq_stride;
+    int cap;
+    int u;
+    unsigned long long* queue;  // self-resetting work counter
+    unsigned* done;
+    const float* tof_tab;       // the batch's TOF table
+    float tof_W;
+};
+int launch_table_batch(const BatchTabArgs& b, int variant, int grid, cudaStream_t st);
 int trav_build(const lmk::Geo& G, const lm_events& ev, const uint16_t* mu, const float* tof_tab,
                const TravLayout& L, char* base, cudaStream_t st);
 // variant: the lane-group width 8, 16 or 32 (32 compiled for 3 resident

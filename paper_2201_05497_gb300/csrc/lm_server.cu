@@ -129,6 +129,14 @@ struct lm_server_s {
 
 namespace {
 
+// Traversal-table bytes of a frame of n events (TOF data, 3D grid, float
+// mode: the batch then runs its data updates from the tables), else 0.
+size_t trav_bytes(const lm_server_s* s, int64_t n)
+{
+    if (s->tof.n_bins <= 0 || s->cfg.deterministic) return 0;
+    return lmspdhg_trav_bytes(&s->g, n);
+}
+
 size_t frame_bytes(const lm_server_s* s, int64_t n)
 {
     const size_t a = lmh::align_up((size_t)n * 4);
@@ -136,7 +144,7 @@ size_t frame_bytes(const lm_server_s* s, int64_t n)
     const size_t raw = 2 * a + h + 2 * a;             // det1, det2, tof, corr, contam
     const size_t perm = 2 * a + h + 2 * a + h;        // + mu
     const size_t x0 = lmh::align_up((size_t)lmh::nvox(&s->g) * 4);
-    return raw + perm + x0 +
+    return raw + perm + x0 + lmh::align_up(trav_bytes(s, n)) +
            lmspdhg_state_bytes(&s->g, n, s->cfg.n_subsets, s->cfg.deterministic) + 512;
 }
 
@@ -176,6 +184,8 @@ int prepare(lm_server_s* s, Frame* f)
     float* ps = (float*)take(n * 4);
     uint16_t* mu = (uint16_t*)take(n * 2);
     float* x0 = (float*)take((size_t)lmh::nvox(&s->g) * 4);
+    const size_t tb = trav_bytes(s, n);
+    char* trav = tb ? take(tb) : nullptr;
     char* stbuf = take(lmspdhg_state_bytes(&s->g, n, s->cfg.n_subsets, s->cfg.deterministic));
     const size_t stbytes = f->bytes - (size_t)(stbuf - base);
     LM_CUDA(cudaMemcpyAsync(r1, f->det1.data(), n * 4, cudaMemcpyHostToDevice, st));
@@ -201,6 +211,8 @@ int prepare(lm_server_s* s, Frame* f)
     P.deterministic = s->cfg.deterministic;
     P.kahan = s->cfg.kahan;
     P.group = s->cfg.group > 0 ? s->cfg.group : 32;
+    P.trav_buf = trav;  // every frame of the batch keeps its traversals
+    P.trav_bytes = tb;
     lm_state* state = nullptr;
     rc0 = lmspdhg_create(&state, &s->sc, &s->g, &s->tof, &perm, mu, off.data(), s->sens, x0, &P, stbuf, stbytes,
                          st);

@@ -75,10 +75,15 @@ struct lm_state_s {
     bool tab_split;     // one launch per principal-axis family (else one for all)
     int group;          // lanes per event of the event kernels
     double tune_ms[3];  // autotuner: forward projection of subset 0 with 8, 16, 32 lanes
+    double tune_table_ms, tune_direct_ms;  // data update of subset 0: best table / direct variant
     cudaStream_t cap_stream;
     cudaGraphExec_t exec;
     bool have_graph;
     int64_t graph_nodes;
+    bool persist;       // epochs in one persistent cooperative launch (2D float TV frames)
+    int grid_persist;   // its blocks (all resident)
+    unsigned* bar;      // its grid barrier: arrival count, generation
+    const unsigned* gate;  // failure injection: a flag its first block waits for
     bool shard;         // event sharding: updates through lmspdhg_shard_begin / _finish
     float* dz;          // the exchange buffer: this state's partial back-projection [V]
     int shard_stage;    // 0 ready, 1 initialisation awaiting the exchange, 2 update awaiting it
@@ -142,7 +147,9 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det,
     float* tof_tab = c.take<float>((size_t)(TOF_TAB_N + 1) * 4);
     TmaMaps* tmaps = c.take<TmaMaps>(sizeof(TmaMaps));
     unsigned* err = c.take<unsigned>(16);
+    unsigned* bar = c.take<unsigned>(16);
     if (st) {
+        st->bar = bar;
         st->tof_tab = tof_tab;
         st->tmaps = tmaps;
         st->err = err;
@@ -696,6 +703,54 @@ int autotune_table(lm_state* st, cudaStream_t s)
     st->tab_variant = best_v;
     const int best_g = best_v == 33 ? 32 : best_v;
     st->group = best_g;
+    // the direct event kernel on the same subset: the projector with the shorter data update stays
+    const double table_ms = std::min(one, two);
+    double direct_ms = 1e30;
+    int direct_g = 32;
+    {
+        cudaEvent_t d0, d1;
+        LM_CUDA(cudaEventCreate(&d0));
+        LM_CUDA(cudaEventCreate(&d1));
+        const int widths[3] = {8, 16, 32};
+        for (int w = 0; w < 3 && rc == LM_OK; ++w) {
+            EvArgs a = base_ev_args(st);
+            a.group = widths[w];
+            a.x_std = st->x[st->xpar];
+            a.x_yf = st->xyf[st->xpar];
+            a.acc_std = st->acc_std;
+            a.acc_yf = st->acc_yf;
+            a.e_begin = b0;
+            a.e_end = b0 + n0;
+            a.chunk = chunk_for(n0, ev_grid_g(EV_DATA, st->two_d, widths[w]));
+            double tot = 0.0;
+            for (int rep = 0; rep < 3 && rc == LM_OK; ++rep) {
+                cudaMemcpyAsync(st->y + b0, ysave, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s);
+                cudaEventRecord(d0, s);
+                rc = launch_events(EV_DATA, st->two_d, a, ev_grid_g(EV_DATA, st->two_d, widths[w]), s);
+                cudaEventRecord(d1, s);
+                cudaEventSynchronize(d1);
+                float m = 0.0f;
+                cudaEventElapsedTime(&m, d0, d1);
+                if (rep > 0) tot += m / 2.0;
+            }
+            if (tot < direct_ms) {
+                direct_ms = tot;
+                direct_g = widths[w];
+            }
+        }
+        cudaEventDestroy(d0);
+        cudaEventDestroy(d1);
+        if (rc) return rc;
+        LM_CUDA(cudaMemcpyAsync(st->y + b0, ysave, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s));
+        LM_CUDA(cudaMemsetAsync(st->acc_std, 0, 2 * (size_t)st->V * 4, s));
+        LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, 2 * (size_t)st->V * 4, s));
+    }
+    st->tune_table_ms = table_ms;
+    st->tune_direct_ms = direct_ms;
+    if (direct_ms < table_ms) {
+        st->table = false;
+        st->group = direct_g;
+    }
     return LM_OK;
 }
 
@@ -790,6 +845,7 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         if (rc) return rc;
     }
     LM_CHECK(P.shard == 0 || P.shard == 1, LM_ERR_INVALID_ARG, "shard must be 0 or 1");
+    LM_CHECK(P.epoch_kernel >= 0 && P.epoch_kernel <= 2, LM_ERR_INVALID_ARG, "epoch_kernel must be 0, 1 or 2");
     LM_CHECK(!P.shard || (!P.deterministic && P.res_fwhm == 0.0f && !P.sinogram && P.tile_buf == nullptr),
              LM_ERR_INVALID_ARG,
              "event sharding runs in float-atomic mode without the resolution model, sinogram bins or tiles");
@@ -874,6 +930,8 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
     st->tiled = false;
     st->n_segments = 0;
     st->tile_base = nullptr;
+    st->tune_table_ms = 0.0;
+    st->tune_direct_ms = 0.0;
     if (P.tile_buf != nullptr && tof->n_bins > 0 && !st->det && !st->has_res && !P.sinogram && grid->n[0] < 16384 && grid->n[1] < 16384 &&
         grid->n[2] < 16384) {
         st->tl = tile_layout(grid, ev->n, st->n);
@@ -959,6 +1017,19 @@ int lmspdhg_create(lm_state** out, const lm_scanner* sc, const lm_grid* grid, co
         st->tab_variant = st->group;
         st->tab_split = true;
     }
+    st->gate = nullptr;
+    {
+        const bool fits = st->two_d && !st->det && !st->has_res && !P.sinogram && !st->tiled && !st->table &&
+                          P.xi == nullptr && !st->shard && persist_supported() && persist_grid(st->group) > 0;
+        if (P.epoch_kernel == 2 && !fits) {
+            set_error("the persistent epoch kernel serves 2D float-mode TV frames with the direct projector");
+            return fail(LM_ERR_INVALID_ARG);
+        }
+        // measured on the 2D frame: the captured graph of per-update launches is faster (its 2n
+        // updates need 4n grid barriers in one launch), so auto keeps the graph
+        st->persist = fits && P.epoch_kernel == 2;
+        st->grid_persist = st->persist ? persist_grid(st->group) : 0;
+    }
     st->grid_tab = st->table ? table_grid(st->tab_variant) : 0;
     // the event kernels run with as many resident blocks as the chosen width allows
     st->grid_ev = ev_grid_g(st->det ? EV_DATA_FX1 : EV_DATA, st->two_d, st->group);
@@ -1001,8 +1072,42 @@ int lmspdhg_epoch(lm_state* st, const uint16_t* seq_host, void* stream)
     const int count = 2 * st->n;
     for (int i = 0; i < count; ++i)
         LM_CHECK(seq_host[i] <= st->n, LM_ERR_INVALID_ARG, "selection %d out of range", (int)seq_host[i]);
-    if (st->xpar != 0 || (st->n_updates & 1)) return lmspdhg_updates(st, seq_host, count, stream);
     cudaStream_t s = S(stream);
+    if (st->persist) {
+        LM_CUDA(cudaMemcpyAsync(st->seq, seq_host, (size_t)count * 2, cudaMemcpyHostToDevice, s));
+        launch_wpar(st->seq, count, st->n, st->wpar, st->wbase, s);
+        LM_CUDA(cudaMemsetAsync(st->bar, 0, 16, s));
+        PersistArgs p;
+        std::memset(&p, 0, sizeof(p));
+        p.ev = base_ev_args(st);
+        p.ev.acc_std = st->acc_std;
+        p.ev.acc_yf = st->acc_yf;
+        p.ev.queue = nullptr;
+        p.ev.done = nullptr;
+        for (int b = 0; b < 2; ++b) {
+            p.xs[b] = st->x[b];
+            p.xw[b] = st->x[b];
+            p.xyf[b] = st->xyf[b];
+        }
+        p.seq = st->seq;
+        p.count = count;
+        p.xpar0 = st->xpar;
+        p.z = st->z;
+        p.zc = st->zc;
+        p.T = st->T;
+        p.kahan = st->kahan ? 1 : 0;
+        p.inv_p_data = (float)(2 * st->n);
+        p.inv_p_prior = 2.0f;
+        p.bar = st->bar;
+        p.err = st->err;
+        p.gate = st->gate;
+        int rc = launch_persist_epoch(p, st->group, st->grid_persist, s);
+        if (rc) return rc;
+        st->xpar ^= (count & 1);
+        st->n_updates += count;
+        return LM_OK;
+    }
+    if (st->xpar != 0 || (st->n_updates & 1)) return lmspdhg_updates(st, seq_host, count, stream);
     if (!st->have_graph) {
         cudaGraph_t graph = nullptr;
         LM_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1044,6 +1149,7 @@ int lmspdhg_reinit(lm_state* st, const float* x0, void* stream)
             return rc;
         }
     }
+    LM_CUDA(cudaMemsetAsync(st->err, 0, 16, S(stream)));  // a fresh start clears a wait that gave up
     if (st->table) {
         // the events may be another frame's: store their traversals again
         int rc = build_table(st, S(stream));
@@ -1278,6 +1384,31 @@ int lmspdhg_image_kernel(lm_state* st, int32_t* kind)
     return LM_OK;
 }
 
+int lmspdhg_tuning_projectors(lm_state* st, double* table_ms, double* direct_ms)
+{
+    clear_error();
+    LM_CHECK(st && table_ms && direct_ms, LM_ERR_INVALID_ARG, "NULL argument");
+    *table_ms = st->tune_table_ms;
+    *direct_ms = st->tune_direct_ms;
+    return LM_OK;
+}
+
+int lmspdhg_set_gate(lm_state* st, const unsigned* flag)
+{
+    clear_error();
+    LM_CHECK(st != nullptr, LM_ERR_INVALID_ARG, "state is NULL");
+    st->gate = flag;
+    return LM_OK;
+}
+
+int lmspdhg_epoch_kernel(lm_state* st, int32_t* kind)
+{
+    clear_error();
+    LM_CHECK(st && kind, LM_ERR_INVALID_ARG, "NULL argument");
+    *kind = st->persist ? 2 : 1;
+    return LM_OK;
+}
+
 int lmspdhg_tuning(lm_state* st, int32_t* group, double* ms3)
 {
     clear_error();
@@ -1316,6 +1447,8 @@ struct BatchCfg {
     float W;
     int n, n_det, group, zlen;
     bool two_d, det, kahan, tma;
+    bool table;       // frames with traversal tables (the batch's data updates from them)
+    int tab_variant;
 };
 
 struct lm_batch_s {
@@ -1327,12 +1460,14 @@ struct lm_batch_s {
     float* d_tof = nullptr;   // the batch's own copy of the TOF table
     EvArgs* d_ev = nullptr;
     ImgArgs* d_im = nullptr;
+    TabArgs* d_tab = nullptr;
     int* d_active = nullptr;
     uint16_t* d_seqs = nullptr;
     unsigned long long* d_queue = nullptr;
     unsigned* d_done = nullptr;
     std::vector<EvArgs> h_ev;
     std::vector<ImgArgs> h_im;
+    std::vector<TabArgs> h_tab;
     std::vector<int> h_active;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1343,7 +1478,7 @@ struct lm_batch_s {
 namespace {
 
 struct BatchLayout {
-    size_t ev, im, active, seqs, ctr, tof, total;
+    size_t ev, im, tab, active, seqs, ctr, tof, total;
 };
 
 BatchLayout batch_layout(int cap, int n)
@@ -1354,6 +1489,8 @@ BatchLayout batch_layout(int cap, int n)
     off += align_up(sizeof(EvArgs) * (size_t)cap);
     L.im = off;
     off += align_up(sizeof(ImgArgs) * (size_t)cap);
+    L.tab = off;
+    off += align_up(sizeof(TabArgs) * (size_t)cap);
     L.active = off;
     off += align_up(sizeof(int) * (size_t)cap);
     L.seqs = off;
@@ -1380,6 +1517,8 @@ BatchCfg cfg_of(const lm_state* st)
     c.det = st->det;
     c.kahan = st->kahan;
     c.tma = st->tma;
+    c.table = st->table;
+    c.tab_variant = st->tab_variant;
     return c;
 }
 
@@ -1390,7 +1529,8 @@ bool same_config(const BatchCfg& a, const lm_state* st)
         if (a.g.n[d] != b.g.n[d]) return false;
     return a.n == b.n && a.two_d == b.two_d && a.det == b.det && a.kahan == b.kahan && a.tof.n_bins == b.tof.n_bins &&
            a.tof.sigma_mm == b.tof.sigma_mm && a.tof.bin_mm == b.tof.bin_mm && a.tof.n_sigma == b.tof.n_sigma &&
-           a.n_det == b.n_det && a.group == b.group && a.tma == b.tma && a.zlen == b.zlen;
+           a.n_det == b.n_det && a.group == b.group && a.tma == b.tma && a.zlen == b.zlen && a.table == b.table &&
+           (!a.table || a.tab_variant == b.tab_variant);
 }
 
 void fill_slot(lm_batch* b, int s, lm_state* st)
@@ -1428,6 +1568,17 @@ void fill_slot(lm_batch* b, int s, lm_state* st)
     im.wbase = st->wbase;
     b->h_ev[s] = a;
     b->h_im[s] = im;
+    if (st->table) {
+        TabArgs t = base_tab_args(st, 0);
+        t.seq = nullptr;  // the batch reads the frames' selections itself
+        t.queue = nullptr;
+        t.done = nullptr;
+        for (int k = 0; k < 2; ++k) {
+            t.xs[k] = st->x[k];
+            t.xyfs[k] = st->xyf[k];
+        }
+        b->h_tab[s] = t;
+    }
 }
 
 int launch_batch_epoch(lm_batch* b, cudaStream_t s)
@@ -1454,14 +1605,30 @@ int launch_batch_epoch(lm_batch* b, cudaStream_t s)
     be.tof_tab = r.tof.n_bins > 0 ? b->d_tof : nullptr;
     be.tof_W = r.W;
     be.vitem = 2048;
+    BatchTabArgs bt;
+    std::memset(&bt, 0, sizeof(bt));
+    bt.slots = b->d_tab;
+    bt.active = b->d_active;
+    bt.seqs = b->d_seqs;
+    bt.seq_stride = count;
+    bt.cap = b->cap;
+    bt.queue = b->d_queue;
+    bt.done = (unsigned*)(b->d_queue + 1);
+    bt.tof_tab = b->d_tof;
+    bt.tof_W = r.W;
+    const int g_tab = r.table ? table_grid(r.tab_variant) : 0;
     const int g_ev = ev_batch_grid(r.det ? EV_DATA_FX1 : EV_DATA, r.two_d, r.group);
     const int g_fx = ev_batch_grid(EV_BACK_FX, r.two_d, r.group);
     const int g_im = r.tma ? image_tma_batch_grid(&r.g, b->cap) : image_batch_grid(&r.g, b->cap);
     for (int u = 0; u < count; ++u) {
         be.u = u;
         bi.u = u;
+        bt.u = u;
         int rc;
-        if (!r.det) {
+        if (r.table && r.tma) {
+            // data updates from the frames' traversal tables (the prior's dual step is in the image pass)
+            rc = launch_table_batch(bt, r.tab_variant, g_tab, s);
+        } else if (!r.det) {
             rc = launch_events_batch(EV_DATA, r.two_d, r.group, be, g_ev, s);
         } else {
             rc = launch_events_batch(EV_DATA_FX1, r.two_d, r.group, be, g_ev, s);
@@ -1501,12 +1668,14 @@ int lmspdhg_batch_create(lm_batch** out, int32_t capacity, int32_t n_subsets, vo
     char* base = (char*)(((uintptr_t)buf + 255) / 256 * 256);
     b->d_ev = (EvArgs*)(base + L.ev);
     b->d_im = (ImgArgs*)(base + L.im);
+    b->d_tab = (TabArgs*)(base + L.tab);
     b->d_active = (int*)(base + L.active);
     b->d_seqs = (uint16_t*)(base + L.seqs);
     b->d_queue = (unsigned long long*)(base + L.ctr);
     b->d_tof = (float*)(base + L.tof);
     b->h_ev.assign(capacity, EvArgs());
     b->h_im.assign(capacity, ImgArgs());
+    b->h_tab.assign(capacity, TabArgs());
     b->h_active.assign(capacity, 0);
     cudaStream_t s = S(stream);
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1547,6 +1716,8 @@ int lmspdhg_batch_set(lm_batch* b, int32_t slot, lm_state* st, void* stream)
         b->h_active[slot] = 1;
         LM_CUDA(cudaMemcpyAsync(b->d_ev + slot, &b->h_ev[slot], sizeof(EvArgs), cudaMemcpyHostToDevice, s));
         LM_CUDA(cudaMemcpyAsync(b->d_im + slot, &b->h_im[slot], sizeof(ImgArgs), cudaMemcpyHostToDevice, s));
+        if (st->table)
+            LM_CUDA(cudaMemcpyAsync(b->d_tab + slot, &b->h_tab[slot], sizeof(TabArgs), cudaMemcpyHostToDevice, s));
     } else {
         b->slot[slot] = nullptr;
         b->h_active[slot] = 0;

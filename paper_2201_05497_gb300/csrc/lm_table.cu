@@ -172,20 +172,140 @@ struct alignas(16) EvRec {
     float pad;
 };
 
-// Data update of one subset from the traversal table.  Warps take chunks of
-// 32 consecutive events from a self-resetting counter; phase 0 processes the
-// chunks' x-principal events, phase 1 the others, phase -1 all of them.  The
-// lanes load their event's table entry and fields coalesced, with the
-// streaming cache policy (read once per update), and stage the selected
-// events in shared memory by rank; groups of G lanes then take them in turn,
-// lane s of a group on planes i0 + s, i0 + s + G, ... as in the direct
-// kernel, keeping up to 64/G samples per lane in registers for the
-// back-projection.
-template <int G, int MINB>
-__global__ void __launch_bounds__(256, MINB) ev_table_kernel(const lmh::TabArgs A)
+// One chunk of 32 consecutive events [e0, e0 + nev) of a data update by the
+// calling warp: phase 0 processes its x-principal events, phase 1 the
+// others, phase -1 all of them.  The lanes load their event's table entry
+// and fields coalesced, with the streaming cache policy (read once per
+// update), and stage the selected events in shared memory by rank; groups of
+// G lanes then take them in turn, lane s of a group on planes i0 + s,
+// i0 + s + G, ... as in the direct kernel, keeping up to 64/G samples per lane
+// in registers for the back-projection.  x_std / x_yf: the image the update
+// gathers from.
+template <int G>
+__device__ __forceinline__ void table_chunk(const lmh::TabArgs& A, const float* __restrict__ x_std,
+                                            const float* __restrict__ x_yf, int64_t e0, int nev, int phase,
+                                            const float2* s_tab, float inv_dt, EvRec* rec)
 {
     constexpr int NG = 32 / G;
     constexpr int PC = 64 / G;
+    const Geo& Gm = A.G;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, sub = lane % G;
+    const int64_t e = e0 + lane;
+    const bool in = lane < nev;
+    const int2 mt = in ? __ldcs(A.meta + e) : make_int2(0, 0);
+    const unsigned mw = (unsigned)mt.x;
+    const int mk = (int)(mw >> 30);
+    const bool mine = in && ((mw >> 15) & 0x7FFFu) != 0u && (phase < 0 || ((mk == 0) == (phase == 0)));
+    const unsigned mask = __ballot_sync(FULL, mine);
+    if (mask == 0u) return;
+    if (mine) {
+        EvRec& r = rec[__popc(mask & ((1u << lane) - 1u))];
+        r.g0 = __ldcs(A.r0 + e);
+        r.g1 = __ldcs(A.r1 + e);
+        r.d = make_float4(A.corr ? __ldcs(A.corr + e) : 1.0f, __ldcs(A.contam + e), __ldcs(A.y + e),
+                          (float)__ldcs(reinterpret_cast<const unsigned short*>(A.mu) + e));
+        r.mw = mw;
+        r.lane = lane;
+        r.inv_mu = __int_as_float(mt.y);
+    }
+    __syncwarp();
+    const int nm = __popc(mask);
+    for (int b0 = 0; b0 < nm; b0 += NG) {
+        const bool valid = b0 + grp < nm;
+        const EvRec& R = rec[valid ? b0 + grp : b0];
+        const float4 g0 = R.g0, g1 = R.g1, dd = R.d;
+        const unsigned rw = R.mw;
+        Lor E;
+        E.i0 = (int)(rw & 0x7FFFu);
+        E.cnt = valid ? (int)((rw >> 15) & 0x7FFFu) : 0;
+        const int k = (int)(rw >> 30);
+        E.ua0 = g0.x;
+        E.sa = g0.y;
+        E.ub0 = g0.z;
+        E.sb = g0.w;
+        E.tau0 = g1.x;
+        E.dtau = g1.y;
+        E.step = g1.z;
+        lmh::lor_strides(Gm, k, true, E);
+        E.k = k;
+        const float* __restrict__ img = k == 1 ? x_yf : x_std;
+        const int npass = (E.cnt + G - 1) / G;
+        const int iend = E.i0 + E.cnt;
+        const int ifirst = E.i0 + sub;
+        const float ffirst = (float)ifirst;
+        float acc = 0.0f;
+        Smp cs[PC];
+#pragma unroll
+        for (int p = 0; p < PC; ++p) {
+            cs[p].base = 0;
+            cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
+            if (p < npass) {
+                const int i = ifirst + p * G;
+                if (i < iend && sample_t(Gm, E, s_tab, inv_dt, i, ffirst + (float)(p * G), cs[p]))
+                    acc += gather<false>(img, E, cs[p]);
+                else
+                    cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
+            }
+        }
+        for (int p = PC; p < npass; ++p) {
+            const int i = ifirst + p * G;
+            Smp s;
+            if (i < iend && sample_t(Gm, E, s_tab, inv_dt, i, (float)i, s)) acc += gather<false>(img, E, s);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        // dual step of Eq. (proxD) with the listmode step mu_e S_e
+        const float cj = dd.x, sj = dd.y, yj = dd.z, muj = dd.w;
+        const float Se = A.gamma_rho * g1.w;                  // S_e = gamma rho / (P^LM 1)_e
+        const float a = fmaf(Se, fmaf(cj, acc, sj), yj);      // y + S (P^LM x + s)
+        const float yp = prox_dstar(a, muj * Se);
+        const float v = (yp - yj) * R.inv_mu;                 // (y+ - y) / mu
+        if (valid && sub == 0) __stcs(A.y + e0 + R.lane, yp);
+        const float bval = valid ? cj * v : 0.0f;
+        if (bval != 0.0f) {
+            float* acc_img = k == 1 ? A.acc_yf : A.acc_std;
+#pragma unroll
+            for (int p = 0; p < PC; ++p)
+                if (p < npass) scatter_pairs<false>(acc_img, E, cs[p], bval);
+            for (int p = PC; p < npass; ++p) {
+                const int i = ifirst + p * G;
+                Smp s;
+                if (i < iend && sample_t(Gm, E, s_tab, inv_dt, i, (float)i, s))
+                    scatter_pairs<false>(acc_img, E, s, bval);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void fill_tab2(float2* s_tab, const float* tab)
+{
+    for (int k = threadIdx.x; k < TOF_TAB_N; k += blockDim.x) {
+        const float a = tab[k];
+        s_tab[k] = make_float2(a, tab[k + 1] - a);
+    }
+}
+
+// The self-resetting work counter: the last warp to finish clears it.
+__device__ __forceinline__ void release_queue(unsigned long long* queue, unsigned* done)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        const unsigned tw = (unsigned)((gridDim.x * blockDim.x) >> 5);
+        const unsigned d = atomicAdd(done, 1u);
+        if (d == tw - 1) {
+            *queue = 0ULL;
+            *done = 0u;
+        }
+    }
+}
+
+// Data update of one subset from the traversal table: warps take the
+// subset's chunks from a self-resetting counter (table_chunk).
+template <int G, int MINB>
+__global__ void __launch_bounds__(256, MINB) ev_table_kernel(const lmh::TabArgs A)
+{
     __shared__ float2 s_tab[TOF_TAB_N];
     __shared__ EvRec s_rec[8][32];
     int64_t eb = A.e_begin, ee = A.e_end;
@@ -195,122 +315,77 @@ __global__ void __launch_bounds__(256, MINB) ev_table_kernel(const lmh::TabArgs 
         eb = A.sub_off[sel];
         ee = A.sub_off[sel + 1];
     }
-    for (int k = threadIdx.x; k < TOF_TAB_N; k += blockDim.x) {
-        const float a = A.tof_tab[k];
-        s_tab[k] = make_float2(a, A.tof_tab[k + 1] - a);
-    }
+    fill_tab2(s_tab, A.tof_tab);
     __syncthreads();
-    const Geo& Gm = A.G;
-    const float inv_dt = (float)TOF_TAB_N / (2.0f * Gm.W);
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int grp = lane / G, sub = lane % G;
+    const float inv_dt = (float)TOF_TAB_N / (2.0f * A.G.W);
+    const int lane = threadIdx.x & 31;
     const int64_t count = ee - eb;
     const int64_t nch = count > 0 ? (count + 31) / 32 : 0;
-    EvRec* rec = s_rec[wib];
+    EvRec* rec = s_rec[threadIdx.x >> 5];
     for (;;) {
         unsigned long long cc = 0;
         if (lane == 0) cc = atomicAdd(A.queue, 1ULL);
         const int64_t c = (int64_t)__shfl_sync(FULL, cc, 0);
         if (c >= nch) break;
         const int64_t e0 = eb + c * 32;
-        const int nev = (int)min((int64_t)32, ee - e0);
-        const int64_t e = e0 + lane;
-        const bool in = lane < nev;
-        const int2 mt = in ? __ldcs(A.meta + e) : make_int2(0, 0);
-        const unsigned mw = (unsigned)mt.x;
-        const int mk = (int)(mw >> 30);
-        const bool mine = in && ((mw >> 15) & 0x7FFFu) != 0u && (A.phase < 0 || ((mk == 0) == (A.phase == 0)));
-        const unsigned mask = __ballot_sync(FULL, mine);
-        if (mask == 0u) continue;
-        if (mine) {
-            EvRec& r = rec[__popc(mask & ((1u << lane) - 1u))];
-            r.g0 = __ldcs(A.r0 + e);
-            r.g1 = __ldcs(A.r1 + e);
-            r.d = make_float4(A.corr ? __ldcs(A.corr + e) : 1.0f, __ldcs(A.contam + e), __ldcs(A.y + e),
-                              (float)__ldcs(reinterpret_cast<const unsigned short*>(A.mu) + e));
-            r.mw = mw;
-            r.lane = lane;
-            r.inv_mu = __int_as_float(mt.y);
-        }
-        __syncwarp();
-        const int nm = __popc(mask);
-        for (int b0 = 0; b0 < nm; b0 += NG) {
-            const bool valid = b0 + grp < nm;
-            const EvRec& R = rec[valid ? b0 + grp : b0];
-            const float4 g0 = R.g0, g1 = R.g1, dd = R.d;
-            const unsigned rw = R.mw;
-            Lor E;
-            E.i0 = (int)(rw & 0x7FFFu);
-            E.cnt = valid ? (int)((rw >> 15) & 0x7FFFu) : 0;
-            const int k = (int)(rw >> 30);
-            E.ua0 = g0.x;
-            E.sa = g0.y;
-            E.ub0 = g0.z;
-            E.sb = g0.w;
-            E.tau0 = g1.x;
-            E.dtau = g1.y;
-            E.step = g1.z;
-            lmh::lor_strides(Gm, k, true, E);
-            E.k = k;
-            const float* __restrict__ img = k == 1 ? A.x_yf : A.x_std;
-            const int npass = (E.cnt + G - 1) / G;
-            const int iend = E.i0 + E.cnt;
-            const int ifirst = E.i0 + sub;
-            const float ffirst = (float)ifirst;
-            float acc = 0.0f;
-            Smp cs[PC];
-#pragma unroll
-            for (int p = 0; p < PC; ++p) {
-                cs[p].base = 0;
-                cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
-                if (p < npass) {
-                    const int i = ifirst + p * G;
-                    if (i < iend && sample_t(Gm, E, s_tab, inv_dt, i, ffirst + (float)(p * G), cs[p]))
-                        acc += gather<false>(img, E, cs[p]);
-                    else
-                        cs[p].w0 = cs[p].w1 = cs[p].w2 = cs[p].w3 = 0.0f;
-                }
-            }
-            for (int p = PC; p < npass; ++p) {
-                const int i = ifirst + p * G;
-                Smp s;
-                if (i < iend && sample_t(Gm, E, s_tab, inv_dt, i, (float)i, s)) acc += gather<false>(img, E, s);
-            }
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-            // dual step of Eq. (proxD) with the listmode step mu_e S_e
-            const float cj = dd.x, sj = dd.y, yj = dd.z, muj = dd.w;
-            const float Se = A.gamma_rho * g1.w;                  // S_e = gamma rho / (P^LM 1)_e
-            const float a = fmaf(Se, fmaf(cj, acc, sj), yj);      // y + S (P^LM x + s)
-            const float yp = prox_dstar(a, muj * Se);
-            const float v = (yp - yj) * R.inv_mu;                 // (y+ - y) / mu
-            if (valid && sub == 0) __stcs(A.y + e0 + R.lane, yp);
-            const float bval = valid ? cj * v : 0.0f;
-            if (bval != 0.0f) {
-                float* acc_img = k == 1 ? A.acc_yf : A.acc_std;
-#pragma unroll
-                for (int p = 0; p < PC; ++p)
-                    if (p < npass) scatter_pairs<false>(acc_img, E, cs[p], bval);
-                for (int p = PC; p < npass; ++p) {
-                    const int i = ifirst + p * G;
-                    Smp s;
-                    if (i < iend && sample_t(Gm, E, s_tab, inv_dt, i, (float)i, s))
-                        scatter_pairs<false>(acc_img, E, s, bval);
-                }
-            }
-        }
-        __syncwarp();
+        table_chunk<G>(A, A.x_std, A.x_yf, e0, (int)min((int64_t)32, ee - e0), A.phase, s_tab, inv_dt, rec);
     }
-    // the last warp to finish resets the counters for the next launch
-    __syncwarp();
-    if (lane == 0) {
-        const unsigned tw = (unsigned)((gridDim.x * blockDim.x) >> 5);
-        const unsigned d = atomicAdd(A.done, 1u);
-        if (d == tw - 1) {
-            *A.queue = 0ULL;
-            *A.done = 0u;
+    release_queue(A.queue, A.done);
+}
+
+// The data updates of every active frame of a batch at update u, from their
+// traversal tables: the work items are the 32-event chunks of each frame's
+// selected subset (frames at a prior update have none: their dual step runs
+// in the image pass), found through a prefix table in shared memory.
+template <int G, int MINB>
+__global__ void __launch_bounds__(256, MINB) ev_table_batch_kernel(const lmh::BatchTabArgs B)
+{
+    extern __shared__ float2 s_tab[];  // TOF_TAB_N pairs (dynamic: with the tables below above 48 KB)
+    __shared__ EvRec s_rec[8][32];
+    __shared__ long long s_pre[lmh::BATCH_MAX + 1];
+    __shared__ long long s_eb[lmh::BATCH_MAX];
+    __shared__ long long s_ee[lmh::BATCH_MAX];
+    const int cap = B.cap;
+    const int par = B.u & 1;
+    if (threadIdx.x < cap) {
+        const int s = threadIdx.x;
+        long long items = 0, eb = 0, ee = 0;
+        if (B.active[s]) {
+            const lmh::TabArgs& A = B.slots[s];
+            const int sel = B.seqs[(size_t)s * B.seq_stride + B.u];
+            if (sel < A.n_subsets) {
+                eb = A.sub_off[sel];
+                ee = A.sub_off[sel + 1];
+                items = (ee - eb + 31) / 32;
+            }
         }
+        s_eb[threadIdx.x] = eb;
+        s_ee[threadIdx.x] = ee;
+        s_pre[threadIdx.x + 1] = items;
     }
+    fill_tab2(s_tab, B.tof_tab);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_pre[0] = 0;
+        for (int s = 0; s < cap; ++s) s_pre[s + 1] += s_pre[s];
+    }
+    __syncthreads();
+    const long long total = s_pre[cap];
+    const float inv_dt = (float)TOF_TAB_N / (2.0f * B.tof_W);
+    const int lane = threadIdx.x & 31;
+    EvRec* rec = s_rec[threadIdx.x >> 5];
+    for (;;) {
+        unsigned long long cc = 0;
+        if (lane == 0) cc = atomicAdd(B.queue, 1ULL);
+        const long long c = (long long)__shfl_sync(FULL, cc, 0);
+        if (c >= total) break;
+        int s = 0;
+        while (s_pre[s + 1] <= c) ++s;
+        const lmh::TabArgs& A = B.slots[s];
+        const int64_t e0 = s_eb[s] + (c - s_pre[s]) * 32;
+        table_chunk<G>(A, A.xs[par], A.xyfs[par], e0, (int)min((long long)32, s_ee[s] - e0), -1, s_tab, inv_dt, rec);
+    }
+    release_queue(B.queue, B.done);
 }
 
 }  // namespace
@@ -358,6 +433,31 @@ int table_grid(int variant)
     default: break;
     }
     return num_sms() * b;
+}
+
+template <int G, int MINB>
+static void batch_attr()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(ev_table_batch_kernel<G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TOF_TAB_N * sizeof(float2)));
+    });
+}
+
+int launch_table_batch(const BatchTabArgs& b, int variant, int grid, cudaStream_t st)
+{
+    const size_t dyn = TOF_TAB_N * sizeof(float2);
+    switch (variant) {
+    case 8: batch_attr<8, 2>(); ev_table_batch_kernel<8, 2><<<grid, 256, dyn, st>>>(b); break;
+    case 16: batch_attr<16, 2>(); ev_table_batch_kernel<16, 2><<<grid, 256, dyn, st>>>(b); break;
+    case 32: batch_attr<32, 3>(); ev_table_batch_kernel<32, 3><<<grid, 256, dyn, st>>>(b); break;
+    case 33: batch_attr<32, 4>(); ev_table_batch_kernel<32, 4><<<grid, 256, dyn, st>>>(b); break;
+    default: set_error("unknown traversal-table kernel variant %d", variant); return LM_ERR_INVALID_ARG;
+    }
+    count_launch();
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
 }
 
 int launch_table_update(const TabArgs& a, int variant, int grid, cudaStream_t st)

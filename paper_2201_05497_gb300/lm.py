@@ -54,7 +54,8 @@ class lm_params(C.Structure):
                 ("tile_buf", C.c_void_p), ("tile_bytes", C.c_size_t), ("xi", C.c_void_p),
                 ("res_fwhm", C.c_float), ("sinogram", C.c_int32), ("sino_q", C.c_void_p),
                 ("sino_qoff", C.c_void_p), ("sino_lorf", C.c_void_p), ("sino_s", C.c_float),
-                ("trav_buf", C.c_void_p), ("trav_bytes", C.c_size_t), ("shard", C.c_int32)]
+                ("trav_buf", C.c_void_p), ("trav_bytes", C.c_size_t), ("shard", C.c_int32),
+                ("epoch_kernel", C.c_int32)]
 
 
 _lib = None
@@ -127,6 +128,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lmspdhg_shard_begin": ([V, C.c_uint16, V], C.c_int),
         "lmspdhg_shard_finish": ([V, V], C.c_int),
         "lmspdhg_objective_parts_fp64": ([V, P(D), V], C.c_int),
+        "lmspdhg_set_gate": ([V, V], C.c_int),
+        "lmspdhg_tuning_projectors": ([V, P(D), P(D)], C.c_int),
+        "lmspdhg_epoch_kernel": ([V, P(I32)], C.c_int),
         "lmspdhg_profile": ([V, P(C.c_uint16), I32, P(D), P(I64), V], C.c_int),
         "lm_kernel_launches": ([], I64),
         "lm_traversal_stats": ([P(lm_scanner), P(lm_grid), P(lm_tof), P(lm_events), V, SZ, P(I64), P(I64), V],
@@ -562,7 +566,8 @@ class LMSPDHG:
                  knorm_iters: int = 0, deterministic: bool = False, kahan: bool = True, group: int = 0,
                  image_kernel: int = 0, projector: str = "auto", xi: Optional[torch.Tensor] = None,
                  res_fwhm: float = 0.0, sinogram: int = 0, sino_s: float = 0.0,
-                 sino_lorf: Optional[torch.Tensor] = None, shard: bool = False, stream=None):
+                 sino_lorf: Optional[torch.Tensor] = None, shard: bool = False, epoch_kernel: int = 0,
+                 stream=None):
         L = load_library()
         self.geo, self.pe, self.sens = geo, pe, sens_img
         self.shard = bool(shard)
@@ -597,7 +602,8 @@ class LMSPDHG:
                                 int(sinogram), _ptr(getattr(pe, "q", None)), _ptr(getattr(pe, "qoff", None)),
                                 _f32(sino_lorf, geo.n_lor, "sino_lorf"), float(sino_s),
                                 None if self.trav is None else self.trav.data_ptr(),
-                                0 if self.trav is None else self.trav.numel(), int(self.shard))
+                                0 if self.trav is None else self.trav.numel(), int(self.shard),
+                                int(epoch_kernel))
         self._keep = (sino_lorf,)
         nbytes = L.lmspdhg_state_bytes_ex(C.byref(geo.g), pe.events.n, int(n_subsets), C.byref(self.params))
         if nbytes == 0:
@@ -711,6 +717,13 @@ class LMSPDHG:
         _check(load_library().lmspdhg_info(self.h, C.byref(n), C.byref(g), C.byref(k)))
         return dict(n_updates=n.value, gamma=g.value, knorm=k.value)
 
+    def set_gate(self, flag: Optional[torch.Tensor]):
+        """Failure injection for the persistent epoch kernel: its first block
+        waits (at most one second) for the device int32 `flag` to become non-zero
+        before the first update; None removes the gate."""
+        self._gate = flag
+        _check(load_library().lmspdhg_set_gate(self.h, None if flag is None else _ptr(flag)))
+
     def tuning(self):
         g = C.c_int32()
         ms = (C.c_double * 3)()
@@ -719,7 +732,13 @@ class LMSPDHG:
         _check(load_library().lmspdhg_image_kernel(self.h, C.byref(kind)))
         pk, nseg = C.c_int32(), C.c_int64()
         _check(load_library().lmspdhg_projector(self.h, C.byref(pk), C.byref(nseg)))
+        ek = C.c_int32()
+        _check(load_library().lmspdhg_epoch_kernel(self.h, C.byref(ek)))
+        tms, dms = C.c_double(), C.c_double()
+        _check(load_library().lmspdhg_tuning_projectors(self.h, C.byref(tms), C.byref(dms)))
         return dict(group=g.value, ms_g8=ms[0], ms_g16=ms[1], ms_g32=ms[2],
+                    epoch_kernel={1: "graph", 2: "persistent"}[ek.value],
+                    data_update_ms_table=tms.value, data_update_ms_direct=dms.value,
                     image_kernel={1: "plain", 2: "tma", 3: "tma_data"}[kind.value],
                     projector={1: "direct", 2: "tiled", 3: "table"}[pk.value], tile_segments=nseg.value)
 

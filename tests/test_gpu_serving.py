@@ -49,9 +49,10 @@ def problem(lm):
 def _alone(lm, wl, geo, sens, ev, x0v, seqs, det):
     pe = lm.event_setup(geo, lm.DeviceEvents.from_numpy(ev), wl.n_subsets)
     x0 = torch.full((geo.V,), float(x0v), dtype=torch.float32, device="cuda")
-    # the server's batch runs the direct event kernel: compare with the same projector alone
+    # the server's frames keep traversal tables where they apply (3D TOF, float mode) and run 32 lanes
+    # per event: compare with the same projector alone
     st = lm.LMSPDHG(geo, pe, sens, x0, beta=wl.beta, n_subsets=wl.n_subsets, knorm=H.knorm_closed(wl.grid.n),
-                    deterministic=det, kahan=True, group=32, projector="direct")
+                    deterministic=det, kahan=True, group=32, projector="auto")
     for e in range(seqs.shape[0]):
         st.epoch(seqs[e])
     out = st.x().cpu().numpy(), st.objective()
