@@ -524,6 +524,31 @@ def run_gpu(args):
         roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": d["peak_gbs"], "unit": "GB/s",
                     "frac": d["frac"], "traffic": None, "kernel": dom, "peak_source": peak_src}
     roofline["kernel_time_shares"] = {k: v / sum(shares.values()) for k, v in shares.items()}
+    if args.res_fwhm > 0:
+        # G alone on the frame's current x (warm L2, as inside an update): on 3D grids the fused x/y
+        # pass and the z pass, each reading and writing one image (16 B per voxel in all)
+        xg = st.x()
+        gout = torch.empty_like(xg)
+        gws = torch.empty(L.load_library().lm_res_workspace_bytes(geo.g), dtype=torch.uint8, device=dev)
+        L.res_apply(geo, args.res_fwhm, xg, out=gout, ws=gws)
+        torch.cuda.synchronize()
+        reps = 20
+        graph = torch.cuda.CUDAGraph()  # replayed, so that no host time falls between the calls
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                L.res_apply(geo, args.res_fwhm, xg, out=gout, ws=gws)
+        graph.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        b.synchronize()
+        us = 1e3 * a.elapsed_time(b) / reps
+        gbs = 16.0 * V / (us / 1e6) / 1e9
+        kern["resolution_G"] = {"launches_per_apply": 2 if nd == 3 else 1, "avg_us": us, "bound": "hbm",
+                                "bytes_per_apply": 16 * V, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                                "frac": gbs / hbm_peak, "note": "lm_res_apply on x, 20 calls in one graph"}
+        del xg, gout, gws, graph
 
     # ---- sinogram SPDHG (Alg. 1) on the same frame, outside the timed region ----
     sino = None

@@ -329,8 +329,11 @@ typedef struct {
                           /* per event); each data update then reads them        */
                           /* instead of setting the traversals up again.  Same   */
                           /* per-sample arithmetic as the direct kernel; S_e and */
-                          /* (y+ - y)/mu from the stored reciprocals.  Not used  */
-                          /* by batches.                                         */
+                          /* (y+ - y)/mu from the stored reciprocals.  Batches   */
+                          /* (lmspdhg_batch_*) run their frames' tables too.     */
+                          /* With group = 0 the autotuner also times the direct  */
+                          /* event kernel on one subset and keeps the faster     */
+                          /* projector unless trav_keep is set.                  */
     int32_t shard;        /* 1: event sharding of one frame over several states  */
                           /* (one per GPU), each holding a slice of every        */
                           /* subset's events (mu counted over the whole list:   */
@@ -355,6 +358,10 @@ typedef struct {
                           /* Its grid-wide barriers wait at most one second; a   */
                           /* wait that gives up ends the kernel and the next     */
                           /* lmspdhg_objective_fp64 returns LM_ERR_TIMEOUT.      */
+    int32_t trav_keep;    /* 1: keep the traversal table whenever trav_buf serves */
+                          /* the frame (no timing against the direct kernel;     */
+                          /* lmspdhg_tuning_projectors then reports 0 for it).   */
+                          /* 0: the faster of the two, as measured at create.    */
 } lm_params;
 
 /* Bytes of the optional traversal-table buffer (lm_params.trav_buf): 40 per

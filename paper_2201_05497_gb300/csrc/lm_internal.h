@@ -479,9 +479,15 @@ struct ResPlan {
 };
 int res_plan(const lm_grid* g, float fwhm, ResPlan& p);
 // dst = G src via temporaries t1, t2; skipped when seq[u] >= n_subsets (seq set);
-// pair_out: dst is a pair accumulator (values go to the first halves)
+// pair_out: dst is a pair accumulator (values go to the first halves, the
+// second halves are left zero); dst_yf: also the y-fastest copy of dst (or NULL)
 int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* t1, float* t2,
-               const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out);
+               const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out, float* dst_yf);
+// G applied to the float pair accumulators (std and y-fastest) folded into
+// one image; the result goes to the first halves of the std pairs and every
+// other half is left zero.  s1, s2: V-float scratch images.
+int launch_res_back(const lm_grid* g, const ResPlan& p, float* acc_std, float* acc_yf, float* s1, float* s2,
+                    const uint16_t* seq, int u, int n_subsets, cudaStream_t st);
 // out = the float pair accumulators (std and y-fastest) folded into one image; clears them
 void launch_res_fold(const lm_grid* g, float* acc_std, float* acc_yf, float* out, const uint16_t* seq, int u,
                      int n_subsets, cudaStream_t st);

@@ -234,9 +234,271 @@ __global__ void __launch_bounds__(256) res_fold_kernel(float* __restrict__ acc_s
     }
 }
 
+// ---- fused passes: the x and y passes of one z slice in one block, then
+// the z pass (with the layouts the caller needs) in a second kernel.  Each
+// output is the same chain of fused multiply-adds over the same inputs as
+// in res_row_kernel and res_march_kernel, so the results are identical.
+constexpr int RT_X = 32, RT_Y = 32, RZ_SEG = 8;
+
+// Input of the x and y passes at voxel (gx, gy) of slice z: the image, or
+// (fold) the back-projection accumulators folded as res_fold_kernel does
+// (std part; the y-fastest part is added by the caller).
+__device__ __forceinline__ float res_in_std(const float* __restrict__ src, const float* __restrict__ acc_std,
+                                            int64_t j, int64_t sz, bool below)
+{
+    if (acc_std == nullptr) return __ldg(src + j);
+    return __ldg(acc_std + 2 * j) + (below ? __ldg(acc_std + 2 * (j - sz) + 1) : 0.0f);
+}
+
+// Loads of the x/y pass's input tile of slice z (thread tid's share, NL
+// values): the std part into vs and, for the fold, the y-fastest part into vy.
+template <int R, int NL>
+__device__ __forceinline__ void res_xy_load(const float* __restrict__ src, const float* __restrict__ acc_std,
+                                            const float* __restrict__ acc_yf, int nx, int ny, int x0, int y0, int z,
+                                            int tid, float* vs, float* vy)
+{
+    constexpr int W = RT_X + 2 * R, H = RT_Y + 2 * R;
+    const int64_t sz = (int64_t)nx * ny;
+    const bool below = z > 0;
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        const int i = tid + 256 * q;
+        const int ly = i / W, lx = i - ly * W;
+        const int gx = x0 - R + lx, gy = y0 - R + ly;
+        vs[q] = 0.0f;
+        if (i < H * W && gx <= nx - 1 + R && gy <= ny - 1 + R)
+            vs[q] = res_in_std(src, acc_std, (int64_t)z * sz + (int64_t)mirror(gy, ny) * nx + mirror(gx, nx), sz,
+                               below);
+    }
+    if (acc_yf != nullptr) {
+        // the y-fastest accumulators, read along y (coalesced)
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int i = tid + 256 * q;
+            const int lx = i / H, ly = i - lx * H;
+            const int gx = x0 - R + lx, gy = y0 - R + ly;
+            vy[q] = 0.0f;
+            if (i < H * W && gx <= nx - 1 + R && gy <= ny - 1 + R) {
+                const int64_t k = ((int64_t)z * nx + mirror(gx, nx)) * ny + mirror(gy, ny);
+                vy[q] = __ldg(acc_yf + 2 * k) + (below ? __ldg(acc_yf + 2 * (k - sz) + 1) : 0.0f);
+            }
+        }
+    }
+}
+
+// x pass then y pass of a RT_X x RT_Y tile of slice blockIdx.z, from the
+// (RT_X + 2R) x (RT_Y + 2R) mirrored inputs around it staged in shared
+// memory; every thread issues all of its loads before the first store (one
+// tile per block: on the 200 x 200 x 96 grid this beat a resident grid
+// looping over the tiles, with or without the next tile's loads in flight).
+// Input: src, or with acc_std set the folded accumulators (read, not
+// cleared: neighbouring tiles read them as halo).  Output: dst (x-fastest),
+// or pairs (value, 0) when pair_out.
+template <int R>
+__global__ void __launch_bounds__(256) res_xy_kernel(const float* __restrict__ src, const float* __restrict__ acc_std,
+                                                     const float* __restrict__ acc_yf, float* __restrict__ dst, int nx,
+                                                     int ny, lmh::ResAxis wx, lmh::ResAxis wy, const uint16_t* seq,
+                                                     int u, int n_subsets, int pair_out)
+{
+    if (seq != nullptr && seq[u] >= n_subsets) return;
+    constexpr int W = RT_X + 2 * R, H = RT_Y + 2 * R, NL = (H * W + 255) / 256;
+    __shared__ float s_in[H][W + 1];
+    __shared__ float s_x[H][RT_X + 1];
+    const int x0 = blockIdx.x * RT_X, y0 = blockIdx.y * RT_Y, z = blockIdx.z;
+    const int tid = threadIdx.x;
+    const int64_t sz = (int64_t)nx * ny;
+    float vs[NL], vy[NL];
+    res_xy_load<R, NL>(src, acc_std, acc_yf, nx, ny, x0, y0, z, tid, vs, vy);
+    const bool fold_std_only = acc_std != nullptr && acc_yf == nullptr;
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        const int i = tid + 256 * q;
+        const int ly = i / W, lx = i - ly * W;
+        // (as the fold without y-fastest accumulators: the std part plus 0)
+        if (i < H * W) s_in[ly][lx] = fold_std_only ? vs[q] + 0.0f : vs[q];
+    }
+    if (acc_yf != nullptr) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int i = tid + 256 * q;
+            const int lx = i / H, ly = i - lx * H;
+            if (i < H * W) s_in[ly][lx] = s_in[ly][lx] + vy[q];
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < H * RT_X; i += 256) {
+        const int ly = i / RT_X, ox = i - ly * RT_X;
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wx.w[k], s_in[ly][ox + k], acc);
+        s_x[ly][ox] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < RT_X * RT_Y; i += 256) {
+        const int oy = i / RT_X, ox = i - oy * RT_X;
+        const int gx = x0 + ox, gy = y0 + oy;
+        if (gx < nx && gy < ny) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wy.w[k], s_x[oy + k][ox], acc);
+            const int64_t j = (int64_t)z * sz + (int64_t)gy * nx + gx;
+            if (pair_out)
+                reinterpret_cast<float2*>(dst)[j] = make_float2(acc, 0.0f);
+            else
+                dst[j] = acc;
+        }
+    }
+}
+
+// z pass of a RT_X x RT_Y column tile over RZ_SEG slices (one item per
+// block): each thread loads the RZ_SEG + 2R inputs of each of its four
+// columns into registers at once, then forms the columns' outputs from
+// them.  Outputs: dst (x-fastest, or pairs (value, 0) when pair_out), dst_yf
+// (y-fastest copy through a shared-memory transpose, or NULL); clear
+// (n_clear floats, 16-byte aligned) is zeroed by the blocks together (the
+// y-fastest accumulators, already folded by res_xy_kernel).
+template <int R>
+__global__ void __launch_bounds__(256) res_z_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                                    float* __restrict__ dst_yf, float* __restrict__ clear,
+                                                    int64_t n_clear, int nx, int ny, int nz, lmh::ResAxis wz,
+                                                    const uint16_t* seq, int u, int n_subsets, int pair_out)
+{
+    if (seq != nullptr && seq[u] >= n_subsets) return;
+    __shared__ float s_t[RT_Y][RT_X + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * RT_X, y0 = blockIdx.y * RT_Y;
+    const int64_t sz = (int64_t)nx * ny;
+    if (clear != nullptr) {
+        // this block's share of the n_clear floats: a range of whole float4s
+        const int64_t nb = (int64_t)gridDim.x * gridDim.y * gridDim.z;
+        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        const int64_t per = ((n_clear + nb - 1) / nb + 3) & ~(int64_t)3;
+        const int64_t e0 = min(n_clear, b * per), e1 = min(n_clear, e0 + per);
+        for (int64_t q = (e0 >> 2) + threadIdx.x; q < (e1 >> 2); q += 256)
+            reinterpret_cast<float4*>(clear)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int64_t i = (e1 & ~(int64_t)3) + threadIdx.x; i < e1; i += 256)
+            if (i >= e0) clear[i] = 0.0f;
+    }
+    const int c0 = blockIdx.z * RZ_SEG;
+    const int c1 = min(nz, c0 + RZ_SEG);
+    constexpr int NV = RZ_SEG + 2 * R;  // inputs of a column's RZ_SEG outputs
+    float wr[2 * R + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) wr[k] = wz.w[k];
+    const int gx = x0 + tx;
+    bool ok[4];
+    int64_t base[4];
+    float v[4][NV];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int gy = y0 + ty + 8 * q;
+        ok[q] = gx < nx && gy < ny;
+        base[q] = (int64_t)gy * nx + gx;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const int c = c0 - R + k;
+            v[q][k] = (ok[q] && c <= nz - 1 + R) ? __ldg(src + base[q] + (int64_t)mirror(c, nz) * sz) : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < RZ_SEG; ++cc) {
+        const int c = c0 + cc;
+        if (c >= c1) break;  // the same for the whole block
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wr[k], v[q][cc + k], acc);
+            const int64_t j = (int64_t)c * sz + base[q];
+            if (ok[q]) {
+                if (pair_out)
+                    reinterpret_cast<float2*>(dst)[j] = make_float2(acc, 0.0f);
+                else
+                    dst[j] = acc;
+            }
+            if (dst_yf != nullptr) s_t[ty + 8 * q][tx] = acc;
+        }
+        if (dst_yf != nullptr) {
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int lx = ty + 8 * q;  // lanes along y
+                const int xx = x0 + lx, yy = y0 + tx;
+                if (xx < nx && yy < ny) dst_yf[((int64_t)c * nx + xx) * ny + yy] = s_t[tx][lx];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
 namespace lmh {
+
+// Whether the fused passes serve plan p: x, y (and z) with one radius on x
+// and y of at most 8 taps per side (and at most 8 on z).
+static int fused_kind(const lm_grid* g, const ResPlan& p)
+{
+    if (p.n_axes < 2 || p.axis[0] != 0 || p.axis[1] != 1) return 0;
+    const int r = p.ax[0].r;
+    if (r < 1 || r > 8 || p.ax[1].r != r) return 0;
+    if (p.n_axes == 2) return g->n[2] == 1 ? 2 : 0;
+    if (p.axis[2] != 2 || p.ax[2].r < 1 || p.ax[2].r > 8 || g->n[2] > 65535) return 0;
+    return 3;
+}
+
+template <int R>
+static void launch_xy_r(const lm_grid* g, const ResPlan& p, const float* src, const float* acc_std,
+                        const float* acc_yf, float* dst, const uint16_t* seq, int u, int n_subsets, cudaStream_t st,
+                        bool pair_out)
+{
+    const dim3 grid((g->n[0] + RT_X - 1) / RT_X, (g->n[1] + RT_Y - 1) / RT_Y, g->n[2]);
+    res_xy_kernel<R><<<grid, 256, 0, st>>>(src, acc_std, acc_yf, dst, g->n[0], g->n[1], p.ax[0], p.ax[1], seq, u,
+                                           n_subsets, pair_out ? 1 : 0);
+}
+
+static void launch_xy(const lm_grid* g, const ResPlan& p, const float* src, const float* acc_std,
+                      const float* acc_yf, float* dst, const uint16_t* seq, int u, int n_subsets, cudaStream_t st,
+                      bool pair_out)
+{
+    switch (p.ax[0].r) {
+        case 1: launch_xy_r<1>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+        case 2: launch_xy_r<2>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+        case 3: launch_xy_r<3>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+        case 4: launch_xy_r<4>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+        case 5: launch_xy_r<5>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+        case 6: launch_xy_r<6>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+        case 7: launch_xy_r<7>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+        default: launch_xy_r<8>(g, p, src, acc_std, acc_yf, dst, seq, u, n_subsets, st, pair_out); break;
+    }
+    count_launch();
+}
+
+template <int R>
+static void launch_z_r(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* dst_yf, float* clear,
+                       int64_t n_clear, const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out)
+{
+    const dim3 grid((g->n[0] + RT_X - 1) / RT_X, (g->n[1] + RT_Y - 1) / RT_Y, (g->n[2] + RZ_SEG - 1) / RZ_SEG);
+    res_z_kernel<R><<<grid, 256, 0, st>>>(src, dst, dst_yf, clear, n_clear, g->n[0], g->n[1], g->n[2], p.ax[2], seq,
+                                          u, n_subsets, pair_out ? 1 : 0);
+}
+
+static void launch_z(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* dst_yf, float* clear,
+                     int64_t n_clear, const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out)
+{
+    switch (p.ax[2].r) {
+        case 1: launch_z_r<1>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+        case 2: launch_z_r<2>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+        case 3: launch_z_r<3>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+        case 4: launch_z_r<4>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+        case 5: launch_z_r<5>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+        case 6: launch_z_r<6>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+        case 7: launch_z_r<7>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+        default: launch_z_r<8>(g, p, src, dst, dst_yf, clear, n_clear, seq, u, n_subsets, st, pair_out); break;
+    }
+    count_launch();
+}
 
 int res_plan(const lm_grid* g, float fwhm, ResPlan& p)
 {
@@ -271,13 +533,28 @@ int res_plan(const lm_grid* g, float fwhm, ResPlan& p)
 // is src with one pass).  pair_out: dst is a pair accumulator (first halves).
 // With seq set, nothing runs when seq[u] selects the prior.
 int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* t1, float* t2,
-               const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out)
+               const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out, float* dst_yf)
 {
     const int V = (int)nvox(g);
     const dim3 blocks = res_grid(g);
     const int k = p.n_axes;
     if (k == 0) {
         if (src != dst) LM_CUDA(cudaMemcpyAsync(dst, src, (size_t)V * 4, cudaMemcpyDeviceToDevice, st));
+        if (dst_yf != nullptr) launch_transpose_to_yf(g, dst, dst_yf, st);
+        return LM_OK;
+    }
+    const int fk = fused_kind(g, p);
+    if (fk == 3) {
+        // x and y passes into t1, then the z pass into dst (and the y-fastest copy)
+        launch_xy(g, p, src, nullptr, nullptr, t1, seq, u, n_subsets, st, false);
+        launch_z(g, p, t1, dst, dst_yf, nullptr, 0, seq, u, n_subsets, st, pair_out);
+        LM_CUDA(cudaGetLastError());
+        return LM_OK;
+    }
+    if (fk == 2 && src != dst) {
+        launch_xy(g, p, src, nullptr, nullptr, dst, seq, u, n_subsets, st, pair_out);
+        if (dst_yf != nullptr) launch_transpose_to_yf(g, dst, dst_yf, st);
+        LM_CUDA(cudaGetLastError());
         return LM_OK;
     }
     const float* in = src;
@@ -325,8 +602,25 @@ int launch_res(const lm_grid* g, const ResPlan& p, const float* src, float* dst,
                                                          u, n_subsets, pair_out ? 1 : 0);
         count_launch();
     }
+    if (dst_yf != nullptr) launch_transpose_to_yf(g, dst, dst_yf, st);
     LM_CUDA(cudaGetLastError());
     return LM_OK;
+}
+
+int launch_res_back(const lm_grid* g, const ResPlan& p, float* acc_std, float* acc_yf, float* s1, float* s2,
+                    const uint16_t* seq, int u, int n_subsets, cudaStream_t st)
+{
+    if (fused_kind(g, p) == 3) {
+        // fold inside the x/y passes (the accumulators are read as halo by neighbouring
+        // tiles, so they are cleared afterwards): the z pass writes every std pair as
+        // (G A^T v, 0) and zeroes the y-fastest pairs
+        launch_xy(g, p, nullptr, acc_std, acc_yf, s1, seq, u, n_subsets, st, false);
+        launch_z(g, p, s1, acc_std, nullptr, acc_yf, acc_yf ? 2 * nvox(g) : 0, seq, u, n_subsets, st, true);
+        LM_CUDA(cudaGetLastError());
+        return LM_OK;
+    }
+    launch_res_fold(g, acc_std, acc_yf, s2, seq, u, n_subsets, st);
+    return launch_res(g, p, s2, acc_std, s1, s2, seq, u, n_subsets, st, true, nullptr);
 }
 
 void launch_res_fold(const lm_grid* g, float* acc_std, float* acc_yf, float* out, const uint16_t* seq, int u,
@@ -364,7 +658,7 @@ int lm_res_apply(const lm_grid* grid, float fwhm, const float* x, float* out, vo
     if (rc) return rc;
     float* t1 = (float*)ws;
     float* t2 = (float*)((char*)ws + lmh::align_up((size_t)lmh::nvox(grid) * 4));
-    return lmh::launch_res(grid, p, x, out, t1, t2, nullptr, 0, 0, lmh::S(stream), false);
+    return lmh::launch_res(grid, p, x, out, t1, t2, nullptr, 0, 0, lmh::S(stream), false, nullptr);
 }
 
 }  // extern "C"

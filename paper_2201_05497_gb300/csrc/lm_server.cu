@@ -212,6 +212,7 @@ int prepare(lm_server_s* s, Frame* f)
     P.kahan = s->cfg.kahan;
     P.group = s->cfg.group > 0 ? s->cfg.group : 32;
     P.trav_buf = trav;  // every frame of the batch keeps its traversals
+    P.trav_keep = 1;
     P.trav_bytes = tb;
     lm_state* state = nullptr;
     rc0 = lmspdhg_create(&state, &s->sc, &s->g, &s->tof, &perm, mu, off.data(), s->sens, x0, &P, stbuf, stbytes,

@@ -57,6 +57,7 @@ struct lm_state_s {
     bool tma_data;    // TMA-staged data passes, plain prior passes (image_kernel 3)
     bool has_res;     // resolution model P = A G: the event kernels read G x from gx / gxyf
     float *gx, *gxyf; // G x in both layouts (float mode; scratch of the back-projection's G)
+    float* rt;        // scratch image of the resolution model's passes (float mode)
     float* dtvd;      // directional TV: P (w+ - w) of the last prior dual step [ndim][V]
     ResPlan res;
     int zlen;         // z slices per TMA work item
@@ -129,6 +130,7 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det,
     // G x for the resolution model, both layouts (8 B per voxel, float mode)
     float* gx = det ? nullptr : F(V);
     float* gxyf = det ? nullptr : F(V);
+    float* rt = det ? nullptr : F(V);
     float* dtvd = dtv ? F(nd * V) : nullptr;
     float* dz = shard ? F(V) : nullptr;
     float* y = F((size_t)std::max<int64_t>(N, 1));
@@ -159,7 +161,7 @@ void carve(lm_state* st, Carve& c, const lm_grid* g, int64_t N, int n, bool det,
         st->y = y; st->scr = scr; st->scr_bytes = scr_bytes; st->sub_off = sub_off; st->seq = seq;
         st->wpar = wpar; st->wbase = wbase; st->maxbits = maxbits; st->queue = queue; st->done = done;
         st->redf = redf; st->redd = redd;
-        st->gx = gx; st->gxyf = gxyf; st->dtvd = dtvd; st->dz = dz;
+        st->gx = gx; st->gxyf = gxyf; st->rt = rt; st->dtvd = dtvd; st->dz = dz;
     }
 }
 
@@ -296,29 +298,22 @@ int build_table(lm_state* st, cudaStream_t s)
     return trav_build(st->G, ev, st->mu, st->tof_tab, st->tv, st->tv_base, s);
 }
 
-// Resolution model: G x into gx (x-fastest) and gxyf (y-fastest).  The pair
-// accumulators, zero between updates, hold the passes' temporaries and are
-// cleared again.
+// Resolution model: G x into gx (x-fastest) and gxyf (y-fastest), through the
+// scratch image rt (gxyf is the second scratch of the unfused passes, written
+// last by the y-fastest copy).
 int res_fwd(lm_state* st, const float* x, cudaStream_t s)
 {
-    float* t1 = st->acc_std;
-    float* t2 = st->acc_std + st->V;
-    int rc = launch_res(&st->g, st->res, x, st->gx, t1, t2, nullptr, 0, 0, s, false);
-    if (rc) return rc;
-    LM_CUDA(cudaMemsetAsync(st->acc_std, 0, 2 * (size_t)st->V * 4, s));
-    if (st->g.n[1] > 1) launch_transpose_to_yf(&st->g, st->gx, st->gxyf, s);
-    LM_CUDA(cudaGetLastError());
-    return LM_OK;
+    return launch_res(&st->g, st->res, x, st->gx, st->rt, st->gxyf, nullptr, 0, 0, s, false,
+                      st->g.n[1] > 1 ? st->gxyf : nullptr);
 }
 
-// Resolution model: dz = G (A^T v).  The accumulators are folded into gx
-// (and cleared), blurred, and written back as the first halves of the std
-// pairs, so the image pass merges G A^T v unchanged.  Skipped on the device
-// when seq[u] selects the prior.
+// Resolution model: G (A^T v) from the accumulators, written back as the
+// first halves of the std pairs (every other half zero), so the image pass
+// merges G A^T v unchanged.  G x is no longer needed by this update, so gx
+// serves as scratch.  Skipped on the device when seq[u] selects the prior.
 int res_back(lm_state* st, const uint16_t* seq, int u, cudaStream_t s)
 {
-    launch_res_fold(&st->g, st->acc_std, st->acc_yf, st->gx, seq, u, st->n, s);
-    return launch_res(&st->g, st->res, st->gx, st->acc_std, st->gxyf, st->gx, seq, u, st->n, s, true);
+    return launch_res_back(&st->g, st->res, st->acc_std, st->acc_yf, st->rt, st->gx, seq, u, st->n, s);
 }
 
 // The event part of update u (selection st->seq[u], x in buffer cur, scale
@@ -704,10 +699,11 @@ int autotune_table(lm_state* st, cudaStream_t s)
     const int best_g = best_v == 33 ? 32 : best_v;
     st->group = best_g;
     // the direct event kernel on the same subset: the projector with the shorter data update stays
+    // (unless the caller keeps the table)
     const double table_ms = std::min(one, two);
     double direct_ms = 1e30;
     int direct_g = 32;
-    {
+    if (!st->P.trav_keep) {
         cudaEvent_t d0, d1;
         LM_CUDA(cudaEventCreate(&d0));
         LM_CUDA(cudaEventCreate(&d1));
@@ -746,8 +742,8 @@ int autotune_table(lm_state* st, cudaStream_t s)
         LM_CUDA(cudaMemsetAsync(st->acc_yf, 0, 2 * (size_t)st->V * 4, s));
     }
     st->tune_table_ms = table_ms;
-    st->tune_direct_ms = direct_ms;
-    if (direct_ms < table_ms) {
+    st->tune_direct_ms = st->P.trav_keep ? 0.0 : direct_ms;
+    if (!st->P.trav_keep && direct_ms < table_ms) {
         st->table = false;
         st->group = direct_g;
     }
@@ -1276,7 +1272,7 @@ int lmspdhg_objective_parts_fp64(lm_state* st, double* out4, void* stream)
             // G x into the (zero) accumulators, which the next update does not read before clearing
             float* t = st->acc_std;
             int rc = launch_res(&st->g, st->res, st->x[xb], t, t + st->V, st->acc_yf ? st->acc_yf : t + st->V,
-                                nullptr, 0, 0, s, false);
+                                nullptr, 0, 0, s, false, nullptr);
             if (rc) return rc;
             a.x_std = t;
             a.x_yf = nullptr;

@@ -55,7 +55,7 @@ class lm_params(C.Structure):
                 ("res_fwhm", C.c_float), ("sinogram", C.c_int32), ("sino_q", C.c_void_p),
                 ("sino_qoff", C.c_void_p), ("sino_lorf", C.c_void_p), ("sino_s", C.c_float),
                 ("trav_buf", C.c_void_p), ("trav_bytes", C.c_size_t), ("shard", C.c_int32),
-                ("epoch_kernel", C.c_int32)]
+                ("epoch_kernel", C.c_int32), ("trav_keep", C.c_int32)]
 
 
 _lib = None
@@ -335,12 +335,15 @@ def tv_prox(geo: Geometry, w: torch.Tensor, beta: float, stream=None) -> torch.T
     return w
 
 
-def res_apply(geo: Geometry, fwhm: float, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
-    """G x: the image-space resolution model (separable Gaussian, mirrored faces)."""
+def res_apply(geo: Geometry, fwhm: float, x: torch.Tensor, out=None, stream=None,
+              ws: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """G x: the image-space resolution model (separable Gaussian, mirrored faces).
+    `ws`: a workspace of at least lm_res_workspace_bytes bytes (else allocated)."""
     L = load_library()
     if out is None:
         out = torch.empty(geo.V, dtype=torch.float32, device=x.device)
-    ws = _ws(L.lm_res_workspace_bytes(C.byref(geo.g)), x.device)
+    if ws is None or ws.numel() < int(L.lm_res_workspace_bytes(C.byref(geo.g))):
+        ws = _ws(L.lm_res_workspace_bytes(C.byref(geo.g)), x.device)
     _check(L.lm_res_apply(C.byref(geo.g), float(fwhm), _f32(x, geo.V, "x"), _f32(out, geo.V, "out"), _ptr(ws),
                           ws.numel(), _stream(stream)))
     return out
@@ -603,7 +606,7 @@ class LMSPDHG:
                                 _f32(sino_lorf, geo.n_lor, "sino_lorf"), float(sino_s),
                                 None if self.trav is None else self.trav.data_ptr(),
                                 0 if self.trav is None else self.trav.numel(), int(self.shard),
-                                int(epoch_kernel))
+                                int(epoch_kernel), int(projector == "table"))
         self._keep = (sino_lorf,)
         nbytes = L.lmspdhg_state_bytes_ex(C.byref(geo.g), pe.events.n, int(n_subsets), C.byref(self.params))
         if nbytes == 0:

@@ -342,13 +342,20 @@ def test_table_reinit_rebuilds(lm):
 
 
 def test_table_autotuner_picks_width_and_projector(lm):
-    """With the table allowed and the width left to the autotuner, the state
-    times the table's variants and the direct kernel's widths on subset 0 and
-    keeps the faster projector."""
-    g = Case(lm, "3d_mid").gpu(projector="table")
+    """With the table allowed ("auto") and the width left to the autotuner,
+    the state times the table's variants and the direct kernel's widths on
+    subset 0 and keeps the faster projector; asked for the table, it keeps
+    the table without timing the direct kernel."""
+    g = Case(lm, "3d_mid").gpu(projector="auto")
     t = g.tuning()
     assert t["group"] in (8, 16, 32)
     assert min(t["ms_g8"], t["ms_g16"], t["ms_g32"]) > 0.0
     assert t["data_update_ms_table"] > 0.0 and t["data_update_ms_direct"] > 0.0
     faster = "table" if t["data_update_ms_table"] <= t["data_update_ms_direct"] else "direct"
     assert t["projector"] == faster
+    g.close()
+    g = Case(lm, "3d_mid").gpu(projector="table")
+    t = g.tuning()
+    assert t["projector"] == "table" and t["group"] in (8, 16, 32)
+    assert t["data_update_ms_table"] > 0.0 and t["data_update_ms_direct"] == 0.0
+    g.close()

@@ -56,7 +56,9 @@ class Case:
         return lm.LMSPDHG(self.geo_g, pe, sens, torch.from_numpy(self.x0).cuda(), **args)
 
 
-@pytest.mark.parametrize("name,fwhm", [("2d_small", 4.5), ("3d_small", 6.0), ("3d_quad", 9.0)])
+# 2d_small: the fused x/y pass alone; 3d_small, 3d_quad: the fused x/y and z passes (equal and unequal
+# radii); FWHM 40 mm: 10 taps per side, the per-axis passes
+@pytest.mark.parametrize("name,fwhm", [("2d_small", 4.5), ("3d_small", 6.0), ("3d_quad", 9.0), ("3d_small", 40.0)])
 def test_res_apply_matches_oracle(lm, name, fwhm):
     wl = S.workload(name)
     geo_o, geo_g = O.Geometry.from_workload(wl), lm.Geometry.from_workload(wl)
