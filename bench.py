@@ -349,8 +349,10 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     epoch_ms = []
 
-    def frame(record_epochs=False):
-        L.event_setup(geo, raw_dev, n_sub, into=pe, ws=setup_ws)
+    def frame(record_epochs=False, raw_in=None, setup_done=None):
+        L.event_setup(geo, raw_dev if raw_in is None else raw_in, n_sub, into=pe, ws=setup_ws)
+        if setup_done is not None:
+            setup_done.record(stream)  # the raw buffer may be refilled from here on
         st.reinit(x0)
         evs = []
         for s in seqs:
@@ -403,30 +405,58 @@ def run_gpu(args):
     value, t_max, total_events = aggregate(world, rank, events_per_step * args.steps, t_dev)
 
     # ---- e2e: host inputs, host result ----
+    # Every step copies its events from pinned host memory and reads x back. The copies run on a
+    # second stream into two device buffers in turn: step k+1's events are copied while step k
+    # computes (its buffer is free once step k-1's set-up has read it), and step k waits for its
+    # own copy. The timed region runs from the first copy to the last x read.
     e2e = None
     if not args.no_e2e:
         host = {k: getattr(raw, k).cpu().pin_memory() for k in ("det1", "det2", "tof", "corr", "contam")}
         x_host = torch.empty(geo.V, dtype=torch.float32).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host.values())
         d2h = geo.V * 4 + 8
-        e2e_ms = []
+        bufs = [raw_dev, L.DeviceEvents(*(torch.empty_like(getattr(raw_dev, k)) for k in
+                                          ("det1", "det2", "tof", "corr", "contam")))]
+        cstream = torch.cuda.Stream(device=dev)
         n_e2e = max(1, min(args.steps, args.e2e_steps))
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        started = [ev() for _ in range(n_e2e)]
+        copied = [ev() for _ in range(n_e2e)]
+        setup = [ev() for _ in range(n_e2e)]
+        done = [ev() for _ in range(n_e2e)]
+
+        def copy_in(k):
+            if k >= 2:
+                cstream.wait_event(setup[k - 2])
+            started[k].record(cstream)
+            with torch.cuda.stream(cstream):
+                for name, t in host.items():
+                    getattr(bufs[k % 2], name).copy_(t, non_blocking=True)
+            copied[k].record(cstream)
+
         barrier(world)
+        torch.cuda.synchronize()
+        a = ev()
+        a.record(stream)
+        cstream.wait_event(a)
+        copy_in(0)
         for k in range(n_e2e):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for name, t in host.items():
-                getattr(raw_dev, name).copy_(t, non_blocking=True)
-            frame()
+            if k + 1 < n_e2e:
+                copy_in(k + 1)
+            stream.wait_event(copied[k])
+            frame(raw_in=bufs[k % 2], setup_done=setup[k])
             x_host.copy_(st.x(), non_blocking=True)
-            b.record(stream)
-            b.synchronize()
-            e2e_ms.append(a.elapsed_time(b))
-            flush.zero_()
+            done[k].record(stream)
+        done[-1].synchronize()
+        e2e_ms = [a.elapsed_time(done[0])] + [done[k - 1].elapsed_time(done[k]) for k in range(1, n_e2e)]
         barrier(world)
-        te = reduce_max(world, sum(e2e_ms) / 1e3)
+        te = reduce_max(world, a.elapsed_time(done[-1]) / 1e3)
         e2e = {"value": world * events_per_step * n_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * te / n_e2e, "steps": n_e2e}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * te / n_e2e, "steps": n_e2e,
+               "step_ms": e2e_ms, "h2d_ms": [started[k].elapsed_time(copied[k]) for k in range(n_e2e)],
+               "pipelined": "events of step k+1 copied on a second stream during step k; two device buffers"}
+        del bufs, host
+        torch.cuda.empty_cache()
 
     # ---- per-kernel timing of one epoch (direct launches, CUDA events on this stream) ----
     L.event_setup(geo, raw_dev, n_sub, into=pe, ws=setup_ws)

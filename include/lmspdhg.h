@@ -64,6 +64,11 @@ extern "C" {
 const char* lm_last_error(void);
 /* Library ABI version (major*100 + minor). */
 int lm_version(void);
+/* sizeof of the descriptor structs as this library was built, in the order
+ * lm_scanner, lm_grid, lm_tof, lm_events, lm_params, lm_server_config:
+ * writes min(n, 6) values to out (host) and returns 6, so a binding can
+ * check its own struct layouts before the first call. */
+int lm_struct_sizes(size_t* out, int n);
 
 /* ---- descriptors ------------------------------------------------------ */
 /* Crystal centres, mm, float32 [n_rings*n_xtal][3] (device); crystal id =

@@ -1205,6 +1205,14 @@ const char* lm_last_error(void) { return g_err.c_str(); }
 
 int lm_version(void) { return 100; }
 
+int lm_struct_sizes(size_t* out, int n)
+{
+    const size_t sz[6] = {sizeof(lm_scanner), sizeof(lm_grid),   sizeof(lm_tof),
+                          sizeof(lm_events),  sizeof(lm_params), sizeof(lm_server_config)};
+    for (int i = 0; out != nullptr && i < n && i < 6; ++i) out[i] = sz[i];
+    return 6;
+}
+
 int64_t lm_n_lor(const lm_scanner* sc)
 {
     if (!sc || sc->n_xtal < 2 || sc->n_rings < 1) return 0;

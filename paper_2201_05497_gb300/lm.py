@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     sig = {
         "lm_last_error": ([], C.c_char_p),
         "lm_version": ([], C.c_int),
+        "lm_struct_sizes": ([P(SZ), C.c_int], C.c_int),
         "lm_fwd_workspace_bytes": ([P(lm_grid)], SZ),
         "lm_fwd": ([P(lm_scanner), P(lm_grid), P(lm_tof), V, P(lm_events), V, V, SZ, V], C.c_int),
         "lm_back_workspace_bytes": ([P(lm_grid), C.c_int], SZ),
@@ -159,6 +160,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = res
+    # the descriptor structs above must match the library's layout
+    sizes = (C.c_size_t * 6)()
+    L.lm_struct_sizes(sizes, 6)
+    mine = [C.sizeof(t) for t in (lm_scanner, lm_grid, lm_tof, lm_events, lm_params, lm_server_config)]
+    if list(sizes) != mine:
+        raise RuntimeError(f"struct layouts differ from the library's: binding {mine}, library {list(sizes)}")
     _lib = L
     return L
 

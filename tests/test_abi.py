@@ -35,6 +35,17 @@ def test_every_declared_symbol_is_exported(L):
     assert not missing, missing
 
 
+def test_struct_layouts_match_the_binding(L):
+    """The binding's ctypes descriptors have the sizes the library was built with
+    (load_library checks the same and refuses a mismatch)."""
+    from paper_2201_05497_gb300 import lm
+    sizes = (C.c_size_t * 6)()
+    assert L.lm_struct_sizes(sizes, 6) == 6
+    assert list(sizes) == [C.sizeof(t) for t in (lm.lm_scanner, lm.lm_grid, lm.lm_tof, lm.lm_events, lm.lm_params,
+                                                 lm.lm_server_config)]
+    assert L.lm_struct_sizes(None, 0) == 6
+
+
 def test_host_only_queries(L):
     from paper_2201_05497_gb300 import lm
     g = lm.lm_grid((C.c_int32 * 3)(200, 200, 96), (C.c_float * 3)(2.5, 2.5, 2.5), (C.c_float * 3)(0, 0, 0))
