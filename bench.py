@@ -543,9 +543,10 @@ def run_gpu(args):
                                             "paper_2201_05497_gb300/csrc/lm_device.cuh"])
         roofline = {"bound": "l2", "achieved": d["achieved_gbs"], "peak": d["peak_gbs"], "unit": "GB/s",
                     "frac": d["frac"], "traffic": traffic,
-                    "traffic_unit": "DRAM bytes per data-update launch (ncu, warm L2)",
-                    "kernel": ("ev_table_kernel (traversal-table data update: one launch per principal-axis "
-                               "family)" if table else "ev_kernel<EV_DATA> (fused data update)"),
+                    "traffic_unit": "DRAM bytes per data update (ncu, warm L2)",
+                    "kernel": ("ev_table_kernel (traversal-table data update: one launch per update, or one "
+                               "per principal-axis family where the autotuner found that faster)" if table
+                               else "ev_kernel<EV_DATA> (fused data update)"),
                     "peak_source": "in-run L2 probe: harmonic mix of coalesced read %.0f GB/s and float atomic "
                                    "%.0f GB/s weighted by the kernel's gather/atomic bytes" % (peak_read, peak_atom),
                     "hbm_event_stream": {"achieved": d["hbm_event_stream_gbs"], "peak": hbm_peak,
