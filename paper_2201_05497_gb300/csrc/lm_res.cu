@@ -351,13 +351,15 @@ __global__ void __launch_bounds__(256) res_xy_kernel(const float* __restrict__ s
     }
 }
 
-// z pass of a RT_X x RT_Y column tile over RZ_SEG slices (one item per
-// block): each thread loads the RZ_SEG + 2R inputs of each of its four
+// z pass of a RT_X x RZ_Y column tile over RZ_SEG slices (one item per
+// block): each thread loads the RZ_SEG + 2R inputs of each of its two
 // columns into registers at once, then forms the columns' outputs from
 // them.  Outputs: dst (x-fastest, or pairs (value, 0) when pair_out), dst_yf
 // (y-fastest copy through a shared-memory transpose, or NULL); clear
 // (n_clear floats, 16-byte aligned) is zeroed by the blocks together (the
 // y-fastest accumulators, already folded by res_xy_kernel).
+constexpr int RZ_Y = 16, RZ_CQ = RZ_Y / 8;
+
 template <int R>
 __global__ void __launch_bounds__(256) res_z_kernel(const float* __restrict__ src, float* __restrict__ dst,
                                                     float* __restrict__ dst_yf, float* __restrict__ clear,
@@ -365,9 +367,9 @@ __global__ void __launch_bounds__(256) res_z_kernel(const float* __restrict__ sr
                                                     const uint16_t* seq, int u, int n_subsets, int pair_out)
 {
     if (seq != nullptr && seq[u] >= n_subsets) return;
-    __shared__ float s_t[RT_Y][RT_X + 1];
+    __shared__ float s_t[RZ_Y][RT_X + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * RT_X, y0 = blockIdx.y * RT_Y;
+    const int x0 = blockIdx.x * RT_X, y0 = blockIdx.y * RZ_Y;
     const int64_t sz = (int64_t)nx * ny;
     if (clear != nullptr) {
         // this block's share of the n_clear floats: a range of whole float4s
@@ -387,11 +389,11 @@ __global__ void __launch_bounds__(256) res_z_kernel(const float* __restrict__ sr
 #pragma unroll
     for (int k = 0; k <= 2 * R; ++k) wr[k] = wz.w[k];
     const int gx = x0 + tx;
-    bool ok[4];
-    int64_t base[4];
-    float v[4][NV];
+    bool ok[RZ_CQ];
+    int64_t base[RZ_CQ];
+    float v[RZ_CQ][NV];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < RZ_CQ; ++q) {
         const int gy = y0 + ty + 8 * q;
         ok[q] = gx < nx && gy < ny;
         base[q] = (int64_t)gy * nx + gx;
@@ -401,12 +403,14 @@ __global__ void __launch_bounds__(256) res_z_kernel(const float* __restrict__ sr
             v[q][k] = (ok[q] && c <= nz - 1 + R) ? __ldg(src + base[q] + (int64_t)mirror(c, nz) * sz) : 0.0f;
         }
     }
+    // the y-fastest copy: value i = threadIdx.x + 256 q of a slice is (x = i / RZ_Y, y = i % RZ_Y), so
+    // the lanes write runs of RZ_Y consecutive y
 #pragma unroll
     for (int cc = 0; cc < RZ_SEG; ++cc) {
         const int c = c0 + cc;
         if (c >= c1) break;  // the same for the whole block
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RZ_CQ; ++q) {
             float acc = 0.0f;
 #pragma unroll
             for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wr[k], v[q][cc + k], acc);
@@ -422,10 +426,11 @@ __global__ void __launch_bounds__(256) res_z_kernel(const float* __restrict__ sr
         if (dst_yf != nullptr) {
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int lx = ty + 8 * q;  // lanes along y
-                const int xx = x0 + lx, yy = y0 + tx;
-                if (xx < nx && yy < ny) dst_yf[((int64_t)c * nx + xx) * ny + yy] = s_t[tx][lx];
+            for (int q = 0; q < RZ_CQ; ++q) {
+                const int i = threadIdx.x + 256 * q;
+                const int lx = i / RZ_Y, ly = i % RZ_Y;
+                const int xx = x0 + lx, yy = y0 + ly;
+                if (xx < nx && yy < ny) dst_yf[((int64_t)c * nx + xx) * ny + yy] = s_t[ly][lx];
             }
             __syncthreads();
         }
@@ -479,7 +484,7 @@ template <int R>
 static void launch_z_r(const lm_grid* g, const ResPlan& p, const float* src, float* dst, float* dst_yf, float* clear,
                        int64_t n_clear, const uint16_t* seq, int u, int n_subsets, cudaStream_t st, bool pair_out)
 {
-    const dim3 grid((g->n[0] + RT_X - 1) / RT_X, (g->n[1] + RT_Y - 1) / RT_Y, (g->n[2] + RZ_SEG - 1) / RZ_SEG);
+    const dim3 grid((g->n[0] + RT_X - 1) / RT_X, (g->n[1] + RZ_Y - 1) / RZ_Y, (g->n[2] + RZ_SEG - 1) / RZ_SEG);
     res_z_kernel<R><<<grid, 256, 0, st>>>(src, dst, dst_yf, clear, n_clear, g->n[0], g->n[1], g->n[2], p.ax[2], seq,
                                           u, n_subsets, pair_out ? 1 : 0);
 }
