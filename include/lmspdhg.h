@@ -491,7 +491,9 @@ int lmspdhg_objective_parts_fp64(lm_state* st, double* out4, void* stream);
 /* The autotuner's comparison of the projectors (lm_params.trav_buf with
  * group = 0): the data update of subset 0 with the best traversal-table
  * variant and with the best direct-kernel width, in ms (0 when not
- * measured); the state keeps the faster one (lmspdhg_projector). */
+ * measured); the state keeps the faster one (lmspdhg_projector), or the
+ * table when lm_params.trav_keep is set (the direct kernel is then not
+ * timed and direct_ms is 0). */
 int lmspdhg_tuning_projectors(lm_state* st, double* table_ms, double* direct_ms);
 
 /* Failure injection for the persistent epoch kernel (lm_params.epoch_kernel
